@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Benchmark: power-series Newton steps/s on one GB300 (and N replicas).
+
+Workload: quad double, complex, n = 64 polynomials in 64 unknowns plus t, 64
+monomials per polynomial of total degree <= 4 over <= 4 variables, unit-modulus
+coefficients, truncation degree d = 64 (seeded synthetic system; the start point
+x0 solves the system at t = 0).  A step is one Newton step on the truncated
+power series: evaluate and differentiate, Householder QR of A_0, block
+Toeplitz forward substitution, update.  Steps continue the Newton iteration
+from x0 (the work per step does not depend on x).
+
+Timing: W untimed warm-up steps, then exactly K steps, each bracketed by CUDA
+events on the launching stream, L2 flushed (256 MB write) between steps outside
+the events; barrier + synchronize around the timed region; max over ranks.
+For N > 1 every rank runs its own replica (the single system does not shard).
+
+--impl reference times the CPU oracle (oracle/, plain C, OpenMP over the
+paper's jobs) on the host cores for the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "power-series Newton steps/s (qd, n=64, d=64); FP64-pipe % of peak; err vs oracle"
+WORKLOAD = ("quad double complex, n=64 polynomials (+t), 64 monomials each of degree <= 4 over <= 4 variables, "
+            "truncation degree d=64, seed 1")
+CFG = 1
+
+# Table 1 of the paper: double operations per md add / mul (sum of the +,-,*,/ columns)
+TABLE1 = {2: (20, 23), 3: (35, 209), 4: (89, 336), 5: (122, 554), 8: (269, 1742), 10: (397, 3089)}
+
+# FP64 peak derived from unit counts and clocks: 152 SMs x 2 FP64 lanes per SM per
+# cycle x 2.07 GHz (the nominal 1.25 TFLOP/s counting an FMA as two flops).
+FP64_PEAK_INSTR = 152 * 2 * 2.07e9
+
+
+# ----------------------------------------------------------------- op model
+def fp64_instr_counts(K: int) -> dict:
+    """FP64 instructions of the library's md algorithms (TwoSum = 3, TwoProd = 2,
+    FastTwoSum = 3, plain op = 1), common path of the renormalisation."""
+    ts, tp, fts = 3, 2, 3
+
+    def renorm(m):
+        # bottom-up m-1 TwoSums; top-down: K-1 TwoSums, then plain adds for the rest
+        return (m - 1) * ts + (K - 1) * ts + (m - 1 - (K - 1))
+
+    if K == 1:
+        add = mul = 1
+        muld = 1
+    elif K == 2:
+        add = 2 * ts + 2 * fts + 2
+        mul = tp + 2 + 2 + fts
+        muld = tp + 2 + fts
+    else:
+        add = ts * (K * (K + 1) // 2) + (K - 1) + renorm(K + 1)
+        n_ts = sum(n * (n + 1) for n in range(K))
+        level_k = (K - 1) + ((K - 2) + K + K * (K - 1))  # K-1 products, adds of products, lows, carries
+        mul = tp * (K * (K + 1) // 2) + ts * n_ts + level_k + renorm(K + 1)
+        muld = tp * K + ts * (K * (K - 1) // 2) + (K - 1) + renorm(K + 1)
+    return {"add": add, "mul": mul, "mul_d": muld}
+
+
+def complex_mac_instr(K: int, P: int) -> tuple:
+    c = fp64_instr_counts(K)
+    if P == 1:
+        return c["mul"], c["add"]
+    return 4 * c["mul"] + 2 * c["add"], 2 * c["add"]
+
+
+def conv_schedule_counts(s) -> int:
+    """Number of series products in the evaluation schedule of system s."""
+    n = s.n
+    total = 0
+    for i in range(n):
+        for _, pairs in s.monomials(i):
+            xs = [(v, e) for v, e in pairs if v != n]
+            m = len(xs)
+            fch = sum(e - 1 for _, e in xs)
+            F = max(fch - 1, 0)  # first factor is a copy
+            Funit = fch == 0
+            sp = (m - 1) + max(m - 2, 0) + max(m - 2, 0) if m >= 2 else 0
+            g = 0 if (Funit or m == 0) else 1
+            dq = 0
+            if not Funit:
+                dq = m if m >= 2 else (0 if m == 0 else 0)
+            total += F + sp + g + dq
+    return total
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# -------------------------------------------------------------- distributed
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+
+    dist.init_process_group("gloo")
+    return dist
+
+
+def reduce_max(dist, v: float) -> float:
+    if dist is None:
+        return v
+    import torch
+
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- oracle leg
+def oracle_steps_per_s(s, steps: int, warmup: int):
+    import oracle
+
+    orc = oracle.Oracle(threads=os.cpu_count() or 1)
+    x = s.x0.copy()
+    for _ in range(warmup):
+        x, _ = orc.newton_step(s, x)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        x, _ = orc.newton_step(s, x)
+    dt = time.perf_counter() - t0
+    return steps / dt, orc.threads(), dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import mdgen
+
+    s = mdgen.config_system(CFG, args.seed)
+    v, cores, dt = oracle_steps_per_s(s, args.steps, args.warmup)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "arm": "CPU oracle (plain C, OpenMP over polynomials and RHS updates)"},
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} full Newton steps of the workload after {args.warmup} warm-up"},
+            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- main leg
+def run_product(args):
+    import numpy as np
+    import torch
+
+    import mdgen
+    import paper_2012_06607_gb300 as md
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = dist_init(world)
+    dev = torch.device("cuda", local)
+    s = mdgen.config_system(CFG, args.seed)
+    P, K, n, d = s.planes, s.limbs, s.n, s.degree
+    sysd = md.DeviceSystem(s, device=dev)
+    wsb = sysd.workspace_bytes()
+    ws = md.workspace(wsb, device=dev)
+    x = md.to_device(s.x0, dev)
+    nrm = torch.zeros(2, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        md.newton_step(sysd, x, ws, nrm)
+    torch.cuda.synchronize(dev)
+    assert md.device_status(ws) == 0
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    md.profile_read()  # drop anything recorded before
+    md.profile_enable(True)
+    evs = []
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        md.newton_step(sysd, x, ws, nrm)
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    md.profile_enable(False)
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    status = md.device_status(ws)
+    prof = md.profile_read()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = reduce_max(dist, sum(step_ms))
+    value = world * args.steps / (total_ms / 1e3)
+    launches = sum(c for _, c in prof.values())
+
+    # roofline of the dominant kernel (largest total time)
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_launches) = dom
+    cmul_i, cadd_i = complex_mac_instr(K, P)
+    nconv = conv_schedule_counts(s)
+    conv_instr = nconv * ((d + 1) * (d + 2) // 2 * cmul_i + d * (d + 1) // 2 * cadd_i)
+    t1 = TABLE1[K]
+    paper_mul = (4 * t1[1] + 2 * t1[0]) if P == 2 else t1[1]
+    paper_add = 2 * t1[0] if P == 2 else t1[0]
+    conv_paper = nconv * ((d + 1) * (d + 2) // 2 * paper_mul + d * (d + 1) // 2 * paper_add)
+    conv_ms, conv_launches = prof.get("conv_stage", (float("nan"), 0))
+    achieved = conv_instr / (conv_ms / 1e3) if conv_ms > 0 else None
+    roofline = {"bound": "alu", "kernel": "conv_stage", "achieved": achieved / 1e12 if achieved else None,
+                "peak": FP64_PEAK_INSTR / 1e12, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_INSTR if achieved else None,
+                "traffic": None, "counted": "FP64 instructions of the md algorithms (an fma counts once)",
+                "launches_in_timed_region": conv_launches, "avg_launch_ms": conv_ms / max(conv_launches, 1),
+                "dominant_by_time": dom_name,
+                "paper_ops_per_s": conv_paper / (conv_ms / 1e3) if conv_ms > 0 else None}
+    line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "flushed between steps (256 MB write outside the events)",
+                       "parallelism": f"replicas x{world}", "workspace_bytes": wsb},
+            "roofline": roofline, "gpu_launches": launches, "clocks": clk, "device_status": status,
+            "kernel_ms": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
+            "wall_s_timed_region": wall, "dx_norm_last": float(nrm[0].item())}
+
+    # end to end through the C ABI with host buffers: H2D of x, step, D2H of x and norms
+    xh = torch.from_numpy(s.x0.copy()).pin_memory()
+    outh = torch.empty_like(xh).pin_memory()
+    nh = torch.empty(2, dtype=torch.float64).pin_memory()
+    e_ms = []
+    for it in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        x.copy_(xh, non_blocking=True)
+        md.newton_step(sysd, x, ws, nrm)
+        outh.copy_(x, non_blocking=True)
+        nh.copy_(nrm, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e_ms.append(a.elapsed_time(b))
+        xh.copy_(outh)
+    e_total = reduce_max(dist, sum(e_ms))
+    line["e2e"] = {"value": world * args.steps / (e_total / 1e3), "unit": "steps/s",
+                   "h2d_bytes_per_step": int(xh.numel() * 8), "d2h_bytes_per_step": int(outh.numel() * 8 + 16)}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, dt = oracle_steps_per_s(s, 1, 0)
+        line["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                                "sample": "1 full Newton step of the workload from x0 (host cores, OpenMP)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=7)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--impl", default="product", choices=["product", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_product(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

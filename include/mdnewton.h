@@ -1,0 +1,189 @@
+/*
+ * mdnewton.h -- C ABI of the GB300 library for the power-series Newton step
+ * in multiple-double arithmetic (Verschelde, "Parallel Software to Offset the
+ * Cost of Higher Precision", arXiv 2012.06607).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Numbers.  A multiple-double (md) number is an unevaluated sum of K doubles,
+ *   K = limbs in {1, 2, 3, 4, 5, 8, 10} (double, double double, triple, quad,
+ *   penta, octo, deca double; Section 2).  Complex numbers have two planes
+ *   (P = 2: real part, imaginary part); real ones one plane (P = 1).
+ * Layouts (structure of arrays, limbs outermost; all row-major C indices):
+ *   md array of count values .......... [P][K][count]
+ *   series vector (n series, degree d)  [P][K][n][d+1]    coefficient fastest
+ *   matrix series A_0..A_d ............ [P][K][d+1][n][n] each A_k column-major:
+ *                                       element (row r, col c) of A_k at
+ *                                       [p][l][k][c][r]
+ * Memory.  "device" pointers are CUDA global memory owned by the caller; "host"
+ *   pointers are host memory owned by the caller.  The library allocates no
+ *   device memory: every call that needs scratch space takes a caller-owned
+ *   device workspace `ws` of at least the queried number of bytes, 256-byte
+ *   aligned.  A workspace must not be shared by calls that may run
+ *   concurrently.
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Calls enqueue work and return without synchronising, except
+ *   where stated.  Argument errors are returned synchronously; errors found on
+ *   the device (singular A_0, non-finite results) set a sticky word inside the
+ *   workspace, read with md_get_device_status().
+ * Threads.  Entry points are re-entrant for distinct workspaces.
+ */
+#ifndef MDNEWTON_H
+#define MDNEWTON_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum md_status {
+  MD_OK = 0,
+  MD_ERR_ARG = 1,         /* invalid argument (sizes, limbs, pointers, system)  */
+  MD_ERR_WORKSPACE = 2,   /* workspace NULL, misaligned or too small            */
+  MD_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed        */
+  MD_ERR_SINGULAR = 4,    /* A_0 is singular (a Householder column norm is 0)   */
+  MD_ERR_NONFINITE = 5,   /* an update contains Inf or NaN                      */
+  MD_ERR_NOCONV = 6,      /* reserved for drivers that iterate to a tolerance   */
+  MD_ERR_TIMEOUT = 7,     /* reserved: a bounded device wait ran out            */
+  MD_ERR_UNSUPPORTED = 8  /* valid request this build does not implement        */
+} md_status;
+
+/* Maximum number of (variable, exponent) pairs per monomial. */
+#define MD_MAXV 4
+
+/*
+ * A polynomial system f(x) = 0 of n polynomials in the n unknowns x_0..x_{n-1}
+ * and the series parameter t, which has variable index n (Section 4: systems
+ * with one more variable than equations have power series solutions; t is the
+ * extra variable).  Polynomial i is cst[i] + sum over its monomials
+ * m in [poly_ptr[i], poly_ptr[i+1]) of coef[m] * prod_q var(idx[m][q])^expo[m][q].
+ *
+ *   structure (HOST pointers, read during the call):
+ *     poly_ptr [n+1]            CSR offsets, poly_ptr[0] = 0, poly_ptr[n] = nmono
+ *     nvar     [nmono]          number of used pairs, 0..MD_MAXV
+ *     idx      [nmono*MD_MAXV]  distinct variable indices in 0..n (n = t)
+ *     expo     [nmono*MD_MAXV]  exponents >= 1 for the used pairs
+ *   values (DEVICE pointers):
+ *     coef     [P][K][nmono]    monomial coefficients
+ *     cst      [P][K][n]        constant terms
+ */
+typedef struct md_system {
+  int limbs;
+  int is_complex;
+  int n;
+  int degree;
+  int nmono;
+  const int *poly_ptr;
+  const int *nvar;
+  const int *idx;
+  const int *expo;
+  const double *coef;
+  const double *cst;
+} md_system;
+
+/* flags */
+#define MD_FLAG_PLAIN 0x0 /* plain multiple-double kernels for every step        */
+
+/* Version of this ABI (major*100 + minor). */
+int md_version(void);
+
+/* Human-readable name of a status code (static string). */
+const char *md_status_string(md_status st);
+
+/*
+ * Workspace bytes needed by md_eval_diff / md_newton_series_step for `sys`
+ * (reads only the host structure arrays).  Returns 0 if `sys` is invalid.
+ */
+size_t md_workspace_bytes(const md_system *sys, int flags);
+
+/* Workspace bytes needed by md_linsolve_series. */
+size_t md_linsolve_workspace_bytes(int limbs, int is_complex, int n, int degree, int flags);
+
+/*
+ * Elementwise md arithmetic on `count` values (Section 2, Table 1 operations).
+ *   op: 0 add (z = x + y), 1 sub (z = x - y), 2 mul, 3 div, 4 sqrt (real only,
+ *       y unused), 5 multiply by a double (y: DEVICE double[count]).
+ *   x, y, z: DEVICE [P][K][count] (z may alias x or y).
+ * Results are identical to a sequential evaluation of the same operation
+ * sequence in IEEE binary64 round-to-nearest (see the library's design notes
+ * for the algorithms).
+ */
+md_status md_elementwise(int op, int limbs, int is_complex, long long count, const double *x, const double *y,
+                         double *z, void *stream);
+
+/*
+ * Products of `count` pairs of truncated power series (Section 3):
+ * z_k = sum_{i=0..k} x_i y_{k-i}, k = 0..degree, summed in ascending i.
+ *   x, y, z: DEVICE [P][K][count][degree+1]; z must not alias x or y.
+ */
+md_status md_series_conv(int limbs, int is_complex, int degree, long long count, const double *x, const double *y,
+                         double *z, void *stream);
+
+/*
+ * Evaluate and differentiate the system at the series vector x (Section 4):
+ *   f[i](t)   = f_i(x(t), t) truncated at degree d,
+ *   A_k[i][j] = coefficient k of d f_i / d x_j (x(t), t),  j < n (no t column).
+ *   x: DEVICE [P][K][n][d+1]     input series
+ *   f: DEVICE [P][K][n][d+1]     output
+ *   A: DEVICE [P][K][d+1][n][n]  output (column-major blocks)
+ *   ws: DEVICE workspace of md_workspace_bytes(sys, 0) bytes.
+ * Monomials are evaluated with Speelpenning products (value and all partials
+ * at about three times the cost of the value); every sum is taken in the order
+ * of the definition, so f and A are the same bits on every run.
+ */
+md_status md_eval_diff(const md_system *sys, const double *x, double *f, double *A, void *ws, size_t ws_bytes,
+                       void *stream);
+
+/*
+ * Solve the lower triangular block Toeplitz system A(t) dx(t) = b(t) of
+ * Section 4: A_0 dx_k = b_k - sum_{j<k} A_{k-j} dx_j, k = 0..d, with a
+ * Householder QR of A_0.
+ *   A : DEVICE [P][K][d+1][n][n]  (read only)
+ *   b : DEVICE [P][K][n][d+1]
+ *   dx: DEVICE [P][K][n][d+1]     output
+ *   ws: DEVICE workspace of md_linsolve_workspace_bytes(...) bytes.
+ * A singular A_0 sets MD_ERR_SINGULAR in the workspace status word.
+ */
+md_status md_linsolve_series(int limbs, int is_complex, int n, int degree, const double *A, const double *b,
+                             double *dx, void *ws, size_t ws_bytes, int flags, void *stream);
+
+/*
+ * One Newton step on truncated power series (Section 4): x <- x + dx where
+ * A(t) dx(t) = -f(x(t)).
+ *   x:       DEVICE [P][K][n][d+1], updated in place
+ *   dx_norm: DEVICE double[2] or NULL: [0] = max_i |dx_{d,i}| (modulus of the
+ *            update to the last coefficient, Section 6), [1] = max over all
+ *            coefficients; both from the leading limbs.
+ *   ws:      DEVICE workspace of md_workspace_bytes(sys, flags) bytes.
+ */
+md_status md_newton_series_step(const md_system *sys, double *x, double *dx_norm, void *ws, size_t ws_bytes,
+                                int flags, void *stream);
+
+/*
+ * Synchronise `stream`, read the sticky device status word of `ws` (written by
+ * the calls above that used this workspace), clear it and return it
+ * (MD_OK, MD_ERR_SINGULAR or MD_ERR_NONFINITE).
+ */
+md_status md_get_device_status(void *ws, void *stream);
+
+/*
+ * Optional timing of the library's own kernels (tracing support; not part of
+ * the computation).  While enabled, every kernel launch of every call in this
+ * process is bracketed by two CUDA events on its stream.
+ *   md_profile_enable(1|0)   switch on / off (host only, no synchronisation).
+ *   md_profile_read(ms, launches, nkinds): waits for the recorded events, adds
+ *     their elapsed milliseconds and launch counts per kernel class into
+ *     HOST arrays ms[nkinds], launches[nkinds] (either may be NULL), clears the
+ *     record and returns the number of classes (or -1 if an event failed).
+ *   md_profile_kind_name(k): static name of class k.
+ */
+void md_profile_enable(int on);
+int md_profile_read(double *ms, long long *launches, int nkinds);
+const char *md_profile_kind_name(int kind);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MDNEWTON_H */

@@ -1,0 +1,219 @@
+"""GB300 library for the power-series Newton step in multiple-double arithmetic.
+
+Thin Python binding over the C ABI of ``libmdnewton.so`` (``include/mdnewton.h``).
+Every step of the computation runs in the library's CUDA kernels; this module
+only marshals arguments: PyTorch provides device memory and streams.  There is
+no CPU fallback -- importing the binding without the built library, or calling
+it without a CUDA device, raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmdnewton.so")
+
+MAXV = 4
+STATUS = {0: "MD_OK", 1: "MD_ERR_ARG", 2: "MD_ERR_WORKSPACE", 3: "MD_ERR_CUDA", 4: "MD_ERR_SINGULAR",
+          5: "MD_ERR_NONFINITE", 6: "MD_ERR_NOCONV", 7: "MD_ERR_TIMEOUT", 8: "MD_ERR_UNSUPPORTED"}
+OPS = {"add": 0, "sub": 1, "mul": 2, "div": 3, "sqrt": 4, "mul_d": 5}
+
+
+class MdError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {STATUS.get(code, code)}")
+
+
+class md_system(ctypes.Structure):
+    _fields_ = [("limbs", ctypes.c_int), ("is_complex", ctypes.c_int), ("n", ctypes.c_int), ("degree", ctypes.c_int),
+                ("nmono", ctypes.c_int), ("poly_ptr", ctypes.c_void_p), ("nvar", ctypes.c_void_p),
+                ("idx", ctypes.c_void_p), ("expo", ctypes.c_void_p), ("coef", ctypes.c_void_p),
+                ("cst", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2012_06607_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, sz, ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_longlong
+        L.md_version.restype = i
+        L.md_status_string.restype = ctypes.c_char_p
+        L.md_status_string.argtypes = [i]
+        L.md_workspace_bytes.restype = sz
+        L.md_workspace_bytes.argtypes = [ctypes.POINTER(md_system), i]
+        L.md_linsolve_workspace_bytes.restype = sz
+        L.md_linsolve_workspace_bytes.argtypes = [i, i, i, i, i]
+        L.md_elementwise.argtypes = [i, i, i, ll, vp, vp, vp, vp]
+        L.md_series_conv.argtypes = [i, i, i, ll, vp, vp, vp, vp]
+        L.md_eval_diff.argtypes = [ctypes.POINTER(md_system), vp, vp, vp, vp, sz, vp]
+        L.md_linsolve_series.argtypes = [i, i, i, i, vp, vp, vp, vp, sz, i, vp]
+        L.md_newton_series_step.argtypes = [ctypes.POINTER(md_system), vp, vp, vp, sz, i, vp]
+        L.md_get_device_status.argtypes = [vp, vp]
+        L.md_profile_enable.argtypes = [i]
+        L.md_profile_enable.restype = None
+        L.md_profile_read.argtypes = [vp, vp, i]
+        L.md_profile_read.restype = i
+        L.md_profile_kind_name.argtypes = [i]
+        L.md_profile_kind_name.restype = ctypes.c_char_p
+        for name in ("md_elementwise", "md_series_conv", "md_eval_diff", "md_linsolve_series",
+                     "md_newton_series_step", "md_get_device_status"):
+            getattr(L, name).restype = i
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return ["md_version", "md_status_string", "md_workspace_bytes", "md_linsolve_workspace_bytes",
+            "md_elementwise", "md_series_conv", "md_eval_diff", "md_linsolve_series",
+            "md_newton_series_step", "md_get_device_status", "md_profile_enable", "md_profile_read",
+            "md_profile_kind_name"]
+
+
+# --------------------------------------------------------------- helpers
+def _torch():
+    import torch
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("paper_2012_06607_gb300 needs a CUDA device")
+    return torch
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        raise MdError(code, what)
+
+
+def to_device(a: np.ndarray, device="cuda"):
+    torch = _torch()
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(device)
+
+
+def workspace(nbytes: int, device="cuda"):
+    torch = _torch()
+    return torch.zeros(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+# ------------------------------------------------------------- the system
+class DeviceSystem:
+    """A system with host structure arrays and device coefficient arrays.
+
+    ``s`` is any object with the fields of ``md_system`` as numpy arrays
+    (poly_ptr, nvar, idx, expo int32; coef [P][K][nmono], cst [P][K][n] float64).
+    """
+
+    def __init__(self, s, device="cuda"):
+        self.limbs, self.is_complex, self.n, self.degree = int(s.limbs), bool(s.is_complex), int(s.n), int(s.degree)
+        self.poly_ptr = np.ascontiguousarray(s.poly_ptr, dtype=np.int32)
+        self.nvar = np.ascontiguousarray(s.nvar, dtype=np.int32)
+        self.idx = np.ascontiguousarray(s.idx, dtype=np.int32)
+        self.expo = np.ascontiguousarray(s.expo, dtype=np.int32)
+        self.nmono = int(self.nvar.shape[0])
+        self.coef = to_device(s.coef, device)
+        self.cst = to_device(s.cst, device)
+        self._c = md_system(self.limbs, int(self.is_complex), self.n, self.degree, self.nmono,
+                            self.poly_ptr.ctypes.data, self.nvar.ctypes.data if self.nmono else None,
+                            self.idx.ctypes.data if self.nmono else None, self.expo.ctypes.data if self.nmono else None,
+                            _ptr(self.coef) if self.nmono else None, _ptr(self.cst))
+
+    @property
+    def planes(self):
+        return 2 if self.is_complex else 1
+
+    def c(self):
+        return ctypes.byref(self._c)
+
+    def workspace_bytes(self, flags: int = 0) -> int:
+        return int(lib().md_workspace_bytes(self.c(), flags))
+
+
+# ------------------------------------------------------------ entry points
+def elementwise(op: str, limbs: int, is_complex: bool, x, y=None, out=None, stream=None):
+    """x, y: CUDA tensors [P][K][count] (y: [count] doubles for mul_d)."""
+    z = out if out is not None else x.new_empty(x.shape)
+    count = x.shape[-1]
+    _check(lib().md_elementwise(OPS[op], limbs, int(is_complex), count, _ptr(x), _ptr(y), _ptr(z), _stream(stream)),
+           "md_elementwise")
+    return z
+
+
+def series_conv(limbs: int, is_complex: bool, x, y, out=None, stream=None):
+    """x, y: CUDA tensors [P][K][count][d+1]."""
+    z = out if out is not None else x.new_empty(x.shape)
+    _check(lib().md_series_conv(limbs, int(is_complex), x.shape[-1] - 1, x.shape[2], _ptr(x), _ptr(y), _ptr(z),
+                                _stream(stream)), "md_series_conv")
+    return z
+
+
+def eval_diff(sysd: DeviceSystem, x, ws, f=None, A=None, stream=None):
+    torch = _torch()
+    P, K, n, d = sysd.planes, sysd.limbs, sysd.n, sysd.degree
+    f = f if f is not None else torch.empty((P, K, n, d + 1), dtype=torch.float64, device=x.device)
+    A = A if A is not None else torch.empty((P, K, d + 1, n, n), dtype=torch.float64, device=x.device)
+    _check(lib().md_eval_diff(sysd.c(), _ptr(x), _ptr(f), _ptr(A), _ptr(ws), ws.numel(), _stream(stream)),
+           "md_eval_diff")
+    return f, A
+
+
+def linsolve_workspace_bytes(limbs: int, is_complex: bool, n: int, degree: int, flags: int = 0) -> int:
+    return int(lib().md_linsolve_workspace_bytes(limbs, int(is_complex), n, degree, flags))
+
+
+def linsolve(limbs: int, is_complex: bool, A, b, ws, dx=None, flags: int = 0, stream=None):
+    """A: [P][K][d+1][n][n], b: [P][K][n][d+1] CUDA tensors -> dx like b."""
+    n, d = b.shape[2], b.shape[3] - 1
+    dx = dx if dx is not None else b.new_empty(b.shape)
+    _check(lib().md_linsolve_series(limbs, int(is_complex), n, d, _ptr(A), _ptr(b), _ptr(dx), _ptr(ws), ws.numel(),
+                                    flags, _stream(stream)), "md_linsolve_series")
+    return dx
+
+
+def newton_step(sysd: DeviceSystem, x, ws, dx_norm=None, flags: int = 0, stream=None):
+    """In-place step on x ([P][K][n][d+1] CUDA tensor); dx_norm: CUDA double[2] or None."""
+    _check(lib().md_newton_series_step(sysd.c(), _ptr(x), _ptr(dx_norm), _ptr(ws), ws.numel(), flags,
+                                       _stream(stream)), "md_newton_series_step")
+    return x
+
+
+def device_status(ws, stream=None) -> int:
+    return int(lib().md_get_device_status(_ptr(ws), _stream(stream)))
+
+
+# ------------------------------------------------------------------ profiling
+def profile_enable(on: bool = True) -> None:
+    lib().md_profile_enable(int(on))
+
+
+def profile_read() -> dict:
+    """{kernel class: (milliseconds, launches)} since the last read (synchronises)."""
+    n = 32
+    ms = np.zeros(n)
+    cnt = np.zeros(n, dtype=np.int64)
+    k = lib().md_profile_read(ms.ctypes.data, cnt.ctypes.data, n)
+    if k < 0:
+        raise RuntimeError("md_profile_read failed")
+    return {lib().md_profile_kind_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(k) if cnt[i]}

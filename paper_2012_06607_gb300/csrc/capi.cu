@@ -1,0 +1,578 @@
+// C ABI of the library (declared in include/mdnewton.h): argument checks,
+// host planning of the evaluation schedule, workspace layout and dispatch to
+// the templated launchers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <vector>
+
+#include "../../include/mdnewton.h"
+#include "internal.h"
+
+namespace {
+
+using mdk::EvalDev;
+using mdk::SolveDev;
+
+bool valid_limbs(int K) { return K == 1 || K == 2 || K == 3 || K == 4 || K == 5 || K == 8 || K == 10; }
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ------------------------------------------------------------ dispatch
+template <int K>
+cudaError_t dispatch_p(int P, int what, const void *a, cudaStream_t s, int op = 0, long long count = 0, int d = 0,
+                       const double *x = nullptr, const double *y = nullptr, double *z = nullptr) {
+  if (P == 1) {
+    switch (what) {
+      case 0: return mdk::Impl<K, 1>::elementwise(op, count, x, y, z, s);
+      case 1: return mdk::Impl<K, 1>::series_conv(d, count, x, y, z, s);
+      case 2: return mdk::Impl<K, 1>::eval(*static_cast<const EvalDev *>(a), s);
+      case 3: return mdk::Impl<K, 1>::solve(*static_cast<const SolveDev *>(a), s);
+    }
+  } else {
+    switch (what) {
+      case 0: return mdk::Impl<K, 2>::elementwise(op, count, x, y, z, s);
+      case 1: return mdk::Impl<K, 2>::series_conv(d, count, x, y, z, s);
+      case 2: return mdk::Impl<K, 2>::eval(*static_cast<const EvalDev *>(a), s);
+      case 3: return mdk::Impl<K, 2>::solve(*static_cast<const SolveDev *>(a), s);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t dispatch(int K, int P, int what, const void *a, cudaStream_t s, int op = 0, long long count = 0, int d = 0,
+                     const double *x = nullptr, const double *y = nullptr, double *z = nullptr) {
+  switch (K) {
+    case 1: return dispatch_p<1>(P, what, a, s, op, count, d, x, y, z);
+    case 2: return dispatch_p<2>(P, what, a, s, op, count, d, x, y, z);
+    case 3: return dispatch_p<3>(P, what, a, s, op, count, d, x, y, z);
+    case 4: return dispatch_p<4>(P, what, a, s, op, count, d, x, y, z);
+    case 5: return dispatch_p<5>(P, what, a, s, op, count, d, x, y, z);
+    case 8: return dispatch_p<8>(P, what, a, s, op, count, d, x, y, z);
+    case 10: return dispatch_p<10>(P, what, a, s, op, count, d, x, y, z);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------- solve layout
+struct SolveLayout {
+  size_t off_M, off_Y, off_W, off_vd, off_beta, off_rinv, off_r, off_dxw, off_part, bytes;
+  int maxchunk;
+};
+
+SolveLayout solve_layout(int K, int P, int n, int d, size_t base) {
+  SolveLayout L;
+  const size_t VS = sizeof(double) * P * K;
+  const size_t nn = (size_t)n * n;
+  int maxchunk = 1;
+  for (int k = 0; k <= d; ++k) {
+    int C, nc;
+    mdk::rhs_chunking(n, k, C, nc);
+    maxchunk = std::max(maxchunk, nc);
+  }
+  L.maxchunk = maxchunk;
+  size_t o = base;
+  L.off_M = o; o = align256(o + nn * VS);
+  L.off_Y = o; o = align256(o + nn * VS);
+  L.off_W = o; o = align256(o + nn * VS);
+  L.off_vd = o; o = align256(o + n * VS);
+  L.off_beta = o; o = align256(o + n * sizeof(double) * K);
+  L.off_rinv = o; o = align256(o + n * VS);
+  L.off_r = o; o = align256(o + (size_t)(d + 1) * n * VS);
+  L.off_dxw = o; o = align256(o + (size_t)(d + 1) * n * VS);
+  L.off_part = o; o = align256(o + (size_t)n * maxchunk * VS);
+  L.bytes = o - base;
+  return L;
+}
+
+// --------------------------------------------------------- eval planning
+struct Plan {
+  int K = 0, P = 0, n = 0, d = 0, nmono = 0;
+  int nslots = 0;
+  std::vector<int> tasks;      // 8 ints per task, stage-major
+  std::vector<int> stage_off;  // nstages + 1
+  std::vector<int> scal_src;   // (monomial, exponent factor)
+  std::vector<int> groups;     // (row, col or -1, first contribution, count)
+  std::vector<int> contrib;    // (slot or -1, scal index, t shift, 0)
+  // workspace offsets (bytes)
+  size_t off_pool = 0, off_scal = 0, off_tasks = 0, off_scalsrc = 0, off_groups = 0, off_contrib = 0;
+  size_t off_f = 0, off_A = 0, off_solve = 0, total = 0;
+  SolveLayout sl{};
+  uint64_t checksum = 0;
+};
+
+uint64_t fnv(uint64_t h, const void *p, size_t bytes) {
+  const unsigned char *c = static_cast<const unsigned char *>(p);
+  for (size_t i = 0; i < bytes; ++i) {
+    h ^= c[i];
+    h *= 1099511628211ULL;
+  }
+  return h;
+}
+
+uint64_t structure_checksum(const md_system *s) {
+  uint64_t h = 1469598103934665603ULL;
+  const int hdr[5] = {s->limbs, s->is_complex, s->n, s->degree, s->nmono};
+  h = fnv(h, hdr, sizeof(hdr));
+  h = fnv(h, s->poly_ptr, sizeof(int) * (s->n + 1));
+  h = fnv(h, s->nvar, sizeof(int) * s->nmono);
+  h = fnv(h, s->idx, sizeof(int) * s->nmono * MD_MAXV);
+  h = fnv(h, s->expo, sizeof(int) * s->nmono * MD_MAXV);
+  return h;
+}
+
+md_status check_system(const md_system *s) {
+  if (!s || !valid_limbs(s->limbs) || s->n < 1 || s->degree < 0 || s->nmono < 0) return MD_ERR_ARG;
+  if (!s->poly_ptr || (s->nmono > 0 && (!s->nvar || !s->idx || !s->expo || !s->coef)) || !s->cst) return MD_ERR_ARG;
+  if (s->poly_ptr[0] != 0 || s->poly_ptr[s->n] != s->nmono) return MD_ERR_ARG;
+  for (int i = 0; i < s->n; ++i)
+    if (s->poly_ptr[i + 1] < s->poly_ptr[i]) return MD_ERR_ARG;
+  for (int m = 0; m < s->nmono; ++m) {
+    if (s->nvar[m] < 0 || s->nvar[m] > MD_MAXV) return MD_ERR_ARG;
+    for (int q = 0; q < s->nvar[m]; ++q) {
+      const int v = s->idx[m * MD_MAXV + q], e = s->expo[m * MD_MAXV + q];
+      if (v < 0 || v > s->n || e < 1) return MD_ERR_ARG;
+      for (int q2 = 0; q2 < q; ++q2)
+        if (s->idx[m * MD_MAXV + q2] == v) return MD_ERR_ARG;
+    }
+  }
+  return MD_OK;
+}
+
+// Builds the product schedule of every monomial in the order of the
+// definition (common factor, Speelpenning forward / backward / cross products,
+// F*P and F*partials), the stage of each product and the accumulation lists.
+md_status build_plan(const md_system *s, Plan &p) {
+  md_status st = check_system(s);
+  if (st != MD_OK) return st;
+  const int n = s->n, d = s->degree;
+  p.K = s->limbs;
+  p.P = s->is_complex ? 2 : 1;
+  p.n = n;
+  p.d = d;
+  p.nmono = s->nmono;
+  p.nslots = n;
+  std::vector<int> stage(n, 0);
+  struct Op {
+    int out, a, b, st;
+  };
+  std::vector<Op> ops;
+  auto conv = [&](int a, int b) {
+    const int out = p.nslots++;
+    const int sg = 1 + std::max(stage[a], stage[b]);
+    stage.push_back(sg);
+    ops.push_back({out, a, b, sg});
+    return out;
+  };
+  // -1 is the unit series
+  auto conv_or_copy = [&](int a, int b) {
+    if (a < 0) return b;
+    if (b < 0) return a;
+    return conv(a, b);
+  };
+  std::vector<int> fcon;  // f contributions, 4 ints each, polynomial-major
+  std::vector<int> alist;  // A contributions, 4 ints each
+  std::map<std::pair<int, int>, std::vector<int>> acon;  // (row, col) -> indices into alist
+  std::vector<int> fgroup_first(n), fgroup_count(n);
+  for (int i = 0; i < n; ++i) {
+    fgroup_first[i] = (int)fcon.size() / 4;
+    fgroup_count[i] = s->poly_ptr[i + 1] - s->poly_ptr[i];
+    for (int mo = s->poly_ptr[i]; mo < s->poly_ptr[i + 1]; ++mo) {
+      int m = 0, at = 0, vj[MD_MAXV], va[MD_MAXV];
+      for (int q = 0; q < s->nvar[mo]; ++q) {
+        const int v = s->idx[mo * MD_MAXV + q], e = s->expo[mo * MD_MAXV + q];
+        if (v == n) {
+          at = e;
+        } else {
+          vj[m] = v;
+          va[m] = e;
+          ++m;
+        }
+      }
+      // common factor F = prod x_j^(a_j - 1)
+      int F = -1;
+      for (int q = 0; q < m; ++q)
+        for (int e = 1; e < va[q]; ++e) F = (F < 0) ? vj[q] : conv(F, vj[q]);
+      // Speelpenning products
+      int pf[MD_MAXV], sb[MD_MAXV];
+      int Pser = -1;
+      if (m >= 1) {
+        pf[0] = vj[0];
+        for (int q = 1; q < m; ++q) pf[q] = conv(pf[q - 1], vj[q]);
+        sb[m - 1] = vj[m - 1];
+        for (int q = m - 2; q >= 1; --q) sb[q] = conv(vj[q], sb[q + 1]);
+        Pser = pf[m - 1];
+      }
+      const int G = conv_or_copy(F, Pser);
+      const int sv = (int)p.scal_src.size() / 2;
+      p.scal_src.push_back(mo);
+      p.scal_src.push_back(1);
+      fcon.insert(fcon.end(), {G, sv, at, 0});
+      for (int q = 0; q < m; ++q) {
+        int der;
+        if (m == 1)
+          der = -1;
+        else if (q == 0)
+          der = sb[1];
+        else if (q == m - 1)
+          der = pf[m - 2];
+        else
+          der = conv(pf[q - 1], sb[q + 1]);
+        const int D = conv_or_copy(F, der);
+        const int sq = (int)p.scal_src.size() / 2;
+        p.scal_src.push_back(mo);
+        p.scal_src.push_back(va[q]);
+        acon[{i, vj[q]}].push_back((int)alist.size() / 4);
+        alist.insert(alist.end(), {D, sq, at, 0});
+      }
+    }
+  }
+  // f groups first, then one group per (row, col) with its contributions in monomial order
+  p.contrib = fcon;
+  for (int i = 0; i < n; ++i) p.groups.insert(p.groups.end(), {i, -1, fgroup_first[i], fgroup_count[i]});
+  for (auto &kv : acon) {
+    const int first = (int)p.contrib.size() / 4;
+    for (int a : kv.second) p.contrib.insert(p.contrib.end(), alist.begin() + 4 * a, alist.begin() + 4 * a + 4);
+    p.groups.insert(p.groups.end(), {kv.first.first, kv.first.second, first, (int)kv.second.size()});
+  }
+  // stages and tasks
+  int nst = 0;
+  for (const Op &o : ops) nst = std::max(nst, o.st);
+  p.stage_off.assign(1, 0);
+  for (int sg = 1; sg <= nst; ++sg) {
+    std::vector<int> middles;  // ops whose middle coefficient is left
+    for (const Op &o : ops) {
+      if (o.st != sg) continue;
+      for (int k = 0; 2 * k < d; ++k) p.tasks.insert(p.tasks.end(), {o.out, o.a, o.b, k, o.out, o.a, o.b, 0});
+      if (d % 2 == 0) middles.push_back((int)(&o - ops.data()));
+    }
+    for (size_t q = 0; q < middles.size(); q += 2) {
+      const Op &A = ops[middles[q]];
+      if (q + 1 < middles.size()) {
+        const Op &B = ops[middles[q + 1]];
+        p.tasks.insert(p.tasks.end(), {A.out, A.a, A.b, d / 2, B.out, B.a, B.b, 0});
+      } else {
+        p.tasks.insert(p.tasks.end(), {A.out, A.a, A.b, d / 2, -1, -1, -1, 0});
+      }
+    }
+    p.stage_off.push_back((int)p.tasks.size() / 8);
+  }
+  // workspace layout
+  const size_t VS = sizeof(double) * p.P * p.K;
+  size_t o = 256;  // header: status word
+  p.off_pool = o; o = align256(o + (size_t)p.nslots * (d + 1) * VS);
+  const int nscal = (int)p.scal_src.size() / 2;
+  p.off_scal = o; o = align256(o + (size_t)std::max(nscal, 1) * VS);
+  p.off_tasks = o; o = align256(o + sizeof(int) * std::max<size_t>(p.tasks.size(), 8));
+  p.off_scalsrc = o; o = align256(o + sizeof(int) * std::max<size_t>(p.scal_src.size(), 2));
+  p.off_groups = o; o = align256(o + sizeof(int) * std::max<size_t>(p.groups.size(), 4));
+  p.off_contrib = o; o = align256(o + sizeof(int) * std::max<size_t>(p.contrib.size(), 4));
+  p.off_f = o; o = align256(o + (size_t)n * (d + 1) * VS);
+  p.off_A = o; o = align256(o + (size_t)(d + 1) * n * n * VS);
+  p.off_solve = o;
+  p.sl = solve_layout(p.K, p.P, n, d, o);
+  p.total = o + p.sl.bytes;
+  p.checksum = structure_checksum(s);
+  return MD_OK;
+}
+
+// Plans are cached per system structure (checksum) together with a pinned host
+// image of their integer tables; every call copies that image into its
+// workspace with one asynchronous copy, so a workspace needs no state between
+// calls.  Cached images live until the process exits (in-flight copies may
+// still read them).
+struct PlanEntry {
+  Plan plan;
+  int *pinned = nullptr;  // tables laid out exactly as in the workspace, from off_tasks
+  size_t image_bytes = 0;
+};
+std::mutex g_mu;
+std::map<uint64_t, PlanEntry *> g_plans;
+
+md_status prepare(const md_system *s, void *ws, size_t ws_bytes, cudaStream_t stream, Plan *&out) {
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return MD_ERR_WORKSPACE;
+  md_status st = check_system(s);
+  if (st != MD_OK) return st;
+  const uint64_t cs = structure_checksum(s);
+  PlanEntry *pe = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_plans.find(cs);
+    if (it != g_plans.end()) {
+      pe = it->second;
+    } else {
+      std::unique_ptr<PlanEntry> e(new PlanEntry);
+      st = build_plan(s, e->plan);
+      if (st != MD_OK) return st;
+      const Plan &p = e->plan;
+      e->image_bytes = p.off_f - p.off_tasks;
+      void *h = nullptr;
+      if (cudaHostAlloc(&h, e->image_bytes, cudaHostAllocDefault) != cudaSuccess) return MD_ERR_CUDA;
+      e->pinned = static_cast<int *>(h);
+      std::memset(h, 0, e->image_bytes);
+      auto put = [&](size_t off, const std::vector<int> &v) {
+        if (!v.empty()) std::memcpy(static_cast<char *>(h) + (off - p.off_tasks), v.data(), sizeof(int) * v.size());
+      };
+      put(p.off_tasks, p.tasks);
+      put(p.off_scalsrc, p.scal_src);
+      put(p.off_groups, p.groups);
+      put(p.off_contrib, p.contrib);
+      pe = e.release();
+      g_plans[cs] = pe;
+    }
+  }
+  const Plan &p = pe->plan;
+  if (p.total > ws_bytes) return MD_ERR_WORKSPACE;
+  if (cudaMemcpyAsync(static_cast<char *>(ws) + p.off_tasks, pe->pinned, pe->image_bytes, cudaMemcpyHostToDevice,
+                      stream) != cudaSuccess)
+    return MD_ERR_CUDA;
+  out = &pe->plan;
+  return MD_OK;
+}
+
+EvalDev make_eval(const Plan &p, const md_system *s, const double *x, double *f, double *A, char *base) {
+  EvalDev e;
+  e.n = p.n;
+  e.d = p.d;
+  e.nmono = p.nmono;
+  e.x = x;
+  e.f = f;
+  e.A = A;
+  e.coef = s->coef;
+  e.cst = s->cst;
+  e.pool = reinterpret_cast<double *>(base + p.off_pool);
+  e.scal = reinterpret_cast<double *>(base + p.off_scal);
+  e.tasks = reinterpret_cast<const int *>(base + p.off_tasks);
+  e.stage_off = p.stage_off.data();
+  e.nstages = (int)p.stage_off.size() - 1;
+  e.scal_src = reinterpret_cast<const int *>(base + p.off_scalsrc);
+  e.nscal = (int)p.scal_src.size() / 2;
+  e.groups = reinterpret_cast<const int *>(base + p.off_groups);
+  e.ngroups = (int)p.groups.size() / 4;
+  e.contrib = reinterpret_cast<const int *>(base + p.off_contrib);
+  return e;
+}
+
+SolveDev make_solve(const SolveLayout &L, int n, int d, char *base) {
+  SolveDev v;
+  v.n = n;
+  v.d = d;
+  v.M = reinterpret_cast<double *>(base + L.off_M);
+  v.Y = reinterpret_cast<double *>(base + L.off_Y);
+  v.W = reinterpret_cast<double *>(base + L.off_W);
+  v.vd = reinterpret_cast<double *>(base + L.off_vd);
+  v.beta = reinterpret_cast<double *>(base + L.off_beta);
+  v.rinv = reinterpret_cast<double *>(base + L.off_rinv);
+  v.r = reinterpret_cast<double *>(base + L.off_r);
+  v.dxw = reinterpret_cast<double *>(base + L.off_dxw);
+  v.part = reinterpret_cast<double *>(base + L.off_part);
+  v.status = reinterpret_cast<int *>(base);
+  v.maxchunk = L.maxchunk;
+  return v;
+}
+
+md_status cuda_status(cudaError_t e) { return e == cudaSuccess ? MD_OK : MD_ERR_CUDA; }
+
+// ------------------------------------------------------------- profiling
+// Optional per-launch timing: when enabled, every launch is bracketed by a
+// pair of CUDA events recorded on its stream; md_profile_read sums the
+// elapsed times per kernel class.
+std::atomic<bool> g_prof_on{false};
+std::mutex g_prof_mu;
+struct ProfRec {
+  int kind;
+  cudaEvent_t a, b;
+};
+std::vector<ProfRec> g_prof_recs;
+std::vector<cudaEvent_t> g_prof_free;
+
+cudaEvent_t prof_event() {
+  if (!g_prof_free.empty()) {
+    cudaEvent_t e = g_prof_free.back();
+    g_prof_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+}  // namespace
+
+namespace mdk {
+bool prof_enabled() { return g_prof_on.load(std::memory_order_relaxed); }
+int prof_begin(int kind, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  ProfRec r{kind, prof_event(), prof_event()};
+  cudaEventRecord(r.a, s);
+  g_prof_recs.push_back(r);
+  return (int)g_prof_recs.size() - 1;
+}
+void prof_end(int id, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (id >= 0 && id < (int)g_prof_recs.size()) cudaEventRecord(g_prof_recs[id].b, s);
+}
+}  // namespace mdk
+
+namespace {
+const char *kProfNames[mdk::PK_COUNT] = {"pool_load_x", "prep_scal", "conv_stage", "accum", "qr_house", "qr_apply",
+                                         "rinv", "backsub", "rhs_partial", "rhs_finish", "wmv", "finish_dx",
+                                         "elementwise", "series_conv"};
+
+}  // namespace
+
+extern "C" {
+
+int md_version(void) { return 100; }
+
+const char *md_status_string(md_status st) {
+  switch (st) {
+    case MD_OK: return "ok";
+    case MD_ERR_ARG: return "invalid argument";
+    case MD_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case MD_ERR_CUDA: return "CUDA error";
+    case MD_ERR_SINGULAR: return "A_0 is singular";
+    case MD_ERR_NONFINITE: return "non-finite update";
+    case MD_ERR_NOCONV: return "no convergence";
+    case MD_ERR_TIMEOUT: return "device wait timed out";
+    case MD_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+size_t md_workspace_bytes(const md_system *sys, int flags) {
+  (void)flags;
+  Plan p;
+  if (build_plan(sys, p) != MD_OK) return 0;
+  return p.total;
+}
+
+size_t md_linsolve_workspace_bytes(int limbs, int is_complex, int n, int degree, int flags) {
+  (void)flags;
+  if (!valid_limbs(limbs) || n < 1 || degree < 0) return 0;
+  return 256 + solve_layout(limbs, is_complex ? 2 : 1, n, degree, 256).bytes;
+}
+
+md_status md_elementwise(int op, int limbs, int is_complex, long long count, const double *x, const double *y,
+                         double *z, void *stream) {
+  if (!valid_limbs(limbs) || op < 0 || op > 5 || count < 0 || (op == 4 && is_complex)) return MD_ERR_ARG;
+  if (count > 0 && (!x || !z || (op != 4 && !y))) return MD_ERR_ARG;
+  return cuda_status(dispatch(limbs, is_complex ? 2 : 1, 0, nullptr, static_cast<cudaStream_t>(stream), op, count, 0,
+                              x, y, z));
+}
+
+md_status md_series_conv(int limbs, int is_complex, int degree, long long count, const double *x, const double *y,
+                         double *z, void *stream) {
+  if (!valid_limbs(limbs) || degree < 0 || count < 0) return MD_ERR_ARG;
+  if (count > 0 && (!x || !y || !z)) return MD_ERR_ARG;
+  return cuda_status(dispatch(limbs, is_complex ? 2 : 1, 1, nullptr, static_cast<cudaStream_t>(stream), 0, count,
+                              degree, x, y, z));
+}
+
+md_status md_eval_diff(const md_system *sys, const double *x, double *f, double *A, void *ws, size_t ws_bytes,
+                       void *stream) {
+  if (!x || !f || !A) return MD_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Plan *p = nullptr;
+  md_status st = prepare(sys, ws, ws_bytes, s, p);
+  if (st != MD_OK) return st;
+  char *base = static_cast<char *>(ws);
+  if (cudaMemsetAsync(base, 0, 256, s) != cudaSuccess) return MD_ERR_CUDA;
+  EvalDev e = make_eval(*p, sys, x, f, A, base);
+  return cuda_status(dispatch(p->K, p->P, 2, &e, s));
+}
+
+md_status md_linsolve_series(int limbs, int is_complex, int n, int degree, const double *A, const double *b,
+                             double *dx, void *ws, size_t ws_bytes, int flags, void *stream) {
+  (void)flags;
+  if (!valid_limbs(limbs) || n < 1 || degree < 0 || !A || !b || !dx) return MD_ERR_ARG;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return MD_ERR_WORKSPACE;
+  const int P = is_complex ? 2 : 1;
+  SolveLayout L = solve_layout(limbs, P, n, degree, 256);
+  if (256 + L.bytes > ws_bytes) return MD_ERR_WORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char *base = static_cast<char *>(ws);
+  if (cudaMemsetAsync(base, 0, 256, s) != cudaSuccess) return MD_ERR_CUDA;
+  SolveDev v = make_solve(L, n, degree, base);
+  v.A = A;
+  v.b = b;
+  v.sgn = 1.0;
+  v.dx_out = dx;
+  return cuda_status(dispatch(limbs, P, 3, &v, s));
+}
+
+md_status md_newton_series_step(const md_system *sys, double *x, double *dx_norm, void *ws, size_t ws_bytes, int flags,
+                                void *stream) {
+  (void)flags;
+  if (!x) return MD_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Plan *p = nullptr;
+  md_status st = prepare(sys, ws, ws_bytes, s, p);
+  if (st != MD_OK) return st;
+  char *base = static_cast<char *>(ws);
+  if (cudaMemsetAsync(base, 0, 256, s) != cudaSuccess) return MD_ERR_CUDA;
+  if (dx_norm && cudaMemsetAsync(dx_norm, 0, 2 * sizeof(double), s) != cudaSuccess) return MD_ERR_CUDA;
+  double *f = reinterpret_cast<double *>(base + p->off_f);
+  double *A = reinterpret_cast<double *>(base + p->off_A);
+  EvalDev e = make_eval(*p, sys, x, f, A, base);
+  cudaError_t err = dispatch(p->K, p->P, 2, &e, s);
+  if (err != cudaSuccess) return MD_ERR_CUDA;
+  SolveDev v = make_solve(p->sl, p->n, p->d, base);
+  v.A = A;
+  v.b = f;
+  v.sgn = -1.0;
+  v.x = x;
+  v.nrm = dx_norm;
+  return cuda_status(dispatch(p->K, p->P, 3, &v, s));
+}
+
+void md_profile_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on.store(on != 0);
+}
+
+int md_profile_read(double *ms, long long *launches, int nkinds) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (ms)
+    for (int k = 0; k < nkinds; ++k) ms[k] = 0.0;
+  if (launches)
+    for (int k = 0; k < nkinds; ++k) launches[k] = 0;
+  int bad = 0;
+  for (ProfRec &r : g_prof_recs) {
+    float t = 0.f;
+    if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) ++bad;
+    if (r.kind < nkinds) {
+      if (ms) ms[r.kind] += t;
+      if (launches) launches[r.kind] += 1;
+    }
+    g_prof_free.push_back(r.a);
+    g_prof_free.push_back(r.b);
+  }
+  g_prof_recs.clear();
+  return bad ? -1 : (int)mdk::PK_COUNT;
+}
+
+const char *md_profile_kind_name(int kind) {
+  if (kind < 0 || kind >= mdk::PK_COUNT) return "unknown";
+  return kProfNames[kind];
+}
+
+md_status md_get_device_status(void *ws, void *stream) {
+  if (!ws) return MD_ERR_WORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MD_ERR_CUDA;
+  int word = 0;
+  if (cudaMemcpy(&word, ws, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MD_ERR_CUDA;
+  if (cudaMemset(ws, 0, sizeof(int)) != cudaSuccess) return MD_ERR_CUDA;
+  if (word & mdk::ST_SINGULAR) return MD_ERR_SINGULAR;
+  if (word & mdk::ST_NONFINITE) return MD_ERR_NONFINITE;
+  return MD_OK;
+}
+
+}  // extern "C"

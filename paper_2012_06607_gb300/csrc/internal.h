@@ -1,0 +1,89 @@
+// Host-side descriptors passed from the C ABI layer to the templated launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+namespace mdk {
+
+enum : int { ST_SINGULAR = 1, ST_NONFINITE = 2 };
+
+// Kernel classes for the optional per-launch timing (md_profile_*).
+enum ProfKind : int {
+  PK_POOL = 0, PK_SCAL, PK_CONV, PK_ACCUM, PK_QR_HOUSE, PK_QR_APPLY, PK_RINV, PK_BACKSUB,
+  PK_RHS_PARTIAL, PK_RHS_FINISH, PK_WMV, PK_FINISH, PK_ELEMENTWISE, PK_SERIES, PK_COUNT
+};
+bool prof_enabled();
+int prof_begin(int kind, cudaStream_t s);
+void prof_end(int id, cudaStream_t s);
+
+struct ProfScope {
+  int id;
+  cudaStream_t s;
+  ProfScope(int kind, cudaStream_t st) : id(prof_enabled() ? prof_begin(kind, st) : -1), s(st) {}
+  ~ProfScope() {
+    if (id >= 0) prof_end(id, s);
+  }
+};
+
+// Lanes targeted by one split launch: 152 SMs x 4 sub-partitions x 2 warps x 32.
+constexpr int kTargetLanes = 152 * 4 * 2 * 32;
+
+struct EvalDev {
+  int n = 0, d = 0, nmono = 0;
+  const double *x = nullptr;
+  double *f = nullptr;
+  double *A = nullptr;
+  const double *coef = nullptr;
+  const double *cst = nullptr;
+  double *pool = nullptr;
+  double *scal = nullptr;
+  const int *tasks = nullptr;
+  const int *stage_off = nullptr;  // HOST array, nstages + 1 entries
+  int nstages = 0;
+  const int *scal_src = nullptr;
+  int nscal = 0;
+  const int *groups = nullptr;
+  int ngroups = 0;
+  const int *contrib = nullptr;
+};
+
+struct SolveDev {
+  int n = 0, d = 0;
+  const double *A = nullptr;  // caller layout [P][K][d+1][n][n]
+  const double *b = nullptr;  // caller layout [P][K][n][d+1]
+  double sgn = 1.0;           // r_k = sgn * b_k - ...
+  double *dx_out = nullptr;   // caller layout, may be null
+  double *x = nullptr;        // x += dx when not null
+  double *nrm = nullptr;      // device double[2] or null
+  double *M = nullptr, *Y = nullptr, *W = nullptr;
+  double *vd = nullptr, *beta = nullptr, *rinv = nullptr;
+  double *r = nullptr, *dxw = nullptr, *part = nullptr;
+  int *status = nullptr;
+  int maxchunk = 1;
+};
+
+inline void rhs_chunking(int n, int k, int &C, int &nchunk) {
+  const long long terms = (long long)k * n;
+  if (terms == 0) {
+    C = 1;
+    nchunk = 0;
+    return;
+  }
+  long long c = (terms * n + kTargetLanes - 1) / kTargetLanes;
+  if (c < 1) c = 1;
+  C = (int)c;
+  nchunk = (int)((terms + c - 1) / c);
+}
+
+template <int K, int P>
+struct Impl {
+  static cudaError_t elementwise(int op, long long count, const double *x, const double *y, double *z,
+                                 cudaStream_t s);
+  static cudaError_t series_conv(int d, long long count, const double *x, const double *y, double *z,
+                                 cudaStream_t s);
+  static cudaError_t eval(const EvalDev &e, cudaStream_t s);
+  static cudaError_t solve(const SolveDev &v, cudaStream_t s);
+};
+
+}  // namespace mdk

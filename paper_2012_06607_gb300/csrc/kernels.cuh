@@ -1,0 +1,574 @@
+// Kernels of the power-series Newton step (templated on limbs K and planes P).
+//
+// Evaluate and differentiate (Section 4, algorithmic differentiation):
+//   the host plans every series product of every monomial (common factor,
+//   Speelpenning forward / backward / cross products, factor times product) and
+//   groups them in dependency stages; one launch per stage computes all
+//   products of that stage across all monomials.  A product z = x * y of two
+//   series truncated at degree d has output coefficient k = sum_{i<=k} x_i y_{k-i}
+//   (Section 3), summed in ascending i; a thread owns two output coefficients
+//   whose term counts add up to d+2 (k and d-k, or two middle coefficients of
+//   two products), so every lane of a warp runs the same d+2 iterations.
+//   A second kernel accumulates f_i = cst_i + sum c_m G_m and
+//   A_k[i][j] = sum (c_m a_j) D_mj in the order of the monomials.  Both keep
+//   the summation order of the definition, so they agree with a sequential
+//   evaluation bit for bit.
+//
+// Solve (Section 4, lower triangular block Toeplitz system):
+//   Householder QR of A_0, one launch per column for the reflector and one
+//   for its application to the trailing columns and to the identity (which
+//   builds Q^H alongside); column-oriented back substitution of R W = Q^H for
+//   all n columns at once gives W = R^-1 Q^H = A_0^-1; then degree by degree
+//   r_k = b_k - sum_{j<k} A_{k-j} dx_j (split into chunks over all lanes) and
+//   dx_k = W r_k.  Reductions here are trees across lanes.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "md.cuh"
+
+namespace mdk {
+
+// ------------------------------------------------------------------ helpers
+template <int K, int P>
+__device__ __forceinline__ void warp_sum(mdv<K, P> &v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    mdv<K, P> o;
+    shfl_xor<K, P>(v, off, o);
+    c_add<K, P>(v, o, v);
+  }
+}
+
+// Sum over the block; every thread gets the result.  smem: NT/32 values.
+template <int K, int P>
+__device__ __forceinline__ void block_sum(mdv<K, P> &v, mdv<K, P> *smem) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  warp_sum<K, P>(v);
+  if (lane == 0) smem[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    mdv<K, P> t;
+    if (lane < nw)
+      t = smem[lane];
+    else
+      c_zero<K, P>(t);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      if (off < nw) {  // uniform across the warp; lanes >= nw hold zero
+        mdv<K, P> o;
+        shfl_xor<K, P>(t, off, o);
+        c_add<K, P>(t, o, t);
+      }
+    }
+    if (lane == 0) smem[0] = t;
+  }
+  __syncthreads();
+  v = smem[0];
+  __syncthreads();
+}
+
+template <int K>
+__device__ __forceinline__ void real_to(const double (&r)[K], mdv<K, 1> &z) {
+#pragma unroll
+  for (int l = 0; l < K; ++l) z.v[0][l] = r[l];
+}
+
+// ---------------------------------------------------------------- elementwise
+// op: 0 add, 1 sub, 2 mul, 3 div, 4 sqrt (real), 5 multiply by a double.
+template <int K, int P, int OP>
+__global__ void elementwise_kernel(long long count, const double *__restrict__ x, const double *__restrict__ y,
+                                   double *__restrict__ z) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  mdv<K, P> a, b, c;
+  ld_soa<K, P>(x + i, count, a);
+  if constexpr (OP <= 3) ld_soa<K, P>(y + i, count, b);
+  if constexpr (OP == 0) c_add<K, P>(a, b, c);
+  if constexpr (OP == 1) c_sub<K, P>(a, b, c);
+  if constexpr (OP == 2) c_mul<K, P>(a, b, c);
+  if constexpr (OP == 3) c_div<K, P>(a, b, c);
+  if constexpr (OP == 4) {
+    md_sqrt<K>(a.v[0], c.v[0]);
+    if constexpr (P == 2) {
+#pragma unroll
+      for (int l = 0; l < K; ++l) c.v[1][l] = 0.0;
+    }
+  }
+  if constexpr (OP == 5) c_mul_d<K, P>(a, y[i], c);
+  st_soa<K, P>(z + i, count, c);
+}
+
+// series products of `count` independent pairs, SoA layout [P][K][count][d+1];
+// one thread per output coefficient (the reference form of a series product).
+template <int K, int P>
+__global__ void series_conv_kernel(int d, long long count, const double *__restrict__ x, const double *__restrict__ y,
+                                   double *__restrict__ z) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= count * (d + 1)) return;
+  const long long c = e / (d + 1);
+  const int k = (int)(e % (d + 1));
+  const long long stride = count * (d + 1);
+  const double *xs = x + c * (d + 1);
+  const double *ys = y + c * (d + 1);
+  mdv<K, P> acc, a, b, t;
+  ld_soa<K, P>(xs, stride, a);
+  ld_soa<K, P>(ys + k, stride, b);
+  c_mul<K, P>(a, b, acc);
+  for (int i = 1; i <= k; ++i) {
+    ld_soa<K, P>(xs + i, stride, a);
+    ld_soa<K, P>(ys + (k - i), stride, b);
+    c_mul<K, P>(a, b, t);
+    c_add<K, P>(acc, t, acc);
+  }
+  st_soa<K, P>(z + e, stride, acc);
+}
+
+// -------------------------------------------------------------------- eval
+// Pool of series, AoS: value (slot s, coefficient k) at pool[(s*(d+1) + k)*P*K].
+template <int K, int P>
+__global__ void pool_load_x_kernel(const double *__restrict__ x, double *__restrict__ pool, int n, int d) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)n * (d + 1)) return;
+  mdv<K, P> v;
+  ld_soa<K, P>(x + e, (long long)n * (d + 1), v);
+  st_aos<K, P>(pool + e * (P * K), v);
+}
+
+// scal[i] = c_mono (a == 1) or c_mono * a (exponent factor of a derivative).
+template <int K, int P>
+__global__ void prep_scal_kernel(const int *__restrict__ src, int nscal, const double *__restrict__ coef, int nmono,
+                                 double *__restrict__ scal) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nscal) return;
+  const int mono = src[2 * i], a = src[2 * i + 1];
+  mdv<K, P> c, z;
+  ld_soa<K, P>(coef + mono, nmono, c);
+  if (a == 1)
+    z = c;
+  else
+    c_mul_d<K, P>(c, (double)a, z);
+  st_aos<K, P>(scal + (long long)i * (P * K), z);
+}
+
+// One launch per stage.  task = {outA, xA, yA, kA, outB, xB, yB, -}; kB = d - kA.
+template <int K, int P>
+__global__ void __launch_bounds__(64) conv_stage_kernel(const int *__restrict__ tasks, int ntask,
+                                                         double *pool, int d) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntask) return;
+  const int4 t0 = __ldg(reinterpret_cast<const int4 *>(tasks) + 2 * t);
+  const int4 t1 = __ldg(reinterpret_cast<const int4 *>(tasks) + 2 * t + 1);
+  const int outA = t0.x, xA = t0.y, yA = t0.z, kA = t0.w, outB = t1.x, xB = t1.y, yB = t1.z;
+  const int kB = d - kA;
+  const long long VS = P * K, SS = (long long)(d + 1) * VS;
+  const int total = (outB >= 0) ? (d + 2) : (kA + 1);
+  mdv<K, P> acc, a, b, prod, na, nb;
+  // operands of iteration it: first job (it <= kA): x_it * y_{kA-it};
+  // second job: x_i * y_{kB-i} with i = it - kA - 1.
+  auto addr = [&](int it, const double *&xp, const double *&yp) {
+    const bool first = it <= kA;
+    const int i = first ? it : it - kA - 1;
+    xp = pool + (first ? xA : xB) * SS + i * VS;
+    yp = pool + (first ? yA : yB) * SS + ((first ? kA : kB) - i) * VS;
+  };
+  const double *xp, *yp;
+  addr(0, xp, yp);
+  ld_aos_nc<K, P>(xp, na);
+  ld_aos_nc<K, P>(yp, nb);
+  for (int it = 0; it < total; ++it) {
+    a = na;
+    b = nb;
+    if (it + 1 < total) {
+      addr(it + 1, xp, yp);
+      ld_aos_nc<K, P>(xp, na);
+      ld_aos_nc<K, P>(yp, nb);
+    }
+    c_mul<K, P>(a, b, prod);
+    if (it == 0 || it == kA + 1)
+      acc = prod;
+    else
+      c_add<K, P>(acc, prod, acc);
+    if (it == kA) st_aos<K, P>(pool + outA * SS + kA * VS, acc);
+  }
+  if (outB >= 0) st_aos<K, P>(pool + outB * SS + kB * VS, acc);
+}
+
+// group = {row, col (-1: f_row), first contribution, count};
+// contribution = {slot (-1: the unit series), scal index, shift a_t, -}.
+template <int K, int P>
+__global__ void accum_kernel(const int4 *__restrict__ groups, int ngroups, const int4 *__restrict__ contrib,
+                             const double *__restrict__ pool, const double *__restrict__ scal,
+                             const double *__restrict__ cst, double *__restrict__ f, double *__restrict__ A, int n,
+                             int d) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)ngroups * (d + 1)) return;
+  const int g = (int)(e / (d + 1)), k = (int)(e % (d + 1));
+  const int4 G = groups[g];
+  const long long VS = P * K, SS = (long long)(d + 1) * VS;
+  mdv<K, P> acc, v, c, s;
+  c_zero<K, P>(acc);
+  if (G.y < 0 && k == 0) ld_soa<K, P>(cst + G.x, n, acc);
+  for (int q = 0; q < G.w; ++q) {
+    const int4 C = contrib[G.z + q];
+    c_zero<K, P>(v);
+    if (k >= C.z) {
+      ld_aos<K, P>(scal + (long long)C.y * VS, c);
+      if (C.x < 0) {
+        if (k == C.z) v = c;
+      } else {
+        ld_aos<K, P>(pool + C.x * SS + (k - C.z) * VS, s);
+        c_mul<K, P>(c, s, v);
+      }
+    }
+    c_add<K, P>(acc, v, acc);
+  }
+  if (G.y < 0) {
+    st_soa<K, P>(f + (long long)G.x * (d + 1) + k, (long long)n * (d + 1), acc);
+  } else {
+    const long long nn = (long long)n * n;
+    st_soa<K, P>(A + (long long)k * nn + (long long)G.y * n + G.x, (long long)(d + 1) * nn, acc);
+  }
+}
+
+// ------------------------------------------------------------------- solve
+// Work matrices are AoS, column-major: element (r, c) at M[(c*n + r)*P*K].
+template <int K, int P>
+__global__ void solve_init_kernel(const double *__restrict__ A, double *__restrict__ M, double *__restrict__ Y, int n,
+                                  int d) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nn = (long long)n * n;
+  if (e >= nn) return;
+  mdv<K, P> v;
+  ld_soa<K, P>(A + e, (long long)(d + 1) * nn, v);  // A_0, column-major, e = c*n + r
+  st_aos<K, P>(M + e * (P * K), v);
+  c_zero<K, P>(v);
+  const long long r = e % n, c = e / n;
+  if (r == c) v.v[0][0] = 1.0;
+  st_aos<K, P>(Y + e * (P * K), v);
+}
+
+// Householder vector of column j (Golub-Van Loan): alpha = ||x||, phase
+// e = x_0/|x_0|, v = x + e alpha e_1, beta = 1/(alpha (alpha + |x_0|)), R_jj = -e alpha.
+template <int K, int P>
+__global__ void __launch_bounds__(256) house_kernel(double *__restrict__ M, double *__restrict__ vd,
+                                                    double *__restrict__ beta, int *__restrict__ status, int n, int j) {
+  __shared__ mdv<K, 1> red[8];
+  __shared__ double s_alpha[K], s_a0[K], s_beta[K];
+  __shared__ mdv<K, P> s_ph;
+  const int tid = threadIdx.x;
+  const long long VS = P * K;
+  mdv<K, 1> acc;
+  c_zero<K, 1>(acc);
+  bool have = false;
+  for (int i = j + tid; i < n; i += blockDim.x) {
+    mdv<K, P> x;
+    ld_aos<K, P>(M + ((long long)j * n + i) * VS, x);
+    double a2[K];
+    c_abs2<K, P>(x, a2);
+    if (!have) {
+      real_to<K>(a2, acc);
+      have = true;
+    } else {
+      mdv<K, 1> t;
+      real_to<K>(a2, t);
+      c_add<K, 1>(acc, t, acc);
+    }
+  }
+  block_sum<K, 1>(acc, red);
+  mdv<K, P> x0;
+  ld_aos<K, P>(M + ((long long)j * n + j) * VS, x0);
+  if (tid == 0) {
+    double al[K];
+    md_sqrt<K>(acc.v[0], al);
+#pragma unroll
+    for (int l = 0; l < K; ++l) s_alpha[l] = al[l];
+  }
+  if (tid == 32) {
+    double a0[K];
+    if constexpr (P == 1) {
+      const bool neg = x0.v[0][0] < 0.0;
+#pragma unroll
+      for (int l = 0; l < K; ++l) a0[l] = neg ? -x0.v[0][l] : x0.v[0][l];
+    } else {
+      double s2[K];
+      c_abs2<K, P>(x0, s2);
+      md_sqrt<K>(s2, a0);
+    }
+#pragma unroll
+    for (int l = 0; l < K; ++l) s_a0[l] = a0[l];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double al[K], a0[K], t[K], den[K], one[K], bt[K];
+#pragma unroll
+    for (int l = 0; l < K; ++l) {
+      al[l] = s_alpha[l];
+      a0[l] = s_a0[l];
+      one[l] = 0.0;
+    }
+    one[0] = 1.0;
+    if (!nonzero(al[0])) atomicOr(status, ST_SINGULAR);
+    md_add<K>(al, a0, t);
+    md_mul<K>(al, t, den);
+    md_div<K>(one, den, bt);
+#pragma unroll
+    for (int l = 0; l < K; ++l) s_beta[l] = bt[l];
+  }
+  if (P == 1 && tid == 32) {
+    mdv<K, P> ph;
+    c_zero<K, P>(ph);
+    ph.v[0][0] = (x0.v[0][0] < 0.0) ? -1.0 : 1.0;
+    s_ph = ph;
+  }
+  if constexpr (P == 2) {
+    if (tid == 32 || tid == 64) {
+      const int p = (tid == 32) ? 0 : 1;
+      double a0[K], q[K];
+#pragma unroll
+      for (int l = 0; l < K; ++l) a0[l] = s_a0[l];
+      if (!nonzero(a0[0])) {
+#pragma unroll
+        for (int l = 0; l < K; ++l) q[l] = 0.0;
+        if (p == 0) q[0] = 1.0;
+      } else {
+        md_div<K>(x0.v[p], a0, q);
+      }
+#pragma unroll
+      for (int l = 0; l < K; ++l) s_ph.v[p][l] = q[l];
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double al[K];
+#pragma unroll
+    for (int l = 0; l < K; ++l) al[l] = s_alpha[l];
+    mdv<K, P> ph = s_ph, pa, v0, rjj;
+    c_mul_real<K, P>(ph, al, pa);
+    c_add<K, P>(x0, pa, v0);
+#pragma unroll
+    for (int p = 0; p < P; ++p) md_neg<K>(pa.v[p], rjj.v[p]);
+    st_aos<K, P>(vd + (long long)j * VS, v0);
+    st_aos<K, P>(M + ((long long)j * n + j) * VS, rjj);
+#pragma unroll
+    for (int l = 0; l < K; ++l) beta[(long long)j * K + l] = s_beta[l];
+  }
+}
+
+// Apply H_j = I - beta_j v v^H to the trailing columns of M and to all columns
+// of Y (which accumulates Q^H).  One warp per target column.
+template <int K, int P>
+__global__ void __launch_bounds__(128) house_apply_kernel(double *__restrict__ M, double *__restrict__ Y,
+                                                          const double *__restrict__ vd,
+                                                          const double *__restrict__ beta, int n, int j) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int nm = n - j - 1;
+  if (warp >= nm + n) return;
+  double *T;
+  int c;
+  if (warp < nm) {
+    T = M;
+    c = j + 1 + warp;
+  } else {
+    T = Y;
+    c = warp - nm;
+  }
+  const long long VS = P * K;
+  mdv<K, P> w, v, cv, t, prod;
+  c_zero<K, P>(w);
+  bool have = false;
+  for (int i = j + lane; i < n; i += 32) {
+    if (i == j)
+      ld_aos<K, P>(vd + (long long)j * VS, v);
+    else
+      ld_aos<K, P>(M + ((long long)j * n + i) * VS, v);
+    c_conj<K, P>(v, cv);
+    ld_aos<K, P>(T + ((long long)c * n + i) * VS, t);
+    c_mul<K, P>(cv, t, prod);
+    if (!have) {
+      w = prod;
+      have = true;
+    } else {
+      c_add<K, P>(w, prod, w);
+    }
+  }
+  warp_sum<K, P>(w);
+  double bt[K];
+#pragma unroll
+  for (int l = 0; l < K; ++l) bt[l] = beta[(long long)j * K + l];
+  mdv<K, P> tau;
+  c_mul_real<K, P>(w, bt, tau);
+  for (int i = j + lane; i < n; i += 32) {
+    if (i == j)
+      ld_aos<K, P>(vd + (long long)j * VS, v);
+    else
+      ld_aos<K, P>(M + ((long long)j * n + i) * VS, v);
+    ld_aos<K, P>(T + ((long long)c * n + i) * VS, t);
+    c_mul<K, P>(tau, v, prod);
+    c_sub<K, P>(t, prod, t);
+    st_aos<K, P>(T + ((long long)c * n + i) * VS, t);
+  }
+}
+
+// rinv[j] = 1 / R_jj
+template <int K, int P>
+__global__ void rinv_kernel(const double *__restrict__ M, double *__restrict__ rinv, int n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const long long VS = P * K;
+  mdv<K, P> r, one, z;
+  ld_aos<K, P>(M + ((long long)j * n + j) * VS, r);
+  c_zero<K, P>(one);
+  one.v[0][0] = 1.0;
+  c_div<K, P>(one, r, z);
+  st_aos<K, P>(rinv + (long long)j * VS, z);
+}
+
+// Column-oriented back substitution step c of R W = Y (all n right-hand sides):
+// W[c][:] = Y[c][:] / R_cc; Y[i][:] -= R_ic W[c][:] for i < c.  W is row-major.
+template <int K, int P>
+__global__ void backsub_kernel(const double *__restrict__ M, double *__restrict__ Y, double *__restrict__ W,
+                               const double *__restrict__ rinv, int n, int c) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)(c + 1) * n) return;
+  const int i = (int)(e / n), col = (int)(e % n);
+  const long long VS = P * K;
+  mdv<K, P> y, ri, w;
+  ld_aos<K, P>(Y + ((long long)col * n + c) * VS, y);
+  ld_aos<K, P>(rinv + (long long)c * VS, ri);
+  c_mul<K, P>(y, ri, w);
+  if (i == c) {
+    st_aos<K, P>(W + ((long long)c * n + col) * VS, w);
+  } else {
+    mdv<K, P> rc, t, yi;
+    ld_aos<K, P>(M + ((long long)c * n + i) * VS, rc);
+    ld_aos<K, P>(Y + ((long long)col * n + i) * VS, yi);
+    c_mul<K, P>(rc, w, t);
+    c_sub<K, P>(yi, t, yi);
+    st_aos<K, P>(Y + ((long long)col * n + i) * VS, yi);
+  }
+}
+
+// Partial sums of sum_{j<k} A_{k-j} dx_j for (row, chunk); term index
+// t = j*n + col over [chunk*C, min((chunk+1)*C, k*n)).  A is the caller's
+// SoA [P][K][d+1][n][n] (column-major blocks); dx is AoS [k][i].
+template <int K, int P>
+__global__ void rhs_partial_kernel(const double *__restrict__ A, const double *__restrict__ dx,
+                                   double *__restrict__ part, int n, int d, int k, int C, int nchunk) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)n * nchunk) return;
+  const int row = (int)(e % n), chunk = (int)(e / n);
+  const long long nn = (long long)n * n, VS = P * K, stride = (long long)(d + 1) * nn;
+  const int t0 = chunk * C, t1 = min(t0 + C, k * n);
+  mdv<K, P> acc, a, x, prod;
+  c_zero<K, P>(acc);
+  for (int t = t0; t < t1; ++t) {
+    const int j = t / n, col = t % n;
+    ld_soa<K, P>(A + (long long)(k - j) * nn + (long long)col * n + row, stride, a);
+    ld_aos<K, P>(dx + ((long long)j * n + col) * VS, x);
+    c_mul<K, P>(a, x, prod);
+    if (t == t0)
+      acc = prod;
+    else
+      c_add<K, P>(acc, prod, acc);
+  }
+  st_aos<K, P>(part + ((long long)row * nchunk + chunk) * VS, acc);
+}
+
+// r_k[row] = sgn * b_k[row] - sum of partials.  One block per row.
+template <int K, int P>
+__global__ void __launch_bounds__(128) rhs_finish_kernel(const double *__restrict__ b, double sgn,
+                                                         const double *__restrict__ part, double *__restrict__ r,
+                                                         int n, int d, int k, int nchunk) {
+  __shared__ mdv<K, P> red[4];
+  const int row = blockIdx.x;
+  const long long VS = P * K;
+  mdv<K, P> acc, t;
+  c_zero<K, P>(acc);
+  bool have = false;
+  for (int c = threadIdx.x; c < nchunk; c += blockDim.x) {
+    ld_aos<K, P>(part + ((long long)row * nchunk + c) * VS, t);
+    if (!have) {
+      acc = t;
+      have = true;
+    } else {
+      c_add<K, P>(acc, t, acc);
+    }
+  }
+  if (nchunk > 0) block_sum<K, P>(acc, red);
+  if (threadIdx.x == 0) {
+    mdv<K, P> bv, z;
+    ld_soa<K, P>(b + (long long)row * (d + 1) + k, (long long)n * (d + 1), bv);
+    if (sgn < 0.0)
+#pragma unroll
+      for (int p = 0; p < P; ++p) md_neg<K>(bv.v[p], bv.v[p]);
+    if (nchunk > 0)
+      c_sub<K, P>(bv, acc, z);
+    else
+      z = bv;
+    st_aos<K, P>(r + ((long long)k * n + row) * VS, z);
+  }
+}
+
+// dx_k[row] = sum_col W[row][col] r_k[col].  One block per row.
+template <int K, int P>
+__global__ void __launch_bounds__(128) wmv_kernel(const double *__restrict__ W, const double *__restrict__ r,
+                                                  double *__restrict__ dx, int n, int k) {
+  __shared__ mdv<K, P> red[4];
+  const int row = blockIdx.x;
+  const long long VS = P * K;
+  mdv<K, P> acc, w, x, prod;
+  c_zero<K, P>(acc);
+  bool have = false;
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    ld_aos<K, P>(W + ((long long)row * n + c) * VS, w);
+    ld_aos<K, P>(r + ((long long)k * n + c) * VS, x);
+    c_mul<K, P>(w, x, prod);
+    if (!have) {
+      acc = prod;
+      have = true;
+    } else {
+      c_add<K, P>(acc, prod, acc);
+    }
+  }
+  block_sum<K, P>(acc, red);
+  if (threadIdx.x == 0) st_aos<K, P>(dx + ((long long)k * n + row) * VS, acc);
+}
+
+// dx (AoS [k][i]) -> SoA [P][K][n][d+1]; optionally x += dx and the norms
+// nrm[0] = max_i |dx_{d,i}|, nrm[1] = max |dx| from the leading limbs.
+template <int K, int P>
+__global__ void finish_dx_kernel(const double *__restrict__ dxw, double *__restrict__ dx_out, double *__restrict__ x,
+                                 double *__restrict__ nrm, int *__restrict__ status, int n, int d) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)n * (d + 1)) return;
+  const int j = (int)(e / (d + 1)), k = (int)(e % (d + 1));
+  const long long VS = P * K, stride = (long long)n * (d + 1);
+  mdv<K, P> v;
+  ld_aos<K, P>(dxw + ((long long)k * n + j) * VS, v);
+  bool finite = true;
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+#pragma unroll
+    for (int l = 0; l < K; ++l) finite = finite && isfinite(v.v[p][l]);
+  if (!finite) atomicOr(status, ST_NONFINITE);
+  if (dx_out) st_soa<K, P>(dx_out + e, stride, v);
+  if (x) {
+    mdv<K, P> xv;
+    ld_soa<K, P>(x + e, stride, xv);
+    c_add<K, P>(xv, v, xv);
+    st_soa<K, P>(x + e, stride, xv);
+  }
+  if (nrm) {
+    const double re = v.v[0][0];
+    const double im = (P == 2) ? v.v[P - 1][0] : 0.0;
+    const double mod = __dsqrt_rn(__dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im)));
+    if (finite) {
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(mod);
+      atomicMax(reinterpret_cast<unsigned long long *>(nrm) + 1, bits);
+      if (k == d) atomicMax(reinterpret_cast<unsigned long long *>(nrm), bits);
+    }
+  }
+}
+
+}  // namespace mdk

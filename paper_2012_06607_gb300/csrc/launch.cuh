@@ -1,0 +1,118 @@
+// Templated launchers; explicitly instantiated once per limb count (inst_k*.cu).
+#pragma once
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace mdk {
+
+inline unsigned blocks_for(long long work, int threads) { return (unsigned)((work + threads - 1) / threads); }
+
+template <int K, int P>
+cudaError_t Impl<K, P>::elementwise(int op, long long count, const double *x, const double *y, double *z,
+                                    cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const int T = 128;
+  const unsigned B = blocks_for(count, T);
+  ProfScope prof(PK_ELEMENTWISE, s);
+  switch (op) {
+    case 0: elementwise_kernel<K, P, 0><<<B, T, 0, s>>>(count, x, y, z); break;
+    case 1: elementwise_kernel<K, P, 1><<<B, T, 0, s>>>(count, x, y, z); break;
+    case 2: elementwise_kernel<K, P, 2><<<B, T, 0, s>>>(count, x, y, z); break;
+    case 3: elementwise_kernel<K, P, 3><<<B, T, 0, s>>>(count, x, y, z); break;
+    case 4: elementwise_kernel<K, P, 4><<<B, T, 0, s>>>(count, x, y, z); break;
+    case 5: elementwise_kernel<K, P, 5><<<B, T, 0, s>>>(count, x, y, z); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <int K, int P>
+cudaError_t Impl<K, P>::series_conv(int d, long long count, const double *x, const double *y, double *z,
+                                    cudaStream_t s) {
+  const long long work = count * (d + 1);
+  if (work <= 0) return cudaSuccess;
+  const int T = 64;
+  ProfScope prof(PK_SERIES, s);
+  series_conv_kernel<K, P><<<blocks_for(work, T), T, 0, s>>>(d, count, x, y, z);
+  return cudaGetLastError();
+}
+
+template <int K, int P>
+cudaError_t Impl<K, P>::eval(const EvalDev &e, cudaStream_t s) {
+  const int n = e.n, d = e.d;
+  cudaError_t err;
+  const long long nx = (long long)n * (d + 1);
+  {
+    ProfScope prof(PK_POOL, s);
+    pool_load_x_kernel<K, P><<<blocks_for(nx, 128), 128, 0, s>>>(e.x, e.pool, n, d);
+  }
+  if (e.nscal > 0) {
+    ProfScope prof(PK_SCAL, s);
+    prep_scal_kernel<K, P><<<blocks_for(e.nscal, 64), 64, 0, s>>>(e.scal_src, e.nscal, e.coef, e.nmono, e.scal);
+  }
+  for (int st = 0; st < e.nstages; ++st) {
+    const int t0 = e.stage_off[st], t1 = e.stage_off[st + 1];
+    if (t1 > t0) {
+      ProfScope prof(PK_CONV, s);
+      conv_stage_kernel<K, P><<<blocks_for(t1 - t0, 64), 64, 0, s>>>(e.tasks + 8LL * t0, t1 - t0, e.pool, d);
+    }
+  }
+  const size_t Abytes = sizeof(double) * P * K * (size_t)(d + 1) * n * n;
+  if ((err = cudaMemsetAsync(e.A, 0, Abytes, s)) != cudaSuccess) return err;
+  const long long work = (long long)e.ngroups * (d + 1);
+  if (work > 0) {
+    ProfScope prof(PK_ACCUM, s);
+    accum_kernel<K, P><<<blocks_for(work, 128), 128, 0, s>>>(reinterpret_cast<const int4 *>(e.groups), e.ngroups,
+                                                             reinterpret_cast<const int4 *>(e.contrib), e.pool, e.scal,
+                                                             e.cst, e.f, e.A, n, d);
+  }
+  return cudaGetLastError();
+}
+
+template <int K, int P>
+cudaError_t Impl<K, P>::solve(const SolveDev &v, cudaStream_t s) {
+  const int n = v.n, d = v.d;
+  const long long nn = (long long)n * n;
+  {
+    ProfScope prof(PK_QR_HOUSE, s);
+    solve_init_kernel<K, P><<<blocks_for(nn, 128), 128, 0, s>>>(v.A, v.M, v.Y, n, d);
+  }
+  for (int j = 0; j < n; ++j) {
+    {
+      ProfScope prof(PK_QR_HOUSE, s);
+      house_kernel<K, P><<<1, 256, 0, s>>>(v.M, v.vd, v.beta, v.status, n, j);
+    }
+    ProfScope prof(PK_QR_APPLY, s);
+    const int ncols = (n - j - 1) + n;
+    house_apply_kernel<K, P><<<blocks_for((long long)ncols * 32, 128), 128, 0, s>>>(v.M, v.Y, v.vd, v.beta, n, j);
+  }
+  {
+    ProfScope prof(PK_RINV, s);
+    rinv_kernel<K, P><<<blocks_for(n, 64), 64, 0, s>>>(v.M, v.rinv, n);
+  }
+  for (int c = n - 1; c >= 0; --c) {
+    ProfScope prof(PK_BACKSUB, s);
+    backsub_kernel<K, P><<<blocks_for((long long)(c + 1) * n, 64), 64, 0, s>>>(v.M, v.Y, v.W, v.rinv, n, c);
+  }
+  for (int k = 0; k <= d; ++k) {
+    int C, nchunk;
+    rhs_chunking(n, k, C, nchunk);
+    if (nchunk > 0) {
+      ProfScope prof(PK_RHS_PARTIAL, s);
+      rhs_partial_kernel<K, P><<<blocks_for((long long)n * nchunk, 64), 64, 0, s>>>(v.A, v.dxw, v.part, n, d, k, C,
+                                                                                    nchunk);
+    }
+    {
+      ProfScope prof(PK_RHS_FINISH, s);
+      rhs_finish_kernel<K, P><<<n, 128, 0, s>>>(v.b, v.sgn, v.part, v.r, n, d, k, nchunk);
+    }
+    ProfScope prof(PK_WMV, s);
+    wmv_kernel<K, P><<<n, 128, 0, s>>>(v.W, v.r, v.dxw, n, k);
+  }
+  const long long nx = (long long)n * (d + 1);
+  ProfScope prof(PK_FINISH, s);
+  finish_dx_kernel<K, P><<<blocks_for(nx, 128), 128, 0, s>>>(v.dxw, v.dx_out, v.x, v.nrm, v.status, n, d);
+  return cudaGetLastError();
+}
+
+}  // namespace mdk

@@ -1,0 +1,434 @@
+// Multiple-double (md) arithmetic on the FP64 pipe, sm_103a.
+//
+// An md number is an unevaluated sum of K doubles (Section 2 of the paper,
+// K in {1,2,3,4,5,8,10}: double, double double, ..., deca double).  The
+// algorithms are fixed as follows (the paper cites QDlib and CAMPARY but does
+// not write them out):
+//   * error-free transformations: TwoSum, FastTwoSum, TwoProd with an fma;
+//   * K = 2 addition: AccurateDWPlusDW (Joldes, Muller, Popescu 2017);
+//   * K = 2 multiplication: TwoProd(x0,y0) plus the cross products, then
+//     FastTwoSum (Hida, Li, Bailey 2001);
+//   * K >= 3: terms of order 2^(-53 n) (level n) are summed by a TwoSum chain
+//     whose errors move to level n+1; level K is summed with plain additions;
+//     products x_i y_j use TwoProd when i+j <= K-1 and a plain product when
+//     i+j = K; the K+1 level sums are renormalised into K limbs by a
+//     bottom-up TwoSum sweep followed by a top-down sweep that skips zero
+//     errors;
+//   * division: long division with K+1 quotient limbs;
+//   * square root: hardware sqrt of the leading limb and ceil(log2 K)+1
+//     Heron steps s <- (s + a/s)/2.
+//
+// GB300 specifics.  The FP64 pipe issues one warp instruction per ~64 cycles
+// per SM sub-partition, so FP64 instruction count is the cost.  TwoSum is done
+// as "order the operands by magnitude (integer compare of the bit patterns,
+// integer selects), then FastTwoSum": 3 FP64 instructions instead of 6, with
+// the identical sum and exact error.  Zero tests use the integer pipe too.
+// Build with -fmad=false: every +,-,* is separately rounded and fmas appear
+// only where __fma_rn is written.
+#pragma once
+#include <cstdint>
+
+namespace mdk {
+
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
+
+__device__ __forceinline__ bool mag_ge(double a, double b) {
+  unsigned long long ia = (unsigned long long)__double_as_longlong(a) & 0x7fffffffffffffffULL;
+  unsigned long long ib = (unsigned long long)__double_as_longlong(b) & 0x7fffffffffffffffULL;
+  return ia >= ib;
+}
+
+__device__ __forceinline__ bool nonzero(double a) { return ((unsigned long long)__double_as_longlong(a) << 1) != 0ULL; }
+__device__ __forceinline__ bool negative(double a) { return __double_as_longlong(a) < 0 && nonzero(a); }
+
+// s = fl(a + b), e = (a + b) - s exactly.
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e) {
+  const bool ge = mag_ge(a, b);
+  const double hi = ge ? a : b;
+  const double lo = ge ? b : a;
+  const double ss = dadd(hi, lo);
+  e = dsub(lo, dsub(ss, hi));
+  s = ss;
+}
+
+__device__ __forceinline__ void fast_two_sum(double a, double b, double &s, double &e) {
+  const double ss = dadd(a, b);
+  e = dsub(b, dsub(ss, a));
+  s = ss;
+}
+
+__device__ __forceinline__ void two_prod(double a, double b, double &p, double &e) {
+  const double pp = dmul(a, b);
+  e = __fma_rn(a, b, -pp);
+  p = pp;
+}
+
+// M terms t (roughly by decreasing order) -> K non-overlapping limbs.
+template <int M, int K>
+__device__ __forceinline__ void renorm(const double (&t)[M], double (&z)[K]) {
+  double c[M];
+  double s = t[M - 1];
+#pragma unroll
+  for (int i = M - 2; i >= 0; --i) two_sum(t[i], s, s, c[i + 1]);
+  c[0] = s;
+#pragma unroll
+  for (int q = 0; q < K; ++q) z[q] = 0.0;
+  int j = 0;
+  double e = c[0];
+#pragma unroll
+  for (int i = 1; i < M; ++i) {
+    if (j < K - 1) {
+      double r, f;
+      two_sum(e, c[i], r, f);
+      const bool nz = nonzero(f);
+#pragma unroll
+      for (int q = 0; q < K - 1; ++q)
+        if (nz && q == j) z[q] = r;
+      e = nz ? f : r;
+      j += nz ? 1 : 0;
+    } else {
+      e = dadd(e, c[i]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < K; ++q)
+    if (q == j) z[q] = e;
+}
+
+template <int K>
+__device__ __forceinline__ void md_add(const double (&x)[K], const double (&y)[K], double (&z)[K]) {
+  if constexpr (K == 1) {
+    z[0] = dadd(x[0], y[0]);
+  } else if constexpr (K == 2) {
+    double sh, sl, th, tl, vh, vl;
+    two_sum(x[0], y[0], sh, sl);
+    two_sum(x[1], y[1], th, tl);
+    const double c = dadd(sl, th);
+    fast_two_sum(sh, c, vh, vl);
+    const double w = dadd(tl, vl);
+    fast_two_sum(vh, w, z[0], z[1]);
+  } else {
+    double lv[K + 1];
+    double carry[K], nc[K];
+    two_sum(x[0], y[0], lv[0], carry[0]);
+#pragma unroll
+    for (int n = 1; n < K; ++n) {
+      double s;
+      two_sum(x[n], y[n], s, nc[0]);
+#pragma unroll
+      for (int i = 0; i < n; ++i) two_sum(s, carry[i], s, nc[i + 1]);
+      lv[n] = s;
+#pragma unroll
+      for (int i = 0; i <= n; ++i) carry[i] = nc[i];
+    }
+    double s = carry[0];
+#pragma unroll
+    for (int i = 1; i < K; ++i) s = dadd(s, carry[i]);
+    lv[K] = s;
+    renorm<K + 1, K>(lv, z);
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void md_neg(const double (&x)[K], double (&z)[K]) {
+#pragma unroll
+  for (int i = 0; i < K; ++i) z[i] = -x[i];
+}
+
+template <int K>
+__device__ __forceinline__ void md_sub(const double (&x)[K], const double (&y)[K], double (&z)[K]) {
+  double ny[K];
+  md_neg<K>(y, ny);
+  md_add<K>(x, ny, z);
+}
+
+template <int K>
+__device__ __forceinline__ void md_mul(const double (&x)[K], const double (&y)[K], double (&z)[K]) {
+  if constexpr (K == 1) {
+    z[0] = dmul(x[0], y[0]);
+  } else if constexpr (K == 2) {
+    double p, e;
+    two_prod(x[0], y[0], p, e);
+    const double t1 = dmul(x[0], y[1]);
+    const double t2 = dmul(x[1], y[0]);
+    e = dadd(e, dadd(t1, t2));
+    fast_two_sum(p, e, z[0], z[1]);
+  } else {
+    constexpr int MC = K * (K - 1);
+    double lv[K + 1];
+    double carry[MC], nc[MC];
+    double low[K], nlow[K], hi[K];
+#pragma unroll
+    for (int n = 0; n < K; ++n) {
+#pragma unroll
+      for (int i = 0; i <= n; ++i) two_prod(x[i], y[n - i], hi[i], nlow[i]);
+      double s = hi[0];
+#pragma unroll
+      for (int i = 1; i <= n; ++i) two_sum(s, hi[i], s, nc[i - 1]);
+#pragma unroll
+      for (int i = 0; i < n; ++i) two_sum(s, low[i], s, nc[n + i]);
+#pragma unroll
+      for (int i = 0; i < (n - 1) * n; ++i) two_sum(s, carry[i], s, nc[2 * n + i]);
+      lv[n] = s;
+#pragma unroll
+      for (int i = 0; i < n * (n + 1); ++i) carry[i] = nc[i];
+#pragma unroll
+      for (int i = 0; i <= n; ++i) low[i] = nlow[i];
+    }
+    double s = dmul(x[1], y[K - 1]);
+#pragma unroll
+    for (int i = 2; i <= K - 1; ++i) s = dadd(s, dmul(x[i], y[K - i]));
+#pragma unroll
+    for (int i = 0; i < K; ++i) s = dadd(s, low[i]);
+#pragma unroll
+    for (int i = 0; i < MC; ++i) s = dadd(s, carry[i]);
+    lv[K] = s;
+    renorm<K + 1, K>(lv, z);
+  }
+}
+
+// md times double
+template <int K>
+__device__ __forceinline__ void md_mul_d(const double (&x)[K], double b, double (&z)[K]) {
+  if constexpr (K == 1) {
+    z[0] = dmul(x[0], b);
+  } else if constexpr (K == 2) {
+    double p, e;
+    two_prod(x[0], b, p, e);
+    e = dadd(e, dmul(x[1], b));
+    fast_two_sum(p, e, z[0], z[1]);
+  } else {
+    double lv[K + 1];
+    double carry[K], nc[K];
+    double lo_prev;
+    two_prod(x[0], b, lv[0], lo_prev);
+#pragma unroll
+    for (int n = 1; n < K; ++n) {
+      double h, l, s;
+      two_prod(x[n], b, h, l);
+      s = h;
+      two_sum(s, lo_prev, s, nc[0]);
+#pragma unroll
+      for (int i = 0; i < n - 1; ++i) two_sum(s, carry[i], s, nc[i + 1]);
+      lv[n] = s;
+#pragma unroll
+      for (int i = 0; i < n; ++i) carry[i] = nc[i];
+      lo_prev = l;
+    }
+    double s = lo_prev;
+#pragma unroll
+    for (int i = 0; i < K - 1; ++i) s = dadd(s, carry[i]);
+    lv[K] = s;
+    renorm<K + 1, K>(lv, z);
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void md_div(const double (&x)[K], const double (&y)[K], double (&z)[K]) {
+  if constexpr (K == 1) {
+    z[0] = ddiv(x[0], y[0]);
+  } else {
+    double q[K + 1], r[K], t[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) r[i] = x[i];
+#pragma unroll
+    for (int i = 0; i <= K; ++i) {
+      q[i] = ddiv(r[0], y[0]);
+      if (i < K) {
+        md_mul_d<K>(y, q[i], t);
+        md_sub<K>(r, t, r);
+      }
+    }
+    renorm<K + 1, K>(q, z);
+  }
+}
+
+template <int K>
+__host__ __device__ constexpr int sqrt_iters() {
+  int l = 0;
+  while ((1 << l) < K) ++l;
+  return l + 1;
+}
+
+template <int K>
+__device__ __forceinline__ void md_sqrt(const double (&a)[K], double (&z)[K]) {
+  if constexpr (K == 1) {
+    z[0] = __dsqrt_rn(a[0]);
+  } else {
+    if (!nonzero(a[0])) {
+#pragma unroll
+      for (int i = 0; i < K; ++i) z[i] = 0.0;
+      return;
+    }
+    double s[K], t[K];
+    s[0] = __dsqrt_rn(a[0]);
+#pragma unroll
+    for (int i = 1; i < K; ++i) s[i] = 0.0;
+#pragma unroll 1
+    constexpr int iters = sqrt_iters<K>();
+    for (int k = 0; k < iters; ++k) {
+      md_div<K>(a, s, t);
+      md_add<K>(s, t, s);
+#pragma unroll
+      for (int i = 0; i < K; ++i) s[i] = dmul(s[i], 0.5);
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) z[i] = s[i];
+  }
+}
+
+// ----------------------------------------------------------------- complex
+// P = 1: real, P = 2: complex (v[0] real part, v[1] imaginary part).
+template <int K, int P>
+struct mdv {
+  double v[P][K];
+};
+
+template <int K, int P>
+__device__ __forceinline__ void c_zero(mdv<K, P> &z) {
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+#pragma unroll
+    for (int l = 0; l < K; ++l) z.v[p][l] = 0.0;
+}
+
+template <int K, int P>
+__device__ __forceinline__ void c_add(const mdv<K, P> &a, const mdv<K, P> &b, mdv<K, P> &z) {
+#pragma unroll
+  for (int p = 0; p < P; ++p) md_add<K>(a.v[p], b.v[p], z.v[p]);
+}
+
+template <int K, int P>
+__device__ __forceinline__ void c_sub(const mdv<K, P> &a, const mdv<K, P> &b, mdv<K, P> &z) {
+#pragma unroll
+  for (int p = 0; p < P; ++p) md_sub<K>(a.v[p], b.v[p], z.v[p]);
+}
+
+template <int K, int P>
+__device__ __forceinline__ void c_mul(const mdv<K, P> &a, const mdv<K, P> &b, mdv<K, P> &z) {
+  if constexpr (P == 1) {
+    md_mul<K>(a.v[0], b.v[0], z.v[0]);
+  } else {
+    double ac[K], bd[K], ad[K], bc[K];
+    md_mul<K>(a.v[0], b.v[0], ac);
+    md_mul<K>(a.v[1], b.v[1], bd);
+    md_mul<K>(a.v[0], b.v[1], ad);
+    md_mul<K>(a.v[1], b.v[0], bc);
+    md_sub<K>(ac, bd, z.v[0]);
+    md_add<K>(ad, bc, z.v[1]);
+  }
+}
+
+template <int K, int P>
+__device__ __forceinline__ void c_mul_real(const mdv<K, P> &a, const double (&r)[K], mdv<K, P> &z) {
+#pragma unroll
+  for (int p = 0; p < P; ++p) md_mul<K>(a.v[p], r, z.v[p]);
+}
+
+template <int K, int P>
+__device__ __forceinline__ void c_mul_d(const mdv<K, P> &a, double b, mdv<K, P> &z) {
+#pragma unroll
+  for (int p = 0; p < P; ++p) md_mul_d<K>(a.v[p], b, z.v[p]);
+}
+
+template <int K, int P>
+__device__ __forceinline__ void c_conj(const mdv<K, P> &a, mdv<K, P> &z) {
+  z = a;
+  if constexpr (P == 2) md_neg<K>(a.v[1], z.v[1]);
+}
+
+template <int K, int P>
+__device__ __forceinline__ void c_abs2(const mdv<K, P> &a, double (&z)[K]) {
+  if constexpr (P == 1) {
+    md_mul<K>(a.v[0], a.v[0], z);
+  } else {
+    double t1[K], t2[K];
+    md_mul<K>(a.v[0], a.v[0], t1);
+    md_mul<K>(a.v[1], a.v[1], t2);
+    md_add<K>(t1, t2, z);
+  }
+}
+
+template <int K, int P>
+__device__ __forceinline__ void c_div(const mdv<K, P> &a, const mdv<K, P> &b, mdv<K, P> &z) {
+  if constexpr (P == 1) {
+    md_div<K>(a.v[0], b.v[0], z.v[0]);
+  } else {
+    double cc[K], dd[K], den[K], t1[K], t2[K], nr[K], ni[K];
+    md_mul<K>(b.v[0], b.v[0], cc);
+    md_mul<K>(b.v[1], b.v[1], dd);
+    md_add<K>(cc, dd, den);
+    md_mul<K>(a.v[0], b.v[0], t1);
+    md_mul<K>(a.v[1], b.v[1], t2);
+    md_add<K>(t1, t2, nr);
+    md_mul<K>(a.v[1], b.v[0], t1);
+    md_mul<K>(a.v[0], b.v[1], t2);
+    md_sub<K>(t1, t2, ni);
+    md_div<K>(nr, den, z.v[0]);
+    md_div<K>(ni, den, z.v[1]);
+  }
+}
+
+// ------------------------------------------------------ loads and stores
+// AoS value: P*K consecutive doubles, plane-major ([p][l]).
+template <int K, int P>
+__device__ __forceinline__ void ld_aos(const double *__restrict__ src, mdv<K, P> &z) {
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+#pragma unroll
+    for (int l = 0; l < K; ++l) z.v[p][l] = src[p * K + l];
+}
+
+template <int K, int P>
+__device__ __forceinline__ void ld_aos_nc(const double *src, mdv<K, P> &z) {
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+#pragma unroll
+    for (int l = 0; l < K; ++l) z.v[p][l] = __ldg(src + p * K + l);
+}
+
+template <int K, int P>
+__device__ __forceinline__ void st_aos(double *dst, const mdv<K, P> &z) {
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+#pragma unroll
+    for (int l = 0; l < K; ++l) dst[p * K + l] = z.v[p][l];
+}
+
+// SoA value: limb l of plane p at src[(p*K + l) * plane_stride].
+template <int K, int P>
+__device__ __forceinline__ void ld_soa(const double *src, long long stride, mdv<K, P> &z) {
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+#pragma unroll
+    for (int l = 0; l < K; ++l) z.v[p][l] = src[(long long)(p * K + l) * stride];
+}
+
+template <int K, int P>
+__device__ __forceinline__ void st_soa(double *dst, long long stride, const mdv<K, P> &z) {
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+#pragma unroll
+    for (int l = 0; l < K; ++l) dst[(long long)(p * K + l) * stride] = z.v[p][l];
+}
+
+template <int K, int P>
+__device__ __forceinline__ void shfl_xor(mdv<K, P> &z, int lanemask, mdv<K, P> &out) {
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+#pragma unroll
+    for (int l = 0; l < K; ++l) out.v[p][l] = __shfl_xor_sync(0xffffffffu, z.v[p][l], lanemask);
+}
+
+template <int K, int P>
+__device__ __forceinline__ void shfl_idx(mdv<K, P> &z, int src, mdv<K, P> &out) {
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+#pragma unroll
+    for (int l = 0; l < K; ++l) out.v[p][l] = __shfl_sync(0xffffffffu, z.v[p][l], src);
+}
+
+}  // namespace mdk

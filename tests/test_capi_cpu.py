@@ -1,0 +1,137 @@
+"""Host-side checks of the C ABI (no GPU needed).
+
+* the library builds for sm_103a, loads, and exports every entry point that
+  include/mdnewton.h declares;
+* argument validation happens on the host before any CUDA call;
+* workspace sizes follow the system structure.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import mdgen
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", fn)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        for m in re.finditer(r"\b(md_[a-z0-9_]+)\s*\(", txt):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def mdlib():
+    from paper_2012_06607_gb300 import build
+
+    build.build()
+    import paper_2012_06607_gb300 as md
+
+    return md.lib()
+
+
+def test_exports_every_declared_symbol(mdlib):
+    names = declared_symbols()
+    assert len(names) >= 9
+    for name in names:
+        assert hasattr(mdlib, name), name
+    import paper_2012_06607_gb300 as md
+
+    assert set(md.exported_symbols()) <= set(names)
+
+
+def test_version_and_strings(mdlib):
+    assert mdlib.md_version() >= 100
+    assert mdlib.md_status_string(4) == b"A_0 is singular"
+    assert mdlib.md_status_string(99) == b"unknown status"
+
+
+def _csys(s, coef_ptr=1, cst_ptr=1):
+    import paper_2012_06607_gb300 as md
+
+    pp = np.ascontiguousarray(s.poly_ptr, np.int32)
+    nv = np.ascontiguousarray(s.nvar, np.int32)
+    ix = np.ascontiguousarray(s.idx, np.int32)
+    ex = np.ascontiguousarray(s.expo, np.int32)
+    c = md.md_system(s.limbs, int(s.is_complex), s.n, s.degree, s.nmono, pp.ctypes.data, nv.ctypes.data,
+                     ix.ctypes.data, ex.ctypes.data, coef_ptr, cst_ptr)
+    return c, (pp, nv, ix, ex)
+
+
+def test_workspace_bytes(mdlib):
+    s0 = mdgen.config_system(0, 1)
+    c, keep = _csys(s0)
+    b0 = mdlib.md_workspace_bytes(ctypes.byref(c), 0)
+    assert b0 > 0 and b0 % 256 == 0
+    s1 = mdgen.circle_system(2, 8)
+    c1, keep1 = _csys(s1)
+    b1 = mdlib.md_workspace_bytes(ctypes.byref(c1), 0)
+    assert 0 < b1
+    # more limbs need more space
+    s4 = s0.with_limbs(4)
+    c4, keep4 = _csys(s4)
+    assert mdlib.md_workspace_bytes(ctypes.byref(c4), 0) > b0
+    assert mdlib.md_linsolve_workspace_bytes(4, 1, 64, 64, 0) > mdlib.md_linsolve_workspace_bytes(4, 1, 8, 8, 0) > 0
+    assert mdlib.md_linsolve_workspace_bytes(6, 1, 8, 8, 0) == 0  # 6 limbs are not a supported precision
+
+
+def test_invalid_systems_rejected(mdlib):
+    s = mdgen.config_system(0, 1)
+    bad_limbs = mdgen.config_system(0, 1)
+    bad_limbs.limbs = 7
+    c, keep = _csys(bad_limbs)
+    assert mdlib.md_workspace_bytes(ctypes.byref(c), 0) == 0
+    # variable index out of range
+    s2 = mdgen.config_system(0, 1)
+    s2.idx = s2.idx.copy()
+    s2.idx[0] = s2.n + 1
+    c2, keep2 = _csys(s2)
+    assert mdlib.md_workspace_bytes(ctypes.byref(c2), 0) == 0
+    # repeated variable in one monomial
+    s3 = mdgen.config_system(0, 1)
+    s3.nvar = s3.nvar.copy()
+    s3.idx = s3.idx.copy()
+    m = 0
+    s3.nvar[m] = 2
+    s3.idx[m * 4 + 1] = s3.idx[m * 4]
+    s3.expo = s3.expo.copy()
+    s3.expo[m * 4 + 1] = 1
+    c3, keep3 = _csys(s3)
+    assert mdlib.md_workspace_bytes(ctypes.byref(c3), 0) == 0
+    # CSR offsets inconsistent with nmono
+    s5 = mdgen.config_system(0, 1)
+    s5.poly_ptr = s5.poly_ptr.copy()
+    s5.poly_ptr[-1] += 1
+    c5, keep5 = _csys(s5)
+    assert mdlib.md_workspace_bytes(ctypes.byref(c5), 0) == 0
+    # a valid one for comparison
+    c0, keep0 = _csys(s)
+    assert mdlib.md_workspace_bytes(ctypes.byref(c0), 0) > 0
+
+
+def test_argument_errors_before_cuda(mdlib):
+    """Errors detected on the host return without touching the device."""
+    assert mdlib.md_elementwise(0, 6, 0, 10, 1, 1, 1, None) == 1  # 6 limbs
+    assert mdlib.md_elementwise(9, 2, 0, 10, 1, 1, 1, None) == 1  # unknown op
+    assert mdlib.md_elementwise(4, 2, 1, 10, 1, 1, 1, None) == 1  # complex sqrt
+    assert mdlib.md_elementwise(0, 2, 0, 10, None, 1, 1, None) == 1
+    assert mdlib.md_series_conv(2, 1, -1, 3, 1, 1, 1, None) == 1
+    assert mdlib.md_linsolve_series(2, 1, 0, 4, 1, 1, 1, 256, 1 << 20, 0, None) == 1
+    assert mdlib.md_linsolve_series(2, 1, 4, 4, 1, 1, 1, None, 1 << 20, 0, None) == 2
+    assert mdlib.md_linsolve_series(2, 1, 4, 4, 1, 1, 1, 257, 1 << 20, 0, None) == 2  # misaligned
+    assert mdlib.md_linsolve_series(2, 1, 4, 4, 1, 1, 1, 256, 16, 0, None) == 2  # too small
+    s = mdgen.config_system(0, 1)
+    c, keep = _csys(s)
+    assert mdlib.md_newton_series_step(ctypes.byref(c), 1, None, None, 1 << 20, 0, None) == 2
+    assert mdlib.md_newton_series_step(ctypes.byref(c), 1, None, 256, 64, 0, None) == 2
+    assert mdlib.md_eval_diff(ctypes.byref(c), None, 1, 1, 256, 1 << 30, None) == 1
+    assert mdlib.md_get_device_status(None, None) == 2
