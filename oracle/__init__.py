@@ -98,9 +98,9 @@ class Oracle:
         self.lib.orc_count_reset()
 
     def counts(self) -> dict:
-        out = np.zeros(9, dtype=np.int64)
+        out = np.zeros(10, dtype=np.int64)
         self.lib.orc_count_get(_p(out))
-        keys = ["add", "sub", "mul", "div", "fma", "sqrt", "twoprod", "series_mul", "series_add"]
+        keys = ["add", "sub", "mul", "div", "fma", "sqrt", "twoprod", "series_mul", "series_add", "twosum"]
         return dict(zip(keys, [int(v) for v in out]))
 
     # -- elementwise ----------------------------------------------------

@@ -56,8 +56,8 @@
 
 /* ------------------------------------------------------------------ counts */
 #ifdef ORACLE_COUNT
-/* add, sub, mul, div, fma, sqrt, twoprod calls, series-level md mul, series-level md add */
-long long orc_cnt[9];
+/* add, sub, mul, div, fma, sqrt, twoprod calls, series-level md mul, series-level md add, twosum calls */
+long long orc_cnt[10];
 static double oADD(double a, double b) { orc_cnt[0]++; return a + b; }
 static double oSUB(double a, double b) { orc_cnt[1]++; return a - b; }
 static double oMUL(double a, double b) { orc_cnt[2]++; return a * b; }
@@ -67,8 +67,9 @@ static double oSQRT(double a) { orc_cnt[5]++; return sqrt(a); }
 #define CNT_TWOPROD() (orc_cnt[6]++)
 #define CNT_SMUL() (orc_cnt[7]++)
 #define CNT_SADD() (orc_cnt[8]++)
+#define CNT_TWOSUM() (orc_cnt[9]++)
 #else
-long long orc_cnt[9];
+long long orc_cnt[10];
 #define oADD(a, b) ((a) + (b))
 #define oSUB(a, b) ((a) - (b))
 #define oMUL(a, b) ((a) * (b))
@@ -78,6 +79,7 @@ long long orc_cnt[9];
 #define CNT_TWOPROD() ((void)0)
 #define CNT_SMUL() ((void)0)
 #define CNT_SADD() ((void)0)
+#define CNT_TWOSUM() ((void)0)
 #endif
 
 void orc_count_reset(void) { memset(orc_cnt, 0, sizeof(orc_cnt)); }
@@ -92,6 +94,7 @@ int orc_is_counting(void) {
 
 /* --------------------------------------------- error-free transformations */
 static void two_sum(double a, double b, double *s, double *e) {
+  CNT_TWOSUM();
   double ss = oADD(a, b);
   double t = oSUB(ss, a);
   *e = oADD(oSUB(a, oSUB(ss, t)), oSUB(b, t));
