@@ -278,13 +278,15 @@ def run_product(args):
     paper_add = 2 * t1[0] if P == 2 else t1[0]
     conv_paper = nconv * ((d + 1) * (d + 2) // 2 * paper_mul + d * (d + 1) // 2 * paper_add)
     conv_ms, conv_launches = prof.get("conv_stage", (float("nan"), 0))
-    achieved = conv_instr / (conv_ms / 1e3) if conv_ms > 0 else None
+    # the timed region ran args.steps steps: conv_ms and conv_launches cover all of them
+    achieved = args.steps * conv_instr / (conv_ms / 1e3) if conv_ms > 0 else None
     roofline = {"bound": "alu", "kernel": "conv_stage", "achieved": achieved / 1e12 if achieved else None,
                 "peak": FP64_PEAK_INSTR / 1e12, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_INSTR if achieved else None,
                 "traffic": None, "counted": "FP64 instructions of the md algorithms (an fma counts once)",
                 "launches_in_timed_region": conv_launches, "avg_launch_ms": conv_ms / max(conv_launches, 1),
                 "dominant_by_time": dom_name,
-                "paper_ops_per_s": conv_paper / (conv_ms / 1e3) if conv_ms > 0 else None}
+                "paper_ops_per_s": args.steps * conv_paper / (conv_ms / 1e3) if conv_ms > 0 else None,
+                "algorithmic_fp64_per_step": conv_instr}
     line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

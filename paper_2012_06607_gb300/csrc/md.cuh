@@ -20,7 +20,7 @@
 //
 // GB300 specifics.  The FP64 pipe issues one warp instruction per ~64 cycles
 // per SM sub-partition, so FP64 instruction count is the cost.  TwoSum is done
-// as "order the operands by magnitude (integer compare of the bit patterns,
+// as "order the operands by exponent (32-bit integer compare of the high words,
 // integer selects), then FastTwoSum": 3 FP64 instructions instead of 6, with
 // the identical sum and exact error.  Zero tests use the integer pipe too.
 // Build with -fmad=false: every +,-,* is separately rounded and fmas appear
@@ -35,18 +35,22 @@ __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a,
 __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
 
-__device__ __forceinline__ bool mag_ge(double a, double b) {
-  unsigned long long ia = (unsigned long long)__double_as_longlong(a) & 0x7fffffffffffffffULL;
-  unsigned long long ib = (unsigned long long)__double_as_longlong(b) & 0x7fffffffffffffffULL;
-  return ia >= ib;
+// Exponent order for FastTwoSum (Dekker needs exponent(hi) >= exponent(lo)):
+// compare the high words with the sign cleared.  32-bit integer ops only, so
+// that nothing lands on the FP64 pipe.
+__device__ __forceinline__ bool exp_ge(double a, double b) {
+  const unsigned ha = (unsigned)__double2hiint(a) & 0x7fffffffu;
+  const unsigned hb = (unsigned)__double2hiint(b) & 0x7fffffffu;
+  return ha >= hb;
 }
 
-__device__ __forceinline__ bool nonzero(double a) { return ((unsigned long long)__double_as_longlong(a) << 1) != 0ULL; }
-__device__ __forceinline__ bool negative(double a) { return __double_as_longlong(a) < 0 && nonzero(a); }
+__device__ __forceinline__ bool nonzero(double a) {
+  return (((unsigned)__double2hiint(a) & 0x7fffffffu) | (unsigned)__double2loint(a)) != 0u;
+}
 
 // s = fl(a + b), e = (a + b) - s exactly.
 __device__ __forceinline__ void two_sum(double a, double b, double &s, double &e) {
-  const bool ge = mag_ge(a, b);
+  const bool ge = exp_ge(a, b);
   const double hi = ge ? a : b;
   const double lo = ge ? b : a;
   const double ss = dadd(hi, lo);
