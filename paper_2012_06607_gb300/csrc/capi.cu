@@ -300,35 +300,35 @@ md_status prepare(const md_system *s, void *ws, size_t ws_bytes, cudaStream_t st
   md_status st = check_system(s);
   if (st != MD_OK) return st;
   const uint64_t cs = structure_checksum(s);
+  std::lock_guard<std::mutex> lk(g_mu);
   PlanEntry *pe = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_mu);
-    auto it = g_plans.find(cs);
-    if (it != g_plans.end()) {
-      pe = it->second;
-    } else {
-      std::unique_ptr<PlanEntry> e(new PlanEntry);
-      st = build_plan(s, e->plan);
-      if (st != MD_OK) return st;
-      const Plan &p = e->plan;
-      e->image_bytes = p.off_f - p.off_tasks;
-      void *h = nullptr;
-      if (cudaHostAlloc(&h, e->image_bytes, cudaHostAllocDefault) != cudaSuccess) return MD_ERR_CUDA;
-      e->pinned = static_cast<int *>(h);
-      std::memset(h, 0, e->image_bytes);
-      auto put = [&](size_t off, const std::vector<int> &v) {
-        if (!v.empty()) std::memcpy(static_cast<char *>(h) + (off - p.off_tasks), v.data(), sizeof(int) * v.size());
-      };
-      put(p.off_tasks, p.tasks);
-      put(p.off_scalsrc, p.scal_src);
-      put(p.off_groups, p.groups);
-      put(p.off_contrib, p.contrib);
-      pe = e.release();
-      g_plans[cs] = pe;
-    }
+  auto it = g_plans.find(cs);
+  if (it != g_plans.end()) {
+    pe = it->second;
+  } else {
+    std::unique_ptr<PlanEntry> e(new PlanEntry);
+    st = build_plan(s, e->plan);
+    if (st != MD_OK) return st;
+    pe = e.release();
+    g_plans[cs] = pe;
   }
   const Plan &p = pe->plan;
   if (p.total > ws_bytes) return MD_ERR_WORKSPACE;
+  if (!pe->pinned) {  // pinned image of the integer tables, created at the first upload
+    const size_t bytes = p.off_f - p.off_tasks;
+    void *h = nullptr;
+    if (cudaHostAlloc(&h, bytes, cudaHostAllocDefault) != cudaSuccess) return MD_ERR_CUDA;
+    std::memset(h, 0, bytes);
+    auto put = [&](size_t off, const std::vector<int> &v) {
+      if (!v.empty()) std::memcpy(static_cast<char *>(h) + (off - p.off_tasks), v.data(), sizeof(int) * v.size());
+    };
+    put(p.off_tasks, p.tasks);
+    put(p.off_scalsrc, p.scal_src);
+    put(p.off_groups, p.groups);
+    put(p.off_contrib, p.contrib);
+    pe->image_bytes = bytes;
+    pe->pinned = static_cast<int *>(h);
+  }
   if (cudaMemcpyAsync(static_cast<char *>(ws) + p.off_tasks, pe->pinned, pe->image_bytes, cudaMemcpyHostToDevice,
                       stream) != cudaSuccess)
     return MD_ERR_CUDA;
