@@ -168,6 +168,34 @@ md_status md_newton_series_step(const md_system *sys, double *x, double *dx_norm
 md_status md_get_device_status(void *ws, void *stream);
 
 /*
+ * Allocation-free block Toeplitz solve.  The paper has no counterpart: this is
+ * an interface for callers that cannot allocate device memory for a workspace
+ * -- applications whose device memory belongs to another allocator or is
+ * reserved up to the limit, latency-critical code where cudaMalloc/cudaFree
+ * would synchronise the device, plug-in or callback contexts that forbid
+ * allocation.
+ *
+ * Same computation, arguments and layouts as md_linsolve_series, without `ws`:
+ * the scratch space is a static device array of MD_STATIC_WS_BYTES (16 MiB)
+ * inside the library, which every GPU that loads the library holds until the
+ * process exits.  Requests whose md_linsolve_workspace_bytes() exceeds it are
+ * rejected with MD_ERR_WORKSPACE before any device work (16 MiB holds, e.g.,
+ * n = 64, d = 64 in quad double complex).  The call allocates nothing.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture on the device.
+ *   - Every call on a device shares the one array and it keeps the last call's
+ *     contents; calls whose work may overlap on the GPU (different streams,
+ *     host threads) race on it and must be serialised by the caller.
+ *   - The device status word lives in that array too, so device-detected
+ *     conditions (singular A_0) are not readable through
+ *     md_get_device_status; a singular A_0 shows as non-finite entries of dx.
+ */
+#define MD_STATIC_WS_BYTES (16u << 20)
+md_status md_linsolve_series_static(int limbs, int is_complex, int n, int degree, const double *A, const double *b,
+                                    double *dx, int flags, void *stream);
+
+/*
  * Optional timing of the library's own kernels (tracing support; not part of
  * the computation).  While enabled, every kernel launch of every call in this
  * process is bracketed by two CUDA events on its stream.

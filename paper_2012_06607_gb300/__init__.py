@@ -60,6 +60,8 @@ def lib():
         L.md_linsolve_series.argtypes = [i, i, i, i, vp, vp, vp, vp, sz, i, vp]
         L.md_newton_series_step.argtypes = [ctypes.POINTER(md_system), vp, vp, vp, sz, i, vp]
         L.md_get_device_status.argtypes = [vp, vp]
+        L.md_linsolve_series_static.argtypes = [i, i, i, i, vp, vp, vp, i, vp]
+        L.md_linsolve_series_static.restype = i
         L.md_profile_enable.argtypes = [i]
         L.md_profile_enable.restype = None
         L.md_profile_read.argtypes = [vp, vp, i]
@@ -76,7 +78,8 @@ def lib():
 def exported_symbols():
     return ["md_version", "md_status_string", "md_workspace_bytes", "md_linsolve_workspace_bytes",
             "md_elementwise", "md_series_conv", "md_eval_diff", "md_linsolve_series",
-            "md_newton_series_step", "md_get_device_status", "md_profile_enable", "md_profile_read",
+            "md_newton_series_step", "md_get_device_status", "md_linsolve_series_static", "md_profile_enable",
+            "md_profile_read",
             "md_profile_kind_name"]
 
 

@@ -34,6 +34,7 @@ def nvcc() -> str:
 def sources():
     srcs = [os.path.join(CSRC, f"inst_k{k}_p{p}.cu") for k in LIMBS for p in (1, 2)]
     srcs.append(os.path.join(CSRC, "capi.cu"))
+    srcs.append(os.path.join(CSRC, "noalloc.cu"))
     return srcs
 
 
