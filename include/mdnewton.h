@@ -152,9 +152,10 @@ md_status md_linsolve_series(int limbs, int is_complex, int n, int degree, const
  * One Newton step on truncated power series (Section 4): x <- x + dx where
  * A(t) dx(t) = -f(x(t)).
  *   x:       DEVICE [P][K][n][d+1], updated in place
- *   dx_norm: DEVICE double[2] or NULL: [0] = max_i |dx_{d,i}| (modulus of the
- *            update to the last coefficient, Section 6), [1] = max over all
- *            coefficients; both from the leading limbs.
+ *   dx_norm: DEVICE double[2] or NULL: [0] = max_i |dx_{d,i}| (the size of
+ *            the update of the degree-d coefficient, the convergence measure
+ *            of Section 6), [1] = max over all coefficients; both from the
+ *            leading limbs.
  *   ws:      DEVICE workspace of md_workspace_bytes(sys, flags) bytes.
  */
 md_status md_newton_series_step(const md_system *sys, double *x, double *dx_norm, void *ws, size_t ws_bytes,

@@ -24,7 +24,7 @@
  *                     evaluation, one job per right-hand side update; jobs
  *                     never change a summation order, so the threaded run is
  *                     bit-identical to the serial one.
- *   Sec. 6            ||dx|| = modulus of the update to the last coefficient.
+ *   Sec. 6            ||dx||: size of the update of the highest-degree coefficient.
  *
  * The md algorithms are not written out in the paper (it uses QDlib and
  * CAMPARY-generated code); the readings taken here are:
@@ -923,7 +923,7 @@ int orc_linsolve(int K, int cplx, int n, int d, const double *A, const double *b
 /* ------------------------------------------------------ one Newton step */
 /*
  * x <- x + dx with A(t) dx(t) = -f(x(t)) (Sec. 4).  dxnorm[0] = max_i |dx_{d,i}|
- * (modulus of the update to the last coefficient, Sec. 6, from the leading
+ * (size of the update of the highest-degree coefficient, Sec. 6, from the leading
  * limbs), dxnorm[1] = max over all coefficients of |dx_{k,i}|.
  */
 int orc_newton_step(int K, int cplx, int n, int d, int nmono, const int *poly_ptr, const int *nvar, const int *idx,
