@@ -84,6 +84,18 @@ typedef struct md_system {
 
 /* flags */
 #define MD_FLAG_PLAIN 0x0 /* plain multiple-double kernels for every step        */
+/*
+ * Split-product form of the block Toeplitz update r_k = b_k - sum_j A_{k-j} dx_j:
+ * every md number of a row of A_i (and of dx_j) is cut into signed 8-bit integer
+ * slices relative to a shared power of two; all slice products are exact BF16
+ * tensor-core products with exact fp32 accumulation (K <= 1024 per product), and
+ * the terms of r_k are added exactly in a fixed-point integer before one
+ * conversion to K limbs.  Error: 2^(12 - 8S) of the largest term (S slices per
+ * number, 8S >= 53K + 24 bits).  The QR of A_0, the Householder norms and
+ * dx_k = (R^-1 Q^H) r_k stay in multiple-double arithmetic.  Needs the larger
+ * workspace reported for this flag.
+ */
+#define MD_FLAG_OZAKI 0x1
 
 /* Version of this ABI (major*100 + minor). */
 int md_version(void);

@@ -443,3 +443,40 @@ def random_md_array(rng: np.random.Generator, K: int, count: int, *, spread: flo
             v += Fraction(float(rng.uniform(-1.0, 1.0) * scale)) / (1 << (53 * j))
         out[:, c] = md_from_fraction(v, K)
     return out
+
+
+# ----------------------------------------------------------------------------
+# linearized solve with an ill-conditioned A_0 (split-product comparison)
+
+
+def solve_config3(seed: int = 1, n: int = 256, d: int = 16, K: int = 4, cond: float = 1e8):
+    """Quad double, real, n = 256, d = 16 block Toeplitz system.
+
+    A_0 = U diag(sigma) V^T with seeded orthogonal U, V (QR of Gaussian matrices,
+    in double) and sigma log-spaced on [1/cond, 1]; its double entries are the
+    leading limbs (lower limbs zero).  A_1..A_d and b have N(0,1) leading limbs;
+    each lower limb is uniform within half an ulp of the limb above it.
+    Returns (A [1][K][d+1][n][n] column-major blocks, b [1][K][n][d+1]).
+    """
+    rng = np.random.default_rng([seed, 3])
+    U, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    sig = np.logspace(0.0, -np.log10(cond), n)
+    A0 = (U * sig) @ V.T
+    A = np.zeros((1, K, d + 1, n, n))
+    A[0, 0, 0] = A0.T  # column-major: [col][row]
+    def lifted(shape):
+        # leading limb N(0,1); limb l uniform in (-ulp/2, ulp/2) of limb l-1, so the
+        # expansion is non-overlapping by construction (about 2^-53 per limb)
+        out = np.zeros((K,) + shape)
+        out[0] = rng.standard_normal(shape)
+        for l in range(1, K):
+            _, e = np.frexp(out[l - 1])
+            out[l] = rng.uniform(-0.5, 0.5, size=shape) * np.ldexp(1.0, e - 53)
+            out[l][out[l - 1] == 0.0] = 0.0
+        return out
+
+    A[0, :, 1:] = lifted((d, n, n))
+    b = np.zeros((1, K, n, d + 1))
+    b[0] = lifted((n, d + 1))
+    return A, b

@@ -63,10 +63,16 @@ cudaError_t dispatch(int K, int P, int what, const void *a, cudaStream_t s, int 
 // ---------------------------------------------------------- solve layout
 struct SolveLayout {
   size_t off_M, off_Y, off_W, off_vd, off_beta, off_rinv, off_r, off_dxw, off_part, bytes;
+  size_t off_As = 0, off_Xs = 0, off_eA = 0, off_ex = 0, off_C = 0;
   int maxchunk;
+  int ozaki = 0;
 };
 
-SolveLayout solve_layout(int K, int P, int n, int d, size_t base) {
+// slices and accumulator sizes of the split-product form (must match ozaki.cuh)
+int oz_slices_host(int K) { return (((53 * K + 24 + 7) / 8) + 15) / 16 * 16; }
+int oz_kpad_host(int n) { return (n + 15) / 16 * 16; }
+
+SolveLayout solve_layout(int K, int P, int n, int d, size_t base, int flags = 0) {
   SolveLayout L;
   const size_t VS = sizeof(double) * P * K;
   const size_t nn = (size_t)n * n;
@@ -87,6 +93,15 @@ SolveLayout solve_layout(int K, int P, int n, int d, size_t base) {
   L.off_r = o; o = align256(o + (size_t)(d + 1) * n * VS);
   L.off_dxw = o; o = align256(o + (size_t)(d + 1) * n * VS);
   L.off_part = o; o = align256(o + (size_t)n * maxchunk * VS);
+  if (flags & MD_FLAG_OZAKI) {
+    const size_t S = oz_slices_host(K), kp = oz_kpad_host(n), M = (size_t)n * P * S, N = (size_t)P * S;
+    L.ozaki = 1;
+    L.off_As = o; o = align256(o + (size_t)(d + 1) * M * kp * 2);
+    L.off_Xs = o; o = align256(o + (size_t)(d + 1) * N * kp * 2);
+    L.off_eA = o; o = align256(o + sizeof(int) * (size_t)(d + 1) * n);
+    L.off_ex = o; o = align256(o + sizeof(int) * (size_t)(d + 1));
+    L.off_C = o; o = align256(o + sizeof(float) * (size_t)std::max(d, 1) * M * N);
+  }
   L.bytes = o - base;
   return L;
 }
@@ -148,7 +163,7 @@ md_status check_system(const md_system *s) {
 // Builds the product schedule of every monomial in the order of the
 // definition (common factor, Speelpenning forward / backward / cross products,
 // F*P and F*partials), the stage of each product and the accumulation lists.
-md_status build_plan(const md_system *s, Plan &p) {
+md_status build_plan(const md_system *s, Plan &p, int flags = 0) {
   md_status st = check_system(s);
   if (st != MD_OK) return st;
   const int n = s->n, d = s->degree;
@@ -276,7 +291,7 @@ md_status build_plan(const md_system *s, Plan &p) {
   p.off_f = o; o = align256(o + (size_t)n * (d + 1) * VS);
   p.off_A = o; o = align256(o + (size_t)(d + 1) * n * n * VS);
   p.off_solve = o;
-  p.sl = solve_layout(p.K, p.P, n, d, o);
+  p.sl = solve_layout(p.K, p.P, n, d, o, flags);
   p.total = o + p.sl.bytes;
   p.checksum = structure_checksum(s);
   return MD_OK;
@@ -295,11 +310,11 @@ struct PlanEntry {
 std::mutex g_mu;
 std::map<uint64_t, PlanEntry *> g_plans;
 
-md_status prepare(const md_system *s, void *ws, size_t ws_bytes, cudaStream_t stream, Plan *&out) {
+md_status prepare(const md_system *s, void *ws, size_t ws_bytes, cudaStream_t stream, Plan *&out, int flags = 0) {
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return MD_ERR_WORKSPACE;
   md_status st = check_system(s);
   if (st != MD_OK) return st;
-  const uint64_t cs = structure_checksum(s);
+  const uint64_t cs = structure_checksum(s) ^ (0x9e3779b97f4a7c15ULL * (uint64_t)(flags & MD_FLAG_OZAKI));
   std::lock_guard<std::mutex> lk(g_mu);
   PlanEntry *pe = nullptr;
   auto it = g_plans.find(cs);
@@ -307,7 +322,7 @@ md_status prepare(const md_system *s, void *ws, size_t ws_bytes, cudaStream_t st
     pe = it->second;
   } else {
     std::unique_ptr<PlanEntry> e(new PlanEntry);
-    st = build_plan(s, e->plan);
+    st = build_plan(s, e->plan, flags);
     if (st != MD_OK) return st;
     pe = e.release();
     g_plans[cs] = pe;
@@ -374,6 +389,14 @@ SolveDev make_solve(const SolveLayout &L, int n, int d, char *base) {
   v.part = reinterpret_cast<double *>(base + L.off_part);
   v.status = reinterpret_cast<int *>(base);
   v.maxchunk = L.maxchunk;
+  if (L.ozaki) {
+    v.ozaki = 1;
+    v.oz_As = base + L.off_As;
+    v.oz_Xs = base + L.off_Xs;
+    v.oz_eA = reinterpret_cast<int *>(base + L.off_eA);
+    v.oz_ex = reinterpret_cast<int *>(base + L.off_ex);
+    v.oz_C = reinterpret_cast<float *>(base + L.off_C);
+  }
   return v;
 }
 
@@ -423,7 +446,7 @@ void prof_end(int id, cudaStream_t s) {
 namespace {
 const char *kProfNames[mdk::PK_COUNT] = {"pool_load_x", "prep_scal", "conv_stage", "accum", "qr_house", "qr_apply",
                                          "rinv", "backsub", "rhs_partial", "rhs_finish", "wmv", "finish_dx",
-                                         "elementwise", "series_conv"};
+                                         "elementwise", "series_conv", "oz_split", "oz_gemm", "oz_accum"};
 
 }  // namespace
 
@@ -447,16 +470,14 @@ const char *md_status_string(md_status st) {
 }
 
 size_t md_workspace_bytes(const md_system *sys, int flags) {
-  (void)flags;
   Plan p;
-  if (build_plan(sys, p) != MD_OK) return 0;
+  if (build_plan(sys, p, flags) != MD_OK) return 0;
   return p.total;
 }
 
 size_t md_linsolve_workspace_bytes(int limbs, int is_complex, int n, int degree, int flags) {
-  (void)flags;
   if (!valid_limbs(limbs) || n < 1 || degree < 0) return 0;
-  return 256 + solve_layout(limbs, is_complex ? 2 : 1, n, degree, 256).bytes;
+  return 256 + solve_layout(limbs, is_complex ? 2 : 1, n, degree, 256, flags).bytes;
 }
 
 md_status md_elementwise(int op, int limbs, int is_complex, long long count, const double *x, const double *y,
@@ -490,11 +511,10 @@ md_status md_eval_diff(const md_system *sys, const double *x, double *f, double 
 
 md_status md_linsolve_series(int limbs, int is_complex, int n, int degree, const double *A, const double *b,
                              double *dx, void *ws, size_t ws_bytes, int flags, void *stream) {
-  (void)flags;
   if (!valid_limbs(limbs) || n < 1 || degree < 0 || !A || !b || !dx) return MD_ERR_ARG;
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return MD_ERR_WORKSPACE;
   const int P = is_complex ? 2 : 1;
-  SolveLayout L = solve_layout(limbs, P, n, degree, 256);
+  SolveLayout L = solve_layout(limbs, P, n, degree, 256, flags);
   if (256 + L.bytes > ws_bytes) return MD_ERR_WORKSPACE;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   char *base = static_cast<char *>(ws);
@@ -509,11 +529,10 @@ md_status md_linsolve_series(int limbs, int is_complex, int n, int degree, const
 
 md_status md_newton_series_step(const md_system *sys, double *x, double *dx_norm, void *ws, size_t ws_bytes, int flags,
                                 void *stream) {
-  (void)flags;
   if (!x) return MD_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Plan *p = nullptr;
-  md_status st = prepare(sys, ws, ws_bytes, s, p);
+  md_status st = prepare(sys, ws, ws_bytes, s, p, flags);
   if (st != MD_OK) return st;
   char *base = static_cast<char *>(ws);
   if (cudaMemsetAsync(base, 0, 256, s) != cudaSuccess) return MD_ERR_CUDA;

@@ -2,6 +2,7 @@
 #pragma once
 #include "internal.h"
 #include "kernels.cuh"
+#include "ozaki.cuh"
 
 namespace mdk {
 
@@ -94,7 +95,32 @@ cudaError_t Impl<K, P>::solve(const SolveDev &v, cudaStream_t s) {
     ProfScope prof(PK_BACKSUB, s);
     backsub_kernel<K, P><<<blocks_for((long long)(c + 1) * n, 64), 64, 0, s>>>(v.M, v.Y, v.W, v.rinv, n, c);
   }
+  constexpr int S = oz_slices(K);
+  __nv_bfloat16 *As = static_cast<__nv_bfloat16 *>(v.oz_As), *Xs = static_cast<__nv_bfloat16 *>(v.oz_Xs);
+  if (v.ozaki && d >= 1) {
+    ProfScope prof(PK_OZ_SPLIT, s);
+    oz_split_rows_kernel<K, P><<<blocks_for((long long)d * n * 32, 128), 128, 0, s>>>(v.A, As, v.oz_eA, n, d);
+  }
   for (int k = 0; k <= d; ++k) {
+    if (v.ozaki) {
+      if (k >= 1) {
+        {
+          ProfScope prof(PK_OZ_SPLIT, s);
+          oz_split_vec_kernel<K, P><<<1, 128, 0, s>>>(v.dxw, Xs, v.oz_ex, n, k - 1);
+        }
+        ProfScope prof(PK_OZ_GEMM, s);
+        const long long tiles = (long long)k * (n * P * S / 16) * (P * S / 8);
+        oz_gemm_kernel<S, P><<<blocks_for(tiles * 32, 128), 128, 0, s>>>(As, Xs, v.oz_C, n, k);
+      }
+      {
+        ProfScope prof(PK_OZ_ACCUM, s);
+        oz_accum_kernel<K, P><<<blocks_for((long long)n * P * 32, 128), 128, 0, s>>>(v.oz_C, v.oz_eA, v.oz_ex, v.b,
+                                                                                     v.sgn, v.r, n, d, k);
+      }
+      ProfScope prof(PK_WMV, s);
+      wmv_kernel<K, P><<<n, 128, 0, s>>>(v.W, v.r, v.dxw, n, k);
+      continue;
+    }
     int C, nchunk;
     rhs_chunking(n, k, C, nchunk);
     if (nchunk > 0) {

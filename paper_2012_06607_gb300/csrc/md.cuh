@@ -271,8 +271,8 @@ __device__ __forceinline__ void md_sqrt(const double (&a)[K], double (&z)[K]) {
     s[0] = __dsqrt_rn(a[0]);
 #pragma unroll
     for (int i = 1; i < K; ++i) s[i] = 0.0;
-#pragma unroll 1
     constexpr int iters = sqrt_iters<K>();
+#pragma unroll 1
     for (int k = 0; k < iters; ++k) {
       md_div<K>(a, s, t);
       md_add<K>(s, t, s);

@@ -1,0 +1,120 @@
+"""Split-product (Ozaki) form of the block Toeplitz update against the oracle.
+
+The form changes only how r_k = b_k - sum_j A_{k-j} dx_j is computed (exact
+slice products on the BF16 tensor pipe, exact fixed-point accumulation, one
+rounding to K limbs), so it must meet the same per-degree tolerance as the
+plain form, and on the ill-conditioned quad-double system (n = 256, d = 16,
+cond(A_0) = 1e8) its error against the oracle must not exceed the plain
+form's (equal accuracy).
+"""
+import numpy as np
+import pytest
+
+import mdgen
+from mdcompare import md_diff, md_value, modulus
+
+pytestmark = pytest.mark.gpu
+
+OZAKI = 1
+
+
+def eps(K):
+    return 2.0 ** (-52 * K)
+
+
+@pytest.fixture(scope="module")
+def md():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2012_06607_gb300 import build
+
+    build.build()
+    import paper_2012_06607_gb300 as m
+
+    return m
+
+
+def _rel_by_degree(got, want):
+    diff = modulus(md_diff(got, want))
+    scale = np.maximum(modulus(md_value(want)).max(axis=0), 1e-300)
+    return diff.max(axis=0) / scale
+
+
+def _random_linear(K, cplx, n, d, seed, diag=4.0):
+    rng = np.random.default_rng(seed)
+    P = 2 if cplx else 1
+    sc = np.array([2.0 ** (-53 * l) for l in range(K)])
+    A = rng.standard_normal((P, K, d + 1, n, n)) * sc[None, :, None, None, None]
+    for c in range(n):
+        A[0, 0, 0, c, c] += diag
+    b = rng.standard_normal((P, K, n, d + 1)) * sc[None, :, None, None]
+    return A, b
+
+
+def _solve(md, K, cplx, A, b, flags):
+    n, d = b.shape[2], b.shape[3] - 1
+    ws = md.workspace(md.linsolve_workspace_bytes(K, cplx, n, d, flags))
+    dx = md.linsolve(K, cplx, md.to_device(A), md.to_device(b), ws, flags=flags).cpu().numpy()
+    assert md.device_status(ws) == 0
+    return dx
+
+
+@pytest.mark.parametrize("K,cplx,n,d", [(2, True, 8, 8), (4, False, 9, 5), (4, True, 16, 12), (8, False, 7, 4),
+                                        (3, True, 33, 3), (5, False, 20, 6), (10, True, 6, 3), (1, False, 5, 6)])
+def test_ozaki_linsolve_close_to_oracle(md, orc, K, cplx, n, d):
+    A, b = _random_linear(K, cplx, n, d, seed=K * 7 + n)
+    got = _solve(md, K, cplx, A, b, OZAKI)
+    want = orc.linsolve(K, cplx, A, b)
+    rel = _rel_by_degree(got, want)
+    print("ozaki linsolve", K, cplx, n, d, "max rel/eps:", float((rel / eps(K)).max()))
+    for k in range(d + 1):
+        assert rel[k] <= 1e3 * eps(K) * (k + 1), (k, rel[k] / eps(K))
+
+
+def test_ozaki_newton_steps(md, orc):
+    import torch
+
+    for s, steps in ((mdgen.config_system(0, 1), 4), (mdgen.sqrt_system(4, 16), 5)):
+        sysd = md.DeviceSystem(s)
+        ws = md.workspace(sysd.workspace_bytes(OZAKI))
+        x = md.to_device(s.x0)
+        xo = s.x0.copy()
+        for _ in range(steps):
+            md.newton_step(sysd, x, ws, flags=OZAKI)
+            assert md.device_status(ws) == 0
+            xo, _ = orc.newton_step(s, xo)
+        rel = _rel_by_degree(x.cpu().numpy(), xo)
+        print(s.name, "ozaki newton worst rel/eps:", float((rel / eps(s.limbs)).max()))
+        assert float((rel / eps(s.limbs)).max()) <= 1e6
+
+
+def test_ozaki_full_size_newton_step(md, orc):
+    """Quad double complex n = 64, d = 64: one step with the split-product update."""
+    s = mdgen.config_system(1, 1)
+    sysd = md.DeviceSystem(s)
+    ws = md.workspace(sysd.workspace_bytes(OZAKI))
+    x = md.to_device(s.x0)
+    md.newton_step(sysd, x, ws, flags=OZAKI)
+    assert md.device_status(ws) == 0
+    xo, _ = orc.newton_step(s, s.x0)
+    rel = _rel_by_degree(x.cpu().numpy(), xo)
+    print("cfg1 ozaki step worst rel/eps:", float((rel / eps(4)).max()))
+    assert float((rel / eps(4)).max()) <= 1e12
+
+
+def test_ill_conditioned_solve_equal_accuracy(md, orc):
+    """Quad double real n = 256, d = 16, cond(A_0) = 1e8: split-product and plain
+    forms against the oracle, degree by degree."""
+    A, b = mdgen.solve_config3(1)
+    K = 4
+    want = orc.linsolve(K, False, A, b)
+    plain = _solve(md, K, False, A, b, 0)
+    oz = _solve(md, K, False, A, b, OZAKI)
+    rp = _rel_by_degree(plain, want)
+    ro = _rel_by_degree(oz, want)
+    print("cfg3 rel err vs oracle per degree (plain):", [f"{v:.1e}" for v in rp])
+    print("cfg3 rel err vs oracle per degree (ozaki):", [f"{v:.1e}" for v in ro])
+    for k in range(b.shape[3]):
+        assert ro[k] <= 10.0 * rp[k] + 1e3 * eps(K), (k, ro[k], rp[k])
