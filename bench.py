@@ -329,6 +329,142 @@ def run_product(args):
     return 0
 
 
+# --------------------------------------------------------- the other forms
+def run_solve3(args):
+    """Linearized solve, quad double real n=256 d=16, cond(A_0) = 1e8: plain
+    block Toeplitz update against the split-product (Ozaki) update."""
+    import numpy as np
+    import torch
+
+    import mdgen
+    import paper_2012_06607_gb300 as md
+
+    A, b = mdgen.solve_config3(args.seed)
+    K, n, d = 4, 256, 16
+    Ad, bd = md.to_device(A), md.to_device(b)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, flags in (("plain", 0), ("ozaki", md.FLAG_OZAKI)):
+        ws = md.workspace(md.linsolve_workspace_bytes(K, False, n, d, flags))
+        dx = torch.empty_like(bd)
+        for _ in range(args.warmup):
+            md.linsolve(K, False, Ad, bd, ws, dx, flags=flags)
+        torch.cuda.synchronize()
+        md.profile_read()
+        md.profile_enable(True)
+        evs = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            md.linsolve(K, False, Ad, bd, ws, dx, flags=flags)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        md.profile_enable(False)
+        prof = md.profile_read()
+        assert md.device_status(ws) == 0
+        res[name] = {"ms_per_solve": statistics.mean(a.elapsed_time(b) for a, b in evs),
+                     "kernel_ms_per_solve": {k: round(v[0] / args.steps, 3) for k, v in
+                                             sorted(prof.items(), key=lambda kv: -kv[1][0])},
+                     "dx": dx.cpu().numpy()}
+    err = {}
+    if not args.no_cpu_baseline:
+        import oracle
+
+        from math import fsum
+        want = oracle.Oracle(threads=os.cpu_count() or 1).linsolve(K, False, A, b)
+        for name in ("plain", "ozaki"):
+            got = res[name]["dx"]
+            e = []
+            for k in range(d + 1):
+                diff = max(abs(fsum(list(got[0, :, i, k]) + [-v for v in want[0, :, i, k]])) for i in range(n))
+                scale = max(abs(want[0, 0, i, k]) for i in range(n))
+                e.append(diff / scale)
+            err[name] = max(e)
+    upd = {name: sum(v for k, v in res[name]["kernel_ms_per_solve"].items()
+                     if k in ("rhs_partial", "rhs_finish", "oz_split", "oz_gemm", "oz_accum")) for name in res}
+    line = {"metric": "linearized block Toeplitz solves/s (qd real, n=256, d=16, cond(A_0)=1e8)",
+            "unit": "solves/s", "form": "plain vs split-product",
+            "value_plain": 1e3 / res["plain"]["ms_per_solve"], "value_ozaki": 1e3 / res["ozaki"]["ms_per_solve"],
+            "speedup_solve": res["plain"]["ms_per_solve"] / res["ozaki"]["ms_per_solve"],
+            "update_ms_plain": upd["plain"], "update_ms_ozaki": upd["ozaki"],
+            "speedup_update": upd["plain"] / max(upd["ozaki"], 1e-9),
+            "max_rel_err_vs_oracle": err, "kernel_ms_plain": res["plain"]["kernel_ms_per_solve"],
+            "kernel_ms_ozaki": res["ozaki"]["kernel_ms_per_solve"], "steps": args.steps, "warmup": args.warmup,
+            "data": "synthetic", "dtype": "f64 (quad double); bf16 slices for the split products"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_batched(args):
+    """2048 complex systems, n ~ U{8..64}, d ~ U{8..32}, double double / quad
+    double: one persistent launch per precision class per Newton iteration
+    (autotuned, replayed from a CUDA graph) against a per-system launch loop."""
+    import numpy as np
+    import torch
+
+    import mdgen
+    import paper_2012_06607_gb300 as md
+
+    systems = mdgen.batch_systems(args.seed, count=args.batch)
+    sds = [md.DeviceSystem(s) for s in systems]
+    flags = md.FLAG_AUTOTUNE | md.FLAG_GRAPH
+    ws = md.workspace(md.batched_workspace_bytes(sds, flags))
+    xs = [md.to_device(s.x0) for s in systems]
+    nrm = torch.zeros((len(systems), 2), dtype=torch.float64, device="cuda")
+    times = torch.zeros((len(systems), 2), dtype=torch.int64, device="cuda")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            md.newton_step_batched(sds, xs, ws, nrm, times, flags=flags, stream=stream)
+        torch.cuda.synchronize()
+        ms = []
+        lat = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            md.newton_step_batched(sds, xs, ws, nrm, times, flags=flags, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            t = times.cpu().numpy()
+            lat.append((t[:, 1] - t[:, 0]) / 1e6)
+        torch.cuda.synchronize()
+    assert md.device_status(ws) == 0
+    lat = np.concatenate(lat)
+    it_ms = sum(ms) / len(ms)
+    # per-system launch loop on the same systems (plain single-system steps)
+    loop_ms = None
+    if not args.no_loop:
+        wmax = max(sd.workspace_bytes() for sd in sds)
+        ws1 = md.workspace(wmax)
+        xs1 = [md.to_device(s.x0) for s in systems]
+        for i, sd in enumerate(sds[:4]):
+            md.newton_step(sd, xs1[i], ws1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i, sd in enumerate(sds):
+            md.newton_step(sd, xs1[i], ws1)
+        torch.cuda.synchronize()
+        loop_ms = (time.perf_counter() - t0) * 1e3
+    kinds = {}
+    for s in systems:
+        kinds[s.limbs] = kinds.get(s.limbs, 0) + 1
+    line = {"metric": "batched Newton iterations/s (2048 systems, n~U{8..64}, d~U{8..32}, dd/qd, complex)",
+            "unit": "iterations/s", "value": 1e3 / it_ms, "ms_per_iteration": it_ms,
+            "system_steps_per_s": len(systems) * 1e3 / it_ms,
+            "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+            "loop_ms_per_iteration": loop_ms,
+            "speedup_vs_loop": (loop_ms / it_ms) if loop_ms else None,
+            "systems": len(systems), "limb_counts": kinds, "workspace_gib": ws.numel() / 2 ** 30,
+            "steps": args.steps, "warmup": args.warmup, "flags": "autotune+graph", "data": "synthetic",
+            "dtype": "f64 (double double / quad double)"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -337,11 +473,20 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--impl", default="product", choices=["product", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--form", default="plain", choices=["plain", "solve3", "batched"],
+                    help="plain: the Newton-step benchmark; solve3: plain vs split-product solve; "
+                         "batched: 2048-system batched step vs a per-system loop")
+    ap.add_argument("--batch", type=int, default=2048)
+    ap.add_argument("--no-loop", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.form == "solve3":
+        return run_solve3(args)
+    if args.form == "batched":
+        return run_batched(args)
     return run_product(args)
 
 

@@ -96,6 +96,18 @@ typedef struct md_system {
  * workspace reported for this flag.
  */
 #define MD_FLAG_OZAKI 0x1
+/* batched form: pick CTAs per SM per precision class by timing trial steps
+   (first call only; trial steps do not update x) */
+#define MD_FLAG_AUTOTUNE 0x2
+/* batched form: capture the step (plan upload + persistent launches) in a CUDA
+   graph on the first call and replay it on later calls with the same arguments
+   (needs a non-default stream) */
+#define MD_FLAG_GRAPH 0x4
+/* single-system step: run every phase on `stream` in order.  By default the
+   factorisation of A_0 runs on a second (library-owned, highest-priority)
+   stream on a few SMs while the higher coefficients are evaluated on the rest;
+   results are identical either way. */
+#define MD_FLAG_SERIAL 0x8
 
 /* Version of this ABI (major*100 + minor). */
 int md_version(void);
@@ -172,6 +184,26 @@ md_status md_linsolve_series(int limbs, int is_complex, int n, int degree, const
  */
 md_status md_newton_series_step(const md_system *sys, double *x, double *dx_norm, void *ws, size_t ws_bytes,
                                 int flags, void *stream);
+
+/*
+ * One Newton step for each of `nsys` independent systems (uneven n, degree and
+ * precision), as in md_newton_series_step, in one persistent launch per
+ * precision class: each CTA takes the next system from an atomic job counter
+ * (most expensive first) and runs its whole step; there are no waits between
+ * CTAs.  Every system gets the same bits as md_newton_series_step on it alone.
+ *   sys:     HOST array of nsys systems (structure host, values device)
+ *   x:       HOST array of nsys DEVICE pointers, each [P][K][n][d+1], updated
+ *   dx_norm: DEVICE double[nsys][2] or NULL (per system, as in the single step)
+ *   times:   DEVICE unsigned long long[nsys][2] or NULL: global-timer
+ *            nanoseconds at the start and end of each system's step
+ *   ws:      DEVICE workspace of md_batched_workspace_bytes() bytes; the status
+ *            word covers the whole batch
+ *   flags:   MD_FLAG_AUTOTUNE, MD_FLAG_GRAPH
+ */
+size_t md_batched_workspace_bytes(int nsys, const md_system *sys, int flags);
+md_status md_newton_series_step_batched(int nsys, const md_system *sys, double *const *x, double *dx_norm,
+                                        unsigned long long *times, void *ws, size_t ws_bytes, int flags,
+                                        void *stream);
 
 /*
  * Synchronise `stream`, read the sticky device status word of `ws` (written by

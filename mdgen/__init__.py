@@ -480,3 +480,124 @@ def solve_config3(seed: int = 1, n: int = 256, d: int = 16, K: int = 4, cond: fl
     b = np.zeros((1, K, n, d + 1))
     b[0] = lifted((n, d + 1))
     return A, b
+
+
+# ----------------------------------------------------------------------------
+# many systems of uneven size for the batched form
+
+
+def _fixed_unit(rng, size, bits=11):
+    """cos t + i sin t, t ~ U[0, 2 pi), each part rounded to `bits` fractional bits."""
+    th = rng.uniform(0.0, 2 * math.pi, size)
+    sc = float(1 << bits)
+    return np.round(np.cos(th) * sc) / sc + 1j * (np.round(np.sin(th) * sc) / sc)
+
+
+def small_system_fast(rng, n: int, d: int, K: int, monos: int, cond_max: float = 1e6, name: str = "") -> System:
+    """System as in the double-double n=3 configuration but of size n, built fast.
+
+    Per polynomial `monos` distinct monomials of total degree <= 3 over one or two
+    variables (t included; the first monomial contains t).  Coefficients and x0
+    are cos t + i sin t with real and imaginary parts rounded to 11 fractional
+    bits: every product of a coefficient with at most three such numbers has at
+    most 44 fractional bits and every constant term (a sum of at most `monos`
+    such products, below 2^7 in modulus) is exact in double, so x0 solves the
+    system at t = 0 exactly.  Limbs below the leading one are zero.
+    """
+    N = n + 1
+    for _ in range(64):
+        x0 = _fixed_unit(rng, n)
+        V = np.zeros((n, monos, 2), dtype=np.int64)
+        E = np.zeros((n, monos, 2), dtype=np.int64)
+        Mv = np.zeros((n, monos), dtype=np.int64)
+        todo = np.ones((n, monos), dtype=bool)
+        for _round in range(100):
+            cnt = int(todo.sum())
+            if cnt == 0:
+                break
+            m = rng.integers(1, 3, cnt)
+            v1 = rng.integers(0, N, cnt)
+            v2 = rng.integers(0, N - 1, cnt)
+            v2 = v2 + (v2 >= v1)
+            D = m + rng.integers(0, 4 - m, cnt)  # m..3
+            e1 = np.where(m == 1, D, 1 + ((D == 3) & (rng.uniform(size=cnt) < 0.5)))
+            e2 = np.where(m == 1, 0, D - e1)
+            ii, jj = np.nonzero(todo)
+            Mv[ii, jj] = m
+            V[ii, jj, 0], V[ii, jj, 1] = v1, v2
+            E[ii, jj, 0], E[ii, jj, 1] = e1, e2
+            # first monomial of each polynomial contains t
+            first = jj == 0
+            if first.any():
+                rows = ii[first]
+                V[rows, 0, 0] = n
+                V[rows, 0, 1] = rng.integers(0, n, rows.size)
+            # canonical order (smaller variable first) and duplicates
+            swap = (Mv == 2) & (V[:, :, 1] < V[:, :, 0])
+            V[swap] = V[swap][:, ::-1]
+            E[swap] = E[swap][:, ::-1]
+            key = np.where(Mv == 1, V[:, :, 0] * 4 + E[:, :, 0],
+                           ((V[:, :, 0] * 4 + E[:, :, 0]) * (N + 1) + V[:, :, 1] + 1) * 4 + E[:, :, 1] + 10 ** 9)
+            todo[:] = False
+            for i in range(n):
+                _, first_idx = np.unique(key[i], return_index=True)
+                dup = np.ones(monos, dtype=bool)
+                dup[first_idx] = False
+                todo[i] = dup
+        else:
+            continue
+        c = _fixed_unit(rng, (n, monos))
+        xt = np.concatenate([x0, [0.0]])  # t = 0
+        p1 = xt[V[:, :, 0]] ** E[:, :, 0]
+        p2 = np.where(Mv == 2, xt[V[:, :, 1]] ** E[:, :, 1], 1.0)
+        cst = -(c * p1 * p2).sum(axis=1)
+        # Jacobian at (x0, t = 0)
+        Jm = np.zeros((n, n), dtype=complex)
+        rows = np.repeat(np.arange(n), monos)
+        for q in range(2):
+            v = V[:, :, q].ravel()
+            e = E[:, :, q].ravel()
+            ok = (e > 0) & (v < n) & ((q == 0) | (Mv.ravel() == 2))
+            other = np.where(q == 0, np.where(Mv == 2, xt[V[:, :, 1]] ** E[:, :, 1], 1.0),
+                             xt[V[:, :, 0]] ** E[:, :, 0]).ravel()
+            dv = c.ravel() * e * xt[np.minimum(v, n)] ** np.maximum(e - 1, 0) * other
+            np.add.at(Jm, (rows[ok], v[ok]), dv[ok])
+        if np.linalg.cond(Jm) > cond_max:
+            continue
+        P = 2
+        nm = n * monos
+        nvar = Mv.ravel().astype(np.int32)
+        idx = np.full((nm, MAXV), -1, dtype=np.int32)
+        expo = np.zeros((nm, MAXV), dtype=np.int32)
+        idx[:, 0] = V[:, :, 0].ravel()
+        expo[:, 0] = E[:, :, 0].ravel()
+        two = nvar == 2
+        idx[two, 1] = V[:, :, 1].ravel()[two]
+        expo[two, 1] = E[:, :, 1].ravel()[two]
+        coef = np.zeros((P, K, nm))
+        coef[0, 0] = c.real.ravel()
+        coef[1, 0] = c.imag.ravel()
+        cs = np.zeros((P, K, n))
+        cs[0, 0] = cst.real
+        cs[1, 0] = cst.imag
+        xx = np.zeros((P, K, n, d + 1))
+        xx[0, 0, :, 0] = x0.real
+        xx[1, 0, :, 0] = x0.imag
+        poly_ptr = np.arange(0, nm + 1, monos, dtype=np.int32)
+        return System(K, True, n, d, poly_ptr, nvar, idx.ravel(), expo.ravel(), coef, cs, xx, name=name,
+                      meta={"cond_double": float(np.linalg.cond(Jm))})
+    raise RuntimeError("no regular draw found")
+
+
+def batch_systems(seed: int = 1, count: int = 2048, nmin: int = 8, nmax: int = 64, dmin: int = 8, dmax: int = 32):
+    """The batched workload: `count` complex systems, n ~ U{nmin..nmax},
+    d ~ U{dmin..dmax}, n monomials per polynomial of degree <= 3 over <= 2
+    variables, double double or quad double with probability 1/2 each."""
+    rng = np.random.default_rng([seed, 4])
+    out = []
+    for b in range(count):
+        n = int(rng.integers(nmin, nmax + 1))
+        d = int(rng.integers(dmin, dmax + 1))
+        K = 2 if rng.uniform() < 0.5 else 4
+        out.append(small_system_fast(rng, n, d, K, monos=n, name=f"batch{b}"))
+    return out

@@ -60,6 +60,11 @@ def lib():
         L.md_linsolve_series.argtypes = [i, i, i, i, vp, vp, vp, vp, sz, i, vp]
         L.md_newton_series_step.argtypes = [ctypes.POINTER(md_system), vp, vp, vp, sz, i, vp]
         L.md_get_device_status.argtypes = [vp, vp]
+        L.md_batched_workspace_bytes.argtypes = [i, ctypes.POINTER(md_system), i]
+        L.md_batched_workspace_bytes.restype = sz
+        L.md_newton_series_step_batched.argtypes = [i, ctypes.POINTER(md_system), ctypes.POINTER(vp), vp, vp, vp, sz,
+                                                    i, vp]
+        L.md_newton_series_step_batched.restype = i
         L.md_linsolve_series_static.argtypes = [i, i, i, i, vp, vp, vp, i, vp]
         L.md_linsolve_series_static.restype = i
         L.md_profile_enable.argtypes = [i]
@@ -78,7 +83,8 @@ def lib():
 def exported_symbols():
     return ["md_version", "md_status_string", "md_workspace_bytes", "md_linsolve_workspace_bytes",
             "md_elementwise", "md_series_conv", "md_eval_diff", "md_linsolve_series",
-            "md_newton_series_step", "md_get_device_status", "md_linsolve_series_static", "md_profile_enable",
+            "md_newton_series_step", "md_get_device_status", "md_batched_workspace_bytes",
+            "md_newton_series_step_batched", "md_linsolve_series_static", "md_profile_enable",
             "md_profile_read",
             "md_profile_kind_name"]
 
@@ -200,6 +206,31 @@ def newton_step(sysd: DeviceSystem, x, ws, dx_norm=None, flags: int = 0, stream=
     _check(lib().md_newton_series_step(sysd.c(), _ptr(x), _ptr(dx_norm), _ptr(ws), ws.numel(), flags,
                                        _stream(stream)), "md_newton_series_step")
     return x
+
+
+FLAG_OZAKI, FLAG_AUTOTUNE, FLAG_GRAPH = 0x1, 0x2, 0x4
+
+
+def _sys_array(systems):
+    arr = (md_system * len(systems))()
+    for i, sd in enumerate(systems):
+        arr[i] = sd._c
+    return arr
+
+
+def batched_workspace_bytes(systems, flags: int = 0) -> int:
+    return int(lib().md_batched_workspace_bytes(len(systems), _sys_array(systems), flags))
+
+
+def newton_step_batched(systems, xs, ws, dx_norm=None, times=None, flags: int = 0, stream=None):
+    """One Newton step for every system (DeviceSystem list) on its series xs[i]
+    (CUDA tensors, updated in place).  dx_norm: CUDA double [nsys, 2] or None;
+    times: CUDA int64 [nsys, 2] (global-timer ns at start/end) or None."""
+    arr = _sys_array(systems)
+    xp = (ctypes.c_void_p * len(xs))(*[_ptr(x) for x in xs])
+    _check(lib().md_newton_series_step_batched(len(systems), arr, xp, _ptr(dx_norm), _ptr(times), _ptr(ws),
+                                               ws.numel(), flags, _stream(stream)), "md_newton_series_step_batched")
+    return xs
 
 
 def device_status(ws, stream=None) -> int:

@@ -31,11 +31,22 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def sources():
-    srcs = [os.path.join(CSRC, f"inst_k{k}_p{p}.cu") for k in LIMBS for p in (1, 2)]
-    srcs.append(os.path.join(CSRC, "capi.cu"))
-    srcs.append(os.path.join(CSRC, "noalloc.cu"))
-    return srcs
+PARTS = ("ops", "eval", "solve", "batched")
+
+
+def units():
+    """(source, object name, extra flags): one instantiation unit per (K, P, part)."""
+    out = []
+    inst = os.path.join(CSRC, "inst.cu")
+    for k in LIMBS:
+        for p in (1, 2):
+            for i, part in enumerate(PARTS):
+                if part == "batched" and k > 5:
+                    continue  # the batched form covers up to five limbs
+                out.append((inst, f"inst_k{k}_p{p}_{part}.o", [f"-DMDK_K={k}", f"-DMDK_P={p}", f"-DMDK_PART={i}"]))
+    out.append((os.path.join(CSRC, "capi.cu"), "capi.o", []))
+    out.append((os.path.join(CSRC, "noalloc.cu"), "noalloc.o", []))
+    return out
 
 
 def _deps():
@@ -57,11 +68,14 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         return LIB
     objs = []
     jobs = []
-    with cf.ThreadPoolExecutor(max_workers=max(2, min(len(sources()), os.cpu_count() or 4))) as ex:
-        for src in sources():
-            obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
+    todo = units()
+    # longest units first (more limbs, complex) so the pool ends evenly
+    todo.sort(key=lambda u: -sum(int(f.split("=")[1]) for f in u[2] if f.startswith(("-DMDK_K", "-DMDK_P"))) if u[2] else 0)
+    with cf.ThreadPoolExecutor(max_workers=max(2, os.cpu_count() or 4)) as ex:
+        for src, oname, flags in todo:
+            obj = os.path.join(BUILD, oname)
             objs.append(obj)
-            jobs.append(ex.submit(_compile, src, obj, list(extra)))
+            jobs.append(ex.submit(_compile, src, obj, list(extra) + flags))
         for j in jobs:
             j.result()
     tmp = LIB + f".tmp{os.getpid()}"

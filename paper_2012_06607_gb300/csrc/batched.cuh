@@ -1,0 +1,118 @@
+// Batched form: many independent systems of uneven dimension n and degree d,
+// one Newton step each, in one persistent launch per precision class.
+//
+// Every CTA (128 threads) takes the next system from an atomic job counter
+// (systems listed longest first) and runs that system's whole step: series
+// products stage by stage, accumulation of f and A, Householder QR of A_0 with
+// Q^H, W = R^-1 Q^H, the degree loop of the block Toeplitz solve and the update
+// of x -- with __syncthreads between phases and no waiting on other CTAs, so
+// nothing can hang.  The per-item bodies and reduction trees are those of the
+// one-system kernels, so every system gets the same bits as a single-system step.
+#pragma once
+#include "kernels.cuh"
+
+namespace mdk {
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// CTA sizes of the batched kernel: kBatchThreads (default) up to kBatchMaxThreads.
+constexpr int kBatchThreads = 128;
+constexpr int kBatchMaxThreads = 384;
+
+template <int K, int P>
+__global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const BatchJob *__restrict__ jobs,
+                                                                     const int *__restrict__ order, int njobs,
+                                                                     int *__restrict__ counter,
+                                                                     const int *ibase, double *dbase,
+                                                                     double *__restrict__ nrm,
+                                                                     unsigned long long *__restrict__ times,
+                                                                     int *__restrict__ status, int update_x) {
+  __shared__ int s_job;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NT = blockDim.x, nwarp = NT / 32;
+  for (;;) {
+    if (tid == 0) s_job = atomicAdd(counter, 1);
+    __syncthreads();
+    const int q = s_job;
+    __syncthreads();
+    if (q >= njobs) return;
+    const int job = order[q];
+    const BatchJob J = jobs[job];
+    const int n = J.n, d = J.d;
+    if (tid == 0) {
+      if (times) times[2 * job] = global_ns();
+      if (nrm) {
+        nrm[2 * job] = 0.0;
+        nrm[2 * job + 1] = 0.0;
+      }
+    }
+    double *pool = dbase + J.pool;
+    double *scal = dbase + J.scal;
+    double *f = dbase + J.f;
+    double *A = dbase + J.A;
+    // ---- evaluate and differentiate
+    for (long long e = tid; e < (long long)n * (d + 1); e += NT) pool_load_entry<K, P>(J.x, pool, n, d, e);
+    for (int i = tid; i < J.nscal; i += NT) prep_scal_entry<K, P>(ibase + J.scal_src, J.coef, J.nmono, scal, i);
+    const long long Awords = (long long)P * K * (d + 1) * n * n;
+    for (long long e = tid; e < Awords; e += NT) A[e] = 0.0;
+    __syncthreads();
+    const int *ops = ibase + J.ops;
+    const int *soff = ibase + J.stage_off;
+    const int npairs = (d + 2) / 2;  // coefficient pairs (k, d-k); the middle one alone when d is even
+    for (int st = 0; st < J.nstages; ++st) {
+      const int o0 = soff[st], o1 = soff[st + 1];
+      const long long items = (long long)(o1 - o0) * npairs;
+      for (long long it = tid; it < items; it += NT) {
+        const int o = o0 + (int)(it / npairs), p = (int)(it % npairs);
+        const int out = ops[3 * o], a = ops[3 * o + 1], b = ops[3 * o + 2];
+        if (2 * p < d)
+          conv_pair<K, P, false>(pool, d, out, a, b, p, out, a, b);
+        else
+          conv_pair<K, P, false>(pool, d, out, a, b, p, -1, -1, -1);
+      }
+      __syncthreads();
+    }
+    const int4 *groups = reinterpret_cast<const int4 *>(ibase + J.groups);
+    const int4 *contrib = reinterpret_cast<const int4 *>(ibase + J.contrib);
+    for (long long e = tid; e < (long long)J.ngroups * (d + 1); e += NT)
+      accum_entry<K, P>(groups, contrib, pool, scal, J.cst, f, A, n, d, (int)(e / (d + 1)), (int)(e % (d + 1)));
+    __syncthreads();
+    // ---- solve A(t) dx(t) = -f(t)
+    double *M = dbase + J.M, *Y = dbase + J.Y, *W = dbase + J.W;
+    double *vd = dbase + J.vd, *beta = dbase + J.beta, *rinv = dbase + J.rinv;
+    double *r = dbase + J.r, *dxw = dbase + J.dxw, *part = dbase + J.part;
+    for (long long e = tid; e < (long long)n * n; e += NT) solve_init_entry<K, P>(A, M, Y, n, d, e);
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+      house_block<K, P>(M, vd, beta, status, n, j);
+      for (int w = warp; w < (n - j - 1) + n; w += nwarp) house_apply_col<K, P>(M, Y, vd, beta, n, j, w, lane);
+      __syncthreads();
+    }
+    for (int j = tid; j < n; j += NT) rinv_entry<K, P>(M, rinv, n, j);
+    __syncthreads();
+    for (int c = n - 1; c >= 0; --c) {
+      for (long long e = tid; e < (long long)(c + 1) * n; e += NT) backsub_entry<K, P>(M, Y, W, rinv, n, c, e);
+      __syncthreads();
+    }
+    for (int k = 0; k <= d; ++k) {
+      int C, nchunk;
+      rhs_chunking(n, k, C, nchunk);
+      for (long long e = tid; e < (long long)n * nchunk; e += NT)
+        rhs_partial_item<K, P>(A, dxw, part, n, d, k, C, nchunk, e);
+      __syncthreads();
+      for (int row = warp; row < n; row += nwarp) rhs_finish_row<K, P>(f, -1.0, part, r, n, d, k, nchunk, row, lane);
+      __syncthreads();
+      for (int row = warp; row < n; row += nwarp) wmv_row<K, P>(W, r, dxw, n, k, row, lane);
+      __syncthreads();
+    }
+    for (long long e = tid; e < (long long)n * (d + 1); e += NT)
+      finish_entry<K, P>(dxw, nullptr, update_x ? J.x : nullptr, nrm ? nrm + 2 * job : nullptr, status, n, d, e);
+    __syncthreads();
+    if (tid == 0 && times) times[2 * job + 1] = global_ns();
+  }
+}
+
+}  // namespace mdk

@@ -34,6 +34,13 @@ cudaError_t dispatch_p(int P, int what, const void *a, cudaStream_t s, int op = 
       case 1: return mdk::Impl<K, 1>::series_conv(d, count, x, y, z, s);
       case 2: return mdk::Impl<K, 1>::eval(*static_cast<const EvalDev *>(a), s);
       case 3: return mdk::Impl<K, 1>::solve(*static_cast<const SolveDev *>(a), s);
+      case 4:
+        if constexpr (K <= mdk::kBatchMaxLimbs) return mdk::Impl<K, 1>::batched(*static_cast<const mdk::BatchDev *>(a), s);
+        return cudaErrorNotSupported;
+      case 5: return mdk::Impl<K, 1>::eval0(*static_cast<const EvalDev *>(a), s);
+      case 6: return mdk::Impl<K, 1>::eval_rest(*static_cast<const EvalDev *>(a), s);
+      case 7: return mdk::Impl<K, 1>::factor(*static_cast<const SolveDev *>(a), s);
+      case 8: return mdk::Impl<K, 1>::degrees(*static_cast<const SolveDev *>(a), s);
     }
   } else {
     switch (what) {
@@ -41,6 +48,13 @@ cudaError_t dispatch_p(int P, int what, const void *a, cudaStream_t s, int op = 
       case 1: return mdk::Impl<K, 2>::series_conv(d, count, x, y, z, s);
       case 2: return mdk::Impl<K, 2>::eval(*static_cast<const EvalDev *>(a), s);
       case 3: return mdk::Impl<K, 2>::solve(*static_cast<const SolveDev *>(a), s);
+      case 4:
+        if constexpr (K <= mdk::kBatchMaxLimbs) return mdk::Impl<K, 2>::batched(*static_cast<const mdk::BatchDev *>(a), s);
+        return cudaErrorNotSupported;
+      case 5: return mdk::Impl<K, 2>::eval0(*static_cast<const EvalDev *>(a), s);
+      case 6: return mdk::Impl<K, 2>::eval_rest(*static_cast<const EvalDev *>(a), s);
+      case 7: return mdk::Impl<K, 2>::factor(*static_cast<const SolveDev *>(a), s);
+      case 8: return mdk::Impl<K, 2>::degrees(*static_cast<const SolveDev *>(a), s);
     }
   }
   return cudaErrorInvalidValue;
@@ -112,11 +126,15 @@ struct Plan {
   int nslots = 0;
   std::vector<int> tasks;      // 8 ints per task, stage-major
   std::vector<int> stage_off;  // nstages + 1
+  std::vector<int> tasks0;     // coefficient-0 tasks (single jobs), stage-major
+  std::vector<int> stage_off0; // nstages + 1
   std::vector<int> scal_src;   // (monomial, exponent factor)
   std::vector<int> groups;     // (row, col or -1, first contribution, count)
   std::vector<int> contrib;    // (slot or -1, scal index, t shift, 0)
+  std::vector<int> ops3;          // (out, a, b) per product, stage-major (batched form)
+  std::vector<int> op_stage_off;  // nstages + 1 product offsets
   // workspace offsets (bytes)
-  size_t off_pool = 0, off_scal = 0, off_tasks = 0, off_scalsrc = 0, off_groups = 0, off_contrib = 0;
+  size_t off_pool = 0, off_scal = 0, off_tasks = 0, off_scalsrc = 0, off_groups = 0, off_contrib = 0, off_tasks0 = 0;
   size_t off_f = 0, off_A = 0, off_solve = 0, total = 0;
   SolveLayout sl{};
   uint64_t checksum = 0;
@@ -259,6 +277,18 @@ md_status build_plan(const md_system *s, Plan &p, int flags = 0) {
   // stages and tasks
   int nst = 0;
   for (const Op &o : ops) nst = std::max(nst, o.st);
+  p.op_stage_off.assign(1, 0);
+  for (int sg = 1; sg <= nst; ++sg) {
+    for (const Op &o : ops)
+      if (o.st == sg) p.ops3.insert(p.ops3.end(), {o.out, o.a, o.b});
+    p.op_stage_off.push_back((int)p.ops3.size() / 3);
+  }
+  p.stage_off0.assign(1, 0);
+  for (int sg = 1; sg <= nst; ++sg) {
+    for (const Op &o : ops)
+      if (o.st == sg) p.tasks0.insert(p.tasks0.end(), {o.out, o.a, o.b, 0, -1, -1, -1, 0});
+    p.stage_off0.push_back((int)p.tasks0.size() / 8);
+  }
   p.stage_off.assign(1, 0);
   for (int sg = 1; sg <= nst; ++sg) {
     std::vector<int> middles;  // ops whose middle coefficient is left
@@ -288,6 +318,7 @@ md_status build_plan(const md_system *s, Plan &p, int flags = 0) {
   p.off_scalsrc = o; o = align256(o + sizeof(int) * std::max<size_t>(p.scal_src.size(), 2));
   p.off_groups = o; o = align256(o + sizeof(int) * std::max<size_t>(p.groups.size(), 4));
   p.off_contrib = o; o = align256(o + sizeof(int) * std::max<size_t>(p.contrib.size(), 4));
+  p.off_tasks0 = o; o = align256(o + sizeof(int) * std::max<size_t>(p.tasks0.size(), 8));
   p.off_f = o; o = align256(o + (size_t)n * (d + 1) * VS);
   p.off_A = o; o = align256(o + (size_t)(d + 1) * n * n * VS);
   p.off_solve = o;
@@ -341,6 +372,7 @@ md_status prepare(const md_system *s, void *ws, size_t ws_bytes, cudaStream_t st
     put(p.off_scalsrc, p.scal_src);
     put(p.off_groups, p.groups);
     put(p.off_contrib, p.contrib);
+    put(p.off_tasks0, p.tasks0);
     pe->image_bytes = bytes;
     pe->pinned = static_cast<int *>(h);
   }
@@ -348,6 +380,267 @@ md_status prepare(const md_system *s, void *ws, size_t ws_bytes, cudaStream_t st
                       stream) != cudaSuccess)
     return MD_ERR_CUDA;
   out = &pe->plan;
+  return MD_OK;
+}
+
+
+// ------------------------------------------------------------ batched form
+// Host plans of single systems, cached by structure checksum (no pinned image).
+Plan *plan_of(const md_system *s, md_status &st) {
+  st = check_system(s);
+  if (st != MD_OK) return nullptr;
+  const uint64_t cs = structure_checksum(s);
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_plans.find(cs);
+  if (it != g_plans.end()) return &it->second->plan;
+  std::unique_ptr<PlanEntry> e(new PlanEntry);
+  st = build_plan(s, e->plan, 0);
+  if (st != MD_OK) return nullptr;
+  PlanEntry *pe = e.release();
+  g_plans[cs] = pe;
+  return &pe->plan;
+}
+
+struct BatchClass {
+  int K = 0, P = 0;
+  std::vector<int> order;  // job indices, most expensive first
+  size_t order_off = 0;    // int offset from off_orders
+  int cps = 2;             // CTAs per SM (autotuned)
+  int threads = 128;       // threads per CTA (autotuned)
+};
+
+struct BatchPlan {
+  int nsys = 0;
+  std::vector<mdk::BatchJob> jobs;
+  std::vector<BatchClass> classes;
+  size_t off_jobs = 0, off_orders = 0, off_ibase = 0, off_dbase = 0, total = 0;
+  char *pinned = nullptr;  // [jobs | orders | ibase] as laid out in the workspace from off_jobs
+  size_t image_bytes = 0;
+  bool tuned = false;
+  cudaGraphExec_t exec = nullptr;
+  const void *exec_ws = nullptr, *exec_nrm = nullptr, *exec_times = nullptr;
+  cudaStream_t exec_stream = nullptr;
+};
+std::map<uint64_t, BatchPlan *> g_batch;
+
+double job_cost(const Plan &p) {
+  const double n = p.n, d = p.d, D1 = d + 1;
+  const double convs = (double)p.ops3.size() / 3;
+  const double macs = convs * D1 * (D1 + 1) / 2 + 2 * n * n * n + n * n * d * D1 / 2 + (double)p.contrib.size() / 4 * D1;
+  const double per = p.K * p.K * (p.P == 2 ? 4.0 : 1.0);
+  return macs * per;
+}
+
+md_status batch_prepare(int nsys, const md_system *sys, double *const *x, BatchPlan *&out, bool need_image) {
+  if (nsys < 1 || !sys) return MD_ERR_ARG;
+  std::vector<Plan *> plans(nsys);
+  uint64_t key = 1469598103934665603ULL;
+  for (int i = 0; i < nsys; ++i) {
+    md_status st;
+    plans[i] = plan_of(&sys[i], st);
+    if (!plans[i]) return st;
+    const uint64_t cs = plans[i]->checksum;
+    key = fnv(key, &cs, sizeof(cs));
+    const void *ptrs[3] = {sys[i].coef, sys[i].cst, x ? (const void *)x[i] : nullptr};
+    key = fnv(key, ptrs, sizeof(ptrs));
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_batch.find(key);
+    if (it != g_batch.end() && (!need_image || it->second->pinned)) {
+      out = it->second;
+      return MD_OK;
+    }
+  }
+  std::unique_ptr<BatchPlan> bp(new BatchPlan);
+  bp->nsys = nsys;
+  bp->jobs.resize(nsys);
+  // classes by (K, P), jobs ordered by decreasing cost
+  std::map<int, int> cls_of;
+  for (int i = 0; i < nsys; ++i) {
+    const int key2 = plans[i]->K * 4 + plans[i]->P;
+    if (!cls_of.count(key2)) {
+      cls_of[key2] = (int)bp->classes.size();
+      BatchClass c;
+      c.K = plans[i]->K;
+      c.P = plans[i]->P;
+      bp->classes.push_back(c);
+    }
+    bp->classes[cls_of[key2]].order.push_back(i);
+  }
+  for (BatchClass &c : bp->classes)
+    std::stable_sort(c.order.begin(), c.order.end(),
+                     [&](int a, int b) { return job_cost(*plans[a]) > job_cost(*plans[b]); });
+  // layout
+  size_t o = 256;
+  bp->off_jobs = o;
+  o = align256(o + sizeof(mdk::BatchJob) * nsys);
+  bp->off_orders = o;
+  size_t oo = 0;
+  for (BatchClass &c : bp->classes) {
+    c.order_off = oo;
+    oo += c.order.size();
+  }
+  o = align256(o + sizeof(int) * oo);
+  bp->off_ibase = o;
+  size_t ni = 0, nd = 0;
+  auto a4 = [](size_t v) { return (v + 3) & ~(size_t)3; };
+  auto a32 = [](size_t v) { return (v + 31) & ~(size_t)31; };
+  for (int i = 0; i < nsys; ++i) {
+    const Plan &p = *plans[i];
+    mdk::BatchJob &J = bp->jobs[i];
+    std::memset(&J, 0, sizeof(J));
+    const long long VS = (long long)p.P * p.K, n = p.n, D1 = p.d + 1;
+    J.n = p.n;
+    J.d = p.d;
+    J.nstages = (int)p.op_stage_off.size() - 1;
+    J.ngroups = (int)p.groups.size() / 4;
+    J.nscal = (int)p.scal_src.size() / 2;
+    J.nmono = p.nmono;
+    J.nops = (int)p.ops3.size() / 3;
+    ni = a4(ni);
+    J.ops = ni; ni += p.ops3.size();
+    J.stage_off = ni; ni += p.op_stage_off.size();
+    J.scal_src = ni; ni += p.scal_src.size();
+    ni = a4(ni);
+    J.groups = ni; ni += p.groups.size();
+    ni = a4(ni);
+    J.contrib = ni; ni += p.contrib.size();
+    nd = a32(nd);
+    J.pool = nd; nd += (size_t)p.nslots * D1 * VS;
+    J.scal = nd; nd += (size_t)std::max(J.nscal, 1) * VS;
+    J.f = nd; nd += (size_t)n * D1 * VS;
+    J.A = nd; nd += (size_t)D1 * n * n * VS;
+    J.M = nd; nd += (size_t)n * n * VS;
+    J.Y = nd; nd += (size_t)n * n * VS;
+    J.W = nd; nd += (size_t)n * n * VS;
+    J.vd = nd; nd += (size_t)n * VS;
+    J.beta = nd; nd += (size_t)n * p.K;
+    J.rinv = nd; nd += (size_t)n * VS;
+    J.r = nd; nd += (size_t)D1 * n * VS;
+    J.dxw = nd; nd += (size_t)D1 * n * VS;
+    J.part = nd; nd += (size_t)n * p.sl.maxchunk * VS;
+    J.coef = sys[i].coef;
+    J.cst = sys[i].cst;
+    J.x = x ? x[i] : nullptr;
+  }
+  o = align256(o + sizeof(int) * ni);
+  bp->off_dbase = o;
+  bp->total = o + sizeof(double) * nd;
+  if (need_image) {
+    bp->image_bytes = bp->off_dbase - bp->off_jobs;
+    void *h = nullptr;
+    if (cudaHostAlloc(&h, bp->image_bytes, cudaHostAllocDefault) != cudaSuccess) return MD_ERR_CUDA;
+    std::memset(h, 0, bp->image_bytes);
+    bp->pinned = static_cast<char *>(h);
+    std::memcpy(bp->pinned, bp->jobs.data(), sizeof(mdk::BatchJob) * nsys);
+    int *ord = reinterpret_cast<int *>(bp->pinned + (bp->off_orders - bp->off_jobs));
+    for (const BatchClass &c : bp->classes)
+      for (size_t q = 0; q < c.order.size(); ++q) ord[c.order_off + q] = c.order[q];
+    int *ib = reinterpret_cast<int *>(bp->pinned + (bp->off_ibase - bp->off_jobs));
+    for (int i = 0; i < nsys; ++i) {
+      const Plan &p = *plans[i];
+      const mdk::BatchJob &J = bp->jobs[i];
+      std::copy(p.ops3.begin(), p.ops3.end(), ib + J.ops);
+      std::copy(p.op_stage_off.begin(), p.op_stage_off.end(), ib + J.stage_off);
+      std::copy(p.scal_src.begin(), p.scal_src.end(), ib + J.scal_src);
+      std::copy(p.groups.begin(), p.groups.end(), ib + J.groups);
+      std::copy(p.contrib.begin(), p.contrib.end(), ib + J.contrib);
+    }
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_batch.find(key);
+  if (it != g_batch.end()) {
+    if (!it->second->pinned && bp->pinned) {
+      g_batch[key] = bp.release();  // the earlier size-only plan is replaced (leaked: tiny)
+    }
+  } else {
+    g_batch[key] = bp.release();
+  }
+  out = g_batch[key];
+  return MD_OK;
+}
+
+int device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 152;
+  return sms > 0 ? sms : 152;
+}
+
+mdk::BatchDev batch_dev(const BatchPlan &bp, const BatchClass &c, int ci, char *base, double *nrm,
+                        unsigned long long *times, int update_x, int sms, int njobs_cap = -1) {
+  mdk::BatchDev b;
+  b.jobs = reinterpret_cast<const mdk::BatchJob *>(base + bp.off_jobs);
+  b.order = reinterpret_cast<const int *>(base + bp.off_orders) + c.order_off;
+  b.njobs = (int)c.order.size();
+  if (njobs_cap >= 0) b.njobs = std::min(b.njobs, njobs_cap);
+  b.counter = reinterpret_cast<int *>(base + 64) + ci;
+  b.ibase = reinterpret_cast<const int *>(base + bp.off_ibase);
+  b.dbase = reinterpret_cast<double *>(base + bp.off_dbase);
+  b.nrm = nrm;
+  b.times = times;
+  b.status = reinterpret_cast<int *>(base);
+  b.update_x = update_x;
+  b.grid = sms * c.cps;
+  b.threads = c.threads;
+  return b;
+}
+
+cudaError_t batch_enqueue(const BatchPlan &bp, char *base, double *nrm, unsigned long long *times, cudaStream_t s,
+                          int sms) {
+  cudaError_t e = cudaMemcpyAsync(base + bp.off_jobs, bp.pinned, bp.image_bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(base, 0, 256, s)) != cudaSuccess) return e;
+  for (size_t ci = 0; ci < bp.classes.size(); ++ci) {
+    const BatchClass &c = bp.classes[ci];
+    mdk::BatchDev b = batch_dev(bp, c, (int)ci, base, nrm, times, 1, sms);
+    if ((e = dispatch(c.K, c.P, 4, &b, s)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Picks (threads per CTA, CTAs per SM) per precision class by timing trial
+// steps that do not update x, on the first 3 x grid jobs of the class.  Only
+// shapes whose registers fit on an SM are tried.
+md_status batch_autotune(BatchPlan &bp, char *base, cudaStream_t s, int sms) {
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return MD_ERR_CUDA;
+  if (cudaMemcpyAsync(base + bp.off_jobs, bp.pinned, bp.image_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return MD_ERR_CUDA;
+  const int shapes[][2] = {{128, 1}, {128, 2}, {128, 3}, {256, 1}, {384, 1}};
+  for (size_t ci = 0; ci < bp.classes.size(); ++ci) {
+    BatchClass &c = bp.classes[ci];
+    float best = 1e30f;
+    int best_t = 128, best_cps = 2;
+    for (const auto &sh : shapes) {
+      c.threads = sh[0];
+      c.cps = sh[1];
+      if (cudaMemsetAsync(base, 0, 256, s) != cudaSuccess) return MD_ERR_CUDA;
+      mdk::BatchDev d = batch_dev(bp, c, (int)ci, base, nullptr, nullptr, 0, sms, 3 * sms * c.cps);
+      cudaEventRecord(a, s);
+      if (dispatch(c.K, c.P, 4, &d, s) != cudaSuccess) {  // shape does not fit: skip it
+        cudaGetLastError();
+        continue;
+      }
+      cudaEventRecord(b, s);
+      if (cudaEventSynchronize(b) != cudaSuccess) return MD_ERR_CUDA;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      const float per_job = ms / (float)std::max(1, d.njobs);
+      if (per_job < best) {
+        best = per_job;
+        best_t = c.threads;
+        best_cps = c.cps;
+      }
+    }
+    c.threads = best_t;
+    c.cps = best_cps;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  bp.tuned = true;
+  bp.exec_ws = nullptr;  // configuration changed: recapture any graph
   return MD_OK;
 }
 
@@ -371,6 +664,8 @@ EvalDev make_eval(const Plan &p, const md_system *s, const double *x, double *f,
   e.groups = reinterpret_cast<const int *>(base + p.off_groups);
   e.ngroups = (int)p.groups.size() / 4;
   e.contrib = reinterpret_cast<const int *>(base + p.off_contrib);
+  e.tasks0 = reinterpret_cast<const int *>(base + p.off_tasks0);
+  e.stage_off0 = p.stage_off0.data();
   return e;
 }
 
@@ -401,6 +696,33 @@ SolveDev make_solve(const SolveLayout &L, int n, int d, char *base) {
 }
 
 md_status cuda_status(cudaError_t e) { return e == cudaSuccess ? MD_OK : MD_ERR_CUDA; }
+
+// Per-device second stream (highest priority) and events for running the
+// factorisation of A_0 alongside the evaluation of the higher coefficients.
+struct DevAux {
+  std::mutex mu;
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+DevAux g_aux[64];
+
+DevAux *aux_for_current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  DevAux &a = g_aux[dev];
+  std::lock_guard<std::mutex> lk(a.mu);
+  if (!a.s2) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&a.s2, cudaStreamNonBlocking, hi) != cudaSuccess) return nullptr;
+    if (cudaEventCreateWithFlags(&a.e0, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    if (cudaEventCreateWithFlags(&a.e1, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+  }
+  return &a;
+}
+
+// SMs left to the factorisation while the evaluation runs resident.
+constexpr int kFactorSms = 12;
 
 // ------------------------------------------------------------- profiling
 // Optional per-launch timing: when enabled, every launch is bracketed by a
@@ -540,15 +862,81 @@ md_status md_newton_series_step(const md_system *sys, double *x, double *dx_norm
   double *f = reinterpret_cast<double *>(base + p->off_f);
   double *A = reinterpret_cast<double *>(base + p->off_A);
   EvalDev e = make_eval(*p, sys, x, f, A, base);
-  cudaError_t err = dispatch(p->K, p->P, 2, &e, s);
-  if (err != cudaSuccess) return MD_ERR_CUDA;
   SolveDev v = make_solve(p->sl, p->n, p->d, base);
   v.A = A;
   v.b = f;
   v.sgn = -1.0;
   v.x = x;
   v.nrm = dx_norm;
-  return cuda_status(dispatch(p->K, p->P, 3, &v, s));
+  DevAux *ax = (flags & MD_FLAG_SERIAL) ? nullptr : aux_for_current_device();
+  if (!ax) {
+    if (dispatch(p->K, p->P, 2, &e, s) != cudaSuccess) return MD_ERR_CUDA;
+    return cuda_status(dispatch(p->K, p->P, 3, &v, s));
+  }
+  // evaluation prologue and coefficient 0 (gives A_0) -> factorisation on the
+  // second stream, concurrently with the remaining products on SMs - kFactorSms
+  // resident CTAs -> degree loop once both are done
+  e.resident_ctas = std::max(1, device_sms() - kFactorSms);
+  std::lock_guard<std::mutex> lk(ax->mu);
+  if (dispatch(p->K, p->P, 5, &e, s) != cudaSuccess) return MD_ERR_CUDA;
+  if (cudaEventRecord(ax->e0, s) != cudaSuccess || cudaStreamWaitEvent(ax->s2, ax->e0, 0) != cudaSuccess)
+    return MD_ERR_CUDA;
+  if (dispatch(p->K, p->P, 7, &v, ax->s2) != cudaSuccess) return MD_ERR_CUDA;
+  if (cudaEventRecord(ax->e1, ax->s2) != cudaSuccess) return MD_ERR_CUDA;
+  if (dispatch(p->K, p->P, 6, &e, s) != cudaSuccess) return MD_ERR_CUDA;
+  if (cudaStreamWaitEvent(s, ax->e1, 0) != cudaSuccess) return MD_ERR_CUDA;
+  return cuda_status(dispatch(p->K, p->P, 8, &v, s));
+}
+
+size_t md_batched_workspace_bytes(int nsys, const md_system *sys, int flags) {
+  (void)flags;
+  BatchPlan *bp = nullptr;
+  if (batch_prepare(nsys, sys, nullptr, bp, false) != MD_OK) return 0;
+  return bp->total;
+}
+
+md_status md_newton_series_step_batched(int nsys, const md_system *sys, double *const *x, double *dx_norm,
+                                        unsigned long long *times, void *ws, size_t ws_bytes, int flags,
+                                        void *stream) {
+  if (nsys < 1 || !sys || !x) return MD_ERR_ARG;
+  for (int i = 0; i < nsys; ++i)
+    if (!x[i]) return MD_ERR_ARG;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return MD_ERR_WORKSPACE;
+  for (int i = 0; i < nsys; ++i)
+    if (sys[i].limbs > mdk::kBatchMaxLimbs) return MD_ERR_UNSUPPORTED;
+  BatchPlan *bp = nullptr;
+  md_status st = batch_prepare(nsys, sys, x, bp, true);
+  if (st != MD_OK) return st;
+  if (bp->total > ws_bytes) return MD_ERR_WORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char *base = static_cast<char *>(ws);
+  const int sms = device_sms();
+  if ((flags & MD_FLAG_AUTOTUNE) && !bp->tuned) {
+    st = batch_autotune(*bp, base, s, sms);
+    if (st != MD_OK) return st;
+  }
+  if ((flags & MD_FLAG_GRAPH) && s != nullptr) {
+    if (!bp->exec || bp->exec_ws != ws || bp->exec_nrm != dx_norm || bp->exec_times != times || bp->exec_stream != s) {
+      if (bp->exec) cudaGraphExecDestroy(bp->exec);
+      bp->exec = nullptr;
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MD_ERR_CUDA;
+      const cudaError_t e = batch_enqueue(*bp, base, dx_norm, times, s, sms);
+      if (cudaStreamEndCapture(s, &g) != cudaSuccess || e != cudaSuccess) return MD_ERR_CUDA;
+      if (cudaGraphInstantiate(&bp->exec, g, 0) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        bp->exec = nullptr;
+        return MD_ERR_CUDA;
+      }
+      cudaGraphDestroy(g);
+      bp->exec_ws = ws;
+      bp->exec_nrm = dx_norm;
+      bp->exec_times = times;
+      bp->exec_stream = s;
+    }
+    return cuda_status(cudaGraphLaunch(bp->exec, s));
+  }
+  return cuda_status(batch_enqueue(*bp, base, dx_norm, times, s, sms));
 }
 
 void md_profile_enable(int on) {

@@ -44,6 +44,9 @@ struct EvalDev {
   int nstages = 0;
   const int *scal_src = nullptr;
   int nscal = 0;
+  const int *tasks0 = nullptr;      // coefficient-0 tasks (single jobs), stage-major
+  const int *stage_off0 = nullptr;  // HOST array, nstages + 1 entries
+  int resident_ctas = 0;            // > 0: run the full stages on this many SM-filling CTAs
   const int *groups = nullptr;
   int ngroups = 0;
   const int *contrib = nullptr;
@@ -69,7 +72,7 @@ struct SolveDev {
   float *oz_C = nullptr;
 };
 
-inline void rhs_chunking(int n, int k, int &C, int &nchunk) {
+__host__ __device__ inline void rhs_chunking(int n, int k, int &C, int &nchunk) {
   const long long terms = (long long)k * n;
   if (terms == 0) {
     C = 1;
@@ -82,14 +85,52 @@ inline void rhs_chunking(int n, int k, int &C, int &nchunk) {
   nchunk = (int)((terms + c - 1) / c);
 }
 
+// Largest limb count of the batched form (larger ones use the per-system step).
+constexpr int kBatchMaxLimbs = 5;
+
+// One system of a batched step (offsets into the batch workspace).
+struct BatchJob {
+  int n, d, nstages, ngroups;
+  int nscal, nmono, nops, pad;
+  long long ops;        // ibase offset: 3 ints per product (out, a, b), stage-major
+  long long stage_off;  // ibase offset: nstages+1 product offsets
+  long long scal_src;   // ibase offset: 2 ints per scaling entry
+  long long groups;     // ibase offset: 4 ints per group (16-byte aligned)
+  long long contrib;    // ibase offset: 4 ints per contribution (16-byte aligned)
+  long long pool, scal, f, A, M, Y, W, vd, beta, rinv, r, dxw, part;  // dbase offsets (doubles)
+  const double *coef;
+  const double *cst;
+  double *x;
+};
+
+struct BatchDev {
+  const BatchJob *jobs = nullptr;
+  const int *order = nullptr;
+  int njobs = 0;
+  int *counter = nullptr;
+  const int *ibase = nullptr;
+  double *dbase = nullptr;
+  double *nrm = nullptr;
+  unsigned long long *times = nullptr;
+  int *status = nullptr;
+  int update_x = 1;
+  int grid = 1;
+  int threads = 128;
+};
+
 template <int K, int P>
 struct Impl {
+  static cudaError_t batched(const BatchDev &b, cudaStream_t s);
   static cudaError_t elementwise(int op, long long count, const double *x, const double *y, double *z,
                                  cudaStream_t s);
   static cudaError_t series_conv(int d, long long count, const double *x, const double *y, double *z,
                                  cudaStream_t s);
   static cudaError_t eval(const EvalDev &e, cudaStream_t s);
+  static cudaError_t eval0(const EvalDev &e, cudaStream_t s);      // prologue + coefficient 0 of f, A
+  static cudaError_t eval_rest(const EvalDev &e, cudaStream_t s);  // all products, coefficients >= 1
   static cudaError_t solve(const SolveDev &v, cudaStream_t s);
+  static cudaError_t factor(const SolveDev &v, cudaStream_t s);    // QR, Q^H, W = R^-1 Q^H
+  static cudaError_t degrees(const SolveDev &v, cudaStream_t s);   // degree loop and update
 };
 
 }  // namespace mdk

@@ -40,12 +40,13 @@ __device__ __forceinline__ void warp_sum(mdv<K, P> &v) {
   }
 }
 
-// Sum over the block; every thread gets the result.  smem: NT/32 values.
+// Sum over the first `active` threads of the block (all threads must call it;
+// the others contribute nothing); every thread gets the result.  smem: active/32 values.
 template <int K, int P>
-__device__ __forceinline__ void block_sum(mdv<K, P> &v, mdv<K, P> *smem) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  warp_sum<K, P>(v);
-  if (lane == 0) smem[warp] = v;
+__device__ __forceinline__ void block_sum(mdv<K, P> &v, mdv<K, P> *smem, int active) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (active + 31) >> 5;
+  if (warp < nw) warp_sum<K, P>(v);
+  if (lane == 0 && warp < nw) smem[warp] = v;
   __syncthreads();
   if (warp == 0) {
     mdv<K, P> t;
@@ -127,20 +128,24 @@ __global__ void series_conv_kernel(int d, long long count, const double *__restr
 // -------------------------------------------------------------------- eval
 // Pool of series, AoS: value (slot s, coefficient k) at pool[(s*(d+1) + k)*P*K].
 template <int K, int P>
-__global__ void pool_load_x_kernel(const double *__restrict__ x, double *__restrict__ pool, int n, int d) {
-  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (e >= (long long)n * (d + 1)) return;
+__device__ __forceinline__ void pool_load_entry(const double *x, double *pool, int n, int d,
+                                                long long e) {
   mdv<K, P> v;
   ld_soa<K, P>(x + e, (long long)n * (d + 1), v);
   st_aos<K, P>(pool + e * (P * K), v);
 }
 
+template <int K, int P>
+__global__ void pool_load_x_kernel(const double *__restrict__ x, double *__restrict__ pool, int n, int d) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)n * (d + 1)) return;
+  pool_load_entry<K, P>(x, pool, n, d, e);
+}
+
 // scal[i] = c_mono (a == 1) or c_mono * a (exponent factor of a derivative).
 template <int K, int P>
-__global__ void prep_scal_kernel(const int *__restrict__ src, int nscal, const double *__restrict__ coef, int nmono,
-                                 double *__restrict__ scal) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nscal) return;
+__device__ __forceinline__ void prep_scal_entry(const int *src, const double *coef, int nmono,
+                                                double *scal, int i) {
   const int mono = src[2 * i], a = src[2 * i + 1];
   mdv<K, P> c, z;
   ld_soa<K, P>(coef + mono, nmono, c);
@@ -151,38 +156,50 @@ __global__ void prep_scal_kernel(const int *__restrict__ src, int nscal, const d
   st_aos<K, P>(scal + (long long)i * (P * K), z);
 }
 
-// One launch per stage.  task = {outA, xA, yA, kA, outB, xB, yB, -}; kB = d - kA.
 template <int K, int P>
-__global__ void __launch_bounds__(64) conv_stage_kernel(const int *__restrict__ tasks, int ntask,
-                                                         double *pool, int d) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ntask) return;
-  const int4 t0 = __ldg(reinterpret_cast<const int4 *>(tasks) + 2 * t);
-  const int4 t1 = __ldg(reinterpret_cast<const int4 *>(tasks) + 2 * t + 1);
-  const int outA = t0.x, xA = t0.y, yA = t0.z, kA = t0.w, outB = t1.x, xB = t1.y, yB = t1.z;
+__global__ void prep_scal_kernel(const int *__restrict__ src, int nscal, const double *__restrict__ coef, int nmono,
+                                 double *__restrict__ scal) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nscal) return;
+  prep_scal_entry<K, P>(src, coef, nmono, scal, i);
+}
+
+// Two output coefficients of series products: the first job computes
+// coefficient kA of product (outA = xA * yA), the second coefficient kB of
+// (outB = xB * yB); kA + kB = d, so the loop has d+2 iterations (outB < 0: only
+// the first job).  Coefficient k is sum_{i<=k} x_i y_{k-i}, ascending i.
+// NC: read through the read-only data path (only when nothing written in the
+// same kernel is read, i.e. one stage per launch).
+template <int K, int P, bool NC = true>
+__device__ __forceinline__ void conv_pair(double *pool, int d, int outA, int xA, int yA, int kA, int outB, int xB,
+                                          int yB) {
   const int kB = d - kA;
   const long long VS = P * K, SS = (long long)(d + 1) * VS;
   const int total = (outB >= 0) ? (d + 2) : (kA + 1);
   mdv<K, P> acc, a, b, prod, na, nb;
-  // operands of iteration it: first job (it <= kA): x_it * y_{kA-it};
-  // second job: x_i * y_{kB-i} with i = it - kA - 1.
   auto addr = [&](int it, const double *&xp, const double *&yp) {
     const bool first = it <= kA;
     const int i = first ? it : it - kA - 1;
     xp = pool + (first ? xA : xB) * SS + i * VS;
     yp = pool + (first ? yA : yB) * SS + ((first ? kA : kB) - i) * VS;
   };
+  auto load = [&](const double *src, mdv<K, P> &z) {
+    if constexpr (NC)
+      ld_aos_nc<K, P>(src, z);
+    else
+      ld_aos<K, P>(src, z);
+  };
   const double *xp, *yp;
   addr(0, xp, yp);
-  ld_aos_nc<K, P>(xp, na);
-  ld_aos_nc<K, P>(yp, nb);
+  load(xp, na);
+  load(yp, nb);
   for (int it = 0; it < total; ++it) {
     a = na;
     b = nb;
     if (it + 1 < total) {
       addr(it + 1, xp, yp);
-      ld_aos_nc<K, P>(xp, na);
-      ld_aos_nc<K, P>(yp, nb);
+      load(xp, na);
+      load(yp, nb);
     }
     c_mul<K, P>(a, b, prod);
     if (it == 0 || it == kA + 1)
@@ -194,16 +211,40 @@ __global__ void __launch_bounds__(64) conv_stage_kernel(const int *__restrict__ 
   if (outB >= 0) st_aos<K, P>(pool + outB * SS + kB * VS, acc);
 }
 
+// One launch per stage.  task = {outA, xA, yA, kA, outB, xB, yB, -}.
+template <int K, int P>
+__global__ void __launch_bounds__(64) conv_stage_kernel(const int *__restrict__ tasks, int ntask,
+                                                         double *pool, int d) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntask) return;
+  const int4 t0 = __ldg(reinterpret_cast<const int4 *>(tasks) + 2 * t);
+  const int4 t1 = __ldg(reinterpret_cast<const int4 *>(tasks) + 2 * t + 1);
+  conv_pair<K, P>(pool, d, t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z);
+}
+
+// Same work with a fixed grid of kConvResidentThreads-thread CTAs that stride
+// over the tasks.  A CTA of this size fills an SM's register file, so a grid of
+// (SMs - R) CTAs occupies exactly SMs - R SMs and leaves R SMs to kernels that
+// run concurrently on another stream.
+constexpr int kConvResidentThreads = 384;
+
+template <int K, int P>
+__global__ void __launch_bounds__(kConvResidentThreads, 1)
+    conv_stage_resident_kernel(const int *__restrict__ tasks, int ntask, double *pool, int d) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntask; t += gridDim.x * blockDim.x) {
+    const int4 t0 = __ldg(reinterpret_cast<const int4 *>(tasks) + 2 * t);
+    const int4 t1 = __ldg(reinterpret_cast<const int4 *>(tasks) + 2 * t + 1);
+    conv_pair<K, P>(pool, d, t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z);
+  }
+}
+
 // group = {row, col (-1: f_row), first contribution, count};
 // contribution = {slot (-1: the unit series), scal index, shift a_t, -}.
 template <int K, int P>
-__global__ void accum_kernel(const int4 *__restrict__ groups, int ngroups, const int4 *__restrict__ contrib,
-                             const double *__restrict__ pool, const double *__restrict__ scal,
-                             const double *__restrict__ cst, double *__restrict__ f, double *__restrict__ A, int n,
-                             int d) {
-  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (e >= (long long)ngroups * (d + 1)) return;
-  const int g = (int)(e / (d + 1)), k = (int)(e % (d + 1));
+__device__ __forceinline__ void accum_entry(const int4 *groups, const int4 *contrib,
+                                            const double *pool, const double *scal,
+                                            const double *cst, double *f,
+                                            double *A, int n, int d, int g, int k) {
   const int4 G = groups[g];
   const long long VS = P * K, SS = (long long)(d + 1) * VS;
   mdv<K, P> acc, v, c, s;
@@ -231,14 +272,25 @@ __global__ void accum_kernel(const int4 *__restrict__ groups, int ngroups, const
   }
 }
 
+// Entries (group, k) for k in [k0, k0 + nk).
+template <int K, int P>
+__global__ void accum_kernel(const int4 *__restrict__ groups, int ngroups, const int4 *__restrict__ contrib,
+                             const double *__restrict__ pool, const double *__restrict__ scal,
+                             const double *__restrict__ cst, double *__restrict__ f, double *__restrict__ A, int n,
+                             int d, int k0, int nk) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)ngroups * nk) return;
+  accum_entry<K, P>(groups, contrib, pool, scal, cst, f, A, n, d, (int)(e / nk), k0 + (int)(e % nk));
+}
+
 // ------------------------------------------------------------------- solve
 // Work matrices are AoS, column-major: element (r, c) at M[(c*n + r)*P*K].
+// Every body below is shared by the one-launch-per-step kernels and by the
+// batched kernel (one CTA per system); the reduction trees are the same in both.
 template <int K, int P>
-__global__ void solve_init_kernel(const double *__restrict__ A, double *__restrict__ M, double *__restrict__ Y, int n,
-                                  int d) {
-  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void solve_init_entry(const double *A, double *M,
+                                                 double *Y, int n, int d, long long e) {
   const long long nn = (long long)n * n;
-  if (e >= nn) return;
   mdv<K, P> v;
   ld_soa<K, P>(A + e, (long long)(d + 1) * nn, v);  // A_0, column-major, e = c*n + r
   st_aos<K, P>(M + e * (P * K), v);
@@ -248,12 +300,23 @@ __global__ void solve_init_kernel(const double *__restrict__ A, double *__restri
   st_aos<K, P>(Y + e * (P * K), v);
 }
 
+template <int K, int P>
+__global__ void solve_init_kernel(const double *__restrict__ A, double *__restrict__ M, double *__restrict__ Y, int n,
+                                  int d) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  solve_init_entry<K, P>(A, M, Y, n, d, e);
+}
+
+constexpr int kHouseThreads = 128;
+
 // Householder vector of column j (Golub-Van Loan): alpha = ||x||, phase
 // e = x_0/|x_0|, v = x + e alpha e_1, beta = 1/(alpha (alpha + |x_0|)), R_jj = -e alpha.
+// Block-level body for kHouseThreads threads.
 template <int K, int P>
-__global__ void __launch_bounds__(256) house_kernel(double *__restrict__ M, double *__restrict__ vd,
-                                                    double *__restrict__ beta, int *__restrict__ status, int n, int j) {
-  __shared__ mdv<K, 1> red[8];
+__device__ __forceinline__ void house_block(double *M, double *vd,
+                                            double *beta, int *status, int n, int j) {
+  __shared__ mdv<K, 1> red[kHouseThreads / 32];
   __shared__ double s_alpha[K], s_a0[K], s_beta[K];
   __shared__ mdv<K, P> s_ph;
   const int tid = threadIdx.x;
@@ -261,7 +324,7 @@ __global__ void __launch_bounds__(256) house_kernel(double *__restrict__ M, doub
   mdv<K, 1> acc;
   c_zero<K, 1>(acc);
   bool have = false;
-  for (int i = j + tid; i < n; i += blockDim.x) {
+  for (int i = j + tid; tid < kHouseThreads && i < n; i += kHouseThreads) {
     mdv<K, P> x;
     ld_aos<K, P>(M + ((long long)j * n + i) * VS, x);
     double a2[K];
@@ -275,7 +338,7 @@ __global__ void __launch_bounds__(256) house_kernel(double *__restrict__ M, doub
       c_add<K, 1>(acc, t, acc);
     }
   }
-  block_sum<K, 1>(acc, red);
+  block_sum<K, 1>(acc, red, kHouseThreads);
   mdv<K, P> x0;
   ld_aos<K, P>(M + ((long long)j * n + j) * VS, x0);
   if (tid == 0) {
@@ -353,29 +416,36 @@ __global__ void __launch_bounds__(256) house_kernel(double *__restrict__ M, doub
 #pragma unroll
     for (int l = 0; l < K; ++l) beta[(long long)j * K + l] = s_beta[l];
   }
+  __syncthreads();
 }
 
-// Apply H_j = I - beta_j v v^H to the trailing columns of M and to all columns
-// of Y (which accumulates Q^H).  One warp per target column.
 template <int K, int P>
-__global__ void __launch_bounds__(128) house_apply_kernel(double *__restrict__ M, double *__restrict__ Y,
-                                                          const double *__restrict__ vd,
-                                                          const double *__restrict__ beta, int n, int j) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(kHouseThreads) house_kernel(double *__restrict__ M, double *__restrict__ vd,
+                                                              double *__restrict__ beta, int *__restrict__ status,
+                                                              int n, int j) {
+  house_block<K, P>(M, vd, beta, status, n, j);
+}
+
+// Apply H_j = I - beta_j v v^H to target column w: w < n-j-1 is column j+1+w of
+// M (trailing columns), otherwise column w-(n-j-1) of Y (accumulating Q^H).
+// Warp-level body.
+template <int K, int P>
+__device__ __forceinline__ void house_apply_col(double *M, double *Y,
+                                                const double *vd, const double *beta, int n,
+                                                int j, int w, int lane) {
   const int nm = n - j - 1;
-  if (warp >= nm + n) return;
   double *T;
   int c;
-  if (warp < nm) {
+  if (w < nm) {
     T = M;
-    c = j + 1 + warp;
+    c = j + 1 + w;
   } else {
     T = Y;
-    c = warp - nm;
+    c = w - nm;
   }
   const long long VS = P * K;
-  mdv<K, P> w, v, cv, t, prod;
-  c_zero<K, P>(w);
+  mdv<K, P> acc, v, cv, t, prod;
+  c_zero<K, P>(acc);
   bool have = false;
   for (int i = j + lane; i < n; i += 32) {
     if (i == j)
@@ -386,18 +456,18 @@ __global__ void __launch_bounds__(128) house_apply_kernel(double *__restrict__ M
     ld_aos<K, P>(T + ((long long)c * n + i) * VS, t);
     c_mul<K, P>(cv, t, prod);
     if (!have) {
-      w = prod;
+      acc = prod;
       have = true;
     } else {
-      c_add<K, P>(w, prod, w);
+      c_add<K, P>(acc, prod, acc);
     }
   }
-  warp_sum<K, P>(w);
+  warp_sum<K, P>(acc);
   double bt[K];
 #pragma unroll
   for (int l = 0; l < K; ++l) bt[l] = beta[(long long)j * K + l];
   mdv<K, P> tau;
-  c_mul_real<K, P>(w, bt, tau);
+  c_mul_real<K, P>(acc, bt, tau);
   for (int i = j + lane; i < n; i += 32) {
     if (i == j)
       ld_aos<K, P>(vd + (long long)j * VS, v);
@@ -410,11 +480,18 @@ __global__ void __launch_bounds__(128) house_apply_kernel(double *__restrict__ M
   }
 }
 
+template <int K, int P>
+__global__ void __launch_bounds__(128) house_apply_kernel(double *__restrict__ M, double *__restrict__ Y,
+                                                          const double *__restrict__ vd,
+                                                          const double *__restrict__ beta, int n, int j) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= (n - j - 1) + n) return;
+  house_apply_col<K, P>(M, Y, vd, beta, n, j, warp, lane);
+}
+
 // rinv[j] = 1 / R_jj
 template <int K, int P>
-__global__ void rinv_kernel(const double *__restrict__ M, double *__restrict__ rinv, int n) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
+__device__ __forceinline__ void rinv_entry(const double *M, double *rinv, int n, int j) {
   const long long VS = P * K;
   mdv<K, P> r, one, z;
   ld_aos<K, P>(M + ((long long)j * n + j) * VS, r);
@@ -424,13 +501,19 @@ __global__ void rinv_kernel(const double *__restrict__ M, double *__restrict__ r
   st_aos<K, P>(rinv + (long long)j * VS, z);
 }
 
+template <int K, int P>
+__global__ void rinv_kernel(const double *__restrict__ M, double *__restrict__ rinv, int n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  rinv_entry<K, P>(M, rinv, n, j);
+}
+
 // Column-oriented back substitution step c of R W = Y (all n right-hand sides):
 // W[c][:] = Y[c][:] / R_cc; Y[i][:] -= R_ic W[c][:] for i < c.  W is row-major.
 template <int K, int P>
-__global__ void backsub_kernel(const double *__restrict__ M, double *__restrict__ Y, double *__restrict__ W,
-                               const double *__restrict__ rinv, int n, int c) {
-  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (e >= (long long)(c + 1) * n) return;
+__device__ __forceinline__ void backsub_entry(const double *M, double *Y,
+                                              double *W, const double *rinv, int n, int c,
+                                              long long e) {
   const int i = (int)(e / n), col = (int)(e % n);
   const long long VS = P * K;
   mdv<K, P> y, ri, w;
@@ -449,14 +532,21 @@ __global__ void backsub_kernel(const double *__restrict__ M, double *__restrict_
   }
 }
 
-// Partial sums of sum_{j<k} A_{k-j} dx_j for (row, chunk); term index
+template <int K, int P>
+__global__ void backsub_kernel(const double *__restrict__ M, double *__restrict__ Y, double *__restrict__ W,
+                               const double *__restrict__ rinv, int n, int c) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)(c + 1) * n) return;
+  backsub_entry<K, P>(M, Y, W, rinv, n, c, e);
+}
+
+// Partial sums of sum_{j<k} A_{k-j} dx_j for item e = (row, chunk); term index
 // t = j*n + col over [chunk*C, min((chunk+1)*C, k*n)).  A is the caller's
 // SoA [P][K][d+1][n][n] (column-major blocks); dx is AoS [k][i].
 template <int K, int P>
-__global__ void rhs_partial_kernel(const double *__restrict__ A, const double *__restrict__ dx,
-                                   double *__restrict__ part, int n, int d, int k, int C, int nchunk) {
-  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (e >= (long long)n * nchunk) return;
+__device__ __forceinline__ void rhs_partial_item(const double *A, const double *dx,
+                                                 double *part, int n, int d, int k, int C, int nchunk,
+                                                 long long e) {
   const int row = (int)(e % n), chunk = (int)(e / n);
   const long long nn = (long long)n * n, VS = P * K, stride = (long long)(d + 1) * nn;
   const int t0 = chunk * C, t1 = min(t0 + C, k * n);
@@ -475,18 +565,24 @@ __global__ void rhs_partial_kernel(const double *__restrict__ A, const double *_
   st_aos<K, P>(part + ((long long)row * nchunk + chunk) * VS, acc);
 }
 
-// r_k[row] = sgn * b_k[row] - sum of partials.  One block per row.
 template <int K, int P>
-__global__ void __launch_bounds__(128) rhs_finish_kernel(const double *__restrict__ b, double sgn,
-                                                         const double *__restrict__ part, double *__restrict__ r,
-                                                         int n, int d, int k, int nchunk) {
-  __shared__ mdv<K, P> red[4];
-  const int row = blockIdx.x;
+__global__ void rhs_partial_kernel(const double *__restrict__ A, const double *__restrict__ dx,
+                                   double *__restrict__ part, int n, int d, int k, int C, int nchunk) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)n * nchunk) return;
+  rhs_partial_item<K, P>(A, dx, part, n, d, k, C, nchunk, e);
+}
+
+// r_k[row] = sgn * b_k[row] - sum of the row's partials.  Warp-level body.
+template <int K, int P>
+__device__ __forceinline__ void rhs_finish_row(const double *b, double sgn,
+                                               const double *part, double *r, int n, int d,
+                                               int k, int nchunk, int row, int lane) {
   const long long VS = P * K;
   mdv<K, P> acc, t;
   c_zero<K, P>(acc);
   bool have = false;
-  for (int c = threadIdx.x; c < nchunk; c += blockDim.x) {
+  for (int c = lane; c < nchunk; c += 32) {
     ld_aos<K, P>(part + ((long long)row * nchunk + c) * VS, t);
     if (!have) {
       acc = t;
@@ -495,8 +591,8 @@ __global__ void __launch_bounds__(128) rhs_finish_kernel(const double *__restric
       c_add<K, P>(acc, t, acc);
     }
   }
-  if (nchunk > 0) block_sum<K, P>(acc, red);
-  if (threadIdx.x == 0) {
+  if (nchunk > 0) warp_sum<K, P>(acc);
+  if (lane == 0) {
     mdv<K, P> bv, z;
     ld_soa<K, P>(b + (long long)row * (d + 1) + k, (long long)n * (d + 1), bv);
     if (sgn < 0.0)
@@ -510,17 +606,22 @@ __global__ void __launch_bounds__(128) rhs_finish_kernel(const double *__restric
   }
 }
 
-// dx_k[row] = sum_col W[row][col] r_k[col].  One block per row.
 template <int K, int P>
-__global__ void __launch_bounds__(128) wmv_kernel(const double *__restrict__ W, const double *__restrict__ r,
-                                                  double *__restrict__ dx, int n, int k) {
-  __shared__ mdv<K, P> red[4];
-  const int row = blockIdx.x;
+__global__ void __launch_bounds__(32) rhs_finish_kernel(const double *__restrict__ b, double sgn,
+                                                        const double *__restrict__ part, double *__restrict__ r,
+                                                        int n, int d, int k, int nchunk) {
+  rhs_finish_row<K, P>(b, sgn, part, r, n, d, k, nchunk, blockIdx.x, threadIdx.x & 31);
+}
+
+// dx_k[row] = sum_col W[row][col] r_k[col].  Warp-level body.
+template <int K, int P>
+__device__ __forceinline__ void wmv_row(const double *W, const double *r,
+                                        double *dx, int n, int k, int row, int lane) {
   const long long VS = P * K;
   mdv<K, P> acc, w, x, prod;
   c_zero<K, P>(acc);
   bool have = false;
-  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+  for (int c = lane; c < n; c += 32) {
     ld_aos<K, P>(W + ((long long)row * n + c) * VS, w);
     ld_aos<K, P>(r + ((long long)k * n + c) * VS, x);
     c_mul<K, P>(w, x, prod);
@@ -531,17 +632,22 @@ __global__ void __launch_bounds__(128) wmv_kernel(const double *__restrict__ W, 
       c_add<K, P>(acc, prod, acc);
     }
   }
-  block_sum<K, P>(acc, red);
-  if (threadIdx.x == 0) st_aos<K, P>(dx + ((long long)k * n + row) * VS, acc);
+  warp_sum<K, P>(acc);
+  if (lane == 0) st_aos<K, P>(dx + ((long long)k * n + row) * VS, acc);
+}
+
+template <int K, int P>
+__global__ void __launch_bounds__(32) wmv_kernel(const double *__restrict__ W, const double *__restrict__ r,
+                                                 double *__restrict__ dx, int n, int k) {
+  wmv_row<K, P>(W, r, dx, n, k, blockIdx.x, threadIdx.x & 31);
 }
 
 // dx (AoS [k][i]) -> SoA [P][K][n][d+1]; optionally x += dx and the norms
 // nrm[0] = max_i |dx_{d,i}|, nrm[1] = max |dx| from the leading limbs.
 template <int K, int P>
-__global__ void finish_dx_kernel(const double *__restrict__ dxw, double *__restrict__ dx_out, double *__restrict__ x,
-                                 double *__restrict__ nrm, int *__restrict__ status, int n, int d) {
-  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (e >= (long long)n * (d + 1)) return;
+__device__ __forceinline__ void finish_entry(const double *dxw, double *dx_out,
+                                             double *x, double *nrm,
+                                             int *status, int n, int d, long long e) {
   const int j = (int)(e / (d + 1)), k = (int)(e % (d + 1));
   const long long VS = P * K, stride = (long long)n * (d + 1);
   mdv<K, P> v;
@@ -569,6 +675,14 @@ __global__ void finish_dx_kernel(const double *__restrict__ dxw, double *__restr
       if (k == d) atomicMax(reinterpret_cast<unsigned long long *>(nrm), bits);
     }
   }
+}
+
+template <int K, int P>
+__global__ void finish_dx_kernel(const double *__restrict__ dxw, double *__restrict__ dx_out, double *__restrict__ x,
+                                 double *__restrict__ nrm, int *__restrict__ status, int n, int d) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)n * (d + 1)) return;
+  finish_entry<K, P>(dxw, dx_out, x, nrm, status, n, d, e);
 }
 
 }  // namespace mdk

@@ -3,6 +3,7 @@
 #include "internal.h"
 #include "kernels.cuh"
 #include "ozaki.cuh"
+#include "batched.cuh"
 
 namespace mdk {
 
@@ -39,7 +40,21 @@ cudaError_t Impl<K, P>::series_conv(int d, long long count, const double *x, con
 }
 
 template <int K, int P>
-cudaError_t Impl<K, P>::eval(const EvalDev &e, cudaStream_t s) {
+cudaError_t Impl<K, P>::batched(const BatchDev &b, cudaStream_t s) {
+  if constexpr (K > kBatchMaxLimbs) {
+    (void)b;
+    (void)s;
+    return cudaErrorNotSupported;
+  } else {
+    if (b.njobs <= 0) return cudaSuccess;
+    batched_step_kernel<K, P><<<b.grid, b.threads, 0, s>>>(b.jobs, b.order, b.njobs, b.counter, b.ibase, b.dbase,
+                                                               b.nrm, b.times, b.status, b.update_x);
+    return cudaGetLastError();
+  }
+}
+
+template <int K, int P>
+cudaError_t Impl<K, P>::eval0(const EvalDev &e, cudaStream_t s) {
   const int n = e.n, d = e.d;
   cudaError_t err;
   const long long nx = (long long)n * (d + 1);
@@ -51,27 +66,64 @@ cudaError_t Impl<K, P>::eval(const EvalDev &e, cudaStream_t s) {
     ProfScope prof(PK_SCAL, s);
     prep_scal_kernel<K, P><<<blocks_for(e.nscal, 64), 64, 0, s>>>(e.scal_src, e.nscal, e.coef, e.nmono, e.scal);
   }
-  for (int st = 0; st < e.nstages; ++st) {
-    const int t0 = e.stage_off[st], t1 = e.stage_off[st + 1];
-    if (t1 > t0) {
-      ProfScope prof(PK_CONV, s);
-      conv_stage_kernel<K, P><<<blocks_for(t1 - t0, 64), 64, 0, s>>>(e.tasks + 8LL * t0, t1 - t0, e.pool, d);
-    }
-  }
   const size_t Abytes = sizeof(double) * P * K * (size_t)(d + 1) * n * n;
   if ((err = cudaMemsetAsync(e.A, 0, Abytes, s)) != cudaSuccess) return err;
-  const long long work = (long long)e.ngroups * (d + 1);
-  if (work > 0) {
+  // coefficient 0 of every product is the single product of the inputs' coefficients 0
+  for (int st = 0; st < e.nstages; ++st) {
+    const int t0 = e.stage_off0[st], t1 = e.stage_off0[st + 1];
+    if (t1 > t0) {
+      ProfScope prof(PK_CONV, s);
+      conv_stage_kernel<K, P><<<blocks_for(t1 - t0, 64), 64, 0, s>>>(e.tasks0 + 8LL * t0, t1 - t0, e.pool, d);
+    }
+  }
+  if (e.ngroups > 0) {
     ProfScope prof(PK_ACCUM, s);
-    accum_kernel<K, P><<<blocks_for(work, 128), 128, 0, s>>>(reinterpret_cast<const int4 *>(e.groups), e.ngroups,
-                                                             reinterpret_cast<const int4 *>(e.contrib), e.pool, e.scal,
-                                                             e.cst, e.f, e.A, n, d);
+    accum_kernel<K, P><<<blocks_for(e.ngroups, 128), 128, 0, s>>>(reinterpret_cast<const int4 *>(e.groups), e.ngroups,
+                                                                  reinterpret_cast<const int4 *>(e.contrib), e.pool,
+                                                                  e.scal, e.cst, e.f, e.A, n, d, 0, 1);
   }
   return cudaGetLastError();
 }
 
 template <int K, int P>
+cudaError_t Impl<K, P>::eval_rest(const EvalDev &e, cudaStream_t s) {
+  const int n = e.n, d = e.d;
+  for (int st = 0; st < e.nstages; ++st) {
+    const int t0 = e.stage_off[st], t1 = e.stage_off[st + 1];
+    if (t1 <= t0) continue;
+    ProfScope prof(PK_CONV, s);
+    if (e.resident_ctas > 0)
+      conv_stage_resident_kernel<K, P><<<e.resident_ctas, kConvResidentThreads, 0, s>>>(e.tasks + 8LL * t0, t1 - t0,
+                                                                                        e.pool, d);
+    else
+      conv_stage_kernel<K, P><<<blocks_for(t1 - t0, 64), 64, 0, s>>>(e.tasks + 8LL * t0, t1 - t0, e.pool, d);
+  }
+  const long long work = (long long)e.ngroups * d;
+  if (work > 0) {
+    ProfScope prof(PK_ACCUM, s);
+    accum_kernel<K, P><<<blocks_for(work, 128), 128, 0, s>>>(reinterpret_cast<const int4 *>(e.groups), e.ngroups,
+                                                             reinterpret_cast<const int4 *>(e.contrib), e.pool, e.scal,
+                                                             e.cst, e.f, e.A, n, d, 1, d);
+  }
+  return cudaGetLastError();
+}
+
+template <int K, int P>
+cudaError_t Impl<K, P>::eval(const EvalDev &e, cudaStream_t s) {
+  cudaError_t err = eval0(e, s);
+  if (err != cudaSuccess) return err;
+  return eval_rest(e, s);
+}
+
+template <int K, int P>
 cudaError_t Impl<K, P>::solve(const SolveDev &v, cudaStream_t s) {
+  cudaError_t err = factor(v, s);
+  if (err != cudaSuccess) return err;
+  return degrees(v, s);
+}
+
+template <int K, int P>
+cudaError_t Impl<K, P>::factor(const SolveDev &v, cudaStream_t s) {
   const int n = v.n, d = v.d;
   const long long nn = (long long)n * n;
   {
@@ -81,7 +133,7 @@ cudaError_t Impl<K, P>::solve(const SolveDev &v, cudaStream_t s) {
   for (int j = 0; j < n; ++j) {
     {
       ProfScope prof(PK_QR_HOUSE, s);
-      house_kernel<K, P><<<1, 256, 0, s>>>(v.M, v.vd, v.beta, v.status, n, j);
+      house_kernel<K, P><<<1, kHouseThreads, 0, s>>>(v.M, v.vd, v.beta, v.status, n, j);
     }
     ProfScope prof(PK_QR_APPLY, s);
     const int ncols = (n - j - 1) + n;
@@ -95,6 +147,12 @@ cudaError_t Impl<K, P>::solve(const SolveDev &v, cudaStream_t s) {
     ProfScope prof(PK_BACKSUB, s);
     backsub_kernel<K, P><<<blocks_for((long long)(c + 1) * n, 64), 64, 0, s>>>(v.M, v.Y, v.W, v.rinv, n, c);
   }
+  return cudaGetLastError();
+}
+
+template <int K, int P>
+cudaError_t Impl<K, P>::degrees(const SolveDev &v, cudaStream_t s) {
+  const int n = v.n, d = v.d;
   constexpr int S = oz_slices(K);
   __nv_bfloat16 *As = static_cast<__nv_bfloat16 *>(v.oz_As), *Xs = static_cast<__nv_bfloat16 *>(v.oz_Xs);
   if (v.ozaki && d >= 1) {
@@ -118,7 +176,7 @@ cudaError_t Impl<K, P>::solve(const SolveDev &v, cudaStream_t s) {
                                                                                      v.sgn, v.r, n, d, k);
       }
       ProfScope prof(PK_WMV, s);
-      wmv_kernel<K, P><<<n, 128, 0, s>>>(v.W, v.r, v.dxw, n, k);
+      wmv_kernel<K, P><<<n, 32, 0, s>>>(v.W, v.r, v.dxw, n, k);
       continue;
     }
     int C, nchunk;
@@ -130,10 +188,10 @@ cudaError_t Impl<K, P>::solve(const SolveDev &v, cudaStream_t s) {
     }
     {
       ProfScope prof(PK_RHS_FINISH, s);
-      rhs_finish_kernel<K, P><<<n, 128, 0, s>>>(v.b, v.sgn, v.part, v.r, n, d, k, nchunk);
+      rhs_finish_kernel<K, P><<<n, 32, 0, s>>>(v.b, v.sgn, v.part, v.r, n, d, k, nchunk);
     }
     ProfScope prof(PK_WMV, s);
-    wmv_kernel<K, P><<<n, 128, 0, s>>>(v.W, v.r, v.dxw, n, k);
+    wmv_kernel<K, P><<<n, 32, 0, s>>>(v.W, v.r, v.dxw, n, k);
   }
   const long long nx = (long long)n * (d + 1);
   ProfScope prof(PK_FINISH, s);

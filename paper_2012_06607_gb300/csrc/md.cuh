@@ -379,7 +379,7 @@ __device__ __forceinline__ void c_div(const mdv<K, P> &a, const mdv<K, P> &b, md
 // ------------------------------------------------------ loads and stores
 // AoS value: P*K consecutive doubles, plane-major ([p][l]).
 template <int K, int P>
-__device__ __forceinline__ void ld_aos(const double *__restrict__ src, mdv<K, P> &z) {
+__device__ __forceinline__ void ld_aos(const double *src, mdv<K, P> &z) {
 #pragma unroll
   for (int p = 0; p < P; ++p)
 #pragma unroll

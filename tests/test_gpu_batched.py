@@ -1,0 +1,103 @@
+"""Batched form: many systems of uneven size and precision in one persistent
+launch per precision class.  Each system must get exactly the bits of the
+single-system step (same per-item bodies and reduction trees), with and
+without the autotuner and the CUDA graph."""
+import numpy as np
+import pytest
+
+import mdgen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def md():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2012_06607_gb300 import build
+
+    build.build()
+    import paper_2012_06607_gb300 as m
+
+    return m
+
+
+def _mixed_systems():
+    rng = np.random.default_rng(77)
+    out = []
+    for b in range(20):
+        n = int(rng.integers(3, 11))
+        d = int(rng.integers(2, 10))
+        K = [2, 4, 3, 1][b % 4]
+        out.append(mdgen.small_system_fast(rng, n, d, K, monos=n, name=f"mix{b}"))
+    out.append(mdgen.config_system(0, 2))  # the n = 3 double-double configuration
+    out.append(mdgen.random_system(9, n=5, K=2, cplx=False, d=6, monos=4, maxvars=3, maxdeg=3, coef_kind="uniform"))
+    out.append(mdgen.circle_system(4, 8))
+    return out
+
+
+def _single_steps(md, systems, steps):
+    import torch
+
+    xs, norms = [], []
+    for s in systems:
+        sd = md.DeviceSystem(s)
+        ws = md.workspace(sd.workspace_bytes())
+        x = md.to_device(s.x0)
+        nrm = torch.zeros(2, dtype=torch.float64, device="cuda")
+        for _ in range(steps):
+            md.newton_step(sd, x, ws, nrm)
+        assert md.device_status(ws) == 0
+        xs.append(x.cpu().numpy())
+        norms.append(nrm.cpu().numpy())
+    return xs, norms
+
+
+def _batched_steps(md, systems, steps, flags=0, stream=None):
+    import torch
+
+    sds = [md.DeviceSystem(s) for s in systems]
+    ws = md.workspace(md.batched_workspace_bytes(sds, flags))
+    xs = [md.to_device(s.x0) for s in systems]
+    nrm = torch.zeros((len(systems), 2), dtype=torch.float64, device="cuda")
+    times = torch.zeros((len(systems), 2), dtype=torch.int64, device="cuda")
+    for _ in range(steps):
+        md.newton_step_batched(sds, xs, ws, nrm, times, flags=flags, stream=stream)
+    torch.cuda.synchronize()
+    assert md.device_status(ws) == 0
+    return [x.cpu().numpy() for x in xs], nrm.cpu().numpy(), times.cpu().numpy()
+
+
+def test_batched_equals_single_system_steps(md):
+    systems = _mixed_systems()
+    want_x, want_n = _single_steps(md, systems, 2)
+    got_x, got_n, times = _batched_steps(md, systems, 2)
+    for i, s in enumerate(systems):
+        assert np.array_equal(got_x[i], want_x[i]), (i, s.name, s.limbs, s.n, s.degree)
+        assert np.array_equal(got_n[i], want_n[i]), (i, s.name)
+    assert (times[:, 1] >= times[:, 0]).all() and (times[:, 0] > 0).all()
+
+
+def test_batched_autotune_and_graph(md):
+    import torch
+
+    systems = _mixed_systems()[:12]
+    ref_x, ref_n, _ = _batched_steps(md, systems, 3)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        got_x, got_n, _ = _batched_steps(md, systems, 3, flags=md.FLAG_AUTOTUNE | md.FLAG_GRAPH, stream=stream)
+    for i in range(len(systems)):
+        assert np.array_equal(got_x[i], ref_x[i]), i
+        assert np.array_equal(got_n[i], ref_n[i]), i
+
+
+def test_batched_rejects_large_limbs(md):
+    s = mdgen.config_system(0, 1).with_limbs(8)
+    sd = md.DeviceSystem(s)
+    ws = md.workspace(1 << 20)
+    x = md.to_device(s.x0)
+    with pytest.raises(md.MdError) as e:
+        md.newton_step_batched([sd], [x], ws)
+    assert e.value.code == 8  # MD_ERR_UNSUPPORTED

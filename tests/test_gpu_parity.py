@@ -225,3 +225,24 @@ def test_deterministic(md):
             md.newton_step(sysd, x, ws)
         outs.append(x.cpu().numpy())
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_overlapped_step_equals_serial(md, cfg):
+    """The default step factors A_0 on a second stream while the higher
+    coefficients are evaluated; MD_FLAG_SERIAL runs every phase in order on the
+    caller's stream.  Same bits."""
+    import torch
+
+    s = mdgen.config_system(cfg, 1)
+    sysd = md.DeviceSystem(s)
+    out = []
+    for flags in (0, 8):
+        ws = md.workspace(sysd.workspace_bytes(flags))
+        x = md.to_device(s.x0)
+        nrm = torch.zeros(2, dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            md.newton_step(sysd, x, ws, nrm, flags=flags)
+        assert md.device_status(ws) == 0
+        out.append((x.cpu().numpy(), nrm.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
