@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
                                                                      unsigned long long *__restrict__ times,
                                                                      int *__restrict__ status, int update_x) {
   __shared__ int s_job;
+  __shared__ double s_row[kRowLanes][K];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NT = blockDim.x, nwarp = NT / 32;
   for (;;) {
     if (tid == 0) s_job = atomicAdd(counter, 1);
@@ -103,10 +104,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
       for (long long e = tid; e < (long long)n * nchunk; e += NT)
         rhs_partial_item<K, P>(A, dxw, part, n, d, k, C, nchunk, e);
       __syncthreads();
-      for (int row = warp; row < n; row += nwarp) rhs_finish_row<K, P>(f, -1.0, part, r, n, d, k, nchunk, row, lane);
-      __syncthreads();
-      for (int row = warp; row < n; row += nwarp) wmv_row<K, P>(W, r, dxw, n, k, row, lane);
-      __syncthreads();
+      for (int row = 0; row < n; ++row) rhs_finish_row<K, P>(f, -1.0, part, r, n, d, k, nchunk, row, s_row);
+      for (int row = 0; row < n; ++row) wmv_row<K, P>(W, r, dxw, n, k, row, s_row);
     }
     for (long long e = tid; e < (long long)n * (d + 1); e += NT)
       finish_entry<K, P>(dxw, nullptr, update_x ? J.x : nullptr, nrm ? nrm + 2 * job : nullptr, status, n, d, e);

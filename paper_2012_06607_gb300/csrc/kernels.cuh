@@ -176,7 +176,7 @@ __device__ __forceinline__ void conv_pair(double *pool, int d, int outA, int xA,
   const int kB = d - kA;
   const long long VS = P * K, SS = (long long)(d + 1) * VS;
   const int total = (outB >= 0) ? (d + 2) : (kA + 1);
-  mdv<K, P> acc, a, b, prod, na, nb;
+  mdv<K, P> acc, a, b, prod;
   auto addr = [&](int it, const double *&xp, const double *&yp) {
     const bool first = it <= kA;
     const int i = first ? it : it - kA - 1;
@@ -189,18 +189,14 @@ __device__ __forceinline__ void conv_pair(double *pool, int d, int outA, int xA,
     else
       ld_aos<K, P>(src, z);
   };
+  // No prefetch: an iteration is ~(cmul + cadd) FP64 instructions, i.e. tens of
+  // thousands of cycles of pipe time per warp, so load latency is hidden by
+  // the other resident warps; the registers go to occupancy instead.
   const double *xp, *yp;
-  addr(0, xp, yp);
-  load(xp, na);
-  load(yp, nb);
   for (int it = 0; it < total; ++it) {
-    a = na;
-    b = nb;
-    if (it + 1 < total) {
-      addr(it + 1, xp, yp);
-      load(xp, na);
-      load(yp, nb);
-    }
+    addr(it, xp, yp);
+    load(xp, a);
+    load(yp, b);
     c_mul<K, P>(a, b, prod);
     if (it == 0 || it == kA + 1)
       acc = prod;
@@ -573,73 +569,156 @@ __global__ void rhs_partial_kernel(const double *__restrict__ A, const double *_
   rhs_partial_item<K, P>(A, dx, part, n, d, k, C, nchunk, e);
 }
 
-// r_k[row] = sgn * b_k[row] - sum of the row's partials.  Warp-level body.
-template <int K, int P>
-__device__ __forceinline__ void rhs_finish_row(const double *b, double sgn,
-                                               const double *part, double *r, int n, int d,
-                                               int k, int nchunk, int row, int lane) {
-  const long long VS = P * K;
-  mdv<K, P> acc, t;
-  c_zero<K, P>(acc);
-  bool have = false;
-  for (int c = lane; c < nchunk; c += 32) {
-    ld_aos<K, P>(part + ((long long)row * nchunk + c) * VS, t);
-    if (!have) {
-      acc = t;
-      have = true;
-    } else {
-      c_add<K, P>(acc, t, acc);
-    }
-  }
-  if (nchunk > 0) warp_sum<K, P>(acc);
-  if (lane == 0) {
-    mdv<K, P> bv, z;
-    ld_soa<K, P>(b + (long long)row * (d + 1) + k, (long long)n * (d + 1), bv);
-    if (sgn < 0.0)
+// ------------------------------------------------ row reductions (CTA level)
+// The finish of r_k and the product dx_k = W r_k reduce one row at a time over
+// a fixed set of kRowLanes virtual lanes: lane v handles plane p = v / Vc
+// (P = 2: real, imaginary part) and column slot cs = v % Vc, Vc = kRowLanes / P.
+// Slot cs sums the row's items cs, cs + Vc, cs + 2 Vc, ... in ascending order;
+// the slots are then added pairwise in shared memory (slot i and slot i + s for
+// s = 1, 2, 4, ...).  The result depends on the row only, never on how many
+// threads run the virtual lanes, so the per-system kernels (one CTA of
+// kRowLanes threads per row) and the batched kernel (its CTA walks the rows)
+// produce the same bits.  An FP64 warp instruction costs the same with one or
+// 32 active lanes, so spreading a row over four warps (one per SM
+// sub-partition) and splitting complex products by plane is what shortens
+// these latency-bound steps.
+constexpr int kRowLanes = 128;
+
+template <int K>
+__device__ __forceinline__ void ld_limbs(const double *src, double (&z)[K]) {
 #pragma unroll
-      for (int p = 0; p < P; ++p) md_neg<K>(bv.v[p], bv.v[p]);
-    if (nchunk > 0)
-      c_sub<K, P>(bv, acc, z);
-    else
-      z = bv;
-    st_aos<K, P>(r + ((long long)k * n + row) * VS, z);
+  for (int l = 0; l < K; ++l) z[l] = src[l];
+}
+
+template <int K>
+__device__ __forceinline__ void st_limbs(double *dst, const double (&z)[K]) {
+#pragma unroll
+  for (int l = 0; l < K; ++l) dst[l] = z[l];
+}
+
+// Pairwise sum of the first nleaf slots of every plane; all threads call it.
+template <int K, int P>
+__device__ __forceinline__ void row_tree(double (*sm)[K], int nleaf) {
+  constexpr int Vc = kRowLanes / P;
+  for (int s = 1; s < nleaf; s <<= 1) {
+    for (int v = threadIdx.x; v < kRowLanes; v += blockDim.x) {
+      const int cs = v % Vc;
+      if ((cs & (2 * s - 1)) == 0 && cs + s < nleaf) {
+        double a[K], b[K], z[K];
+        ld_limbs<K>(sm[v], a);
+        ld_limbs<K>(sm[v + s], b);
+        md_add<K>(a, b, z);
+        st_limbs<K>(sm[v], z);
+      }
+    }
+    __syncthreads();
   }
 }
 
+// r_k[row] = sgn * b_k[row] - (sum of the row's nchunk partials).  CTA body.
 template <int K, int P>
-__global__ void __launch_bounds__(32) rhs_finish_kernel(const double *__restrict__ b, double sgn,
-                                                        const double *__restrict__ part, double *__restrict__ r,
-                                                        int n, int d, int k, int nchunk) {
-  rhs_finish_row<K, P>(b, sgn, part, r, n, d, k, nchunk, blockIdx.x, threadIdx.x & 31);
-}
-
-// dx_k[row] = sum_col W[row][col] r_k[col].  Warp-level body.
-template <int K, int P>
-__device__ __forceinline__ void wmv_row(const double *W, const double *r,
-                                        double *dx, int n, int k, int row, int lane) {
+__device__ __forceinline__ void rhs_finish_row(const double *b, double sgn, const double *part, double *r, int n,
+                                               int d, int k, int nchunk, int row, double (*sm)[K]) {
+  constexpr int Vc = kRowLanes / P;
   const long long VS = P * K;
-  mdv<K, P> acc, w, x, prod;
-  c_zero<K, P>(acc);
-  bool have = false;
-  for (int c = lane; c < n; c += 32) {
-    ld_aos<K, P>(W + ((long long)row * n + c) * VS, w);
-    ld_aos<K, P>(r + ((long long)k * n + c) * VS, x);
-    c_mul<K, P>(w, x, prod);
-    if (!have) {
-      acc = prod;
-      have = true;
-    } else {
-      c_add<K, P>(acc, prod, acc);
+  const int nleaf = min(nchunk, Vc);
+  for (int v = threadIdx.x; v < kRowLanes; v += blockDim.x) {
+    const int p = v / Vc, cs = v % Vc;
+    if (cs < nleaf) {
+      double acc[K], t[K];
+      ld_limbs<K>(part + ((long long)row * nchunk + cs) * VS + p * K, acc);
+      for (int c = cs + Vc; c < nchunk; c += Vc) {
+        ld_limbs<K>(part + ((long long)row * nchunk + c) * VS + p * K, t);
+        md_add<K>(acc, t, acc);
+      }
+      st_limbs<K>(sm[v], acc);
     }
   }
-  warp_sum<K, P>(acc);
-  if (lane == 0) st_aos<K, P>(dx + ((long long)k * n + row) * VS, acc);
+  __syncthreads();
+  row_tree<K, P>(sm, nleaf);
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    double bv[K], a[K], z[K];
+    const long long stride = (long long)n * (d + 1);
+#pragma unroll
+    for (int l = 0; l < K; ++l) bv[l] = b[(long long)row * (d + 1) + k + (long long)(p * K + l) * stride];
+    if (sgn < 0.0) md_neg<K>(bv, bv);
+    if (nleaf > 0) {
+      ld_limbs<K>(sm[p * Vc], a);
+      md_sub<K>(bv, a, z);
+    } else {
+#pragma unroll
+      for (int l = 0; l < K; ++l) z[l] = bv[l];
+    }
+    st_limbs<K>(r + ((long long)k * n + row) * VS + p * K, z);
+  }
+  __syncthreads();
 }
 
 template <int K, int P>
-__global__ void __launch_bounds__(32) wmv_kernel(const double *__restrict__ W, const double *__restrict__ r,
-                                                 double *__restrict__ dx, int n, int k) {
-  wmv_row<K, P>(W, r, dx, n, k, blockIdx.x, threadIdx.x & 31);
+__global__ void __launch_bounds__(kRowLanes) rhs_finish_kernel(const double *__restrict__ b, double sgn,
+                                                               const double *__restrict__ part,
+                                                               double *__restrict__ r, int n, int d, int k,
+                                                               int nchunk) {
+  __shared__ double sm[kRowLanes][K];
+  rhs_finish_row<K, P>(b, sgn, part, r, n, d, k, nchunk, blockIdx.x, sm);
+}
+
+// Plane p of the product w * x, computed as the complex product does it:
+// real part w_re x_re - w_im x_im, imaginary part w_re x_im + w_im x_re.
+template <int K, int P>
+__device__ __forceinline__ void plane_prod(const double *w, const double *x, int p, double (&z)[K]) {
+  if constexpr (P == 1) {
+    double a[K], c[K];
+    ld_limbs<K>(w, a);
+    ld_limbs<K>(x, c);
+    md_mul<K>(a, c, z);
+  } else {
+    double wr[K], wi[K], x1[K], x2[K], t1[K], t2[K];
+    ld_limbs<K>(w, wr);
+    ld_limbs<K>(w + K, wi);
+    ld_limbs<K>(x + (p == 0 ? 0 : K), x1);  // x_re or x_im
+    ld_limbs<K>(x + (p == 0 ? K : 0), x2);  // x_im or x_re
+    md_mul<K>(wr, x1, t1);
+    md_mul<K>(wi, x2, t2);
+    if (p == 0) md_neg<K>(t2, t2);  // a - b is a + (-b)
+    md_add<K>(t1, t2, z);
+  }
+}
+
+// dx_k[row] = sum_col W[row][col] r_k[col].  CTA body.
+template <int K, int P>
+__device__ __forceinline__ void wmv_row(const double *W, const double *r, double *dx, int n, int k, int row,
+                                        double (*sm)[K]) {
+  constexpr int Vc = kRowLanes / P;
+  const long long VS = P * K;
+  const int nleaf = min(n, Vc);
+  for (int v = threadIdx.x; v < kRowLanes; v += blockDim.x) {
+    const int p = v / Vc, cs = v % Vc;
+    if (cs < nleaf) {
+      double acc[K], t[K];
+      plane_prod<K, P>(W + ((long long)row * n + cs) * VS, r + ((long long)k * n + cs) * VS, p, acc);
+      for (int c = cs + Vc; c < n; c += Vc) {
+        plane_prod<K, P>(W + ((long long)row * n + c) * VS, r + ((long long)k * n + c) * VS, p, t);
+        md_add<K>(acc, t, acc);
+      }
+      st_limbs<K>(sm[v], acc);
+    }
+  }
+  __syncthreads();
+  row_tree<K, P>(sm, nleaf);
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    double z[K];
+    ld_limbs<K>(sm[p * Vc], z);
+    st_limbs<K>(dx + ((long long)k * n + row) * VS + p * K, z);
+  }
+  __syncthreads();
+}
+
+template <int K, int P>
+__global__ void __launch_bounds__(kRowLanes) wmv_kernel(const double *__restrict__ W, const double *__restrict__ r,
+                                                        double *__restrict__ dx, int n, int k) {
+  __shared__ double sm[kRowLanes][K];
+  wmv_row<K, P>(W, r, dx, n, k, blockIdx.x, sm);
 }
 
 // dx (AoS [k][i]) -> SoA [P][K][n][d+1]; optionally x += dx and the norms

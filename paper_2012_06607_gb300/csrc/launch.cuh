@@ -176,7 +176,7 @@ cudaError_t Impl<K, P>::degrees(const SolveDev &v, cudaStream_t s) {
                                                                                      v.sgn, v.r, n, d, k);
       }
       ProfScope prof(PK_WMV, s);
-      wmv_kernel<K, P><<<n, 32, 0, s>>>(v.W, v.r, v.dxw, n, k);
+      wmv_kernel<K, P><<<n, kRowLanes, 0, s>>>(v.W, v.r, v.dxw, n, k);
       continue;
     }
     int C, nchunk;
@@ -188,10 +188,10 @@ cudaError_t Impl<K, P>::degrees(const SolveDev &v, cudaStream_t s) {
     }
     {
       ProfScope prof(PK_RHS_FINISH, s);
-      rhs_finish_kernel<K, P><<<n, 32, 0, s>>>(v.b, v.sgn, v.part, v.r, n, d, k, nchunk);
+      rhs_finish_kernel<K, P><<<n, kRowLanes, 0, s>>>(v.b, v.sgn, v.part, v.r, n, d, k, nchunk);
     }
     ProfScope prof(PK_WMV, s);
-    wmv_kernel<K, P><<<n, 32, 0, s>>>(v.W, v.r, v.dxw, n, k);
+    wmv_kernel<K, P><<<n, kRowLanes, 0, s>>>(v.W, v.r, v.dxw, n, k);
   }
   const long long nx = (long long)n * (d + 1);
   ProfScope prof(PK_FINISH, s);

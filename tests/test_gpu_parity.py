@@ -246,3 +246,18 @@ def test_overlapped_step_equals_serial(md, cfg):
         assert md.device_status(ws) == 0
         out.append((x.cpu().numpy(), nrm.cpu().numpy()))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("K,cplx", [(3, True), (5, False), (10, True), (1, True)])
+def test_newton_other_precisions(md, orc, K, cplx):
+    """Triple, penta and deca double (and plain double): several Newton steps of
+    a random system against the oracle in the same precision."""
+    s = mdgen.random_system(40 + K, n=6, K=K, cplx=cplx, d=10, monos=5, maxvars=3, maxdeg=3,
+                            coef_kind="unit" if cplx else "uniform", name=f"k{K}")
+    worst = _newton_compare(md, orc, s, 4, 1e6)
+    assert worst <= 1e6
+
+
+def test_newton_octo_double_two_steps(md, orc):
+    """Octo double real, n = 128, d = 32: two full steps against the oracle."""
+    _newton_compare(md, orc, mdgen.config_system(2, 1), 2, 1e12)
