@@ -224,7 +224,8 @@ def run_product(args):
     s = mdgen.config_system(CFG, args.seed)
     P, K, n, d = s.planes, s.limbs, s.n, s.degree
     sysd = md.DeviceSystem(s, device=dev)
-    wsb = sysd.workspace_bytes()
+    flags = md.FLAG_OZAKI if args.update == "split" else 0
+    wsb = sysd.workspace_bytes(flags)
     ws = md.workspace(wsb, device=dev)
     x = md.to_device(s.x0, dev)
     nrm = torch.zeros(2, dtype=torch.float64, device=dev)
@@ -232,7 +233,7 @@ def run_product(args):
     stream = torch.cuda.current_stream(dev)
 
     for _ in range(args.warmup):
-        md.newton_step(sysd, x, ws, nrm)
+        md.newton_step(sysd, x, ws, nrm, flags=flags)
     torch.cuda.synchronize(dev)
     assert md.device_status(ws) == 0
 
@@ -251,7 +252,7 @@ def run_product(args):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        md.newton_step(sysd, x, ws, nrm)
+        md.newton_step(sysd, x, ws, nrm, flags=flags)
         b.record(stream)
         evs.append((a, b))
     torch.cuda.synchronize(dev)
@@ -291,10 +292,16 @@ def run_product(args):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "l2": "flushed between steps (256 MB write outside the events)",
-                       "parallelism": f"replicas x{world}", "workspace_bytes": wsb},
+                       "parallelism": f"replicas x{world}", "workspace_bytes": wsb,
+                       "update": "split-product (BF16 tensor pipe)" if flags else "md arithmetic"},
             "roofline": roofline, "gpu_launches": launches, "clocks": clk, "device_status": status,
             "kernel_ms": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
-            "wall_s_timed_region": wall, "dx_norm_last": float(nrm[0].item())}
+            "wall_s_timed_region": wall, "dx_norm_last": float(nrm[0].item()),
+            # relative to the size of the last coefficient of x (the solution series
+            # has a small radius of convergence, so its degree-d coefficients are large)
+            "dx_rel_last": float(nrm[0].item()) / max(float(torch.sqrt(x[0, 0, :, d] ** 2 + x[P - 1, 0, :, d] ** 2
+                                                                          if P == 2 else x[0, 0, :, d] ** 2).max().item()),
+                                                      1e-300)}
 
     # end to end through the C ABI with host buffers: H2D of x, step, D2H of x and norms
     xh = torch.from_numpy(s.x0.copy()).pin_memory()
@@ -307,7 +314,7 @@ def run_product(args):
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
         x.copy_(xh, non_blocking=True)
-        md.newton_step(sysd, x, ws, nrm)
+        md.newton_step(sysd, x, ws, nrm, flags=flags)
         outh.copy_(x, non_blocking=True)
         nh.copy_(nrm, non_blocking=True)
         b.record(stream)
@@ -476,6 +483,8 @@ def main():
     ap.add_argument("--form", default="plain", choices=["plain", "solve3", "batched"],
                     help="plain: the Newton-step benchmark; solve3: plain vs split-product solve; "
                          "batched: 2048-system batched step vs a per-system loop")
+    ap.add_argument("--update", default="md", choices=["md", "split"],
+                    help="block Toeplitz update of the plain form: md arithmetic or split-product")
     ap.add_argument("--batch", type=int, default=2048)
     ap.add_argument("--no-loop", action="store_true")
     args = ap.parse_args()

@@ -135,7 +135,7 @@ struct Plan {
   std::vector<int> op_stage_off;  // nstages + 1 product offsets
   // workspace offsets (bytes)
   size_t off_pool = 0, off_scal = 0, off_tasks = 0, off_scalsrc = 0, off_groups = 0, off_contrib = 0, off_tasks0 = 0;
-  size_t off_f = 0, off_A = 0, off_solve = 0, total = 0;
+  size_t off_f = 0, off_A = 0, off_prod = 0, off_solve = 0, total = 0;
   SolveLayout sl{};
   uint64_t checksum = 0;
 };
@@ -321,6 +321,7 @@ md_status build_plan(const md_system *s, Plan &p, int flags = 0) {
   p.off_tasks0 = o; o = align256(o + sizeof(int) * std::max<size_t>(p.tasks0.size(), 8));
   p.off_f = o; o = align256(o + (size_t)n * (d + 1) * VS);
   p.off_A = o; o = align256(o + (size_t)(d + 1) * n * n * VS);
+  p.off_prod = o; o = align256(o + (p.contrib.size() / 4) * (size_t)(d + 1) * VS);
   p.off_solve = o;
   p.sl = solve_layout(p.K, p.P, n, d, o, flags);
   p.total = o + p.sl.bytes;
@@ -568,6 +569,15 @@ int device_sms() {
   return sms > 0 ? sms : 152;
 }
 
+// Largest dynamic shared memory one CTA may opt into (0 if unknown).
+int device_smem_optin() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return 0;
+  return v;
+}
+
 mdk::BatchDev batch_dev(const BatchPlan &bp, const BatchClass &c, int ci, char *base, double *nrm,
                         unsigned long long *times, int update_x, int sms, int njobs_cap = -1) {
   mdk::BatchDev b;
@@ -664,6 +674,8 @@ EvalDev make_eval(const Plan &p, const md_system *s, const double *x, double *f,
   e.groups = reinterpret_cast<const int *>(base + p.off_groups);
   e.ngroups = (int)p.groups.size() / 4;
   e.contrib = reinterpret_cast<const int *>(base + p.off_contrib);
+  e.ncontrib = (int)p.contrib.size() / 4;
+  e.prod = reinterpret_cast<double *>(base + p.off_prod);
   e.tasks0 = reinterpret_cast<const int *>(base + p.off_tasks0);
   e.stage_off0 = p.stage_off0.data();
   return e;
@@ -722,7 +734,10 @@ DevAux *aux_for_current_device() {
 }
 
 // SMs left to the factorisation while the evaluation runs resident.
-constexpr int kFactorSms = 12;
+#ifndef MDK_FACTOR_SMS
+#define MDK_FACTOR_SMS 10
+#endif
+constexpr int kFactorSms = MDK_FACTOR_SMS;
 
 // ------------------------------------------------------------- profiling
 // Optional per-launch timing: when enabled, every launch is bracketed by a
@@ -877,6 +892,7 @@ md_status md_newton_series_step(const md_system *sys, double *x, double *dx_norm
   // second stream, concurrently with the remaining products on SMs - kFactorSms
   // resident CTAs -> degree loop once both are done
   e.resident_ctas = std::max(1, device_sms() - kFactorSms);
+  e.resident_smem = device_smem_optin();
   std::lock_guard<std::mutex> lk(ax->mu);
   if (dispatch(p->K, p->P, 5, &e, s) != cudaSuccess) return MD_ERR_CUDA;
   if (cudaEventRecord(ax->e0, s) != cudaSuccess || cudaStreamWaitEvent(ax->s2, ax->e0, 0) != cudaSuccess)

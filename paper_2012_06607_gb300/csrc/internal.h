@@ -47,9 +47,12 @@ struct EvalDev {
   const int *tasks0 = nullptr;      // coefficient-0 tasks (single jobs), stage-major
   const int *stage_off0 = nullptr;  // HOST array, nstages + 1 entries
   int resident_ctas = 0;            // > 0: run the full stages on this many SM-filling CTAs
+  int resident_smem = 0;            // dynamic shared memory those CTAs reserve (keeps other CTAs off their SMs)
   const int *groups = nullptr;
   int ngroups = 0;
   const int *contrib = nullptr;
+  int ncontrib = 0;
+  double *prod = nullptr;  // contribution values, AoS [ncontrib][d+1]
 };
 
 struct SolveDev {

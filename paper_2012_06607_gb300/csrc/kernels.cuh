@@ -236,30 +236,28 @@ __global__ void __launch_bounds__(kConvResidentThreads, 1)
 
 // group = {row, col (-1: f_row), first contribution, count};
 // contribution = {slot (-1: the unit series), scal index, shift a_t, -}.
+// Coefficient k of one contribution: c * s_{k - a} for a product slot s, c at
+// k = a for the unit series, zero for k < a.
 template <int K, int P>
-__device__ __forceinline__ void accum_entry(const int4 *groups, const int4 *contrib,
-                                            const double *pool, const double *scal,
-                                            const double *cst, double *f,
-                                            double *A, int n, int d, int g, int k) {
-  const int4 G = groups[g];
+__device__ __forceinline__ void accum_contrib_value(const int4 C, const double *pool, const double *scal, int d, int k,
+                                                    mdv<K, P> &v) {
   const long long VS = P * K, SS = (long long)(d + 1) * VS;
-  mdv<K, P> acc, v, c, s;
-  c_zero<K, P>(acc);
-  if (G.y < 0 && k == 0) ld_soa<K, P>(cst + G.x, n, acc);
-  for (int q = 0; q < G.w; ++q) {
-    const int4 C = contrib[G.z + q];
-    c_zero<K, P>(v);
-    if (k >= C.z) {
-      ld_aos<K, P>(scal + (long long)C.y * VS, c);
-      if (C.x < 0) {
-        if (k == C.z) v = c;
-      } else {
-        ld_aos<K, P>(pool + C.x * SS + (k - C.z) * VS, s);
-        c_mul<K, P>(c, s, v);
-      }
+  mdv<K, P> c, s;
+  c_zero<K, P>(v);
+  if (k >= C.z) {
+    ld_aos<K, P>(scal + (long long)C.y * VS, c);
+    if (C.x < 0) {
+      if (k == C.z) v = c;
+    } else {
+      ld_aos<K, P>(pool + C.x * SS + (k - C.z) * VS, s);
+      c_mul<K, P>(c, s, v);
     }
-    c_add<K, P>(acc, v, acc);
   }
+}
+
+template <int K, int P>
+__device__ __forceinline__ void accum_store(const int4 G, const mdv<K, P> &acc, double *f, double *A, int n, int d,
+                                            int k) {
   if (G.y < 0) {
     st_soa<K, P>(f + (long long)G.x * (d + 1) + k, (long long)n * (d + 1), acc);
   } else {
@@ -268,15 +266,73 @@ __device__ __forceinline__ void accum_entry(const int4 *groups, const int4 *cont
   }
 }
 
-// Entries (group, k) for k in [k0, k0 + nk).
+// Coefficient k of one group: the constant term (f rows, k = 0), then the
+// contributions added one by one in list order.
+template <int K, int P>
+__device__ __forceinline__ void accum_entry(const int4 *groups, const int4 *contrib,
+                                            const double *pool, const double *scal,
+                                            const double *cst, double *f,
+                                            double *A, int n, int d, int g, int k) {
+  const int4 G = groups[g];
+  mdv<K, P> acc, v;
+  c_zero<K, P>(acc);
+  if (G.y < 0 && k == 0) ld_soa<K, P>(cst + G.x, n, acc);
+  for (int q = 0; q < G.w; ++q) {
+    accum_contrib_value<K, P>(contrib[G.z + q], pool, scal, d, k, v);
+    c_add<K, P>(acc, v, acc);
+  }
+  accum_store<K, P>(G, acc, f, A, n, d, k);
+}
+
+// Entries (group, k) for k in [k0, k0 + nk); only_A: skip the f rows.
 template <int K, int P>
 __global__ void accum_kernel(const int4 *__restrict__ groups, int ngroups, const int4 *__restrict__ contrib,
                              const double *__restrict__ pool, const double *__restrict__ scal,
                              const double *__restrict__ cst, double *__restrict__ f, double *__restrict__ A, int n,
-                             int d, int k0, int nk) {
+                             int d, int k0, int nk, int only_A) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= (long long)ngroups * nk) return;
-  accum_entry<K, P>(groups, contrib, pool, scal, cst, f, A, n, d, (int)(e / nk), k0 + (int)(e % nk));
+  const int g = (int)(e / nk);
+  if (only_A && groups[g].y < 0) return;
+  accum_entry<K, P>(groups, contrib, pool, scal, cst, f, A, n, d, g, k0 + (int)(e % nk));
+}
+
+// The same accumulation in two passes, so that long groups (the f rows sum
+// one contribution per monomial) do not serialise the products: every
+// contribution value goes to prod (AoS [contribution][k]), then each entry
+// adds its group's values in the same order as accum_entry, which makes the
+// result bit-identical to it.
+template <int K, int P>
+__global__ void accum_prod_kernel(const int4 *__restrict__ contrib, int ncontrib, const double *__restrict__ pool,
+                                  const double *__restrict__ scal, double *__restrict__ prod, int d) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)ncontrib * (d + 1)) return;
+  const int q = (int)(e / (d + 1)), k = (int)(e % (d + 1));
+  mdv<K, P> v;
+  accum_contrib_value<K, P>(contrib[q], pool, scal, d, k, v);
+  st_aos<K, P>(prod + e * (P * K), v);
+}
+
+// Entries (group, k), k in [0, d]; the A groups at k = 0 are skipped when
+// skip_A0 is set (coefficient 0 of A is accumulated beforehand).
+template <int K, int P>
+__global__ void accum_sum_kernel(const int4 *__restrict__ groups, int ngroups, const double *__restrict__ prod,
+                                 const double *__restrict__ cst, double *__restrict__ f, double *__restrict__ A,
+                                 int n, int d, int skip_A0) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)ngroups * (d + 1)) return;
+  const int g = (int)(e / (d + 1)), k = (int)(e % (d + 1));
+  const int4 G = groups[g];
+  if (skip_A0 && k == 0 && G.y >= 0) return;
+  const long long VS = P * K;
+  mdv<K, P> acc, v;
+  c_zero<K, P>(acc);
+  if (G.y < 0 && k == 0) ld_soa<K, P>(cst + G.x, n, acc);
+  for (int q = 0; q < G.w; ++q) {
+    ld_aos<K, P>(prod + ((long long)(G.z + q) * (d + 1) + k) * VS, v);
+    c_add<K, P>(acc, v, acc);
+  }
+  accum_store<K, P>(G, acc, f, A, n, d, k);
 }
 
 // ------------------------------------------------------------------- solve

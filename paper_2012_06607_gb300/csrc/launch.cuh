@@ -76,11 +76,12 @@ cudaError_t Impl<K, P>::eval0(const EvalDev &e, cudaStream_t s) {
       conv_stage_kernel<K, P><<<blocks_for(t1 - t0, 64), 64, 0, s>>>(e.tasks0 + 8LL * t0, t1 - t0, e.pool, d);
     }
   }
+  // coefficient 0 of A (what the factorisation of A_0 needs); f_0 comes with the rest
   if (e.ngroups > 0) {
     ProfScope prof(PK_ACCUM, s);
     accum_kernel<K, P><<<blocks_for(e.ngroups, 128), 128, 0, s>>>(reinterpret_cast<const int4 *>(e.groups), e.ngroups,
                                                                   reinterpret_cast<const int4 *>(e.contrib), e.pool,
-                                                                  e.scal, e.cst, e.f, e.A, n, d, 0, 1);
+                                                                  e.scal, e.cst, e.f, e.A, n, d, 0, 1, 1);
   }
   return cudaGetLastError();
 }
@@ -92,18 +93,34 @@ cudaError_t Impl<K, P>::eval_rest(const EvalDev &e, cudaStream_t s) {
     const int t0 = e.stage_off[st], t1 = e.stage_off[st + 1];
     if (t1 <= t0) continue;
     ProfScope prof(PK_CONV, s);
-    if (e.resident_ctas > 0)
-      conv_stage_resident_kernel<K, P><<<e.resident_ctas, kConvResidentThreads, 0, s>>>(e.tasks + 8LL * t0, t1 - t0,
-                                                                                        e.pool, d);
-    else
+    if (e.resident_ctas > 0) {
+      // The CTAs reserve all the shared memory an SM offers (the kernel does
+      // not use it), so that kernels on the other stream cannot share their
+      // SMs and stay on the SMs left free.
+      int smem = e.resident_smem;
+      if (smem > 0 &&
+          cudaFuncSetAttribute(conv_stage_resident_kernel<K, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+              cudaSuccess) {
+        (void)cudaGetLastError();
+        smem = 0;
+      }
+      conv_stage_resident_kernel<K, P><<<e.resident_ctas, kConvResidentThreads, smem, s>>>(e.tasks + 8LL * t0,
+                                                                                           t1 - t0, e.pool, d);
+    } else {
       conv_stage_kernel<K, P><<<blocks_for(t1 - t0, 64), 64, 0, s>>>(e.tasks + 8LL * t0, t1 - t0, e.pool, d);
+    }
   }
-  const long long work = (long long)e.ngroups * d;
-  if (work > 0) {
+  if (e.ncontrib > 0) {
     ProfScope prof(PK_ACCUM, s);
-    accum_kernel<K, P><<<blocks_for(work, 128), 128, 0, s>>>(reinterpret_cast<const int4 *>(e.groups), e.ngroups,
-                                                             reinterpret_cast<const int4 *>(e.contrib), e.pool, e.scal,
-                                                             e.cst, e.f, e.A, n, d, 1, d);
+    const long long work = (long long)e.ncontrib * (d + 1);
+    accum_prod_kernel<K, P><<<blocks_for(work, 128), 128, 0, s>>>(reinterpret_cast<const int4 *>(e.contrib),
+                                                                  e.ncontrib, e.pool, e.scal, e.prod, d);
+  }
+  if (e.ngroups > 0) {
+    ProfScope prof(PK_ACCUM, s);
+    const long long work = (long long)e.ngroups * (d + 1);
+    accum_sum_kernel<K, P><<<blocks_for(work, 128), 128, 0, s>>>(reinterpret_cast<const int4 *>(e.groups),
+                                                                 e.ngroups, e.prod, e.cst, e.f, e.A, n, d, 1);
   }
   return cudaGetLastError();
 }
