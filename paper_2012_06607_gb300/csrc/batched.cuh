@@ -87,10 +87,17 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
     double *r = dbase + J.r, *dxw = dbase + J.dxw, *part = dbase + J.part;
     for (long long e = tid; e < (long long)n * n; e += NT) solve_init_entry<K, P>(A, M, Y, n, d, e);
     __syncthreads();
+    // QR in the order of the lookahead form (same arithmetic per column): H_j
+    // on column j+1 by the whole CTA, on the other targets by warps, then the
+    // Householder vector of column j+1
+    house_block<K, P>(M, vd, beta, status, n, 0);
     for (int j = 0; j < n; ++j) {
-      house_block<K, P>(M, vd, beta, status, n, j);
-      for (int w = warp; w < (n - j - 1) + n; w += nwarp) house_apply_col<K, P>(M, Y, vd, beta, n, j, w, lane);
+      const bool ahead = j + 1 < n;
+      if (ahead) house_apply_col_cta<K, P>(M, Y, vd, beta, n, j, 0, s_row);
+      for (int w = warp + (ahead ? 1 : 0); w < (n - j - 1) + n; w += nwarp)
+        house_apply_col<K, P>(M, Y, vd, beta, n, j, w, lane);
       __syncthreads();
+      if (ahead) house_block<K, P>(M, vd, beta, status, n, j + 1);
     }
     for (int j = tid; j < n; j += NT) rinv_entry<K, P>(M, rinv, n, j);
     __syncthreads();

@@ -735,7 +735,7 @@ DevAux *aux_for_current_device() {
 
 // SMs left to the factorisation while the evaluation runs resident.
 #ifndef MDK_FACTOR_SMS
-#define MDK_FACTOR_SMS 10
+#define MDK_FACTOR_SMS 6
 #endif
 constexpr int kFactorSms = MDK_FACTOR_SMS;
 

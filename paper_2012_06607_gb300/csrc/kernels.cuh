@@ -69,6 +69,81 @@ __device__ __forceinline__ void block_sum(mdv<K, P> &v, mdv<K, P> *smem, int act
   __syncthreads();
 }
 
+// ------------------------------------------------ row reductions (CTA level)
+// The finish of r_k and the product dx_k = W r_k reduce one row at a time over
+// a fixed set of kRowLanes virtual lanes: lane v handles plane p = v / Vc
+// (P = 2: real, imaginary part) and column slot cs = v % Vc, Vc = kRowLanes / P.
+// Slot cs sums the row's items cs, cs + Vc, cs + 2 Vc, ... in ascending order;
+// the slots are then added pairwise in shared memory (slot i and slot i + s for
+// s = 1, 2, 4, ...).  The result depends on the row only, never on how many
+// threads run the virtual lanes, so the per-system kernels (one CTA of
+// kRowLanes threads per row) and the batched kernel (its CTA walks the rows)
+// produce the same bits.  An FP64 warp instruction costs the same with one or
+// 32 active lanes, so spreading a row over four warps (one per SM
+// sub-partition) and splitting complex products by plane is what shortens
+// these latency-bound steps.
+constexpr int kRowLanes = 128;
+
+template <int K>
+__device__ __forceinline__ void ld_limbs(const double *src, double (&z)[K]) {
+#pragma unroll
+  for (int l = 0; l < K; ++l) z[l] = src[l];
+}
+
+template <int K>
+__device__ __forceinline__ void st_limbs(double *dst, const double (&z)[K]) {
+#pragma unroll
+  for (int l = 0; l < K; ++l) dst[l] = z[l];
+}
+
+// Pairwise sum of the first nleaf slots of every plane; all threads call it.
+template <int K, int P>
+__device__ __forceinline__ void row_tree(double (*sm)[K], int nleaf) {
+  constexpr int Vc = kRowLanes / P;
+  for (int s = 1; s < nleaf; s <<= 1) {
+    for (int v = threadIdx.x; v < kRowLanes; v += blockDim.x) {
+      const int cs = v % Vc;
+      if ((cs & (2 * s - 1)) == 0 && cs + s < nleaf) {
+        double a[K], b[K], z[K];
+        ld_limbs<K>(sm[v], a);
+        ld_limbs<K>(sm[v + s], b);
+        md_add<K>(a, b, z);
+        st_limbs<K>(sm[v], z);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Plane p of the product a * b, computed as the complex product does it:
+// real part a_re b_re - a_im b_im, imaginary part a_re b_im + a_im b_re.
+template <int K, int P>
+__device__ __forceinline__ void plane_prod_v(const mdv<K, P> &a, const mdv<K, P> &b, int p, double (&z)[K]) {
+  if constexpr (P == 1) {
+    md_mul<K>(a.v[0], b.v[0], z);
+  } else {
+    double b1[K], b2[K], t1[K], t2[K];
+#pragma unroll
+    for (int l = 0; l < K; ++l) {
+      b1[l] = p == 0 ? b.v[0][l] : b.v[1][l];  // b_re or b_im
+      b2[l] = p == 0 ? b.v[1][l] : b.v[0][l];  // b_im or b_re
+    }
+    md_mul<K>(a.v[0], b1, t1);
+    md_mul<K>(a.v[1], b2, t2);
+    if (p == 0) md_neg<K>(t2, t2);  // a - b is a + (-b)
+    md_add<K>(t1, t2, z);
+  }
+}
+
+template <int K, int P>
+__device__ __forceinline__ void plane_prod(const double *w, const double *x, int p, double (&z)[K]) {
+  mdv<K, P> a, b;
+  ld_aos<K, P>(w, a);
+  ld_aos<K, P>(x, b);
+  plane_prod_v<K, P>(a, b, p, z);
+}
+
+
 template <int K>
 __device__ __forceinline__ void real_to(const double (&r)[K], mdv<K, 1> &z) {
 #pragma unroll
@@ -218,16 +293,18 @@ __global__ void __launch_bounds__(64) conv_stage_kernel(const int *__restrict__ 
   conv_pair<K, P>(pool, d, t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z);
 }
 
-// Same work with a fixed grid of kConvResidentThreads-thread CTAs that stride
-// over the tasks.  A CTA of this size fills an SM's register file, so a grid of
-// (SMs - R) CTAs occupies exactly SMs - R SMs and leaves R SMs to kernels that
-// run concurrently on another stream.
+// Same work with a fixed grid of kConvResidentThreads-thread CTAs (one per SM)
+// that stride over the tasks, so that a grid of SMs - R CTAs leaves R SMs to
+// kernels that run concurrently on another stream.  Thread numbering is
+// interleaved across CTAs (t = tid * grid + cta): all tasks cost the same, and
+// the last, partial round of tasks is then spread over every SM instead of
+// going whole to the first CTAs, so the SMs end together.
 constexpr int kConvResidentThreads = 384;
 
 template <int K, int P>
 __global__ void __launch_bounds__(kConvResidentThreads, 1)
     conv_stage_resident_kernel(const int *__restrict__ tasks, int ntask, double *pool, int d) {
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntask; t += gridDim.x * blockDim.x) {
+  for (int t = threadIdx.x * gridDim.x + blockIdx.x; t < ntask; t += gridDim.x * blockDim.x) {
     const int4 t0 = __ldg(reinterpret_cast<const int4 *>(tasks) + 2 * t);
     const int4 t1 = __ldg(reinterpret_cast<const int4 *>(tasks) + 2 * t + 1);
     conv_pair<K, P>(pool, d, t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z);
@@ -541,6 +618,99 @@ __global__ void __launch_bounds__(128) house_apply_kernel(double *__restrict__ M
   house_apply_col<K, P>(M, Y, vd, beta, n, j, warp, lane);
 }
 
+// The same application by a whole CTA over kRowLanes virtual lanes (plane,
+// row slot): plane products of conj(v_i) t_i summed per plane with the
+// shared-memory tree, tau = beta * dot, then t_i -= tau v_i plane by plane
+// (each element updated exactly as in house_apply_col).  CTA body.
+template <int K, int P>
+__device__ __forceinline__ void house_apply_col_cta(double *M, double *Y, const double *vd, const double *beta, int n,
+                                                    int j, int w, double (*sm)[K]) {
+  constexpr int Vc = kRowLanes / P;
+  const int nm = n - j - 1;
+  double *T = (w < nm) ? M : Y;
+  const int c = (w < nm) ? j + 1 + w : w - nm;
+  const long long VS = P * K;
+  const int nleaf = min(n - j, Vc);
+  auto ld_v = [&](int i, mdv<K, P> &v) {
+    if (i == j)
+      ld_aos<K, P>(vd + (long long)j * VS, v);
+    else
+      ld_aos<K, P>(M + ((long long)j * n + i) * VS, v);
+  };
+  for (int q = threadIdx.x; q < kRowLanes; q += blockDim.x) {
+    const int p = q / Vc, cs = q % Vc;
+    if (cs < nleaf) {
+      double acc[K], t[K];
+      bool have = false;
+      for (int i = j + cs; i < n; i += Vc) {
+        mdv<K, P> v, cv, x;
+        ld_v(i, v);
+        c_conj<K, P>(v, cv);
+        ld_aos<K, P>(T + ((long long)c * n + i) * VS, x);
+        if (!have) {
+          plane_prod_v<K, P>(cv, x, p, acc);
+          have = true;
+        } else {
+          plane_prod_v<K, P>(cv, x, p, t);
+          md_add<K>(acc, t, acc);
+        }
+      }
+      st_limbs<K>(sm[q], acc);
+    }
+  }
+  __syncthreads();
+  row_tree<K, P>(sm, nleaf);
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    double dt[K], bt[K], z[K];
+    ld_limbs<K>(sm[p * Vc], dt);
+    ld_limbs<K>(beta + (long long)j * K, bt);
+    md_mul<K>(dt, bt, z);
+    st_limbs<K>(sm[p * Vc], z);
+  }
+  __syncthreads();
+  mdv<K, P> tau;
+#pragma unroll
+  for (int p = 0; p < P; ++p) ld_limbs<K>(sm[p * Vc], tau.v[p]);
+  for (int q = threadIdx.x; q < kRowLanes; q += blockDim.x) {
+    const int p = q / Vc, cs = q % Vc;
+    for (int i = j + cs; i < n; i += Vc) {
+      mdv<K, P> v;
+      ld_v(i, v);
+      double pr[K], t[K];
+      plane_prod_v<K, P>(tau, v, p, pr);
+      double *dst = T + ((long long)c * n + i) * VS + p * K;
+      ld_limbs<K>(dst, t);
+      md_sub<K>(t, pr, t);
+      st_limbs<K>(dst, t);
+    }
+  }
+  __syncthreads();
+}
+
+// One step of the QR with lookahead: CTA 0 applies H_j to column j+1 and then
+// builds the Householder vector of column j+1, while the other CTAs apply H_j
+// to columns j+2.. of M and to Y (one warp per column).  The next step needs
+// both, and column j+1 is touched by CTA 0 only, so the step's critical path is
+// the larger of (column j+1 + Householder vector) and the rest of the update,
+// not their sum.
+template <int K, int P>
+__global__ void __launch_bounds__(kHouseThreads) house_step_kernel(double *M, double *Y, double *vd, double *beta,
+                                                                   int *status, int n, int j) {
+  __shared__ double sm[kRowLanes][K];
+  const bool ahead = j + 1 < n;
+  if (blockIdx.x == 0) {
+    if (ahead) {
+      house_apply_col_cta<K, P>(M, Y, vd, beta, n, j, 0, sm);
+      house_block<K, P>(M, vd, beta, status, n, j + 1);
+    }
+    return;
+  }
+  const int warp = ((blockIdx.x - 1) * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int w = warp + (ahead ? 1 : 0);
+  if (w >= (n - j - 1) + n) return;
+  house_apply_col<K, P>(M, Y, vd, beta, n, j, w, lane);
+}
+
 // rinv[j] = 1 / R_jj
 template <int K, int P>
 __device__ __forceinline__ void rinv_entry(const double *M, double *rinv, int n, int j) {
@@ -625,52 +795,6 @@ __global__ void rhs_partial_kernel(const double *__restrict__ A, const double *_
   rhs_partial_item<K, P>(A, dx, part, n, d, k, C, nchunk, e);
 }
 
-// ------------------------------------------------ row reductions (CTA level)
-// The finish of r_k and the product dx_k = W r_k reduce one row at a time over
-// a fixed set of kRowLanes virtual lanes: lane v handles plane p = v / Vc
-// (P = 2: real, imaginary part) and column slot cs = v % Vc, Vc = kRowLanes / P.
-// Slot cs sums the row's items cs, cs + Vc, cs + 2 Vc, ... in ascending order;
-// the slots are then added pairwise in shared memory (slot i and slot i + s for
-// s = 1, 2, 4, ...).  The result depends on the row only, never on how many
-// threads run the virtual lanes, so the per-system kernels (one CTA of
-// kRowLanes threads per row) and the batched kernel (its CTA walks the rows)
-// produce the same bits.  An FP64 warp instruction costs the same with one or
-// 32 active lanes, so spreading a row over four warps (one per SM
-// sub-partition) and splitting complex products by plane is what shortens
-// these latency-bound steps.
-constexpr int kRowLanes = 128;
-
-template <int K>
-__device__ __forceinline__ void ld_limbs(const double *src, double (&z)[K]) {
-#pragma unroll
-  for (int l = 0; l < K; ++l) z[l] = src[l];
-}
-
-template <int K>
-__device__ __forceinline__ void st_limbs(double *dst, const double (&z)[K]) {
-#pragma unroll
-  for (int l = 0; l < K; ++l) dst[l] = z[l];
-}
-
-// Pairwise sum of the first nleaf slots of every plane; all threads call it.
-template <int K, int P>
-__device__ __forceinline__ void row_tree(double (*sm)[K], int nleaf) {
-  constexpr int Vc = kRowLanes / P;
-  for (int s = 1; s < nleaf; s <<= 1) {
-    for (int v = threadIdx.x; v < kRowLanes; v += blockDim.x) {
-      const int cs = v % Vc;
-      if ((cs & (2 * s - 1)) == 0 && cs + s < nleaf) {
-        double a[K], b[K], z[K];
-        ld_limbs<K>(sm[v], a);
-        ld_limbs<K>(sm[v + s], b);
-        md_add<K>(a, b, z);
-        st_limbs<K>(sm[v], z);
-      }
-    }
-    __syncthreads();
-  }
-}
-
 // r_k[row] = sgn * b_k[row] - (sum of the row's nchunk partials).  CTA body.
 template <int K, int P>
 __device__ __forceinline__ void rhs_finish_row(const double *b, double sgn, const double *part, double *r, int n,
@@ -717,28 +841,6 @@ __global__ void __launch_bounds__(kRowLanes) rhs_finish_kernel(const double *__r
                                                                int nchunk) {
   __shared__ double sm[kRowLanes][K];
   rhs_finish_row<K, P>(b, sgn, part, r, n, d, k, nchunk, blockIdx.x, sm);
-}
-
-// Plane p of the product w * x, computed as the complex product does it:
-// real part w_re x_re - w_im x_im, imaginary part w_re x_im + w_im x_re.
-template <int K, int P>
-__device__ __forceinline__ void plane_prod(const double *w, const double *x, int p, double (&z)[K]) {
-  if constexpr (P == 1) {
-    double a[K], c[K];
-    ld_limbs<K>(w, a);
-    ld_limbs<K>(x, c);
-    md_mul<K>(a, c, z);
-  } else {
-    double wr[K], wi[K], x1[K], x2[K], t1[K], t2[K];
-    ld_limbs<K>(w, wr);
-    ld_limbs<K>(w + K, wi);
-    ld_limbs<K>(x + (p == 0 ? 0 : K), x1);  // x_re or x_im
-    ld_limbs<K>(x + (p == 0 ? K : 0), x2);  // x_im or x_re
-    md_mul<K>(wr, x1, t1);
-    md_mul<K>(wi, x2, t2);
-    if (p == 0) md_neg<K>(t2, t2);  // a - b is a + (-b)
-    md_add<K>(t1, t2, z);
-  }
 }
 
 // dx_k[row] = sum_col W[row][col] r_k[col].  CTA body.

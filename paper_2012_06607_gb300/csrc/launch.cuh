@@ -147,14 +147,16 @@ cudaError_t Impl<K, P>::factor(const SolveDev &v, cudaStream_t s) {
     ProfScope prof(PK_QR_HOUSE, s);
     solve_init_kernel<K, P><<<blocks_for(nn, 128), 128, 0, s>>>(v.A, v.M, v.Y, n, d);
   }
+  {
+    ProfScope prof(PK_QR_HOUSE, s);
+    house_kernel<K, P><<<1, kHouseThreads, 0, s>>>(v.M, v.vd, v.beta, v.status, n, 0);
+  }
   for (int j = 0; j < n; ++j) {
-    {
-      ProfScope prof(PK_QR_HOUSE, s);
-      house_kernel<K, P><<<1, kHouseThreads, 0, s>>>(v.M, v.vd, v.beta, v.status, n, j);
-    }
+    // H_j on every target, and the Householder vector of column j+1 (lookahead)
     ProfScope prof(PK_QR_APPLY, s);
-    const int ncols = (n - j - 1) + n;
-    house_apply_kernel<K, P><<<blocks_for((long long)ncols * 32, 128), 128, 0, s>>>(v.M, v.Y, v.vd, v.beta, n, j);
+    const int rest = (n - j - 1) + n - (j + 1 < n ? 1 : 0);
+    house_step_kernel<K, P><<<1 + (int)blocks_for((long long)rest * 32, kHouseThreads), kHouseThreads, 0, s>>>(
+        v.M, v.Y, v.vd, v.beta, v.status, n, j);
   }
   {
     ProfScope prof(PK_RINV, s);
