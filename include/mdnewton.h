@@ -241,6 +241,49 @@ md_status md_linsolve_series_static(int limbs, int is_complex, int n, int degree
                                     double *dx, int flags, void *stream);
 
 /*
+ * Newton's method with degree continuation (the cyclic 128-roots experiment
+ * of Section 6): levels l = 0..nlevels-1 at truncation degrees degree[l]
+ * (nondecreasing, each <= sys->degree).  Level l runs Newton steps on the
+ * coefficients 0..degree[l] of x, at most max_iter[l] of them, and stops as soon
+ * as ||dx|| <= tol, where ||dx|| = max_i |dx_{degree[l],i}| is the size of the
+ * update of the last coefficient (leading limbs).  The next level starts from
+ * this level's series (its higher coefficients are those of x on entry).
+ * After a level that ends with ||dx|| > too_large the ladder stops ("once the
+ * update is too large for one degree, the next degrees are not computed"; the
+ * paper gives no threshold, the caller does).
+ *   sys:   the system at its largest degree D = sys->degree (coefficient arrays
+ *          do not depend on the degree).
+ *   x:     DEVICE [P][K][n][D+1], updated in place.
+ *   sched: HOST schedule; rep: HOST report (may be NULL).
+ *   ws:    DEVICE workspace of md_newton_run_workspace_bytes(sys, sched, flags).
+ *   flags: as for md_newton_series_step.
+ * The call waits for the GPU after every step (it reads ||dx|| to decide).
+ * Errors: MD_ERR_ARG (bad schedule), MD_ERR_WORKSPACE, MD_ERR_SINGULAR /
+ * MD_ERR_NONFINITE when a step's device status reports it (x then holds the
+ * series after that step and rep, if given, the levels up to it), MD_ERR_CUDA.
+ */
+#define MD_MAX_LEVELS 16
+typedef struct {
+  int nlevels;                    /* 1..MD_MAX_LEVELS                         */
+  int degree[MD_MAX_LEVELS];      /* truncation degree of each level          */
+  int max_iter[MD_MAX_LEVELS];    /* at most this many steps per level (>= 1) */
+  double tol;                     /* level converged when ||dx|| <= tol       */
+  double too_large;               /* ladder stops after ||dx|| > too_large    */
+} md_newton_schedule;
+
+typedef struct {
+  int levels_done;                /* levels run (the last may not have converged) */
+  int converged;                  /* 1 if every level run ended with ||dx|| <= tol */
+  int iterations[MD_MAX_LEVELS];  /* steps taken per level                        */
+  double dx_norm[MD_MAX_LEVELS];  /* ||dx|| after the last step of each level     */
+  double dx_max[MD_MAX_LEVELS];   /* max |dx| over all coefficients, same step    */
+} md_newton_report;
+
+size_t md_newton_run_workspace_bytes(const md_system *sys, const md_newton_schedule *sched, int flags);
+md_status md_newton_series_run(const md_system *sys, double *x, const md_newton_schedule *sched,
+                               md_newton_report *rep, void *ws, size_t ws_bytes, int flags, void *stream);
+
+/*
  * Optional timing of the library's own kernels (tracing support; not part of
  * the computation).  While enabled, every kernel launch of every call in this
  * process is bracketed by two CUDA events on its stream.

@@ -50,6 +50,8 @@ def _load(counting: bool):
             lib.orc_eval_diff.argtypes = [i, i, i, i, i, P, P, P, P, P, P, P, P, P]
             lib.orc_linsolve.argtypes = [i, i, i, i, P, P, P, P]
             lib.orc_newton_step.argtypes = [i, i, i, i, i, P, P, P, P, P, P, P, P, P]
+            d = ctypes.c_double
+            lib.orc_newton_run.argtypes = [i, i, i, i, i, P, P, P, P, P, P, P, i, P, P, d, d, P, P, P]
             lib.orc_count_get.argtypes = [P]
             lib.orc_set_threads.argtypes = [i]
             _libs[key] = lib
@@ -159,6 +161,28 @@ class Oracle:
         if want_rdiag:
             return xx, (float(nrm[0]), float(nrm[1])), rd
         return xx, (float(nrm[0]), float(nrm[1]))
+
+    def newton_run(self, s, degrees, max_iter, tol: float, too_large: float, x: Optional[np.ndarray] = None):
+        """Newton with degree continuation (Sec. 6).  Returns (x, report) with
+        report = {levels_done, iterations, dx_norm, dx_max, converged}."""
+        P, K, n, D = s.planes, s.limbs, s.n, s.degree
+        pp, nv, ix, ex, cf, cs = self._sysargs(s)
+        xx = _f64(s.x0 if x is None else x).copy()
+        nlev = len(degrees)
+        dg = np.asarray(degrees, dtype=np.int32)
+        mi = np.asarray(max_iter, dtype=np.int32)
+        it = np.zeros(nlev, dtype=np.int32)
+        dxn = np.zeros(2 * nlev)
+        lv = np.zeros(1, dtype=np.int32)
+        st = self.lib.orc_newton_run(K, int(s.is_complex), n, D, s.nmono, _p(pp), _p(nv), _p(ix), _p(ex), _p(cf),
+                                     _p(cs), _p(xx), nlev, _p(dg), _p(mi), ctypes.c_double(tol),
+                                     ctypes.c_double(too_large), _p(it), _p(dxn), _p(lv))
+        _check(st, "newton_run")
+        L = int(lv[0])
+        rep = {"levels_done": L, "iterations": [int(v) for v in it[:L]],
+               "dx_norm": [float(v) for v in dxn[0:2 * L:2]], "dx_max": [float(v) for v in dxn[1:2 * L:2]]}
+        rep["converged"] = all(v <= tol for v in rep["dx_norm"])
+        return xx, rep
 
     def newton(self, s, steps: int, x: Optional[np.ndarray] = None):
         x = s.x0.copy() if x is None else x

@@ -977,6 +977,52 @@ int orc_newton_step(int K, int cplx, int n, int d, int nmono, const int *poly_pt
   return st;
 }
 
+/* ------------------------------------- Newton with degree continuation */
+/*
+ * The driver of the cyclic 128-roots run in Sec. 6: levels l = 0..nlev-1 at
+ * truncation degrees deg[l].  Level l takes Newton steps on coefficients
+ * 0..deg[l] of x, at most maxit[l] of them, and ends early once ||dx|| (the
+ * update of the last coefficient, dxnorm[0] above) is <= tol.  The next level
+ * starts from this one's series.  The ladder stops after a level whose last
+ * ||dx|| is above too_large (the paper gives no number for "too large"; the
+ * caller does).  x: [P][K][n][D+1] in and out.  Per level: iters[l], the final
+ * ||dx|| in dxn[2l] and max |dx| in dxn[2l+1]; *levels = levels run.
+ */
+int orc_newton_run(int K, int cplx, int n, int D, int nmono, const int *poly_ptr, const int *nvar, const int *idx,
+                   const int *expo, const double *coef, const double *cst, double *x, int nlev, const int *deg,
+                   const int *maxit, double tol, double too_large, int *iters, double *dxn, int *levels) {
+  int P = cplx ? 2 : 1;
+  if (check_system(K, n, D, nmono, poly_ptr, nvar, idx, expo) || nlev < 1) return 1;
+  for (int l = 0; l < nlev; ++l)
+    if (deg[l] < 0 || deg[l] > D || (l > 0 && deg[l] < deg[l - 1]) || maxit[l] < 1) return 1;
+  long rows = (long)P * K * n;
+  double *xl = malloc(sizeof(double) * rows * (D + 1));
+  int st = 0;
+  *levels = 0;
+  for (int l = 0; l < nlev && !st; ++l) {
+    int d = deg[l];
+    for (long r = 0; r < rows; ++r)
+      for (int k = 0; k <= d; ++k) xl[r * (d + 1) + k] = x[r * (D + 1) + k];
+    double nrm[2] = {0.0, 0.0};
+    int it = 0;
+    while (it < maxit[l]) {
+      st = orc_newton_step(K, cplx, n, d, nmono, poly_ptr, nvar, idx, expo, coef, cst, xl, nrm, NULL);
+      if (st) break;
+      ++it;
+      if (nrm[0] <= tol) break;
+    }
+    for (long r = 0; r < rows; ++r)
+      for (int k = 0; k <= d; ++k) x[r * (D + 1) + k] = xl[r * (d + 1) + k];
+    iters[l] = it;
+    dxn[2 * l] = nrm[0];
+    dxn[2 * l + 1] = nrm[1];
+    *levels = l + 1;
+    if (!(nrm[0] <= too_large)) break;
+  }
+  free(xl);
+  return st;
+}
+
 int orc_set_threads(int t) {
 #ifdef _OPENMP
   if (t > 0) omp_set_num_threads(t);

@@ -36,6 +36,20 @@ class md_system(ctypes.Structure):
                 ("cst", ctypes.c_void_p)]
 
 
+MAX_LEVELS = 16
+
+
+class md_newton_schedule(ctypes.Structure):
+    _fields_ = [("nlevels", ctypes.c_int), ("degree", ctypes.c_int * MAX_LEVELS),
+                ("max_iter", ctypes.c_int * MAX_LEVELS), ("tol", ctypes.c_double), ("too_large", ctypes.c_double)]
+
+
+class md_newton_report(ctypes.Structure):
+    _fields_ = [("levels_done", ctypes.c_int), ("converged", ctypes.c_int),
+                ("iterations", ctypes.c_int * MAX_LEVELS), ("dx_norm", ctypes.c_double * MAX_LEVELS),
+                ("dx_max", ctypes.c_double * MAX_LEVELS)]
+
+
 _lib = None
 
 
@@ -73,8 +87,12 @@ def lib():
         L.md_profile_read.restype = i
         L.md_profile_kind_name.argtypes = [i]
         L.md_profile_kind_name.restype = ctypes.c_char_p
+        sched_p, rep_p = ctypes.POINTER(md_newton_schedule), ctypes.POINTER(md_newton_report)
+        L.md_newton_run_workspace_bytes.argtypes = [ctypes.POINTER(md_system), sched_p, i]
+        L.md_newton_run_workspace_bytes.restype = sz
+        L.md_newton_series_run.argtypes = [ctypes.POINTER(md_system), vp, sched_p, rep_p, vp, sz, i, vp]
         for name in ("md_elementwise", "md_series_conv", "md_eval_diff", "md_linsolve_series",
-                     "md_newton_series_step", "md_get_device_status"):
+                     "md_newton_series_step", "md_get_device_status", "md_newton_series_run"):
             getattr(L, name).restype = i
         _lib = L
     return _lib
@@ -85,8 +103,7 @@ def exported_symbols():
             "md_elementwise", "md_series_conv", "md_eval_diff", "md_linsolve_series",
             "md_newton_series_step", "md_get_device_status", "md_batched_workspace_bytes",
             "md_newton_series_step_batched", "md_linsolve_series_static", "md_profile_enable",
-            "md_profile_read",
-            "md_profile_kind_name"]
+            "md_profile_read", "md_profile_kind_name", "md_newton_run_workspace_bytes", "md_newton_series_run"]
 
 
 # --------------------------------------------------------------- helpers
@@ -209,6 +226,35 @@ def newton_step(sysd: DeviceSystem, x, ws, dx_norm=None, flags: int = 0, stream=
 
 
 FLAG_OZAKI, FLAG_AUTOTUNE, FLAG_GRAPH = 0x1, 0x2, 0x4
+
+
+def schedule(degrees, max_iter, tol: float = 1e-32, too_large: float = 1.0) -> md_newton_schedule:
+    """Degree-continuation schedule for newton_run (levels of equal length lists)."""
+    if len(degrees) != len(max_iter) or not 1 <= len(degrees) <= MAX_LEVELS:
+        raise ValueError("degrees and max_iter: 1..16 levels of equal length")
+    sc = md_newton_schedule()
+    sc.nlevels = len(degrees)
+    for l, (d, m) in enumerate(zip(degrees, max_iter)):
+        sc.degree[l] = int(d)
+        sc.max_iter[l] = int(m)
+    sc.tol = float(tol)
+    sc.too_large = float(too_large)
+    return sc
+
+
+def newton_run_workspace_bytes(sysd: DeviceSystem, sched: md_newton_schedule, flags: int = 0) -> int:
+    return int(lib().md_newton_run_workspace_bytes(sysd.c(), ctypes.byref(sched), flags))
+
+
+def newton_run(sysd: DeviceSystem, x, ws, sched: md_newton_schedule, flags: int = 0, stream=None) -> dict:
+    """Newton with degree continuation on x ([P][K][n][D+1] CUDA tensor, in
+    place).  Returns {levels_done, converged, iterations, dx_norm, dx_max}."""
+    rep = md_newton_report()
+    _check(lib().md_newton_series_run(sysd.c(), _ptr(x), ctypes.byref(sched), ctypes.byref(rep), _ptr(ws),
+                                      ws.numel(), flags, _stream(stream)), "md_newton_series_run")
+    L = rep.levels_done
+    return {"levels_done": L, "converged": bool(rep.converged), "iterations": list(rep.iterations[:L]),
+            "dx_norm": list(rep.dx_norm[:L]), "dx_max": list(rep.dx_max[:L])}
 
 
 def _sys_array(systems):

@@ -785,6 +785,45 @@ const char *kProfNames[mdk::PK_COUNT] = {"pool_load_x", "prep_scal", "conv_stage
                                          "rinv", "backsub", "rhs_partial", "rhs_finish", "wmv", "finish_dx",
                                          "elementwise", "series_conv", "oz_split", "oz_gemm", "oz_accum"};
 
+md_status check_schedule(const md_system *s, const md_newton_schedule *sc) {
+  if (!sc || sc->nlevels < 1 || sc->nlevels > MD_MAX_LEVELS) return MD_ERR_ARG;
+  if (!(sc->tol >= 0.0) || !(sc->too_large >= 0.0)) return MD_ERR_ARG;  // also rejects NaN
+  for (int l = 0; l < sc->nlevels; ++l) {
+    if (sc->degree[l] < 0 || sc->degree[l] > s->degree || sc->max_iter[l] < 1) return MD_ERR_ARG;
+    if (l > 0 && sc->degree[l] < sc->degree[l - 1]) return MD_ERR_ARG;
+  }
+  return MD_OK;
+}
+
+md_system at_degree(const md_system *s, int d) {
+  md_system t = *s;
+  t.degree = d;
+  return t;
+}
+
+// Workspace of the driver: [step workspace of the largest level | x at that
+// level's degree | dx norms].
+struct RunLayout {
+  size_t step = 0, off_x = 0, off_nrm = 0, total = 0;
+};
+
+RunLayout run_layout(const md_system *s, const md_newton_schedule *sc, int flags) {
+  RunLayout L;
+  int dmax = 0;
+  for (int l = 0; l < sc->nlevels; ++l) {
+    md_system t = at_degree(s, sc->degree[l]);
+    Plan p;
+    if (build_plan(&t, p, flags) != MD_OK) return RunLayout{};
+    L.step = std::max(L.step, p.total);
+    dmax = std::max(dmax, sc->degree[l]);
+  }
+  const size_t P = s->is_complex ? 2 : 1;
+  L.off_x = align256(L.step);
+  L.off_nrm = align256(L.off_x + sizeof(double) * P * s->limbs * (size_t)s->n * (dmax + 1));
+  L.total = L.off_nrm + 256;
+  return L;
+}
+
 }  // namespace
 
 extern "C" {
@@ -902,6 +941,58 @@ md_status md_newton_series_step(const md_system *sys, double *x, double *dx_norm
   if (dispatch(p->K, p->P, 6, &e, s) != cudaSuccess) return MD_ERR_CUDA;
   if (cudaStreamWaitEvent(s, ax->e1, 0) != cudaSuccess) return MD_ERR_CUDA;
   return cuda_status(dispatch(p->K, p->P, 8, &v, s));
+}
+
+size_t md_newton_run_workspace_bytes(const md_system *sys, const md_newton_schedule *sched, int flags) {
+  if (check_system(sys) != MD_OK || check_schedule(sys, sched) != MD_OK) return 0;
+  return run_layout(sys, sched, flags).total;
+}
+
+md_status md_newton_series_run(const md_system *sys, double *x, const md_newton_schedule *sched,
+                               md_newton_report *rep, void *ws, size_t ws_bytes, int flags, void *stream) {
+  md_status st = check_system(sys);
+  if (st != MD_OK) return st;
+  if (!x || (st = check_schedule(sys, sched)) != MD_OK) return MD_ERR_ARG;
+  const RunLayout L = run_layout(sys, sched, flags);
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) || L.total == 0 || ws_bytes < L.total) return MD_ERR_WORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char *base = static_cast<char *>(ws);
+  double *xl = reinterpret_cast<double *>(base + L.off_x);
+  double *nrm = reinterpret_cast<double *>(base + L.off_nrm);
+  const size_t rows = (size_t)(sys->is_complex ? 2 : 1) * sys->limbs * sys->n;
+  const size_t pitch = sizeof(double) * (sys->degree + 1);
+  md_newton_report r;
+  std::memset(&r, 0, sizeof(r));
+  r.converged = 1;
+  for (int l = 0; l < sched->nlevels; ++l) {
+    const int d = sched->degree[l];
+    const md_system t = at_degree(sys, d);
+    const size_t w = sizeof(double) * (d + 1);
+    // coefficients 0..d of every component, packed as the degree-d layout
+    if (cudaMemcpy2DAsync(xl, w, x, pitch, w, rows, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return MD_ERR_CUDA;
+    double h[2] = {0.0, 0.0};
+    md_status fail = MD_OK;
+    for (int it = 1; it <= sched->max_iter[l]; ++it) {
+      if ((st = md_newton_series_step(&t, xl, nrm, ws, L.step, flags, stream)) != MD_OK) return st;
+      if (cudaMemcpyAsync(h, nrm, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MD_ERR_CUDA;
+      fail = md_get_device_status(ws, stream);  // waits for the step
+      r.iterations[l] = it;
+      r.dx_norm[l] = h[0];
+      r.dx_max[l] = h[1];
+      if (fail != MD_OK || h[0] <= sched->tol) break;
+    }
+    if (cudaMemcpy2DAsync(x, pitch, xl, w, w, rows, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return MD_ERR_CUDA;
+    r.levels_done = l + 1;
+    if (!(r.dx_norm[l] <= sched->tol)) r.converged = 0;
+    if (fail != MD_OK) {
+      if (rep) *rep = r;
+      return cudaStreamSynchronize(s) == cudaSuccess ? fail : MD_ERR_CUDA;
+    }
+    if (!(r.dx_norm[l] <= sched->too_large)) break;
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MD_ERR_CUDA;
+  if (rep) *rep = r;
+  return MD_OK;
 }
 
 size_t md_batched_workspace_bytes(int nsys, const md_system *sys, int flags) {

@@ -135,3 +135,27 @@ def test_argument_errors_before_cuda(mdlib):
     assert mdlib.md_newton_series_step(ctypes.byref(c), 1, None, 256, 64, 0, None) == 2
     assert mdlib.md_eval_diff(ctypes.byref(c), None, 1, 1, 256, 1 << 30, None) == 1
     assert mdlib.md_get_device_status(None, None) == 2
+
+
+def test_newton_run_host_checks(mdlib):
+    """Schedule validation and workspace sizing happen on the host."""
+    import paper_2012_06607_gb300 as md
+
+    s = mdgen.config_system(0, seed=1)
+    c, keep = _csys(s)
+    good = md.schedule([4, s.degree], [3, 3], 1e-28, 1.0)
+    wb = mdlib.md_newton_run_workspace_bytes(ctypes.byref(c), ctypes.byref(good), 0)
+    assert wb >= mdlib.md_workspace_bytes(ctypes.byref(c), 0) > 0
+    for deg, mi, tol in (([s.degree + 1], [1], 0.0), ([4, 2], [1, 1], 0.0), ([4], [0], 0.0),
+                         ([4], [1], float("nan")), ([4], [1], -1.0)):
+        bad = md.schedule(deg, mi, tol, 1.0)
+        assert mdlib.md_newton_run_workspace_bytes(ctypes.byref(c), ctypes.byref(bad), 0) == 0
+        st = mdlib.md_newton_series_run(ctypes.byref(c), 256, ctypes.byref(bad), None, 256, 1 << 30, 0, None)
+        assert st == 1  # MD_ERR_ARG before any CUDA call
+    bad = md.schedule([4], [1])
+    bad.nlevels = 0
+    assert mdlib.md_newton_run_workspace_bytes(ctypes.byref(c), ctypes.byref(bad), 0) == 0
+    # a workspace that is too small or misaligned is refused before any CUDA call
+    assert mdlib.md_newton_series_run(ctypes.byref(c), 256, ctypes.byref(good), None, 256, wb - 1, 0, None) == 2
+    assert mdlib.md_newton_series_run(ctypes.byref(c), 256, ctypes.byref(good), None, 257, wb, 0, None) == 2
+    assert mdlib.md_newton_series_run(ctypes.byref(c), None, ctypes.byref(good), None, 256, wb, 0, None) == 1

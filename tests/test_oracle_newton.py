@@ -10,6 +10,7 @@
 * agreement with the same computation in twice the number of limbs;
 * threaded run (one job per polynomial / per right-hand side) bit-identical to serial.
 """
+import copy
 import os
 from fractions import Fraction
 
@@ -209,3 +210,96 @@ def test_singular_a0_reported(orc):
     s = mdgen._pack(1, 2, False, 4, polys, [[(F(1), F(0)), (F(1), F(0))]], [(F(0), F(0))], [(F(0), F(0))])
     with pytest.raises(oracle.OracleError, match="singular"):
         orc.newton_step(s, s.x0)
+
+
+# ------------------------------------------- Newton with degree continuation
+def _sqrt_start(K, D):
+    """x^2 - 1 - t = 0 from x0 = 1 + t/2 (coefficients 0 and 1 exact)."""
+    s = mdgen.sqrt_system(K, D)
+    x0 = s.x0.copy()
+    x0[0, 0, 0, 1] = 0.5
+    return s, x0
+
+
+def _exact_sqrt_newton(d, steps):
+    """Exact rational Newton on x^2 - 1 - t from 1 + t/2, truncated at degree d:
+    returns the list of updates dx (coefficient lists) of every step."""
+    F = Fraction
+    x = [F(1), F(1, 2)] + [F(0)] * (d - 1)
+    out = []
+    for _ in range(steps):
+        f = [sum(x[i] * x[k - i] for i in range(k + 1)) for k in range(d + 1)]
+        f[0] -= 1
+        f[1] -= 1
+        a = [2 * v for v in x]  # A(t) = 2 x(t); dx = -f / a as a series division
+        dx = []
+        for k in range(d + 1):
+            dx.append((-f[k] - sum(a[k - i] * dx[i] for i in range(k))) / a[0])
+        x = [u + v for u, v in zip(x, dx)]
+        out.append(dx)
+    return out
+
+
+@pytest.mark.parametrize("K,tol", [(2, 1e-28), (4, 1e-58)])
+def test_newton_run_doubling_pins_iterations(orc, K, tol):
+    """Newton on series doubles the number of correct coefficients per step.
+    From 2 correct coefficients, degree 8 (9 coefficients) is exact after 3
+    steps, so the 4th step's update is rounding-sized: 4 steps.  Degree 16
+    then starts with 9 correct coefficients, one step makes 18: 2 steps."""
+    s, x0 = _sqrt_start(K, 16)
+    x, rep = orc.newton_run(s, [8, 16], [8, 8], tol, 1.0, x0)
+    assert rep["levels_done"] == 2 and rep["converged"]
+    assert rep["iterations"] == [4, 2]
+    for k in range(17):
+        want = mdgen.binom_half(k)
+        got = val(x, 0, k)
+        assert abs(got[0] - want) <= 1000 * eps(K) * abs(want), (k, float(got[0] - want))
+
+
+def test_newton_run_too_large_stops_ladder(orc):
+    """Two steps at degree 8 leave coefficient 8 wrong: the last update equals
+    the exact rational one, it is above too_large, and degree 16 is not run."""
+    s, x0 = _sqrt_start(2, 16)
+    x, rep = orc.newton_run(s, [8, 16], [2, 8], 1e-28, 1e-6, x0)
+    assert rep["levels_done"] == 1 and not rep["converged"] and rep["iterations"] == [2]
+    dx = _exact_sqrt_newton(8, 2)
+    assert rep["dx_norm"][0] == pytest.approx(abs(float(dx[1][8])), rel=1e-15)
+    assert rep["dx_max"][0] == pytest.approx(max(abs(float(v)) for v in dx[1]), rel=1e-15)
+    # coefficients above degree 8 were not touched
+    assert np.all(x[..., 9:] == x0[..., 9:])
+    # the same ladder with a larger threshold goes on to degree 16
+    _, rep2 = orc.newton_run(s, [8, 16], [2, 8], 1e-28, 1.0, x0)
+    assert rep2["levels_done"] == 2 and rep2["iterations"][0] == 2
+
+
+def test_newton_run_equals_repeated_steps(orc):
+    """A one-level ladder is the plain step repeated; the level's series then
+    continues the next level (cfg0-type dd complex system)."""
+    s = mdgen.config_system(0, seed=4)
+    x_run, rep = orc.newton_run(s, [s.degree], [3], 0.0, 1e300)
+    x = s.x0.copy()
+    for _ in range(3):
+        x, nr = orc.newton_step(s, x)
+    assert rep["iterations"] == [3] and np.array_equal(x_run, x)
+    assert rep["dx_norm"][0] == nr[0] and rep["dx_max"][0] == nr[1]
+    # two levels: degree 4 then the full degree, the second from the first's series
+    d4 = 4
+    x2, rep2 = orc.newton_run(s, [d4, s.degree], [2, 2], 0.0, 1e300)
+    xl = s.x0[..., :d4 + 1].copy()
+    s4 = copy.copy(s)
+    s4.degree = d4
+    s4.x0 = xl
+    for _ in range(2):
+        xl, _ = orc.newton_step(s4, xl)
+    xf = s.x0.copy()
+    xf[..., :d4 + 1] = xl
+    for _ in range(2):
+        xf, _ = orc.newton_step(s, xf)
+    assert np.array_equal(x2, xf) and rep2["iterations"] == [2, 2]
+
+
+def test_newton_run_rejects_bad_schedules(orc):
+    s, x0 = _sqrt_start(2, 8)
+    for deg, mi in (([9], [1]), ([4, 2], [1, 1]), ([4], [0]), ([-1], [1])):
+        with pytest.raises(RuntimeError):
+            orc.newton_run(s, deg, mi, 1e-28, 1.0, x0)
