@@ -108,6 +108,12 @@ typedef struct md_system {
    stream on a few SMs while the higher coefficients are evaluated on the rest;
    results are identical either way. */
 #define MD_FLAG_SERIAL 0x8
+/* factor A_0 by LU with partial pivoting (Section 4: for N = n "an LU
+   factorization can be applied") instead of Householder QR.  Pivot: the first
+   row of largest |re| + |im| of the leading limbs; multipliers by the
+   reciprocal of the pivot.  Single-system calls only (the batched form
+   returns MD_ERR_UNSUPPORTED). */
+#define MD_FLAG_LU 0x10
 
 /* Version of this ABI (major*100 + minor). */
 int md_version(void);
@@ -239,6 +245,23 @@ md_status md_get_device_status(void *ws, void *stream);
 #define MD_STATIC_WS_BYTES (16u << 20)
 md_status md_linsolve_series_static(int limbs, int is_complex, int n, int degree, const double *A, const double *b,
                                     double *dx, int flags, void *stream);
+
+/*
+ * Reciprocal condition number of A_0 in the 1-norm, 1 / (||A_0||_1 ||A_0^-1||_1)
+ * (Section 6 quotes such an estimate, 4.6E-6, for the cyclic 128-roots
+ * system).  The solve forms A_0^-1 = R^-1 Q^H (or U^-1 L^-1 P) explicitly, so
+ * the value is that of the computed inverse, from the moduli of the leading
+ * limbs summed in double.  It reads the factorisation left in the workspace:
+ *   md_rcond_a0:       after md_newton_series_step(sys, ..., ws, ..., flags)
+ *                      (A_0 of that step's linearisation);
+ *   md_linsolve_rcond: after md_linsolve_series(limbs, ..., A, ..., ws, ...)
+ *                      with the same A.
+ *   rcond: DEVICE double, written on `stream` (no synchronisation).
+ * Errors: MD_ERR_ARG, MD_ERR_WORKSPACE, MD_ERR_CUDA.
+ */
+md_status md_rcond_a0(const md_system *sys, void *ws, size_t ws_bytes, int flags, double *rcond, void *stream);
+md_status md_linsolve_rcond(int limbs, int is_complex, int n, int degree, const double *A, void *ws,
+                            size_t ws_bytes, int flags, double *rcond, void *stream);
 
 /*
  * Newton's method with degree continuation (the cyclic 128-roots experiment

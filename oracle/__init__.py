@@ -49,9 +49,12 @@ def _load(counting: bool):
             lib.orc_series_conv.argtypes = [i, i, i, ctypes.c_long, P, P, P]
             lib.orc_eval_diff.argtypes = [i, i, i, i, i, P, P, P, P, P, P, P, P, P]
             lib.orc_linsolve.argtypes = [i, i, i, i, P, P, P, P]
+            lib.orc_linsolve_m.argtypes = [i, i, i, i, P, P, P, P, i]
+            lib.orc_newton_step_m.argtypes = [i, i, i, i, i, P, P, P, P, P, P, P, P, P, i]
+            lib.orc_rcond.argtypes = [i, i, i, i, P, i, P]
             lib.orc_newton_step.argtypes = [i, i, i, i, i, P, P, P, P, P, P, P, P, P]
             d = ctypes.c_double
-            lib.orc_newton_run.argtypes = [i, i, i, i, i, P, P, P, P, P, P, P, i, P, P, d, d, P, P, P]
+            lib.orc_newton_run.argtypes = [i, i, i, i, i, P, P, P, P, P, P, P, i, P, P, d, d, P, P, P, i]
             lib.orc_count_get.argtypes = [P]
             lib.orc_set_threads.argtypes = [i]
             _libs[key] = lib
@@ -139,30 +142,40 @@ class Oracle:
         _check(st, "eval_diff")
         return f, A
 
-    def linsolve(self, K: int, cplx: bool, A: np.ndarray, b: np.ndarray, want_rdiag: bool = False):
-        """A: [P][K][d+1][n][n] (col-major blocks), b: [P][K][n][d+1] -> dx like b."""
+    def linsolve(self, K: int, cplx: bool, A: np.ndarray, b: np.ndarray, want_rdiag: bool = False, method: int = 0):
+        """A: [P][K][d+1][n][n] (col-major blocks), b: [P][K][n][d+1] -> dx like b.
+        method 0: Householder QR of A_0, 1: LU with partial pivoting."""
         A, b = _f64(A), _f64(b)
         P, _, D1, n, _ = A.shape
         dx = np.zeros_like(b)
         rd = np.zeros(n)
-        _check(self.lib.orc_linsolve(K, int(cplx), n, D1 - 1, _p(A), _p(b), _p(dx), _p(rd)), "linsolve")
+        _check(self.lib.orc_linsolve_m(K, int(cplx), n, D1 - 1, _p(A), _p(b), _p(dx), _p(rd), method), "linsolve")
         return (dx, rd) if want_rdiag else dx
 
-    def newton_step(self, s, x: np.ndarray, want_rdiag: bool = False):
+    def rcond(self, K: int, cplx: bool, A: np.ndarray, method: int = 0) -> float:
+        """1 / (||A_0||_1 ||A_0^-1||_1) from the leading limbs; A as for linsolve."""
+        A = _f64(A)
+        P, _, D1, n, _ = A.shape
+        out = np.zeros(1)
+        _check(self.lib.orc_rcond(K, int(cplx), n, D1 - 1, _p(A), method, _p(out)), "rcond")
+        return float(out[0])
+
+    def newton_step(self, s, x: np.ndarray, want_rdiag: bool = False, method: int = 0):
         """One step; returns (x_new, (|dx_d|, |dx|_inf))."""
         P, K, n, d = s.planes, s.limbs, s.n, s.degree
         pp, nv, ix, ex, cf, cs = self._sysargs(s)
         xx = _f64(x).copy()
         nrm = np.zeros(2)
         rd = np.zeros(n)
-        st = self.lib.orc_newton_step(K, int(s.is_complex), n, d, s.nmono, _p(pp), _p(nv), _p(ix), _p(ex), _p(cf),
-                                      _p(cs), _p(xx), _p(nrm), _p(rd))
+        st = self.lib.orc_newton_step_m(K, int(s.is_complex), n, d, s.nmono, _p(pp), _p(nv), _p(ix), _p(ex),
+                                        _p(cf), _p(cs), _p(xx), _p(nrm), _p(rd), method)
         _check(st, "newton_step")
         if want_rdiag:
             return xx, (float(nrm[0]), float(nrm[1])), rd
         return xx, (float(nrm[0]), float(nrm[1]))
 
-    def newton_run(self, s, degrees, max_iter, tol: float, too_large: float, x: Optional[np.ndarray] = None):
+    def newton_run(self, s, degrees, max_iter, tol: float, too_large: float, x: Optional[np.ndarray] = None,
+                   method: int = 0):
         """Newton with degree continuation (Sec. 6).  Returns (x, report) with
         report = {levels_done, iterations, dx_norm, dx_max, converged}."""
         P, K, n, D = s.planes, s.limbs, s.n, s.degree
@@ -176,7 +189,7 @@ class Oracle:
         lv = np.zeros(1, dtype=np.int32)
         st = self.lib.orc_newton_run(K, int(s.is_complex), n, D, s.nmono, _p(pp), _p(nv), _p(ix), _p(ex), _p(cf),
                                      _p(cs), _p(xx), nlev, _p(dg), _p(mi), ctypes.c_double(tol),
-                                     ctypes.c_double(too_large), _p(it), _p(dxn), _p(lv))
+                                     ctypes.c_double(too_large), _p(it), _p(dxn), _p(lv), method)
         _check(st, "newton_run")
         L = int(lv[0])
         rep = {"levels_done": L, "iterations": [int(v) for v in it[:L]],

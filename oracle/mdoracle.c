@@ -815,6 +815,141 @@ static void qr_backsub(qrf *q, mdc *y, mdc *x) {
   }
 }
 
+/* ------------------------------------------------------------ LU (N = n) */
+/*
+ * Gaussian elimination with partial pivoting (Sec. 4: when N = n an LU
+ * factorization can be applied; Golub-Van Loan, Alg. 3.4.1).  Column j: the
+ * pivot is the first row i >= j of largest |re| + |im| of the leading limbs;
+ * rows j and p are swapped; the multipliers a_ij * (1/a_jj) are stored below
+ * the diagonal; the trailing entries get a_ik -= l_ij a_jk.  Returns 4 when a
+ * pivot is zero (singular A_0).
+ */
+typedef struct {
+  int K, P, n;
+  mdc *a;   /* row-major n x n */
+  int *piv; /* [n] row swapped with row j at step j */
+} luf;
+
+static double cabs1_lead(int P, const mdc *z) { return fabs(z->v[0][0]) + (P == 2 ? fabs(z->v[1][0]) : 0.0); }
+
+static int lu_factor(luf *f) {
+  int K = f->K, P = f->P, n = f->n;
+  mdc *a = f->a;
+  for (int j = 0; j < n; ++j) {
+    int p = j;
+    double best = cabs1_lead(P, &a[(long)j * n + j]);
+    for (int i = j + 1; i < n; ++i) {
+      double v = cabs1_lead(P, &a[(long)i * n + j]);
+      if (v > best) {
+        best = v;
+        p = i;
+      }
+    }
+    if (!(best > 0.0)) return 4;
+    f->piv[j] = p;
+    if (p != j)
+      for (int c = 0; c < n; ++c) {
+        mdc t = a[(long)j * n + c];
+        a[(long)j * n + c] = a[(long)p * n + c];
+        a[(long)p * n + c] = t;
+      }
+    mdc one, ri;
+    c_zero(&one);
+    one.v[0][0] = 1.0;
+    c_div(K, P, &one, &a[(long)j * n + j], &ri);
+    for (int i = j + 1; i < n; ++i) {
+      c_mul(K, P, &a[(long)i * n + j], &ri, &a[(long)i * n + j]);
+      for (int c = j + 1; c < n; ++c) {
+        mdc tt;
+        c_mul(K, P, &a[(long)i * n + j], &a[(long)j * n + c], &tt);
+        c_sub(K, P, &a[(long)i * n + c], &tt, &a[(long)i * n + c]);
+      }
+    }
+  }
+  return 0;
+}
+
+/* A_0 x = y by P, L (unit, forward) and U (backward, row by row, dividing by
+   u_jj); y is overwritten */
+static void lu_solve(const luf *f, mdc *y, mdc *x) {
+  int K = f->K, P = f->P, n = f->n;
+  const mdc *a = f->a;
+  for (int j = 0; j < n; ++j)
+    if (f->piv[j] != j) {
+      mdc t = y[j];
+      y[j] = y[f->piv[j]];
+      y[f->piv[j]] = t;
+    }
+  for (int i = 1; i < n; ++i)
+    for (int j = 0; j < i; ++j) {
+      mdc tt;
+      c_mul(K, P, &a[(long)i * n + j], &y[j], &tt);
+      c_sub(K, P, &y[i], &tt, &y[i]);
+    }
+  for (int i = n - 1; i >= 0; --i) {
+    mdc s = y[i];
+    for (int j = i + 1; j < n; ++j) {
+      mdc tt;
+      c_mul(K, P, &a[(long)i * n + j], &x[j], &tt);
+      c_sub(K, P, &s, &tt, &s);
+    }
+    c_div(K, P, &s, &a[(long)i * n + i], &x[i]);
+  }
+}
+
+/* A_0 factored by QR (method 0) or LU (method 1); solve A_0 x = y */
+typedef struct {
+  int method;
+  qrf q;
+  luf l;
+} fact;
+
+static int fact_init(fact *f, int method, int K, int P, int n, const mdc *a0) {
+  long nn = (long)n * n;
+  memset(f, 0, sizeof(*f));
+  f->method = method;
+  if (method == 1) {
+    f->l.K = K;
+    f->l.P = P;
+    f->l.n = n;
+    f->l.a = malloc(sizeof(mdc) * nn);
+    f->l.piv = malloc(sizeof(int) * n);
+    memcpy(f->l.a, a0, sizeof(mdc) * nn);
+    return lu_factor(&f->l);
+  }
+  f->q.K = K;
+  f->q.P = P;
+  f->q.n = n;
+  f->q.a = malloc(sizeof(mdc) * nn);
+  f->q.vd = malloc(sizeof(mdc) * n);
+  f->q.rd = malloc(sizeof(mdc) * n);
+  f->q.beta = malloc(sizeof(double) * MAXK * n);
+  memcpy(f->q.a, a0, sizeof(mdc) * nn);
+  return qr_factor(&f->q);
+}
+
+static void fact_solve(fact *f, const mdc *r, mdc *x) {
+  int n = f->method == 1 ? f->l.n : f->q.n;
+  mdc *y = malloc(sizeof(mdc) * n);
+  memcpy(y, r, sizeof(mdc) * n);
+  if (f->method == 1) {
+    lu_solve(&f->l, y, x);
+  } else {
+    qr_apply_qh(&f->q, y);
+    qr_backsub(&f->q, y, x);
+  }
+  free(y);
+}
+
+static void fact_free(fact *f) {
+  free(f->l.a);
+  free(f->l.piv);
+  free(f->q.a);
+  free(f->q.vd);
+  free(f->q.rd);
+  free(f->q.beta);
+}
+
 /*
  * Lower triangular block Toeplitz forward substitution (Sec. 4):
  *   r_k = b_k - A_k dx_0 - A_{k-1} dx_1 - ... - A_1 dx_{k-1}   (j ascending)
@@ -825,39 +960,25 @@ static void qr_backsub(qrf *q, mdc *y, mdc *x) {
  * touches one r_k only, so the parallel loop keeps the serial order.
  * as: [(k*n + row)*n + col]; bs, dxs: [k*n + i].
  */
-static int linsolve_internal(int K, int P, int n, int d, mdc *as, const mdc *bs, mdc *dxs, double *rdiag_abs) {
+static int linsolve_internal(int K, int P, int n, int d, mdc *as, const mdc *bs, mdc *dxs, double *rdiag_abs,
+                             int method) {
   long nn = (long)n * n;
-  qrf q;
-  q.K = K;
-  q.P = P;
-  q.n = n;
-  q.a = malloc(sizeof(mdc) * nn);
-  q.vd = malloc(sizeof(mdc) * n);
-  q.rd = malloc(sizeof(mdc) * n);
-  q.beta = malloc(sizeof(double) * MAXK * n);
-  memcpy(q.a, as, sizeof(mdc) * nn);
-  int st = qr_factor(&q);
+  fact f;
+  int st = fact_init(&f, method, K, P, n, as);
   if (st) {
-    free(q.a);
-    free(q.vd);
-    free(q.rd);
-    free(q.beta);
+    fact_free(&f);
     return st;
   }
   if (rdiag_abs)
     for (int i = 0; i < n; ++i) {
-      double re = q.rd[i].v[0][0], im = (P == 2) ? q.rd[i].v[1][0] : 0.0;
+      const mdc *rd = method == 1 ? &f.l.a[(long)i * n + i] : &f.q.rd[i];
+      double re = rd->v[0][0], im = (P == 2) ? rd->v[1][0] : 0.0;
       rdiag_abs[i] = sqrt(re * re + im * im);
     }
   mdc *r = malloc(sizeof(mdc) * (d + 1) * n);
   memcpy(r, bs, sizeof(mdc) * (d + 1) * n);
   for (int k = 0; k <= d; ++k) {
-    mdc *rk = r + (long)k * n;
-    mdc *y = malloc(sizeof(mdc) * n);
-    memcpy(y, rk, sizeof(mdc) * n);
-    qr_apply_qh(&q, y);
-    qr_backsub(&q, y, dxs + (long)k * n);
-    free(y);
+    fact_solve(&f, r + (long)k * n, dxs + (long)k * n);
     /* jobs: r_m -= A_{m-k} dx_k for every m > k */
 #pragma omp parallel for schedule(dynamic, 1)
     for (int m = k + 1; m <= d; ++m) {
@@ -876,10 +997,7 @@ static int linsolve_internal(int K, int P, int n, int d, mdc *as, const mdc *bs,
     }
   }
   free(r);
-  free(q.a);
-  free(q.vd);
-  free(q.rd);
-  free(q.beta);
+  fact_free(&f);
   return 0;
 }
 
@@ -903,7 +1021,8 @@ static void store_vec_dm(int K, int P, int n, int d, const mdc *v, double *x) {
         for (int l = 0; l < K; ++l) x[(((long)p * K + l) * n + i) * D1 + k] = v[(long)k * n + i].v[p][l];
 }
 
-int orc_linsolve(int K, int cplx, int n, int d, const double *A, const double *b, double *dx, double *rdiag_abs) {
+int orc_linsolve_m(int K, int cplx, int n, int d, const double *A, const double *b, double *dx, double *rdiag_abs,
+                   int method) {
   int P = cplx ? 2 : 1;
   if (K < 1 || K > MAXK || n < 1 || d < 0) return 1;
   long nn = (long)n * n;
@@ -912,12 +1031,16 @@ int orc_linsolve(int K, int cplx, int n, int d, const double *A, const double *b
   mdc *dxs = malloc(sizeof(mdc) * (d + 1) * n);
   load_mats(K, P, n, d, A, as);
   load_vec_dm(K, P, n, d, b, bs);
-  int st = linsolve_internal(K, P, n, d, as, bs, dxs, rdiag_abs);
+  int st = linsolve_internal(K, P, n, d, as, bs, dxs, rdiag_abs, method);
   if (!st) store_vec_dm(K, P, n, d, dxs, dx);
   free(as);
   free(bs);
   free(dxs);
   return st;
+}
+
+int orc_linsolve(int K, int cplx, int n, int d, const double *A, const double *b, double *dx, double *rdiag_abs) {
+  return orc_linsolve_m(K, cplx, n, d, A, b, dx, rdiag_abs, 0);
 }
 
 /* ------------------------------------------------------ one Newton step */
@@ -926,8 +1049,9 @@ int orc_linsolve(int K, int cplx, int n, int d, const double *A, const double *b
  * (size of the update of the highest-degree coefficient, Sec. 6, from the leading
  * limbs), dxnorm[1] = max over all coefficients of |dx_{k,i}|.
  */
-int orc_newton_step(int K, int cplx, int n, int d, int nmono, const int *poly_ptr, const int *nvar, const int *idx,
-                    const int *expo, const double *coef, const double *cst, double *x, double *dxnorm, double *rdiag_abs) {
+int orc_newton_step_m(int K, int cplx, int n, int d, int nmono, const int *poly_ptr, const int *nvar, const int *idx,
+                      const int *expo, const double *coef, const double *cst, double *x, double *dxnorm,
+                      double *rdiag_abs, int method) {
   int P = cplx ? 2 : 1;
   if (check_system(K, n, d, nmono, poly_ptr, nvar, idx, expo)) return 1;
   long D1 = d + 1, nn = (long)n * n;
@@ -948,7 +1072,7 @@ int orc_newton_step(int K, int cplx, int n, int d, int nmono, const int *poly_pt
       for (int p = 0; p < P; ++p) md_neg(K, fs[(long)i * D1 + k].v[p], z->v[p]);
       if (P == 1) memset(z->v[1], 0, sizeof(z->v[1]));
     }
-  int st = linsolve_internal(K, P, n, d, as, bs, dxs, rdiag_abs);
+  int st = linsolve_internal(K, P, n, d, as, bs, dxs, rdiag_abs, method);
   if (!st) {
     double nd = 0.0, ninf = 0.0;
     for (int k = 0; k <= d; ++k)
@@ -977,6 +1101,11 @@ int orc_newton_step(int K, int cplx, int n, int d, int nmono, const int *poly_pt
   return st;
 }
 
+int orc_newton_step(int K, int cplx, int n, int d, int nmono, const int *poly_ptr, const int *nvar, const int *idx,
+                    const int *expo, const double *coef, const double *cst, double *x, double *dxnorm, double *rdiag_abs) {
+  return orc_newton_step_m(K, cplx, n, d, nmono, poly_ptr, nvar, idx, expo, coef, cst, x, dxnorm, rdiag_abs, 0);
+}
+
 /* ------------------------------------- Newton with degree continuation */
 /*
  * The driver of the cyclic 128-roots run in Sec. 6: levels l = 0..nlev-1 at
@@ -990,7 +1119,7 @@ int orc_newton_step(int K, int cplx, int n, int d, int nmono, const int *poly_pt
  */
 int orc_newton_run(int K, int cplx, int n, int D, int nmono, const int *poly_ptr, const int *nvar, const int *idx,
                    const int *expo, const double *coef, const double *cst, double *x, int nlev, const int *deg,
-                   const int *maxit, double tol, double too_large, int *iters, double *dxn, int *levels) {
+                   const int *maxit, double tol, double too_large, int *iters, double *dxn, int *levels, int method) {
   int P = cplx ? 2 : 1;
   if (check_system(K, n, D, nmono, poly_ptr, nvar, idx, expo) || nlev < 1) return 1;
   for (int l = 0; l < nlev; ++l)
@@ -1006,7 +1135,7 @@ int orc_newton_run(int K, int cplx, int n, int D, int nmono, const int *poly_ptr
     double nrm[2] = {0.0, 0.0};
     int it = 0;
     while (it < maxit[l]) {
-      st = orc_newton_step(K, cplx, n, d, nmono, poly_ptr, nvar, idx, expo, coef, cst, xl, nrm, NULL);
+      st = orc_newton_step_m(K, cplx, n, d, nmono, poly_ptr, nvar, idx, expo, coef, cst, xl, nrm, NULL, method);
       if (st) break;
       ++it;
       if (nrm[0] <= tol) break;
@@ -1020,6 +1149,50 @@ int orc_newton_run(int K, int cplx, int n, int D, int nmono, const int *poly_ptr
     if (!(nrm[0] <= too_large)) break;
   }
   free(xl);
+  return st;
+}
+
+/* --------------------------------------------------- condition of A_0 */
+/*
+ * 1 / (||A_0||_1 ||A_0^{-1}||_1) (Sec. 6 quotes an estimate of the inverse
+ * condition number of A_0).  A_0^{-1} is computed column by column by solving
+ * A_0 x = e_c with the factorisation of `method`; the 1-norms use the moduli
+ * of the leading limbs, summed in double down each column.
+ * A: [P][K][d+1][n][n] as for orc_linsolve (coefficient 0 is used).
+ */
+int orc_rcond(int K, int cplx, int n, int d, const double *A, int method, double *out) {
+  int P = cplx ? 2 : 1;
+  if (K < 1 || K > MAXK || n < 1 || d < 0) return 1;
+  long nn = (long)n * n;
+  mdc *as = malloc(sizeof(mdc) * (d + 1) * nn);
+  load_mats(K, P, n, d, A, as);
+  fact f;
+  int st = fact_init(&f, method, K, P, n, as);
+  if (!st) {
+    mdc *e = malloc(sizeof(mdc) * n), *x = malloc(sizeof(mdc) * n);
+    double na = 0.0, ni = 0.0;
+    for (int c = 0; c < n; ++c) {
+      for (int i = 0; i < n; ++i) c_zero(&e[i]);
+      e[c].v[0][0] = 1.0;
+      fact_solve(&f, e, x);
+      double sa = 0.0, si = 0.0;
+      for (int r = 0; r < n; ++r) {
+        const mdc *a = &as[(long)r * n + c];
+        double re = a->v[0][0], im = P == 2 ? a->v[1][0] : 0.0;
+        sa += sqrt(re * re + im * im);
+        re = x[r].v[0][0];
+        im = P == 2 ? x[r].v[1][0] : 0.0;
+        si += sqrt(re * re + im * im);
+      }
+      if (sa > na) na = sa;
+      if (si > ni) ni = si;
+    }
+    *out = 1.0 / (na * ni);
+    free(e);
+    free(x);
+  }
+  fact_free(&f);
+  free(as);
   return st;
 }
 

@@ -91,8 +91,11 @@ def lib():
         L.md_newton_run_workspace_bytes.argtypes = [ctypes.POINTER(md_system), sched_p, i]
         L.md_newton_run_workspace_bytes.restype = sz
         L.md_newton_series_run.argtypes = [ctypes.POINTER(md_system), vp, sched_p, rep_p, vp, sz, i, vp]
+        L.md_rcond_a0.argtypes = [ctypes.POINTER(md_system), vp, sz, i, vp, vp]
+        L.md_linsolve_rcond.argtypes = [i, i, i, i, vp, vp, sz, i, vp, vp]
         for name in ("md_elementwise", "md_series_conv", "md_eval_diff", "md_linsolve_series",
-                     "md_newton_series_step", "md_get_device_status", "md_newton_series_run"):
+                     "md_newton_series_step", "md_get_device_status", "md_newton_series_run", "md_rcond_a0",
+                     "md_linsolve_rcond"):
             getattr(L, name).restype = i
         _lib = L
     return _lib
@@ -103,7 +106,8 @@ def exported_symbols():
             "md_elementwise", "md_series_conv", "md_eval_diff", "md_linsolve_series",
             "md_newton_series_step", "md_get_device_status", "md_batched_workspace_bytes",
             "md_newton_series_step_batched", "md_linsolve_series_static", "md_profile_enable",
-            "md_profile_read", "md_profile_kind_name", "md_newton_run_workspace_bytes", "md_newton_series_run"]
+            "md_profile_read", "md_profile_kind_name", "md_newton_run_workspace_bytes", "md_newton_series_run",
+            "md_rcond_a0", "md_linsolve_rcond"]
 
 
 # --------------------------------------------------------------- helpers
@@ -225,7 +229,26 @@ def newton_step(sysd: DeviceSystem, x, ws, dx_norm=None, flags: int = 0, stream=
     return x
 
 
-FLAG_OZAKI, FLAG_AUTOTUNE, FLAG_GRAPH = 0x1, 0x2, 0x4
+FLAG_OZAKI, FLAG_AUTOTUNE, FLAG_GRAPH, FLAG_SERIAL, FLAG_LU = 0x1, 0x2, 0x4, 0x8, 0x10
+
+
+def rcond_a0(sysd: DeviceSystem, ws, flags: int = 0, out=None, stream=None):
+    """1-norm reciprocal condition number of A_0 of the last newton_step on ws
+    (CUDA double tensor [1], written asynchronously)."""
+    torch = _torch()
+    out = out if out is not None else torch.empty(1, dtype=torch.float64, device=ws.device)
+    _check(lib().md_rcond_a0(sysd.c(), _ptr(ws), ws.numel(), flags, _ptr(out), _stream(stream)), "md_rcond_a0")
+    return out
+
+
+def linsolve_rcond(limbs: int, is_complex: bool, A, ws, flags: int = 0, out=None, stream=None):
+    """Same for the A_0 of the last linsolve(A) on ws."""
+    torch = _torch()
+    n, d = A.shape[3], A.shape[2] - 1
+    out = out if out is not None else torch.empty(1, dtype=torch.float64, device=ws.device)
+    _check(lib().md_linsolve_rcond(limbs, int(is_complex), n, d, _ptr(A), _ptr(ws), ws.numel(), flags, _ptr(out),
+                                   _stream(stream)), "md_linsolve_rcond")
+    return out
 
 
 def schedule(degrees, max_iter, tol: float = 1e-32, too_large: float = 1.0) -> md_newton_schedule:

@@ -41,6 +41,7 @@ cudaError_t dispatch_p(int P, int what, const void *a, cudaStream_t s, int op = 
       case 6: return mdk::Impl<K, 1>::eval_rest(*static_cast<const EvalDev *>(a), s);
       case 7: return mdk::Impl<K, 1>::factor(*static_cast<const SolveDev *>(a), s);
       case 8: return mdk::Impl<K, 1>::degrees(*static_cast<const SolveDev *>(a), s);
+      case 9: return mdk::Impl<K, 1>::rcond(*static_cast<const SolveDev *>(a), s);
     }
   } else {
     switch (what) {
@@ -55,6 +56,7 @@ cudaError_t dispatch_p(int P, int what, const void *a, cudaStream_t s, int op = 
       case 6: return mdk::Impl<K, 2>::eval_rest(*static_cast<const EvalDev *>(a), s);
       case 7: return mdk::Impl<K, 2>::factor(*static_cast<const SolveDev *>(a), s);
       case 8: return mdk::Impl<K, 2>::degrees(*static_cast<const SolveDev *>(a), s);
+      case 9: return mdk::Impl<K, 2>::rcond(*static_cast<const SolveDev *>(a), s);
     }
   }
   return cudaErrorInvalidValue;
@@ -783,7 +785,7 @@ void prof_end(int id, cudaStream_t s) {
 namespace {
 const char *kProfNames[mdk::PK_COUNT] = {"pool_load_x", "prep_scal", "conv_stage", "accum", "qr_house", "qr_apply",
                                          "rinv", "backsub", "rhs_partial", "rhs_finish", "wmv", "finish_dx",
-                                         "elementwise", "series_conv", "oz_split", "oz_gemm", "oz_accum"};
+                                         "elementwise", "series_conv", "oz_split", "oz_gemm", "oz_accum", "lu"};
 
 md_status check_schedule(const md_system *s, const md_newton_schedule *sc) {
   if (!sc || sc->nlevels < 1 || sc->nlevels > MD_MAX_LEVELS) return MD_ERR_ARG;
@@ -900,6 +902,7 @@ md_status md_linsolve_series(int limbs, int is_complex, int n, int degree, const
   v.b = b;
   v.sgn = 1.0;
   v.dx_out = dx;
+  v.lu = (flags & MD_FLAG_LU) ? 1 : 0;
   return cuda_status(dispatch(limbs, P, 3, &v, s));
 }
 
@@ -922,6 +925,7 @@ md_status md_newton_series_step(const md_system *sys, double *x, double *dx_norm
   v.sgn = -1.0;
   v.x = x;
   v.nrm = dx_norm;
+  v.lu = (flags & MD_FLAG_LU) ? 1 : 0;
   DevAux *ax = (flags & MD_FLAG_SERIAL) ? nullptr : aux_for_current_device();
   if (!ax) {
     if (dispatch(p->K, p->P, 2, &e, s) != cudaSuccess) return MD_ERR_CUDA;
@@ -941,6 +945,32 @@ md_status md_newton_series_step(const md_system *sys, double *x, double *dx_norm
   if (dispatch(p->K, p->P, 6, &e, s) != cudaSuccess) return MD_ERR_CUDA;
   if (cudaStreamWaitEvent(s, ax->e1, 0) != cudaSuccess) return MD_ERR_CUDA;
   return cuda_status(dispatch(p->K, p->P, 8, &v, s));
+}
+
+md_status md_rcond_a0(const md_system *sys, void *ws, size_t ws_bytes, int flags, double *rcond, void *stream) {
+  if (!rcond) return MD_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Plan *p = nullptr;
+  md_status st = prepare(sys, ws, ws_bytes, s, p, flags);
+  if (st != MD_OK) return st;
+  char *base = static_cast<char *>(ws);
+  SolveDev v = make_solve(p->sl, p->n, p->d, base);
+  v.A = reinterpret_cast<const double *>(base + p->off_A);
+  v.rcond = rcond;
+  return cuda_status(dispatch(p->K, p->P, 9, &v, s));
+}
+
+md_status md_linsolve_rcond(int limbs, int is_complex, int n, int degree, const double *A, void *ws,
+                            size_t ws_bytes, int flags, double *rcond, void *stream) {
+  if (!valid_limbs(limbs) || n < 1 || degree < 0 || !A || !rcond) return MD_ERR_ARG;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return MD_ERR_WORKSPACE;
+  const int P = is_complex ? 2 : 1;
+  SolveLayout L = solve_layout(limbs, P, n, degree, 256, flags);
+  if (256 + L.bytes > ws_bytes) return MD_ERR_WORKSPACE;
+  SolveDev v = make_solve(L, n, degree, static_cast<char *>(ws));
+  v.A = A;
+  v.rcond = rcond;
+  return cuda_status(dispatch(limbs, P, 9, &v, static_cast<cudaStream_t>(stream)));
 }
 
 size_t md_newton_run_workspace_bytes(const md_system *sys, const md_newton_schedule *sched, int flags) {
@@ -1005,6 +1035,7 @@ size_t md_batched_workspace_bytes(int nsys, const md_system *sys, int flags) {
 md_status md_newton_series_step_batched(int nsys, const md_system *sys, double *const *x, double *dx_norm,
                                         unsigned long long *times, void *ws, size_t ws_bytes, int flags,
                                         void *stream) {
+  if (flags & MD_FLAG_LU) return MD_ERR_UNSUPPORTED;
   if (nsys < 1 || !sys || !x) return MD_ERR_ARG;
   for (int i = 0; i < nsys; ++i)
     if (!x[i]) return MD_ERR_ARG;

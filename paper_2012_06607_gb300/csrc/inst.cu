@@ -16,6 +16,7 @@ template cudaError_t mdk::Impl<MDK_K, MDK_P>::eval_rest(const mdk::EvalDev &, cu
 template cudaError_t mdk::Impl<MDK_K, MDK_P>::solve(const mdk::SolveDev &, cudaStream_t);
 template cudaError_t mdk::Impl<MDK_K, MDK_P>::factor(const mdk::SolveDev &, cudaStream_t);
 template cudaError_t mdk::Impl<MDK_K, MDK_P>::degrees(const mdk::SolveDev &, cudaStream_t);
+template cudaError_t mdk::Impl<MDK_K, MDK_P>::rcond(const mdk::SolveDev &, cudaStream_t);
 #elif MDK_PART == 3
 template cudaError_t mdk::Impl<MDK_K, MDK_P>::batched(const mdk::BatchDev &, cudaStream_t);
 #endif

@@ -12,7 +12,7 @@ enum : int { ST_SINGULAR = 1, ST_NONFINITE = 2 };
 enum ProfKind : int {
   PK_POOL = 0, PK_SCAL, PK_CONV, PK_ACCUM, PK_QR_HOUSE, PK_QR_APPLY, PK_RINV, PK_BACKSUB,
   PK_RHS_PARTIAL, PK_RHS_FINISH, PK_WMV, PK_FINISH, PK_ELEMENTWISE, PK_SERIES, PK_OZ_SPLIT, PK_OZ_GEMM,
-  PK_OZ_ACCUM, PK_COUNT
+  PK_OZ_ACCUM, PK_LU, PK_COUNT
 };
 bool prof_enabled();
 int prof_begin(int kind, cudaStream_t s);
@@ -68,6 +68,8 @@ struct SolveDev {
   double *r = nullptr, *dxw = nullptr, *part = nullptr;
   int *status = nullptr;
   int maxchunk = 1;
+  int lu = 0;                 // factor A_0 by LU with partial pivoting instead of QR
+  double *rcond = nullptr;    // rcond kernel output (device double)
   // split-product form (ozaki != 0)
   int ozaki = 0;
   void *oz_As = nullptr, *oz_Xs = nullptr;  // bf16 slices
@@ -134,6 +136,7 @@ struct Impl {
   static cudaError_t solve(const SolveDev &v, cudaStream_t s);
   static cudaError_t factor(const SolveDev &v, cudaStream_t s);    // QR, Q^H, W = R^-1 Q^H
   static cudaError_t degrees(const SolveDev &v, cudaStream_t s);   // degree loop and update
+  static cudaError_t rcond(const SolveDev &v, cudaStream_t s);     // 1-norm rcond of A_0 from A_0 and W
 };
 
 }  // namespace mdk

@@ -762,6 +762,154 @@ __global__ void backsub_kernel(const double *__restrict__ M, double *__restrict_
   backsub_entry<K, P>(M, Y, W, rinv, n, c, e);
 }
 
+// ------------------------------------------------------------ LU (N = n)
+// Gaussian elimination with partial pivoting, the factorisation Section 4
+// allows when N = n.  Column j: pivot row p = the first row i >= j with the
+// largest |re| + |im| of the leading limbs; rows j and p are swapped in M and
+// in Y (Y starts as I and so ends as the permutation P); multipliers
+// l_ij = M_ij * (1 / M_jj); trailing update M_ik -= l_ij M_jk.  Afterwards
+// L Z = P (unit lower triangular, forward) overwrites Y, and U W = Z is the
+// back substitution of the QR path with U in the upper triangle of M, so that
+// W = U^-1 L^-1 P = A_0^-1 feeds the same degree loop.
+template <int P>
+__device__ __forceinline__ double cabs1_lead(const double *v, int K) {
+  return fabs(v[0]) + (P == 2 ? fabs(v[K]) : 0.0);
+}
+
+template <int K, int P>
+__global__ void __launch_bounds__(128) lu_pivot_kernel(double *M, double *Y, double *rinv, int *status, int n, int j) {
+  __shared__ double s_val[128];
+  __shared__ int s_idx[128];
+  const int tid = threadIdx.x;
+  const long long VS = P * K;
+  double best = -1.0;
+  int bi = j;
+  for (int i = j + tid; i < n; i += blockDim.x) {
+    const double v = cabs1_lead<P>(M + ((long long)j * n + i) * VS, K);
+    if (v > best) {  // rows visited in increasing order: ties keep the first
+      best = v;
+      bi = i;
+    }
+  }
+  s_val[tid] = best;
+  s_idx[tid] = bi;
+  __syncthreads();
+  for (int off = 64; off > 0; off >>= 1) {
+    if (tid < off) {
+      const double a = s_val[tid], b = s_val[tid + off];
+      const int ia = s_idx[tid], ib = s_idx[tid + off];
+      if (b > a || (b == a && ib < ia)) {
+        s_val[tid] = b;
+        s_idx[tid] = ib;
+      }
+    }
+    __syncthreads();
+  }
+  const int p = s_idx[0];
+  if (tid == 0 && !(s_val[0] > 0.0)) atomicOr(status, ST_SINGULAR);
+  if (p != j) {
+    for (int c = tid; c < 2 * n; c += blockDim.x) {
+      double *T = c < n ? M : Y;
+      const int cc = c < n ? c : c - n;
+      mdv<K, P> a, b;
+      ld_aos<K, P>(T + ((long long)cc * n + j) * VS, a);
+      ld_aos<K, P>(T + ((long long)cc * n + p) * VS, b);
+      st_aos<K, P>(T + ((long long)cc * n + j) * VS, b);
+      st_aos<K, P>(T + ((long long)cc * n + p) * VS, a);
+    }
+  }
+  __syncthreads();
+  __shared__ mdv<K, P> s_ri;
+  if (tid == 0) {
+    mdv<K, P> piv, one, ri;
+    ld_aos<K, P>(M + ((long long)j * n + j) * VS, piv);
+    c_zero<K, P>(one);
+    one.v[0][0] = 1.0;
+    c_div<K, P>(one, piv, ri);
+    st_aos<K, P>(rinv + (long long)j * VS, ri);
+    s_ri = ri;
+  }
+  __syncthreads();
+  const mdv<K, P> ri = s_ri;
+  for (int i = j + 1 + tid; i < n; i += blockDim.x) {
+    mdv<K, P> a, l;
+    ld_aos<K, P>(M + ((long long)j * n + i) * VS, a);
+    c_mul<K, P>(a, ri, l);
+    st_aos<K, P>(M + ((long long)j * n + i) * VS, l);
+  }
+}
+
+// Trailing update of column j: M_ik -= l_ij M_jk for i, k > j.
+template <int K, int P>
+__global__ void lu_update_kernel(double *__restrict__ M, int n, int j) {
+  const int m = n - j - 1;
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)m * m) return;
+  const int i = j + 1 + (int)(e % m), k = j + 1 + (int)(e / m);
+  const long long VS = P * K;
+  mdv<K, P> l, u, a, t;
+  ld_aos<K, P>(M + ((long long)j * n + i) * VS, l);
+  ld_aos<K, P>(M + ((long long)k * n + j) * VS, u);
+  ld_aos<K, P>(M + ((long long)k * n + i) * VS, a);
+  c_mul<K, P>(l, u, t);
+  c_sub<K, P>(a, t, a);
+  st_aos<K, P>(M + ((long long)k * n + i) * VS, a);
+}
+
+// Forward substitution step j of L Z = Y (unit diagonal): Y_ic -= L_ij Y_jc, i > j.
+template <int K, int P>
+__global__ void lu_forward_kernel(const double *__restrict__ M, double *__restrict__ Y, int n, int j) {
+  const int m = n - j - 1;
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)m * n) return;
+  const int i = j + 1 + (int)(e % m), c = (int)(e / m);
+  const long long VS = P * K;
+  mdv<K, P> l, z, y, t;
+  ld_aos<K, P>(M + ((long long)j * n + i) * VS, l);
+  ld_aos<K, P>(Y + ((long long)c * n + j) * VS, z);
+  ld_aos<K, P>(Y + ((long long)c * n + i) * VS, y);
+  c_mul<K, P>(l, z, t);
+  c_sub<K, P>(y, t, y);
+  st_aos<K, P>(Y + ((long long)c * n + i) * VS, y);
+}
+
+// 1 / (||A_0||_1 ||W||_1) from the leading limbs (moduli in double): the
+// reciprocal condition number of A_0 in the 1-norm, W = A_0^-1 being formed by
+// the solve.  A: caller layout [P][K][d+1][n][n] (coefficient 0, column-major);
+// W: row-major AoS.  One CTA.
+template <int K, int P>
+__global__ void __launch_bounds__(256) rcond_kernel(const double *__restrict__ A, const double *__restrict__ W,
+                                                    double *__restrict__ out, int n, int d) {
+  __shared__ double s_max[2][256];
+  const int tid = threadIdx.x;
+  const long long nn = (long long)n * n, pstride = (long long)K * (d + 1) * nn, VS = P * K;
+  double ma = 0.0, mw = 0.0;
+  for (int c = tid; c < n; c += blockDim.x) {
+    double sa = 0.0, sw = 0.0;
+    for (int r = 0; r < n; ++r) {
+      const double are = A[(long long)c * n + r];
+      const double aim = P == 2 ? A[pstride + (long long)c * n + r] : 0.0;
+      sa += sqrt(are * are + aim * aim);
+      const double *w = W + ((long long)r * n + c) * VS;
+      const double wre = w[0], wim = P == 2 ? w[K] : 0.0;
+      sw += sqrt(wre * wre + wim * wim);
+    }
+    ma = fmax(ma, sa);
+    mw = fmax(mw, sw);
+  }
+  s_max[0][tid] = ma;
+  s_max[1][tid] = mw;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if (tid < off) {
+      s_max[0][tid] = fmax(s_max[0][tid], s_max[0][tid + off]);
+      s_max[1][tid] = fmax(s_max[1][tid], s_max[1][tid + off]);
+    }
+    __syncthreads();
+  }
+  if (tid == 0) out[0] = 1.0 / (s_max[0][0] * s_max[1][0]);
+}
+
 // Partial sums of sum_{j<k} A_{k-j} dx_j for item e = (row, chunk); term index
 // t = j*n + col over [chunk*C, min((chunk+1)*C, k*n)).  A is the caller's
 // SoA [P][K][d+1][n][n] (column-major blocks); dx is AoS [k][i].

@@ -147,6 +147,25 @@ cudaError_t Impl<K, P>::factor(const SolveDev &v, cudaStream_t s) {
     ProfScope prof(PK_QR_HOUSE, s);
     solve_init_kernel<K, P><<<blocks_for(nn, 128), 128, 0, s>>>(v.A, v.M, v.Y, n, d);
   }
+  if (v.lu) {
+    // LU with partial pivoting, L Z = P, then the shared back substitution
+    for (int j = 0; j < n; ++j) {
+      ProfScope prof(PK_LU, s);
+      lu_pivot_kernel<K, P><<<1, 128, 0, s>>>(v.M, v.Y, v.rinv, v.status, n, j);
+      const long long m = n - j - 1;
+      if (m > 0) lu_update_kernel<K, P><<<blocks_for(m * m, 128), 128, 0, s>>>(v.M, n, j);
+    }
+    for (int j = 0; j + 1 < n; ++j) {
+      ProfScope prof(PK_LU, s);
+      const long long m = n - j - 1;
+      lu_forward_kernel<K, P><<<blocks_for(m * n, 128), 128, 0, s>>>(v.M, v.Y, n, j);
+    }
+    for (int c = n - 1; c >= 0; --c) {
+      ProfScope prof(PK_BACKSUB, s);
+      backsub_kernel<K, P><<<blocks_for((long long)(c + 1) * n, 64), 64, 0, s>>>(v.M, v.Y, v.W, v.rinv, n, c);
+    }
+    return cudaGetLastError();
+  }
   {
     ProfScope prof(PK_QR_HOUSE, s);
     house_kernel<K, P><<<1, kHouseThreads, 0, s>>>(v.M, v.vd, v.beta, v.status, n, 0);
@@ -166,6 +185,12 @@ cudaError_t Impl<K, P>::factor(const SolveDev &v, cudaStream_t s) {
     ProfScope prof(PK_BACKSUB, s);
     backsub_kernel<K, P><<<blocks_for((long long)(c + 1) * n, 64), 64, 0, s>>>(v.M, v.Y, v.W, v.rinv, n, c);
   }
+  return cudaGetLastError();
+}
+
+template <int K, int P>
+cudaError_t Impl<K, P>::rcond(const SolveDev &v, cudaStream_t s) {
+  rcond_kernel<K, P><<<1, 256, 0, s>>>(v.A, v.W, v.rcond, v.n, v.d);
   return cudaGetLastError();
 }
 

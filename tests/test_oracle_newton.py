@@ -126,8 +126,10 @@ def test_step_exact_brute_force(orc, seed, n, d, K):
             assert abs(a[1] - b[1]) <= 1000 * eps(K) * sc * 100
 
 
-def test_linsolve_backward_error(orc):
-    """Per degree: ||b_k - sum_{i<=k} A_i dx_{k-i}|| <= 1e3 eps (sum ||A_i|| ||dx_{k-i}|| + ||b_k||)."""
+@pytest.mark.parametrize("method", [0, 1])
+def test_linsolve_backward_error(orc, method):
+    """Per degree: ||b_k - sum_{i<=k} A_i dx_{k-i}|| <= 1e3 eps (sum ||A_i|| ||dx_{k-i}|| + ||b_k||);
+    A_0 factored by Householder QR (method 0) or LU with partial pivoting (1)."""
     K, n, d = 4, 6, 6
     rng = np.random.default_rng(11)
     A = rng.standard_normal((2, K, d + 1, n, n)) * np.array([1.0] + [2.0 ** (-53 * l) for l in range(1, K)])[None, :, None, None, None]
@@ -141,7 +143,7 @@ def test_linsolve_backward_error(orc):
         for p in range(2):
             for c in range(flat.shape[2]):
                 flat[p, :, c] = mdgen.md_from_fraction(mdgen.md_to_fraction(flat[p, :, c]), K)
-    dx = orc.linsolve(K, True, A, b)
+    dx = orc.linsolve(K, True, A, b, method=method)
     Ae = exact.mat_series_exact(A)
     be = exact.vec_series_exact(b)
     dxe = exact.vec_series_exact(dx)
@@ -303,3 +305,66 @@ def test_newton_run_rejects_bad_schedules(orc):
     for deg, mi in (([9], [1]), ([4, 2], [1, 1]), ([4], [0]), ([-1], [1])):
         with pytest.raises(RuntimeError):
             orc.newton_run(s, deg, mi, 1e-28, 1.0, x0)
+
+
+# ------------------------------------------------------------ LU and rcond
+def _mat_series(K, rows, d=0, cplx=False):
+    """[P][K][d+1][n][n] from exact rows of coefficient 0 (others zero)."""
+    n = len(rows)
+    P = 2 if cplx else 1
+    A = np.zeros((P, K, d + 1, n, n))
+    for r in range(n):
+        for c in range(n):
+            A[0, :, 0, c, r] = mdgen.md_from_fraction(Fraction(rows[r][c]), K)
+    return A
+
+
+def test_lu_needs_and_takes_the_pivot(orc):
+    """A_0 = [[0, 1], [1, 1]] has a zero (0,0) entry: only a pivoting LU solves
+    it; the solution of A_0 x = (1, 2) is (1, 1) exactly."""
+    K = 2
+    A = _mat_series(K, [[0, 1], [1, 1]])
+    b = np.zeros((1, K, 2, 1))
+    b[0, 0, 0, 0], b[0, 0, 1, 0] = 1.0, 2.0
+    for method in (0, 1):
+        dx = orc.linsolve(K, False, A, b, method=method)
+        assert abs(dx[0, 0, 0, 0] - 1.0) <= 1e-30 and abs(dx[0, 0, 1, 0] - 1.0) <= 1e-30, method
+    dx = orc.linsolve(K, False, A, b, method=1)
+    assert dx[0, 0, 0, 0] == 1.0 and dx[0, 0, 1, 0] == 1.0 and not dx[0, 1].any()
+
+
+def test_lu_singular_reported(orc):
+    A = _mat_series(2, [[1, 2], [2, 4]])
+    b = np.ones((1, 2, 2, 1))
+    with pytest.raises(RuntimeError):
+        orc.linsolve(2, False, A, b, method=1)
+
+
+@pytest.mark.parametrize("method", [0, 1])
+def test_rcond_closed_forms(orc, method):
+    """1 / (||A||_1 ||A^-1||_1) for matrices whose inverse is known exactly."""
+    K = 4
+    # diagonal: min |d_i| / max |d_i|
+    assert orc.rcond(K, False, _mat_series(K, [[4, 0, 0], [0, -0.5, 0], [0, 0, 2]]), method) == 0.125
+    # unit upper triangular [[1, a], [0, 1]]: inverse [[1, -a], [0, 1]], rcond = 1/(1+|a|)^2
+    a = 3.0
+    assert orc.rcond(K, False, _mat_series(K, [[1, a], [0, 1]]), method) == pytest.approx(1 / (1 + a) ** 2, rel=1e-15)
+    # permutation and scaled identity: 1
+    assert orc.rcond(K, False, _mat_series(K, [[0, 0, 1], [1, 0, 0], [0, 1, 0]]), method) == pytest.approx(1.0, rel=1e-15)
+    assert orc.rcond(K, False, _mat_series(K, [[7, 0], [0, 7]]), method) == pytest.approx(1.0, rel=1e-15)
+
+
+def test_rcond_within_norm_equivalence_of_cond2(orc):
+    """A_0 = U diag(sigma) V^T with orthogonal U, V and sigma log-spaced on
+    [1e-8, 1]: cond_2 = 1e8 up to double rounding of U, V, and the 1-norm
+    condition number lies within a factor n of it."""
+    n, K = 16, 4
+    rng = np.random.default_rng(5)
+    U, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A0 = U @ np.diag(np.logspace(0, -8, n)) @ V.T
+    A = np.zeros((1, K, 1, n, n))
+    A[0, 0, 0] = A0.T  # column-major blocks
+    for method in (0, 1):
+        rc = orc.rcond(K, False, A, method)
+        assert 1e-8 / n / 1.001 <= rc <= n * 1e-8 * 1.001, (method, rc)
