@@ -42,6 +42,12 @@ TABLE1 = {2: (20, 23), 3: (35, 209), 4: (89, 336), 5: (122, 554), 8: (269, 1742)
 # FP64 peak derived from unit counts and clocks: 152 SMs x 2 FP64 lanes per SM per
 # cycle x 2.07 GHz (the nominal 1.25 TFLOP/s counting an FMA as two flops).
 FP64_PEAK_INSTR = 152 * 2 * 2.07e9
+# DRAM bytes (read + write) per launch of the series-product kernel at this
+# workload: ncu dram__bytes_read.sum + dram__bytes_write.sum of the three
+# launches of one step, averaged (8.74 + 32.11 + 9.06 MB), captured on the
+# kernel as it stands; it must be retaken (or set to None) whenever that
+# kernel changes.
+CONV_TRAFFIC_BYTES_PER_LAUNCH = 16.64e6
 
 
 # ----------------------------------------------------------------- op model
@@ -283,7 +289,9 @@ def run_product(args):
     achieved = args.steps * conv_instr / (conv_ms / 1e3) if conv_ms > 0 else None
     roofline = {"bound": "alu", "kernel": "conv_stage", "achieved": achieved / 1e12 if achieved else None,
                 "peak": FP64_PEAK_INSTR / 1e12, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_INSTR if achieved else None,
-                "traffic": None, "counted": "FP64 instructions of the md algorithms (an fma counts once)",
+                "traffic": CONV_TRAFFIC_BYTES_PER_LAUNCH if args.update == "md" else None,
+                "traffic_unit": "bytes per launch (ncu DRAM read + write)",
+                "counted": "FP64 instructions of the md algorithms (an fma counts once)",
                 "launches_in_timed_region": conv_launches, "avg_launch_ms": conv_ms / max(conv_launches, 1),
                 "dominant_by_time": dom_name,
                 "paper_ops_per_s": args.steps * conv_paper / (conv_ms / 1e3) if conv_ms > 0 else None,
