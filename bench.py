@@ -413,6 +413,66 @@ def run_solve3(args):
     return 0
 
 
+def run_ladder(args):
+    """The cost of higher precision (Section 2, Table 1): the Newton step of
+    the same system (the headline workload, its exact coefficients re-expanded
+    into K limbs) at every precision K in {1, 2, 3, 4, 5, 8, 10}."""
+    import torch
+
+    import mdgen
+    import paper_2012_06607_gb300 as md
+
+    base = mdgen.config_system(CFG, args.seed)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    per = {}
+    for K in (1, 2, 3, 4, 5, 8, 10):
+        s = base if K == base.limbs else base.with_limbs(K)
+        sysd = md.DeviceSystem(s)
+        ws = md.workspace(sysd.workspace_bytes())
+        x = md.to_device(s.x0)
+        for _ in range(args.warmup):
+            md.newton_step(sysd, x, ws)
+        torch.cuda.synchronize()
+        md.profile_read()
+        md.profile_enable(True)
+        evs = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            md.newton_step(sysd, x, ws)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        md.profile_enable(False)
+        prof = md.profile_read()
+        assert md.device_status(ws) == 0
+        ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+        cmul_i, cadd_i = complex_mac_instr(K, s.planes)
+        nconv = conv_schedule_counts(s)
+        d = s.degree
+        conv_instr = nconv * ((d + 1) * (d + 2) // 2 * cmul_i + d * (d + 1) // 2 * cadd_i)
+        conv_ms = prof.get("conv_stage", (float("nan"), 0))[0] / args.steps
+        t1 = TABLE1.get(K)
+        per[K] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "conv_ms_per_step": conv_ms,
+                  "conv_fp64_instr_per_step": conv_instr,
+                  "conv_fp64_frac_of_peak": conv_instr / (conv_ms / 1e3) / FP64_PEAK_INSTR if conv_ms > 0 else None,
+                  "table1_ops_per_complex_mac": (4 * t1[1] + 4 * t1[0]) if t1 else None}
+        del ws, sysd, x
+        torch.cuda.empty_cache()
+    dd = per[2]["ms_per_step"]
+    for K in per:
+        per[K]["time_vs_dd"] = per[K]["ms_per_step"] / dd
+    line = {"metric": "power-series Newton steps/s per precision (n=64, d=64, complex)", "form": "precision ladder",
+            "unit": "steps/s", "per_limbs": per, "steps": args.steps, "warmup": args.warmup,
+            "config": {"workload": WORKLOAD.replace("quad double", "K-limb") + " (same exact coefficients)",
+                       "l2": "flushed between steps"},
+            "data": "synthetic", "dtype": "f64 (K limbs)"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batched(args):
     """2048 complex systems, n ~ U{8..64}, d ~ U{8..32}, double double / quad
     double: one persistent launch per precision class per Newton iteration
@@ -488,9 +548,9 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--impl", default="product", choices=["product", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--form", default="plain", choices=["plain", "solve3", "batched"],
+    ap.add_argument("--form", default="plain", choices=["plain", "solve3", "batched", "ladder"],
                     help="plain: the Newton-step benchmark; solve3: plain vs split-product solve; "
-                         "batched: 2048-system batched step vs a per-system loop")
+                         "batched: 2048-system batched step vs a per-system loop; ladder: the headline step at every precision")
     ap.add_argument("--update", default="md", choices=["md", "split"],
                     help="block Toeplitz update of the plain form: md arithmetic or split-product")
     ap.add_argument("--batch", type=int, default=2048)
@@ -504,6 +564,8 @@ def main():
         return run_solve3(args)
     if args.form == "batched":
         return run_batched(args)
+    if args.form == "ladder":
+        return run_ladder(args)
     return run_product(args)
 
 

@@ -53,20 +53,26 @@ typedef enum md_status {
 #define MD_MAXV 4
 
 /*
- * A polynomial system f(x) = 0 of n polynomials in the n unknowns x_0..x_{n-1}
- * and the series parameter t, which has variable index n (Section 4: systems
- * with one more variable than equations have power series solutions; t is the
- * extra variable).  Polynomial i is cst[i] + sum over its monomials
- * m in [poly_ptr[i], poly_ptr[i+1]) of coef[m] * prod_q var(idx[m][q])^expo[m][q].
+ * A polynomial system f(x) = 0 of N polynomials in the n unknowns
+ * x_0..x_{n-1} and the series parameter t, which has variable index n
+ * (Section 4: systems with one more variable than equations have power series
+ * solutions; t is the extra variable).  N = n unless neq > n: then the linear
+ * systems of every Newton step are solved in the least squares sense with the
+ * QR of the N x n matrix A_0 (Section 4, N > n).  Polynomial i is
+ * cst[i] + sum over its monomials m in [poly_ptr[i], poly_ptr[i+1]) of
+ * coef[m] * prod_q var(idx[m][q])^expo[m][q].
  *
  *   structure (HOST pointers, read during the call):
- *     poly_ptr [n+1]            CSR offsets, poly_ptr[0] = 0, poly_ptr[n] = nmono
+ *     poly_ptr [N+1]            CSR offsets, poly_ptr[0] = 0, poly_ptr[N] = nmono
  *     nvar     [nmono]          number of used pairs, 0..MD_MAXV
  *     idx      [nmono*MD_MAXV]  distinct variable indices in 0..n (n = t)
  *     expo     [nmono*MD_MAXV]  exponents >= 1 for the used pairs
  *   values (DEVICE pointers):
  *     coef     [P][K][nmono]    monomial coefficients
- *     cst      [P][K][n]        constant terms
+ *     cst      [P][K][N]        constant terms
+ *   neq: N (0 means N = n; otherwise N >= n).  N > n is not available with
+ *        MD_FLAG_LU (MD_ERR_ARG), MD_FLAG_OZAKI or the batched form
+ *        (MD_ERR_UNSUPPORTED).
  */
 typedef struct md_system {
   int limbs;
@@ -80,6 +86,7 @@ typedef struct md_system {
   const int *expo;
   const double *coef;
   const double *cst;
+  int neq;
 } md_system;
 
 /* flags */
@@ -155,8 +162,8 @@ md_status md_series_conv(int limbs, int is_complex, int degree, long long count,
  *   f[i](t)   = f_i(x(t), t) truncated at degree d,
  *   A_k[i][j] = coefficient k of d f_i / d x_j (x(t), t),  j < n (no t column).
  *   x: DEVICE [P][K][n][d+1]     input series
- *   f: DEVICE [P][K][n][d+1]     output
- *   A: DEVICE [P][K][d+1][n][n]  output (column-major blocks)
+ *   f: DEVICE [P][K][N][d+1]     output
+ *   A: DEVICE [P][K][d+1][n][N]  output (column-major N x n blocks)
  *   ws: DEVICE workspace of md_workspace_bytes(sys, 0) bytes.
  * Monomials are evaluated with Speelpenning products (value and all partials
  * at about three times the cost of the value); every sum is taken in the order
@@ -177,6 +184,22 @@ md_status md_eval_diff(const md_system *sys, const double *x, double *f, double 
  */
 md_status md_linsolve_series(int limbs, int is_complex, int n, int degree, const double *A, const double *b,
                              double *dx, void *ws, size_t ws_bytes, int flags, void *stream);
+
+/*
+ * The same for an N x n A_0 with N >= n equations (Section 4: for N > n the
+ * linear systems are solved in the least squares sense, with QR): per degree
+ * dx_k minimises ||A_0 dx_k - r_k||_2, r_k = b_k - sum_{j<k} A_{k-j} dx_j,
+ * through dx_k = R^-1 (Q^H r_k)[0:n].
+ *   A : DEVICE [P][K][d+1][n][N]  (read only, column-major N x n blocks)
+ *   b : DEVICE [P][K][N][d+1]
+ *   dx: DEVICE [P][K][n][d+1]     output
+ *   ws: DEVICE workspace of md_lstsq_workspace_bytes(...) bytes (0 = invalid).
+ * neq < n is MD_ERR_ARG; with neq > n, MD_FLAG_LU is MD_ERR_ARG and
+ * MD_FLAG_OZAKI is MD_ERR_UNSUPPORTED.  md_linsolve_series is neq = n.
+ */
+size_t md_lstsq_workspace_bytes(int limbs, int is_complex, int neq, int n, int degree, int flags);
+md_status md_lstsq_series(int limbs, int is_complex, int neq, int n, int degree, const double *A, const double *b,
+                          double *dx, void *ws, size_t ws_bytes, int flags, void *stream);
 
 /*
  * One Newton step on truncated power series (Section 4): x <- x + dx where
@@ -262,6 +285,10 @@ md_status md_linsolve_series_static(int limbs, int is_complex, int n, int degree
 md_status md_rcond_a0(const md_system *sys, void *ws, size_t ws_bytes, int flags, double *rcond, void *stream);
 md_status md_linsolve_rcond(int limbs, int is_complex, int n, int degree, const double *A, void *ws,
                             size_t ws_bytes, int flags, double *rcond, void *stream);
+/* N x n A_0 after md_lstsq_series: 1 / (||A_0||_1 ||A_0^+||_1), A_0^+ the
+   pseudo-inverse R^-1 (Q^H)[0:n, :] that the solve forms. */
+md_status md_lstsq_rcond(int limbs, int is_complex, int neq, int n, int degree, const double *A, void *ws,
+                         size_t ws_bytes, int flags, double *rcond, void *stream);
 
 /*
  * Newton's method with degree continuation (the cyclic 128-roots experiment

@@ -112,10 +112,15 @@ class System:
     seed: Optional[int] = None
     name: str = ""
     meta: dict = field(default_factory=dict)
+    neq: int = 0  # number of polynomials N >= n (0: N = n); poly_ptr has N+1 entries, cst N columns
 
     @property
     def planes(self) -> int:
         return 2 if self.is_complex else 1
+
+    @property
+    def N(self) -> int:
+        return self.neq if self.neq else self.n
 
     @property
     def nmono(self) -> int:
@@ -143,15 +148,41 @@ class System:
 
         return System(K, self.is_complex, self.n, self.degree, self.poly_ptr.copy(), self.nvar.copy(),
                       self.idx.copy(), self.expo.copy(), conv(self.coef), conv(self.cst), conv(self.x0),
-                      self.seed, self.name, dict(self.meta))
+                      self.seed, self.name, dict(self.meta), neq=self.neq)
+
+    def augmented(self, rows, scales) -> "System":
+        """Append copies of polynomials rows[r] multiplied by scales[r] (powers of
+        two, so the copies are exact): an overdetermined but consistent system
+        whose least squares solution is the solution of this one."""
+        P, K = self.planes, self.limbs
+        pp = [int(v) for v in self.poly_ptr]
+        nvar, idx, expo = list(self.nvar), list(self.idx), list(self.expo)
+        coef = [self.coef[..., m] for m in range(self.nmono)]
+        cst = [self.cst[..., i] for i in range(self.N)]
+        for r, sc in zip(rows, scales):
+            assert sc != 0 and math.frexp(abs(sc))[0] == 0.5, "scales must be powers of two"
+            for m in range(self.poly_ptr[r], self.poly_ptr[r + 1]):
+                nvar.append(int(self.nvar[m]))
+                idx.extend(int(v) for v in self.idx[m * MAXV:(m + 1) * MAXV])
+                expo.extend(int(v) for v in self.expo[m * MAXV:(m + 1) * MAXV])
+                coef.append(self.coef[..., m] * sc)
+            pp.append(len(nvar))
+            cst.append(self.cst[..., r] * sc)
+        N = len(pp) - 1
+        return System(K, self.is_complex, self.n, self.degree, np.array(pp, np.int32), np.array(nvar, np.int32),
+                      np.array(idx, np.int32), np.array(expo, np.int32), np.stack(coef, axis=-1),
+                      np.stack(cst, axis=-1), self.x0.copy(), self.seed, self.name + "+ls", dict(self.meta),
+                      neq=N)
 
 
 def _pack(n, K, cplx, d, polys, coefs, csts, x0vals, name="", seed=None, meta=None) -> System:
-    """polys: list over i of list of [(var, exp)]; coefs: matching list of (re, im) Fractions."""
+    """polys: list over i of list of [(var, exp)]; coefs: matching list of (re, im) Fractions.
+    len(polys) = N >= n polynomials in n unknowns."""
     P = 2 if cplx else 1
+    N = len(polys)
     poly_ptr = [0]
     nvar, idx, expo, cre = [], [], [], []
-    for i in range(n):
+    for i in range(N):
         for pairs, c in zip(polys[i], coefs[i]):
             assert 0 <= len(pairs) <= MAXV
             nvar.append(len(pairs))
@@ -170,7 +201,7 @@ def _pack(n, K, cplx, d, polys, coefs, csts, x0vals, name="", seed=None, meta=No
         coef[0, :, m] = md_from_fraction(c[0], K)
         if cplx:
             coef[1, :, m] = md_from_fraction(c[1], K)
-    cst = np.zeros((P, K, n))
+    cst = np.zeros((P, K, N))
     for i, c in enumerate(csts):
         cst[0, :, i] = md_from_fraction(c[0], K)
         if cplx:
@@ -181,7 +212,8 @@ def _pack(n, K, cplx, d, polys, coefs, csts, x0vals, name="", seed=None, meta=No
         if cplx:
             x0[1, :, j, 0] = md_from_fraction(v[1], K)
     return System(K, cplx, n, d, np.array(poly_ptr, np.int32), np.array(nvar, np.int32),
-                  np.array(idx, np.int32), np.array(expo, np.int32), coef, cst, x0, seed, name, meta or {})
+                  np.array(idx, np.int32), np.array(expo, np.int32), coef, cst, x0, seed, name, meta or {},
+                  neq=N if N != n else 0)
 
 
 # ----------------------------------------------------------------------------
@@ -240,8 +272,8 @@ def _random_monomials(rng, n, count, minvars, maxvars, maxdeg, force_t):
 def _jacobian_cond(n, polys, coefs, x0vals):
     """Condition number of the Jacobian at (x0, t=0) in plain double (input sanity check)."""
     x = np.array([complex(float(v[0]), float(v[1])) for v in x0vals])
-    J = np.zeros((n, n), dtype=complex)
-    for i in range(n):
+    J = np.zeros((len(polys), n), dtype=complex)
+    for i in range(len(polys)):
         for pairs, c in zip(polys[i], coefs[i]):
             cc = complex(float(c[0]), float(c[1]))
             if any(v == n for v, _ in pairs):
@@ -257,8 +289,12 @@ def _jacobian_cond(n, polys, coefs, x0vals):
 
 def random_system(seed: int, *, n: int, K: int, cplx: bool, d: int, monos: int, minvars: int = 1,
                   maxvars: int, maxdeg: int, coef_kind: str = "unit", cond_max: float = 1e6,
-                  name: str = "") -> System:
+                  name: str = "", neq: int = 0) -> System:
     """Seeded random system whose start point x0 solves it at t = 0.
+
+    neq > n gives N = neq polynomials in n unknowns (all vanish at (x0, 0), so
+    the t = 0 system is consistent; for t != 0 it is solved in the least
+    squares sense), drawn by the same recipe.
 
     Recipe: per polynomial, ``monos`` distinct monomials; each draws m ~ U{minvars..maxvars}
     distinct variables among x_1..x_n and t, total degree ~ U{m..maxdeg} with the extra
@@ -283,7 +319,7 @@ def random_system(seed: int, *, n: int, K: int, cplx: bool, d: int, monos: int, 
                 x0vals.append((md_to_fraction(md_from_fraction(v, K)), Fraction(0)))
         polys, coefs, csts = [], [], []
         xpow_cache = {}
-        for i in range(n):
+        for i in range(max(n, neq)):
             mons = _random_monomials(rng, n, monos, minvars, maxvars, maxdeg, force_t=True)
             cs = []
             for _ in mons:

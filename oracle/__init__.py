@@ -30,10 +30,11 @@ _libs = {}
 
 def build(force: bool = False) -> None:
     """Compile the oracle (plain and counting variants) with gcc."""
-    for out, extra in ((LIB, []), (LIB_COUNT, ["-DORACLE_COUNT"])):
+    # the counting variant is serial: its global counters are not thread-safe
+    for out, flags in ((LIB, CFLAGS), (LIB_COUNT, [f for f in CFLAGS if f != "-fopenmp"] + ["-DORACLE_COUNT"])):
         if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(SRC):
             tmp = out + ".tmp%d" % os.getpid()
-            subprocess.check_call(["gcc", *CFLAGS, *extra, SRC, "-o", tmp, "-lm"])
+            subprocess.check_call(["gcc", *flags, SRC, "-o", tmp, "-lm"])
             os.replace(tmp, out)
 
 
@@ -50,11 +51,14 @@ def _load(counting: bool):
             lib.orc_eval_diff.argtypes = [i, i, i, i, i, P, P, P, P, P, P, P, P, P]
             lib.orc_linsolve.argtypes = [i, i, i, i, P, P, P, P]
             lib.orc_linsolve_m.argtypes = [i, i, i, i, P, P, P, P, i]
+            lib.orc_lstsq.argtypes = [i, i, i, i, i, P, P, P, P, i]
+            lib.orc_eval_diff_ls.argtypes = [i, i, i, i, i, i, P, P, P, P, P, P, P, P, P]
             lib.orc_newton_step_m.argtypes = [i, i, i, i, i, P, P, P, P, P, P, P, P, P, i]
-            lib.orc_rcond.argtypes = [i, i, i, i, P, i, P]
+            lib.orc_newton_step_ls.argtypes = [i, i, i, i, i, i, P, P, P, P, P, P, P, P, P, i]
+            lib.orc_rcond.argtypes = [i, i, i, i, i, P, i, P]
             lib.orc_newton_step.argtypes = [i, i, i, i, i, P, P, P, P, P, P, P, P, P]
             d = ctypes.c_double
-            lib.orc_newton_run.argtypes = [i, i, i, i, i, P, P, P, P, P, P, P, i, P, P, d, d, P, P, P, i]
+            lib.orc_newton_run.argtypes = [i, i, i, i, i, i, P, P, P, P, P, P, P, i, P, P, d, d, P, P, P, i]
             lib.orc_count_get.argtypes = [P]
             lib.orc_set_threads.argtypes = [i]
             _libs[key] = lib
@@ -131,33 +135,35 @@ class Oracle:
         return (_i32(s.poly_ptr), _i32(s.nvar), _i32(s.idx), _i32(s.expo), _f64(s.coef), _f64(s.cst))
 
     def eval_diff(self, s, x: np.ndarray):
-        """Returns (f [P][K][n][d+1], A [P][K][d+1][n][n] column-major blocks)."""
-        P, K, n, d = s.planes, s.limbs, s.n, s.degree
+        """Returns (f [P][K][N][d+1], A [P][K][d+1][n][N] column-major blocks);
+        N = number of polynomials (N >= n)."""
+        P, K, n, d, N = s.planes, s.limbs, s.n, s.degree, s.N
         pp, nv, ix, ex, cf, cs = self._sysargs(s)
         x = _f64(x)
-        f = np.zeros((P, K, n, d + 1))
-        A = np.zeros((P, K, d + 1, n, n))
-        st = self.lib.orc_eval_diff(K, int(s.is_complex), n, d, s.nmono, _p(pp), _p(nv), _p(ix), _p(ex), _p(cf), _p(cs),
-                                    _p(x), _p(f), _p(A))
+        f = np.zeros((P, K, N, d + 1))
+        A = np.zeros((P, K, d + 1, n, N))
+        st = self.lib.orc_eval_diff_ls(K, int(s.is_complex), N, n, d, s.nmono, _p(pp), _p(nv), _p(ix), _p(ex), _p(cf),
+                                       _p(cs), _p(x), _p(f), _p(A))
         _check(st, "eval_diff")
         return f, A
 
     def linsolve(self, K: int, cplx: bool, A: np.ndarray, b: np.ndarray, want_rdiag: bool = False, method: int = 0):
-        """A: [P][K][d+1][n][n] (col-major blocks), b: [P][K][n][d+1] -> dx like b.
-        method 0: Householder QR of A_0, 1: LU with partial pivoting."""
+        """A: [P][K][d+1][n][N] (col-major blocks), b: [P][K][N][d+1] -> dx
+        [P][K][n][d+1]; least squares when N > n.  method 0: Householder QR
+        of A_0, 1: LU with partial pivoting (N = n)."""
         A, b = _f64(A), _f64(b)
-        P, _, D1, n, _ = A.shape
-        dx = np.zeros_like(b)
+        P, _, D1, n, N = A.shape
+        dx = np.zeros((P, K, n, D1))
         rd = np.zeros(n)
-        _check(self.lib.orc_linsolve_m(K, int(cplx), n, D1 - 1, _p(A), _p(b), _p(dx), _p(rd), method), "linsolve")
+        _check(self.lib.orc_lstsq(K, int(cplx), N, n, D1 - 1, _p(A), _p(b), _p(dx), _p(rd), method), "linsolve")
         return (dx, rd) if want_rdiag else dx
 
     def rcond(self, K: int, cplx: bool, A: np.ndarray, method: int = 0) -> float:
         """1 / (||A_0||_1 ||A_0^-1||_1) from the leading limbs; A as for linsolve."""
         A = _f64(A)
-        P, _, D1, n, _ = A.shape
+        P, _, D1, n, N = A.shape
         out = np.zeros(1)
-        _check(self.lib.orc_rcond(K, int(cplx), n, D1 - 1, _p(A), method, _p(out)), "rcond")
+        _check(self.lib.orc_rcond(K, int(cplx), N, n, D1 - 1, _p(A), method, _p(out)), "rcond")
         return float(out[0])
 
     def newton_step(self, s, x: np.ndarray, want_rdiag: bool = False, method: int = 0):
@@ -167,8 +173,8 @@ class Oracle:
         xx = _f64(x).copy()
         nrm = np.zeros(2)
         rd = np.zeros(n)
-        st = self.lib.orc_newton_step_m(K, int(s.is_complex), n, d, s.nmono, _p(pp), _p(nv), _p(ix), _p(ex),
-                                        _p(cf), _p(cs), _p(xx), _p(nrm), _p(rd), method)
+        st = self.lib.orc_newton_step_ls(K, int(s.is_complex), s.N, n, d, s.nmono, _p(pp), _p(nv), _p(ix), _p(ex),
+                                         _p(cf), _p(cs), _p(xx), _p(nrm), _p(rd), method)
         _check(st, "newton_step")
         if want_rdiag:
             return xx, (float(nrm[0]), float(nrm[1])), rd
@@ -187,7 +193,7 @@ class Oracle:
         it = np.zeros(nlev, dtype=np.int32)
         dxn = np.zeros(2 * nlev)
         lv = np.zeros(1, dtype=np.int32)
-        st = self.lib.orc_newton_run(K, int(s.is_complex), n, D, s.nmono, _p(pp), _p(nv), _p(ix), _p(ex), _p(cf),
+        st = self.lib.orc_newton_run(K, int(s.is_complex), s.N, n, D, s.nmono, _p(pp), _p(nv), _p(ix), _p(ex), _p(cf),
                                      _p(cs), _p(xx), nlev, _p(dg), _p(mi), ctypes.c_double(tol),
                                      ctypes.c_double(too_large), _p(it), _p(dxn), _p(lv), method)
         _check(st, "newton_run")

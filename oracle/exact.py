@@ -8,7 +8,9 @@ different algorithm:
   common factor;
 * the linearized system A(t) dx(t) = -f(t) of Section 4 is assembled as the
   dense (d+1)n x (d+1)n lower triangular block Toeplitz matrix and solved by
-  Gaussian elimination over the Gaussian rationals.
+  Gaussian elimination over the Gaussian rationals;
+* for N > n equations, each degree's least squares problem is solved through
+  its normal equations over the Gaussian rationals.
 
 All arithmetic is exact (``fractions.Fraction``); inputs are the exact values
 of the md limbs.
@@ -72,14 +74,16 @@ def series_pow(x: List[C], e: int, d: int) -> List[C]:
 
 
 def eval_diff_exact(s, x: np.ndarray):
-    """Exact f (list over i of series) and A (list over k of n x n lists) at the series x."""
+    """Exact f (list over the N polynomials of series) and A (list over k of
+    N x n lists) at the series x."""
     n, d = s.n, s.degree
+    N = getattr(s, "N", n)
     xs = [[md_exact(x, j, k) for k in range(d + 1)] for j in range(n)]
     tser = [ZERO, ONE] + [ZERO] * (d - 1) if d >= 1 else [ZERO]
     allv = xs + [tser]
     f = []
-    A = [[[ZERO] * n for _ in range(n)] for _ in range(d + 1)]
-    for i in range(n):
+    A = [[[ZERO] * n for _ in range(N)] for _ in range(d + 1)]
+    for i in range(N):
         fi = [md_exact(s.cst, i)] + [ZERO] * d
         for m, pairs in s.monomials(i):
             c = md_exact(s.coef, m)
@@ -146,20 +150,53 @@ def block_toeplitz_solve(A: List[List[List[C]]], b: List[List[C]]) -> List[List[
     return [[sol[k * n + i] for i in range(n)] for k in range(D1)]
 
 
+def block_lstsq(A: List[List[List[C]]], b: List[List[C]]) -> List[List[C]]:
+    """Least squares block Toeplitz solve over Q(i), A[k] N x n, b[k] length N:
+    per degree dx_k solves the normal equations A_0^H A_0 dx_k = A_0^H r_k,
+    r_k = b_k - sum_{j<k} A_{k-j} dx_j (the minimiser of ||A_0 dx_k - r_k||)."""
+    D1, N, n = len(A), len(A[0]), len(A[0][0])
+
+    def conj(z):
+        return (z[0], -z[1])
+
+    A0 = A[0]
+    G = [[ZERO] * n for _ in range(n)]
+    for r in range(n):
+        for c in range(n):
+            acc = ZERO
+            for i in range(N):
+                acc = cadd(acc, cmul(conj(A0[i][r]), A0[i][c]))
+            G[r][c] = acc
+    dx = []
+    for k in range(D1):
+        rk = list(b[k])
+        for j in range(k):
+            for i in range(N):
+                for c in range(n):
+                    rk[i] = csub(rk[i], cmul(A[k - j][i][c], dx[j][c]))
+        h = [ZERO] * n
+        for r in range(n):
+            for i in range(N):
+                h[r] = cadd(h[r], cmul(conj(A0[i][r]), rk[i]))
+        dx.append(solve_dense(G, h))
+    return dx
+
+
 def newton_step_exact(s, x: np.ndarray):
     """Exact step from the md input x: returns (x_new[j][k], dx[k][j], f, A)."""
     n, d = s.n, s.degree
+    N = getattr(s, "N", n)
     f, A = eval_diff_exact(s, x)
-    b = [[(-f[i][k][0], -f[i][k][1]) for i in range(n)] for k in range(d + 1)]
-    dx = block_toeplitz_solve(A, b)
+    b = [[(-f[i][k][0], -f[i][k][1]) for i in range(N)] for k in range(d + 1)]
+    dx = block_toeplitz_solve(A, b) if N == n else block_lstsq(A, b)
     xn = [[cadd(md_exact(x, j, k), dx[k][j]) for k in range(d + 1)] for j in range(n)]
     return xn, dx, f, A
 
 
 def mat_series_exact(A: np.ndarray):
-    """[P][K][d+1][n(col)][n(row)] -> A[k][row][col] exact."""
-    D1, n = A.shape[2], A.shape[3]
-    return [[[md_exact(A, k, c, r) for c in range(n)] for r in range(n)] for k in range(D1)]
+    """[P][K][d+1][n(col)][N(row)] -> A[k][row][col] exact."""
+    D1, n, N = A.shape[2], A.shape[3], A.shape[4]
+    return [[[md_exact(A, k, c, r) for c in range(n)] for r in range(N)] for k in range(D1)]
 
 
 def vec_series_exact(b: np.ndarray):

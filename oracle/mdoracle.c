@@ -399,26 +399,27 @@ static void store_series(int K, int P, int n, int d, const mdc *s, double *x) {
 }
 
 /* matrix series [P][K][d+1][col][row] <-> mdc a[(k*n + row)*n + col] */
-static void load_mats(int K, int P, int n, int d, const double *A, mdc *a) {
-  long nn = (long)n * n;
+/* matrix series: API [P][K][d+1][n columns][N rows] <-> a[(k*N + r)*n + c] */
+static void load_mats(int K, int P, int N, int n, int d, const double *A, mdc *a) {
+  long nn = (long)N * n;
   for (int k = 0; k <= d; ++k)
-    for (int r = 0; r < n; ++r)
+    for (int r = 0; r < N; ++r)
       for (int c = 0; c < n; ++c) {
-        mdc *z = &a[(k * (long)n + r) * n + c];
+        mdc *z = &a[(k * (long)N + r) * n + c];
         c_zero(z);
         for (int p = 0; p < P; ++p)
-          for (int l = 0; l < K; ++l) z->v[p][l] = A[(((long)p * K + l) * (d + 1) + k) * nn + (long)c * n + r];
+          for (int l = 0; l < K; ++l) z->v[p][l] = A[(((long)p * K + l) * (d + 1) + k) * nn + (long)c * N + r];
       }
 }
 
-static void store_mats(int K, int P, int n, int d, const mdc *a, double *A) {
-  long nn = (long)n * n;
+static void store_mats(int K, int P, int N, int n, int d, const mdc *a, double *A) {
+  long nn = (long)N * n;
   for (int k = 0; k <= d; ++k)
-    for (int r = 0; r < n; ++r)
+    for (int r = 0; r < N; ++r)
       for (int c = 0; c < n; ++c)
         for (int p = 0; p < P; ++p)
           for (int l = 0; l < K; ++l)
-            A[(((long)p * K + l) * (d + 1) + k) * nn + (long)c * n + r] = a[(k * (long)n + r) * n + c].v[p][l];
+            A[(((long)p * K + l) * (d + 1) + k) * nn + (long)c * N + r] = a[(k * (long)N + r) * n + c].v[p][l];
 }
 
 /* ------------------------------------------------------------ series ops */
@@ -617,10 +618,11 @@ static int eval_monomial(evctx *cx, int n, int nv, const int *idx, const int *ex
 }
 
 /* f_i = cst_i + sum_mono value; A_k[i][j] = sum_mono (d/dx_j value)_k, in CSR order */
-static void eval_diff_internal(int K, int P, int n, int d, const int *poly_ptr, const int *nvar, const int *idx,
-                               const int *expo, const mdc *coefs, const mdc *csts, const mdc *xs, mdc *fs, mdc *as) {
+static void eval_diff_internal(int K, int P, int N, int n, int d, const int *poly_ptr, const int *nvar,
+                               const int *idx, const int *expo, const mdc *coefs, const mdc *csts, const mdc *xs,
+                               mdc *fs, mdc *as) {
   long D1 = d + 1;
-  long nn = (long)n * n;
+  long nn = (long)N * n;
   for (long e = 0; e < D1 * nn; ++e) c_zero(&as[e]);
 #pragma omp parallel
   {
@@ -632,7 +634,7 @@ static void eval_diff_internal(int K, int P, int n, int d, const int *poly_ptr, 
     mdc *V = malloc(sizeof(mdc) * D1);
     mdc *Dq = malloc(sizeof(mdc) * D1 * MAXV);
 #pragma omp for schedule(dynamic, 1)
-    for (int i = 0; i < n; ++i) {
+    for (int i = 0; i < N; ++i) {
       mdc *f = fs + (long)i * D1;
       for (int k = 0; k <= d; ++k) c_zero(&f[k]);
       f[0] = csts[i];
@@ -642,7 +644,7 @@ static void eval_diff_internal(int K, int P, int n, int d, const int *poly_ptr, 
         for (int k = 0; k <= d; ++k) c_add(K, P, &f[k], &V[k], &f[k]);
         for (int q = 0; q < m; ++q)
           for (int k = 0; k <= d; ++k) {
-            mdc *a = &as[(k * (long)n + i) * n + vj[q]];
+            mdc *a = &as[(k * (long)N + i) * n + vj[q]];
             c_add(K, P, a, &Dq[(long)q * D1 + k], a);
           }
       }
@@ -661,10 +663,12 @@ static void load_scalars(int K, int P, long count, const double *src, mdc *dst) 
   }
 }
 
-static int check_system(int K, int n, int d, int nmono, const int *poly_ptr, const int *nvar, const int *idx, const int *expo) {
-  if (K < 1 || K > MAXK || n < 1 || d < 0) return 1;
-  if (poly_ptr[0] != 0 || poly_ptr[n] != nmono) return 1;
-  for (int i = 0; i < n; ++i)
+/* N polynomials (N >= n) in n unknowns; variable n is t */
+static int check_system(int K, int N, int n, int d, int nmono, const int *poly_ptr, const int *nvar, const int *idx,
+                        const int *expo) {
+  if (K < 1 || K > MAXK || n < 1 || N < n || d < 0) return 1;
+  if (poly_ptr[0] != 0 || poly_ptr[N] != nmono) return 1;
+  for (int i = 0; i < N; ++i)
     if (poly_ptr[i + 1] < poly_ptr[i]) return 1;
   for (int m = 0; m < nmono; ++m) {
     if (nvar[m] < 0 || nvar[m] > MAXV) return 1;
@@ -678,22 +682,24 @@ static int check_system(int K, int n, int d, int nmono, const int *poly_ptr, con
   return 0;
 }
 
-int orc_eval_diff(int K, int cplx, int n, int d, int nmono, const int *poly_ptr, const int *nvar, const int *idx,
-                  const int *expo, const double *coef, const double *cst, const double *x, double *f, double *A) {
+/* f: [P][K][N][d+1], A: [P][K][d+1][n][N] */
+int orc_eval_diff_ls(int K, int cplx, int N, int n, int d, int nmono, const int *poly_ptr, const int *nvar,
+                     const int *idx, const int *expo, const double *coef, const double *cst, const double *x, double *f,
+                     double *A) {
   int P = cplx ? 2 : 1;
-  if (check_system(K, n, d, nmono, poly_ptr, nvar, idx, expo)) return 1;
+  if (check_system(K, N, n, d, nmono, poly_ptr, nvar, idx, expo)) return 1;
   long D1 = d + 1;
   mdc *coefs = malloc(sizeof(mdc) * (nmono > 0 ? nmono : 1));
-  mdc *csts = malloc(sizeof(mdc) * n);
+  mdc *csts = malloc(sizeof(mdc) * N);
   mdc *xs = malloc(sizeof(mdc) * n * D1);
-  mdc *fs = malloc(sizeof(mdc) * n * D1);
-  mdc *as = malloc(sizeof(mdc) * D1 * n * n);
+  mdc *fs = malloc(sizeof(mdc) * N * D1);
+  mdc *as = malloc(sizeof(mdc) * D1 * N * n);
   load_scalars(K, P, nmono, coef, coefs);
-  load_scalars(K, P, n, cst, csts);
+  load_scalars(K, P, N, cst, csts);
   load_series(K, P, n, d, x, xs);
-  eval_diff_internal(K, P, n, d, poly_ptr, nvar, idx, expo, coefs, csts, xs, fs, as);
-  store_series(K, P, n, d, fs, f);
-  store_mats(K, P, n, d, as, A);
+  eval_diff_internal(K, P, N, n, d, poly_ptr, nvar, idx, expo, coefs, csts, xs, fs, as);
+  store_series(K, P, N, d, fs, f);
+  store_mats(K, P, N, n, d, as, A);
   free(coefs);
   free(csts);
   free(xs);
@@ -702,29 +708,35 @@ int orc_eval_diff(int K, int cplx, int n, int d, int nmono, const int *poly_ptr,
   return 0;
 }
 
+int orc_eval_diff(int K, int cplx, int n, int d, int nmono, const int *poly_ptr, const int *nvar, const int *idx,
+                  const int *expo, const double *coef, const double *cst, const double *x, double *f, double *A) {
+  return orc_eval_diff_ls(K, cplx, n, n, d, nmono, poly_ptr, nvar, idx, expo, coef, cst, x, f, A);
+}
+
 /* ------------------------------------------------ Householder QR of A_0 */
 /*
- * Golub-Van Loan Householder QR, complex form.  Column j: x = a[j:n, j],
+ * Golub-Van Loan Householder QR of the N x n matrix A_0 (N >= n; Sec. 4:
+ * least squares for N > n), complex form.  Column j: x = a[j:N, j],
  * alpha = ||x||_2, phase e = x_0/|x_0| (1 if x_0 = 0), v = x + e alpha e_1,
  * beta = 2/(v^H v) = 1/(alpha (alpha + |x_0|)), R_jj = -e alpha; the trailing
  * columns get a_c -= beta (v^H a_c) v.  v_0 is kept in vd[j], v_i (i > j) stays
  * below the diagonal, R above it.  Returns 4 when alpha = 0 (singular A_0).
  */
 typedef struct {
-  int K, P, n;
-  mdc *a;    /* row-major n x n: a[r*n + c] */
+  int K, P, N, n;
+  mdc *a;    /* row-major N x n: a[r*n + c] */
   mdc *vd;   /* [n] v_0 of each reflector */
   mdc *rd;   /* [n] R_jj */
   double (*beta)[MAXK]; /* [n] */
 } qrf;
 
 static int qr_factor(qrf *q) {
-  int K = q->K, P = q->P, n = q->n;
+  int K = q->K, P = q->P, N = q->N, n = q->n;
   mdc *a = q->a;
   for (int j = 0; j < n; ++j) {
     double ss[MAXK], t[MAXK], alpha[MAXK], a0[MAXK], s2[MAXK];
     c_abs2(K, P, &a[(long)j * n + j], ss);
-    for (int i = j + 1; i < n; ++i) {
+    for (int i = j + 1; i < N; ++i) {
       c_abs2(K, P, &a[(long)i * n + j], t);
       md_add(K, ss, t, ss);
     }
@@ -763,7 +775,7 @@ static int qr_factor(qrf *q) {
       mdc w, tt, cv, tau;
       c_conj(K, P, &v0, &cv);
       c_mul(K, P, &cv, &a[(long)j * n + c], &w);
-      for (int i = j + 1; i < n; ++i) {
+      for (int i = j + 1; i < N; ++i) {
         c_conj(K, P, &a[(long)i * n + j], &cv);
         c_mul(K, P, &cv, &a[(long)i * n + c], &tt);
         c_add(K, P, &w, &tt, &w);
@@ -771,7 +783,7 @@ static int qr_factor(qrf *q) {
       c_mul_real(K, P, &w, beta, &tau);
       c_mul(K, P, &tau, &v0, &tt);
       c_sub(K, P, &a[(long)j * n + c], &tt, &a[(long)j * n + c]);
-      for (int i = j + 1; i < n; ++i) {
+      for (int i = j + 1; i < N; ++i) {
         c_mul(K, P, &tau, &a[(long)i * n + j], &tt);
         c_sub(K, P, &a[(long)i * n + c], &tt, &a[(long)i * n + c]);
       }
@@ -780,14 +792,14 @@ static int qr_factor(qrf *q) {
   return 0;
 }
 
-/* y <- Q^H y = H_{n-1} ... H_0 y */
+/* y <- Q^H y = H_{n-1} ... H_0 y (y has N entries) */
 static void qr_apply_qh(qrf *q, mdc *y) {
-  int K = q->K, P = q->P, n = q->n;
+  int K = q->K, P = q->P, N = q->N, n = q->n;
   for (int j = 0; j < n; ++j) {
     mdc w, tt, cv, tau;
     c_conj(K, P, &q->vd[j], &cv);
     c_mul(K, P, &cv, &y[j], &w);
-    for (int i = j + 1; i < n; ++i) {
+    for (int i = j + 1; i < N; ++i) {
       c_conj(K, P, &q->a[(long)i * n + j], &cv);
       c_mul(K, P, &cv, &y[i], &tt);
       c_add(K, P, &w, &tt, &w);
@@ -795,14 +807,15 @@ static void qr_apply_qh(qrf *q, mdc *y) {
     c_mul_real(K, P, &w, q->beta[j], &tau);
     c_mul(K, P, &tau, &q->vd[j], &tt);
     c_sub(K, P, &y[j], &tt, &y[j]);
-    for (int i = j + 1; i < n; ++i) {
+    for (int i = j + 1; i < N; ++i) {
       c_mul(K, P, &tau, &q->a[(long)i * n + j], &tt);
       c_sub(K, P, &y[i], &tt, &y[i]);
     }
   }
 }
 
-/* column-oriented back substitution R x = y (y is overwritten) */
+/* column-oriented back substitution R x = y[0:n] with the top n x n block R
+   (y is overwritten) */
 static void qr_backsub(qrf *q, mdc *y, mdc *x) {
   int K = q->K, P = q->P, n = q->n;
   for (int c = n - 1; c >= 0; --c) {
@@ -904,11 +917,12 @@ typedef struct {
   luf l;
 } fact;
 
-static int fact_init(fact *f, int method, int K, int P, int n, const mdc *a0) {
-  long nn = (long)n * n;
+static int fact_init(fact *f, int method, int K, int P, int N, int n, const mdc *a0) {
+  long nn = (long)N * n;
   memset(f, 0, sizeof(*f));
   f->method = method;
   if (method == 1) {
+    if (N != n) return 1; /* LU is for square A_0 */
     f->l.K = K;
     f->l.P = P;
     f->l.n = n;
@@ -919,6 +933,7 @@ static int fact_init(fact *f, int method, int K, int P, int n, const mdc *a0) {
   }
   f->q.K = K;
   f->q.P = P;
+  f->q.N = N;
   f->q.n = n;
   f->q.a = malloc(sizeof(mdc) * nn);
   f->q.vd = malloc(sizeof(mdc) * n);
@@ -928,10 +943,12 @@ static int fact_init(fact *f, int method, int K, int P, int n, const mdc *a0) {
   return qr_factor(&f->q);
 }
 
+/* x (n entries) solves A_0 x = r (N entries) exactly (N = n) or in the least
+   squares sense (N > n, QR only) */
 static void fact_solve(fact *f, const mdc *r, mdc *x) {
-  int n = f->method == 1 ? f->l.n : f->q.n;
-  mdc *y = malloc(sizeof(mdc) * n);
-  memcpy(y, r, sizeof(mdc) * n);
+  int N = f->method == 1 ? f->l.n : f->q.N;
+  mdc *y = malloc(sizeof(mdc) * N);
+  memcpy(y, r, sizeof(mdc) * N);
   if (f->method == 1) {
     lu_solve(&f->l, y, x);
   } else {
@@ -960,11 +977,11 @@ static void fact_free(fact *f) {
  * touches one r_k only, so the parallel loop keeps the serial order.
  * as: [(k*n + row)*n + col]; bs, dxs: [k*n + i].
  */
-static int linsolve_internal(int K, int P, int n, int d, mdc *as, const mdc *bs, mdc *dxs, double *rdiag_abs,
-                             int method) {
-  long nn = (long)n * n;
+static int linsolve_internal(int K, int P, int N, int n, int d, mdc *as, const mdc *bs, mdc *dxs,
+                             double *rdiag_abs, int method) {
+  long nn = (long)N * n;
   fact f;
-  int st = fact_init(&f, method, K, P, n, as);
+  int st = fact_init(&f, method, K, P, N, n, as);
   if (st) {
     fact_free(&f);
     return st;
@@ -975,17 +992,17 @@ static int linsolve_internal(int K, int P, int n, int d, mdc *as, const mdc *bs,
       double re = rd->v[0][0], im = (P == 2) ? rd->v[1][0] : 0.0;
       rdiag_abs[i] = sqrt(re * re + im * im);
     }
-  mdc *r = malloc(sizeof(mdc) * (d + 1) * n);
-  memcpy(r, bs, sizeof(mdc) * (d + 1) * n);
+  mdc *r = malloc(sizeof(mdc) * (d + 1) * N);
+  memcpy(r, bs, sizeof(mdc) * (d + 1) * N);
   for (int k = 0; k <= d; ++k) {
-    fact_solve(&f, r + (long)k * n, dxs + (long)k * n);
+    fact_solve(&f, r + (long)k * N, dxs + (long)k * n);
     /* jobs: r_m -= A_{m-k} dx_k for every m > k */
 #pragma omp parallel for schedule(dynamic, 1)
     for (int m = k + 1; m <= d; ++m) {
       const mdc *Am = as + (long)(m - k) * nn;
       const mdc *dx = dxs + (long)k * n;
-      mdc *rm = r + (long)m * n;
-      for (int row = 0; row < n; ++row) {
+      mdc *rm = r + (long)m * N;
+      for (int row = 0; row < N; ++row) {
         mdc acc, tt;
         c_mul(K, P, &Am[(long)row * n + 0], &dx[0], &acc);
         for (int col = 1; col < n; ++col) {
@@ -1021,22 +1038,28 @@ static void store_vec_dm(int K, int P, int n, int d, const mdc *v, double *x) {
         for (int l = 0; l < K; ++l) x[(((long)p * K + l) * n + i) * D1 + k] = v[(long)k * n + i].v[p][l];
 }
 
-int orc_linsolve_m(int K, int cplx, int n, int d, const double *A, const double *b, double *dx, double *rdiag_abs,
-                   int method) {
+/* A: [P][K][d+1][n][N], b: [P][K][N][d+1] -> dx: [P][K][n][d+1] */
+int orc_lstsq(int K, int cplx, int N, int n, int d, const double *A, const double *b, double *dx, double *rdiag_abs,
+              int method) {
   int P = cplx ? 2 : 1;
-  if (K < 1 || K > MAXK || n < 1 || d < 0) return 1;
-  long nn = (long)n * n;
+  if (K < 1 || K > MAXK || n < 1 || N < n || d < 0) return 1;
+  long nn = (long)N * n;
   mdc *as = malloc(sizeof(mdc) * (d + 1) * nn);
-  mdc *bs = malloc(sizeof(mdc) * (d + 1) * n);
+  mdc *bs = malloc(sizeof(mdc) * (d + 1) * N);
   mdc *dxs = malloc(sizeof(mdc) * (d + 1) * n);
-  load_mats(K, P, n, d, A, as);
-  load_vec_dm(K, P, n, d, b, bs);
-  int st = linsolve_internal(K, P, n, d, as, bs, dxs, rdiag_abs, method);
+  load_mats(K, P, N, n, d, A, as);
+  load_vec_dm(K, P, N, d, b, bs);
+  int st = linsolve_internal(K, P, N, n, d, as, bs, dxs, rdiag_abs, method);
   if (!st) store_vec_dm(K, P, n, d, dxs, dx);
   free(as);
   free(bs);
   free(dxs);
   return st;
+}
+
+int orc_linsolve_m(int K, int cplx, int n, int d, const double *A, const double *b, double *dx, double *rdiag_abs,
+                   int method) {
+  return orc_lstsq(K, cplx, n, n, d, A, b, dx, rdiag_abs, method);
 }
 
 int orc_linsolve(int K, int cplx, int n, int d, const double *A, const double *b, double *dx, double *rdiag_abs) {
@@ -1049,30 +1072,32 @@ int orc_linsolve(int K, int cplx, int n, int d, const double *A, const double *b
  * (size of the update of the highest-degree coefficient, Sec. 6, from the leading
  * limbs), dxnorm[1] = max over all coefficients of |dx_{k,i}|.
  */
-int orc_newton_step_m(int K, int cplx, int n, int d, int nmono, const int *poly_ptr, const int *nvar, const int *idx,
-                      const int *expo, const double *coef, const double *cst, double *x, double *dxnorm,
-                      double *rdiag_abs, int method) {
+/* N >= n polynomials; the linear systems are solved in the least squares
+   sense when N > n (Sec. 4) */
+int orc_newton_step_ls(int K, int cplx, int N, int n, int d, int nmono, const int *poly_ptr, const int *nvar,
+                       const int *idx, const int *expo, const double *coef, const double *cst, double *x,
+                       double *dxnorm, double *rdiag_abs, int method) {
   int P = cplx ? 2 : 1;
-  if (check_system(K, n, d, nmono, poly_ptr, nvar, idx, expo)) return 1;
-  long D1 = d + 1, nn = (long)n * n;
+  if (check_system(K, N, n, d, nmono, poly_ptr, nvar, idx, expo)) return 1;
+  long D1 = d + 1, nn = (long)N * n;
   mdc *coefs = malloc(sizeof(mdc) * (nmono > 0 ? nmono : 1));
-  mdc *csts = malloc(sizeof(mdc) * n);
+  mdc *csts = malloc(sizeof(mdc) * N);
   mdc *xs = malloc(sizeof(mdc) * n * D1);
-  mdc *fs = malloc(sizeof(mdc) * n * D1);
+  mdc *fs = malloc(sizeof(mdc) * N * D1);
   mdc *as = malloc(sizeof(mdc) * D1 * nn);
-  mdc *bs = malloc(sizeof(mdc) * D1 * n);
+  mdc *bs = malloc(sizeof(mdc) * D1 * N);
   mdc *dxs = malloc(sizeof(mdc) * D1 * n);
   load_scalars(K, P, nmono, coef, coefs);
-  load_scalars(K, P, n, cst, csts);
+  load_scalars(K, P, N, cst, csts);
   load_series(K, P, n, d, x, xs);
-  eval_diff_internal(K, P, n, d, poly_ptr, nvar, idx, expo, coefs, csts, xs, fs, as);
+  eval_diff_internal(K, P, N, n, d, poly_ptr, nvar, idx, expo, coefs, csts, xs, fs, as);
   for (int k = 0; k <= d; ++k)
-    for (int i = 0; i < n; ++i) {
-      mdc *z = &bs[(long)k * n + i];
+    for (int i = 0; i < N; ++i) {
+      mdc *z = &bs[(long)k * N + i];
       for (int p = 0; p < P; ++p) md_neg(K, fs[(long)i * D1 + k].v[p], z->v[p]);
       if (P == 1) memset(z->v[1], 0, sizeof(z->v[1]));
     }
-  int st = linsolve_internal(K, P, n, d, as, bs, dxs, rdiag_abs, method);
+  int st = linsolve_internal(K, P, N, n, d, as, bs, dxs, rdiag_abs, method);
   if (!st) {
     double nd = 0.0, ninf = 0.0;
     for (int k = 0; k <= d; ++k)
@@ -1101,6 +1126,13 @@ int orc_newton_step_m(int K, int cplx, int n, int d, int nmono, const int *poly_
   return st;
 }
 
+int orc_newton_step_m(int K, int cplx, int n, int d, int nmono, const int *poly_ptr, const int *nvar, const int *idx,
+                      const int *expo, const double *coef, const double *cst, double *x, double *dxnorm,
+                      double *rdiag_abs, int method) {
+  return orc_newton_step_ls(K, cplx, n, n, d, nmono, poly_ptr, nvar, idx, expo, coef, cst, x, dxnorm, rdiag_abs,
+                            method);
+}
+
 int orc_newton_step(int K, int cplx, int n, int d, int nmono, const int *poly_ptr, const int *nvar, const int *idx,
                     const int *expo, const double *coef, const double *cst, double *x, double *dxnorm, double *rdiag_abs) {
   return orc_newton_step_m(K, cplx, n, d, nmono, poly_ptr, nvar, idx, expo, coef, cst, x, dxnorm, rdiag_abs, 0);
@@ -1117,11 +1149,11 @@ int orc_newton_step(int K, int cplx, int n, int d, int nmono, const int *poly_pt
  * caller does).  x: [P][K][n][D+1] in and out.  Per level: iters[l], the final
  * ||dx|| in dxn[2l] and max |dx| in dxn[2l+1]; *levels = levels run.
  */
-int orc_newton_run(int K, int cplx, int n, int D, int nmono, const int *poly_ptr, const int *nvar, const int *idx,
+int orc_newton_run(int K, int cplx, int N, int n, int D, int nmono, const int *poly_ptr, const int *nvar, const int *idx,
                    const int *expo, const double *coef, const double *cst, double *x, int nlev, const int *deg,
                    const int *maxit, double tol, double too_large, int *iters, double *dxn, int *levels, int method) {
   int P = cplx ? 2 : 1;
-  if (check_system(K, n, D, nmono, poly_ptr, nvar, idx, expo) || nlev < 1) return 1;
+  if (check_system(K, N, n, D, nmono, poly_ptr, nvar, idx, expo) || nlev < 1) return 1;
   for (int l = 0; l < nlev; ++l)
     if (deg[l] < 0 || deg[l] > D || (l > 0 && deg[l] < deg[l - 1]) || maxit[l] < 1) return 1;
   long rows = (long)P * K * n;
@@ -1135,7 +1167,7 @@ int orc_newton_run(int K, int cplx, int n, int D, int nmono, const int *poly_ptr
     double nrm[2] = {0.0, 0.0};
     int it = 0;
     while (it < maxit[l]) {
-      st = orc_newton_step_m(K, cplx, n, d, nmono, poly_ptr, nvar, idx, expo, coef, cst, xl, nrm, NULL, method);
+      st = orc_newton_step_ls(K, cplx, N, n, d, nmono, poly_ptr, nvar, idx, expo, coef, cst, xl, nrm, NULL, method);
       if (st) break;
       ++it;
       if (nrm[0] <= tol) break;
@@ -1155,36 +1187,40 @@ int orc_newton_run(int K, int cplx, int n, int D, int nmono, const int *poly_ptr
 /* --------------------------------------------------- condition of A_0 */
 /*
  * 1 / (||A_0||_1 ||A_0^{-1}||_1) (Sec. 6 quotes an estimate of the inverse
- * condition number of A_0).  A_0^{-1} is computed column by column by solving
- * A_0 x = e_c with the factorisation of `method`; the 1-norms use the moduli
- * of the leading limbs, summed in double down each column.
- * A: [P][K][d+1][n][n] as for orc_linsolve (coefficient 0 is used).
+ * condition number of A_0).  A_0^{-1} (the pseudo-inverse when N > n) is
+ * computed column by column by solving A_0 x = e_c with the factorisation of
+ * `method`; the 1-norms use the moduli of the leading limbs, summed in double
+ * down each column.  A: [P][K][d+1][n][N] as for orc_lstsq (coefficient 0).
  */
-int orc_rcond(int K, int cplx, int n, int d, const double *A, int method, double *out) {
+int orc_rcond(int K, int cplx, int N, int n, int d, const double *A, int method, double *out) {
   int P = cplx ? 2 : 1;
-  if (K < 1 || K > MAXK || n < 1 || d < 0) return 1;
-  long nn = (long)n * n;
+  if (K < 1 || K > MAXK || n < 1 || N < n || d < 0) return 1;
+  long nn = (long)N * n;
   mdc *as = malloc(sizeof(mdc) * (d + 1) * nn);
-  load_mats(K, P, n, d, A, as);
+  load_mats(K, P, N, n, d, A, as);
   fact f;
-  int st = fact_init(&f, method, K, P, n, as);
+  int st = fact_init(&f, method, K, P, N, n, as);
   if (!st) {
-    mdc *e = malloc(sizeof(mdc) * n), *x = malloc(sizeof(mdc) * n);
+    mdc *e = malloc(sizeof(mdc) * N), *x = malloc(sizeof(mdc) * n);
     double na = 0.0, ni = 0.0;
-    for (int c = 0; c < n; ++c) {
-      for (int i = 0; i < n; ++i) c_zero(&e[i]);
-      e[c].v[0][0] = 1.0;
-      fact_solve(&f, e, x);
-      double sa = 0.0, si = 0.0;
-      for (int r = 0; r < n; ++r) {
+    for (int c = 0; c < n; ++c) { /* ||A_0||_1: N rows of column c */
+      double sa = 0.0;
+      for (int r = 0; r < N; ++r) {
         const mdc *a = &as[(long)r * n + c];
         double re = a->v[0][0], im = P == 2 ? a->v[1][0] : 0.0;
         sa += sqrt(re * re + im * im);
-        re = x[r].v[0][0];
-        im = P == 2 ? x[r].v[1][0] : 0.0;
-        si += sqrt(re * re + im * im);
       }
       if (sa > na) na = sa;
+    }
+    for (int c = 0; c < N; ++c) { /* column c of the (pseudo-)inverse: n rows */
+      for (int i = 0; i < N; ++i) c_zero(&e[i]);
+      e[c].v[0][0] = 1.0;
+      fact_solve(&f, e, x);
+      double si = 0.0;
+      for (int r = 0; r < n; ++r) {
+        double re = x[r].v[0][0], im = P == 2 ? x[r].v[1][0] : 0.0;
+        si += sqrt(re * re + im * im);
+      }
       if (si > ni) ni = si;
     }
     *out = 1.0 / (na * ni);

@@ -33,7 +33,7 @@ class md_system(ctypes.Structure):
     _fields_ = [("limbs", ctypes.c_int), ("is_complex", ctypes.c_int), ("n", ctypes.c_int), ("degree", ctypes.c_int),
                 ("nmono", ctypes.c_int), ("poly_ptr", ctypes.c_void_p), ("nvar", ctypes.c_void_p),
                 ("idx", ctypes.c_void_p), ("expo", ctypes.c_void_p), ("coef", ctypes.c_void_p),
-                ("cst", ctypes.c_void_p)]
+                ("cst", ctypes.c_void_p), ("neq", ctypes.c_int)]
 
 
 MAX_LEVELS = 16
@@ -93,9 +93,13 @@ def lib():
         L.md_newton_series_run.argtypes = [ctypes.POINTER(md_system), vp, sched_p, rep_p, vp, sz, i, vp]
         L.md_rcond_a0.argtypes = [ctypes.POINTER(md_system), vp, sz, i, vp, vp]
         L.md_linsolve_rcond.argtypes = [i, i, i, i, vp, vp, sz, i, vp, vp]
+        L.md_lstsq_workspace_bytes.argtypes = [i, i, i, i, i, i]
+        L.md_lstsq_workspace_bytes.restype = sz
+        L.md_lstsq_series.argtypes = [i, i, i, i, i, vp, vp, vp, vp, sz, i, vp]
+        L.md_lstsq_rcond.argtypes = [i, i, i, i, i, vp, vp, sz, i, vp, vp]
         for name in ("md_elementwise", "md_series_conv", "md_eval_diff", "md_linsolve_series",
                      "md_newton_series_step", "md_get_device_status", "md_newton_series_run", "md_rcond_a0",
-                     "md_linsolve_rcond"):
+                     "md_linsolve_rcond", "md_lstsq_series", "md_lstsq_rcond"):
             getattr(L, name).restype = i
         _lib = L
     return _lib
@@ -107,7 +111,7 @@ def exported_symbols():
             "md_newton_series_step", "md_get_device_status", "md_batched_workspace_bytes",
             "md_newton_series_step_batched", "md_linsolve_series_static", "md_profile_enable",
             "md_profile_read", "md_profile_kind_name", "md_newton_run_workspace_bytes", "md_newton_series_run",
-            "md_rcond_a0", "md_linsolve_rcond"]
+            "md_rcond_a0", "md_linsolve_rcond", "md_lstsq_workspace_bytes", "md_lstsq_series", "md_lstsq_rcond"]
 
 
 # --------------------------------------------------------------- helpers
@@ -153,7 +157,8 @@ class DeviceSystem:
     """A system with host structure arrays and device coefficient arrays.
 
     ``s`` is any object with the fields of ``md_system`` as numpy arrays
-    (poly_ptr, nvar, idx, expo int32; coef [P][K][nmono], cst [P][K][n] float64).
+    (poly_ptr, nvar, idx, expo int32; coef [P][K][nmono], cst [P][K][N] float64)
+    and optionally ``neq`` (N polynomials, 0 or absent: N = n).
     """
 
     def __init__(self, s, device="cuda"):
@@ -165,10 +170,11 @@ class DeviceSystem:
         self.nmono = int(self.nvar.shape[0])
         self.coef = to_device(s.coef, device)
         self.cst = to_device(s.cst, device)
+        self.neq = int(getattr(s, "neq", 0) or 0)
         self._c = md_system(self.limbs, int(self.is_complex), self.n, self.degree, self.nmono,
                             self.poly_ptr.ctypes.data, self.nvar.ctypes.data if self.nmono else None,
                             self.idx.ctypes.data if self.nmono else None, self.expo.ctypes.data if self.nmono else None,
-                            _ptr(self.coef) if self.nmono else None, _ptr(self.cst))
+                            _ptr(self.coef) if self.nmono else None, _ptr(self.cst), self.neq)
 
     @property
     def planes(self):
@@ -202,8 +208,9 @@ def series_conv(limbs: int, is_complex: bool, x, y, out=None, stream=None):
 def eval_diff(sysd: DeviceSystem, x, ws, f=None, A=None, stream=None):
     torch = _torch()
     P, K, n, d = sysd.planes, sysd.limbs, sysd.n, sysd.degree
-    f = f if f is not None else torch.empty((P, K, n, d + 1), dtype=torch.float64, device=x.device)
-    A = A if A is not None else torch.empty((P, K, d + 1, n, n), dtype=torch.float64, device=x.device)
+    N = sysd.neq or n
+    f = f if f is not None else torch.empty((P, K, N, d + 1), dtype=torch.float64, device=x.device)
+    A = A if A is not None else torch.empty((P, K, d + 1, n, N), dtype=torch.float64, device=x.device)
     _check(lib().md_eval_diff(sysd.c(), _ptr(x), _ptr(f), _ptr(A), _ptr(ws), ws.numel(), _stream(stream)),
            "md_eval_diff")
     return f, A
@@ -238,6 +245,30 @@ def rcond_a0(sysd: DeviceSystem, ws, flags: int = 0, out=None, stream=None):
     torch = _torch()
     out = out if out is not None else torch.empty(1, dtype=torch.float64, device=ws.device)
     _check(lib().md_rcond_a0(sysd.c(), _ptr(ws), ws.numel(), flags, _ptr(out), _stream(stream)), "md_rcond_a0")
+    return out
+
+
+def lstsq_workspace_bytes(limbs: int, is_complex: bool, neq: int, n: int, degree: int, flags: int = 0) -> int:
+    return int(lib().md_lstsq_workspace_bytes(limbs, int(is_complex), neq, n, degree, flags))
+
+
+def lstsq(limbs: int, is_complex: bool, A, b, ws, dx=None, flags: int = 0, stream=None):
+    """Least squares block Toeplitz solve: A [P][K][d+1][n][N], b [P][K][N][d+1]
+    CUDA tensors -> dx [P][K][n][d+1]."""
+    n, N, d = A.shape[3], A.shape[4], A.shape[2] - 1
+    dx = dx if dx is not None else b.new_empty((b.shape[0], b.shape[1], n, d + 1))
+    _check(lib().md_lstsq_series(limbs, int(is_complex), N, n, d, _ptr(A), _ptr(b), _ptr(dx), _ptr(ws), ws.numel(),
+                                 flags, _stream(stream)), "md_lstsq_series")
+    return dx
+
+
+def lstsq_rcond(limbs: int, is_complex: bool, A, ws, flags: int = 0, out=None, stream=None):
+    """1 / (||A_0||_1 ||A_0^+||_1) after lstsq(A) on ws."""
+    torch = _torch()
+    n, N, d = A.shape[3], A.shape[4], A.shape[2] - 1
+    out = out if out is not None else torch.empty(1, dtype=torch.float64, device=ws.device)
+    _check(lib().md_lstsq_rcond(limbs, int(is_complex), N, n, d, _ptr(A), _ptr(ws), ws.numel(), flags, _ptr(out),
+                                _stream(stream)), "md_lstsq_rcond")
     return out
 
 

@@ -79,13 +79,13 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
     const int4 *groups = reinterpret_cast<const int4 *>(ibase + J.groups);
     const int4 *contrib = reinterpret_cast<const int4 *>(ibase + J.contrib);
     for (long long e = tid; e < (long long)J.ngroups * (d + 1); e += NT)
-      accum_entry<K, P>(groups, contrib, pool, scal, J.cst, f, A, n, d, (int)(e / (d + 1)), (int)(e % (d + 1)));
+      accum_entry<K, P>(groups, contrib, pool, scal, J.cst, f, A, n, n, d, (int)(e / (d + 1)), (int)(e % (d + 1)));
     __syncthreads();
     // ---- solve A(t) dx(t) = -f(t)
     double *M = dbase + J.M, *Y = dbase + J.Y, *W = dbase + J.W;
     double *vd = dbase + J.vd, *beta = dbase + J.beta, *rinv = dbase + J.rinv;
     double *r = dbase + J.r, *dxw = dbase + J.dxw, *part = dbase + J.part;
-    for (long long e = tid; e < (long long)n * n; e += NT) solve_init_entry<K, P>(A, M, Y, n, d, e);
+    for (long long e = tid; e < (long long)n * n; e += NT) solve_init_entry<K, P>(A, M, Y, n, n, d, e);
     __syncthreads();
     // QR in the order of the lookahead form (same arithmetic per column): H_j
     // on column j+1 by the whole CTA, on the other targets by warps, then the
@@ -93,9 +93,9 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
     house_block<K, P>(M, vd, beta, status, n, 0);
     for (int j = 0; j < n; ++j) {
       const bool ahead = j + 1 < n;
-      if (ahead) house_apply_col_cta<K, P>(M, Y, vd, beta, n, j, 0, s_row);
+      if (ahead) house_apply_col_cta<K, P>(M, Y, vd, beta, n, n, j, 0, s_row);
       for (int w = warp + (ahead ? 1 : 0); w < (n - j - 1) + n; w += nwarp)
-        house_apply_col<K, P>(M, Y, vd, beta, n, j, w, lane);
+        house_apply_col<K, P>(M, Y, vd, beta, n, n, j, w, lane);
       __syncthreads();
       if (ahead) house_block<K, P>(M, vd, beta, status, n, j + 1);
     }
@@ -107,12 +107,12 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
     }
     for (int k = 0; k <= d; ++k) {
       int C, nchunk;
-      rhs_chunking(n, k, C, nchunk);
+      rhs_chunking(n, n, k, C, nchunk);
       for (long long e = tid; e < (long long)n * nchunk; e += NT)
-        rhs_partial_item<K, P>(A, dxw, part, n, d, k, C, nchunk, e);
+        rhs_partial_item<K, P>(A, dxw, part, n, n, d, k, C, nchunk, e);
       __syncthreads();
       for (int row = 0; row < n; ++row) rhs_finish_row<K, P>(f, -1.0, part, r, n, d, k, nchunk, row, s_row);
-      for (int row = 0; row < n; ++row) wmv_row<K, P>(W, r, dxw, n, k, row, s_row);
+      for (int row = 0; row < n; ++row) wmv_row<K, P>(W, r, dxw, n, n, k, row, s_row);
     }
     for (long long e = tid; e < (long long)n * (d + 1); e += NT)
       finish_entry<K, P>(dxw, nullptr, update_x ? J.x : nullptr, nrm ? nrm + 2 * job : nullptr, status, n, d, e);

@@ -88,27 +88,28 @@ struct SolveLayout {
 int oz_slices_host(int K) { return (((53 * K + 24 + 7) / 8) + 15) / 16 * 16; }
 int oz_kpad_host(int n) { return (n + 15) / 16 * 16; }
 
-SolveLayout solve_layout(int K, int P, int n, int d, size_t base, int flags = 0) {
+// N x n A_0 (N >= n): M is N x n, Y (Q^H) N x N, W n x N, r has N rows.
+SolveLayout solve_layout(int K, int P, int N, int n, int d, size_t base, int flags = 0) {
   SolveLayout L;
   const size_t VS = sizeof(double) * P * K;
-  const size_t nn = (size_t)n * n;
+  const size_t Nn = (size_t)N * n, NN = (size_t)N * N;
   int maxchunk = 1;
   for (int k = 0; k <= d; ++k) {
     int C, nc;
-    mdk::rhs_chunking(n, k, C, nc);
+    mdk::rhs_chunking(N, n, k, C, nc);
     maxchunk = std::max(maxchunk, nc);
   }
   L.maxchunk = maxchunk;
   size_t o = base;
-  L.off_M = o; o = align256(o + nn * VS);
-  L.off_Y = o; o = align256(o + nn * VS);
-  L.off_W = o; o = align256(o + nn * VS);
+  L.off_M = o; o = align256(o + Nn * VS);
+  L.off_Y = o; o = align256(o + NN * VS);
+  L.off_W = o; o = align256(o + Nn * VS);
   L.off_vd = o; o = align256(o + n * VS);
   L.off_beta = o; o = align256(o + n * sizeof(double) * K);
   L.off_rinv = o; o = align256(o + n * VS);
-  L.off_r = o; o = align256(o + (size_t)(d + 1) * n * VS);
+  L.off_r = o; o = align256(o + (size_t)(d + 1) * N * VS);
   L.off_dxw = o; o = align256(o + (size_t)(d + 1) * n * VS);
-  L.off_part = o; o = align256(o + (size_t)n * maxchunk * VS);
+  L.off_part = o; o = align256(o + (size_t)N * maxchunk * VS);
   if (flags & MD_FLAG_OZAKI) {
     const size_t S = oz_slices_host(K), kp = oz_kpad_host(n), M = (size_t)n * P * S, N = (size_t)P * S;
     L.ozaki = 1;
@@ -124,7 +125,7 @@ SolveLayout solve_layout(int K, int P, int n, int d, size_t base, int flags = 0)
 
 // --------------------------------------------------------- eval planning
 struct Plan {
-  int K = 0, P = 0, n = 0, d = 0, nmono = 0;
+  int K = 0, P = 0, n = 0, N = 0, d = 0, nmono = 0;
   int nslots = 0;
   std::vector<int> tasks;      // 8 ints per task, stage-major
   std::vector<int> stage_off;  // nstages + 1
@@ -151,11 +152,14 @@ uint64_t fnv(uint64_t h, const void *p, size_t bytes) {
   return h;
 }
 
+// Number of polynomials N >= n (neq = 0 means N = n).
+int neq_of(const md_system *s) { return s->neq ? s->neq : s->n; }
+
 uint64_t structure_checksum(const md_system *s) {
   uint64_t h = 1469598103934665603ULL;
-  const int hdr[5] = {s->limbs, s->is_complex, s->n, s->degree, s->nmono};
+  const int hdr[6] = {s->limbs, s->is_complex, s->n, s->degree, s->nmono, neq_of(s)};
   h = fnv(h, hdr, sizeof(hdr));
-  h = fnv(h, s->poly_ptr, sizeof(int) * (s->n + 1));
+  h = fnv(h, s->poly_ptr, sizeof(int) * (neq_of(s) + 1));
   h = fnv(h, s->nvar, sizeof(int) * s->nmono);
   h = fnv(h, s->idx, sizeof(int) * s->nmono * MD_MAXV);
   h = fnv(h, s->expo, sizeof(int) * s->nmono * MD_MAXV);
@@ -164,9 +168,11 @@ uint64_t structure_checksum(const md_system *s) {
 
 md_status check_system(const md_system *s) {
   if (!s || !valid_limbs(s->limbs) || s->n < 1 || s->degree < 0 || s->nmono < 0) return MD_ERR_ARG;
+  if (s->neq != 0 && s->neq < s->n) return MD_ERR_ARG;
   if (!s->poly_ptr || (s->nmono > 0 && (!s->nvar || !s->idx || !s->expo || !s->coef)) || !s->cst) return MD_ERR_ARG;
-  if (s->poly_ptr[0] != 0 || s->poly_ptr[s->n] != s->nmono) return MD_ERR_ARG;
-  for (int i = 0; i < s->n; ++i)
+  const int N = neq_of(s);
+  if (s->poly_ptr[0] != 0 || s->poly_ptr[N] != s->nmono) return MD_ERR_ARG;
+  for (int i = 0; i < N; ++i)
     if (s->poly_ptr[i + 1] < s->poly_ptr[i]) return MD_ERR_ARG;
   for (int m = 0; m < s->nmono; ++m) {
     if (s->nvar[m] < 0 || s->nvar[m] > MD_MAXV) return MD_ERR_ARG;
@@ -183,13 +189,22 @@ md_status check_system(const md_system *s) {
 // Builds the product schedule of every monomial in the order of the
 // definition (common factor, Speelpenning forward / backward / cross products,
 // F*P and F*partials), the stage of each product and the accumulation lists.
+// Flags that need a square A_0 (N = n).
+md_status flags_for_shape(int N, int n, int flags) {
+  if (N != n && (flags & MD_FLAG_LU)) return MD_ERR_ARG;
+  if (N != n && (flags & MD_FLAG_OZAKI)) return MD_ERR_UNSUPPORTED;
+  return MD_OK;
+}
+
 md_status build_plan(const md_system *s, Plan &p, int flags = 0) {
   md_status st = check_system(s);
   if (st != MD_OK) return st;
-  const int n = s->n, d = s->degree;
+  if ((st = flags_for_shape(neq_of(s), s->n, flags)) != MD_OK) return st;
+  const int n = s->n, N = neq_of(s), d = s->degree;
   p.K = s->limbs;
   p.P = s->is_complex ? 2 : 1;
   p.n = n;
+  p.N = N;
   p.d = d;
   p.nmono = s->nmono;
   p.nslots = n;
@@ -214,8 +229,8 @@ md_status build_plan(const md_system *s, Plan &p, int flags = 0) {
   std::vector<int> fcon;  // f contributions, 4 ints each, polynomial-major
   std::vector<int> alist;  // A contributions, 4 ints each
   std::map<std::pair<int, int>, std::vector<int>> acon;  // (row, col) -> indices into alist
-  std::vector<int> fgroup_first(n), fgroup_count(n);
-  for (int i = 0; i < n; ++i) {
+  std::vector<int> fgroup_first(N), fgroup_count(N);
+  for (int i = 0; i < N; ++i) {
     fgroup_first[i] = (int)fcon.size() / 4;
     fgroup_count[i] = s->poly_ptr[i + 1] - s->poly_ptr[i];
     for (int mo = s->poly_ptr[i]; mo < s->poly_ptr[i + 1]; ++mo) {
@@ -270,7 +285,7 @@ md_status build_plan(const md_system *s, Plan &p, int flags = 0) {
   }
   // f groups first, then one group per (row, col) with its contributions in monomial order
   p.contrib = fcon;
-  for (int i = 0; i < n; ++i) p.groups.insert(p.groups.end(), {i, -1, fgroup_first[i], fgroup_count[i]});
+  for (int i = 0; i < N; ++i) p.groups.insert(p.groups.end(), {i, -1, fgroup_first[i], fgroup_count[i]});
   for (auto &kv : acon) {
     const int first = (int)p.contrib.size() / 4;
     for (int a : kv.second) p.contrib.insert(p.contrib.end(), alist.begin() + 4 * a, alist.begin() + 4 * a + 4);
@@ -321,11 +336,11 @@ md_status build_plan(const md_system *s, Plan &p, int flags = 0) {
   p.off_groups = o; o = align256(o + sizeof(int) * std::max<size_t>(p.groups.size(), 4));
   p.off_contrib = o; o = align256(o + sizeof(int) * std::max<size_t>(p.contrib.size(), 4));
   p.off_tasks0 = o; o = align256(o + sizeof(int) * std::max<size_t>(p.tasks0.size(), 8));
-  p.off_f = o; o = align256(o + (size_t)n * (d + 1) * VS);
-  p.off_A = o; o = align256(o + (size_t)(d + 1) * n * n * VS);
+  p.off_f = o; o = align256(o + (size_t)N * (d + 1) * VS);
+  p.off_A = o; o = align256(o + (size_t)(d + 1) * N * n * VS);
   p.off_prod = o; o = align256(o + (p.contrib.size() / 4) * (size_t)(d + 1) * VS);
   p.off_solve = o;
-  p.sl = solve_layout(p.K, p.P, n, d, o, flags);
+  p.sl = solve_layout(p.K, p.P, N, n, d, o, flags);
   p.total = o + p.sl.bytes;
   p.checksum = structure_checksum(s);
   return MD_OK;
@@ -362,6 +377,8 @@ md_status prepare(const md_system *s, void *ws, size_t ws_bytes, cudaStream_t st
     g_plans[cs] = pe;
   }
   const Plan &p = pe->plan;
+  // the cached plan does not depend on MD_FLAG_LU: check the shape every call
+  if ((st = flags_for_shape(p.N, p.n, flags)) != MD_OK) return st;
   if (p.total > ws_bytes) return MD_ERR_WORKSPACE;
   if (!pe->pinned) {  // pinned image of the integer tables, created at the first upload
     const size_t bytes = p.off_f - p.off_tasks;
@@ -442,6 +459,7 @@ md_status batch_prepare(int nsys, const md_system *sys, double *const *x, BatchP
     md_status st;
     plans[i] = plan_of(&sys[i], st);
     if (!plans[i]) return st;
+    if (plans[i]->N != plans[i]->n) return MD_ERR_UNSUPPORTED;  // the batched form is for square systems
     const uint64_t cs = plans[i]->checksum;
     key = fnv(key, &cs, sizeof(cs));
     const void *ptrs[3] = {sys[i].coef, sys[i].cst, x ? (const void *)x[i] : nullptr};
@@ -659,6 +677,7 @@ md_status batch_autotune(BatchPlan &bp, char *base, cudaStream_t s, int sms) {
 EvalDev make_eval(const Plan &p, const md_system *s, const double *x, double *f, double *A, char *base) {
   EvalDev e;
   e.n = p.n;
+  e.N = p.N;
   e.d = p.d;
   e.nmono = p.nmono;
   e.x = x;
@@ -683,8 +702,9 @@ EvalDev make_eval(const Plan &p, const md_system *s, const double *x, double *f,
   return e;
 }
 
-SolveDev make_solve(const SolveLayout &L, int n, int d, char *base) {
+SolveDev make_solve(const SolveLayout &L, int N, int n, int d, char *base) {
   SolveDev v;
+  v.N = N;
   v.n = n;
   v.d = d;
   v.M = reinterpret_cast<double *>(base + L.off_M);
@@ -830,7 +850,7 @@ RunLayout run_layout(const md_system *s, const md_newton_schedule *sc, int flags
 
 extern "C" {
 
-int md_version(void) { return 100; }
+int md_version(void) { return 101; }
 
 const char *md_status_string(md_status st) {
   switch (st) {
@@ -853,9 +873,13 @@ size_t md_workspace_bytes(const md_system *sys, int flags) {
   return p.total;
 }
 
+size_t md_lstsq_workspace_bytes(int limbs, int is_complex, int neq, int n, int degree, int flags) {
+  if (!valid_limbs(limbs) || n < 1 || neq < n || degree < 0 || flags_for_shape(neq, n, flags) != MD_OK) return 0;
+  return 256 + solve_layout(limbs, is_complex ? 2 : 1, neq, n, degree, 256, flags).bytes;
+}
+
 size_t md_linsolve_workspace_bytes(int limbs, int is_complex, int n, int degree, int flags) {
-  if (!valid_limbs(limbs) || n < 1 || degree < 0) return 0;
-  return 256 + solve_layout(limbs, is_complex ? 2 : 1, n, degree, 256, flags).bytes;
+  return md_lstsq_workspace_bytes(limbs, is_complex, n, n, degree, flags);
 }
 
 md_status md_elementwise(int op, int limbs, int is_complex, long long count, const double *x, const double *y,
@@ -887,23 +911,30 @@ md_status md_eval_diff(const md_system *sys, const double *x, double *f, double 
   return cuda_status(dispatch(p->K, p->P, 2, &e, s));
 }
 
-md_status md_linsolve_series(int limbs, int is_complex, int n, int degree, const double *A, const double *b,
-                             double *dx, void *ws, size_t ws_bytes, int flags, void *stream) {
-  if (!valid_limbs(limbs) || n < 1 || degree < 0 || !A || !b || !dx) return MD_ERR_ARG;
+md_status md_lstsq_series(int limbs, int is_complex, int neq, int n, int degree, const double *A, const double *b,
+                           double *dx, void *ws, size_t ws_bytes, int flags, void *stream) {
+  if (!valid_limbs(limbs) || n < 1 || neq < n || degree < 0 || !A || !b || !dx) return MD_ERR_ARG;
+  md_status st = flags_for_shape(neq, n, flags);
+  if (st != MD_OK) return st;
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return MD_ERR_WORKSPACE;
   const int P = is_complex ? 2 : 1;
-  SolveLayout L = solve_layout(limbs, P, n, degree, 256, flags);
+  SolveLayout L = solve_layout(limbs, P, neq, n, degree, 256, flags);
   if (256 + L.bytes > ws_bytes) return MD_ERR_WORKSPACE;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   char *base = static_cast<char *>(ws);
   if (cudaMemsetAsync(base, 0, 256, s) != cudaSuccess) return MD_ERR_CUDA;
-  SolveDev v = make_solve(L, n, degree, base);
+  SolveDev v = make_solve(L, neq, n, degree, base);
   v.A = A;
   v.b = b;
   v.sgn = 1.0;
   v.dx_out = dx;
   v.lu = (flags & MD_FLAG_LU) ? 1 : 0;
   return cuda_status(dispatch(limbs, P, 3, &v, s));
+}
+
+md_status md_linsolve_series(int limbs, int is_complex, int n, int degree, const double *A, const double *b,
+                             double *dx, void *ws, size_t ws_bytes, int flags, void *stream) {
+  return md_lstsq_series(limbs, is_complex, n, n, degree, A, b, dx, ws, ws_bytes, flags, stream);
 }
 
 md_status md_newton_series_step(const md_system *sys, double *x, double *dx_norm, void *ws, size_t ws_bytes, int flags,
@@ -919,7 +950,7 @@ md_status md_newton_series_step(const md_system *sys, double *x, double *dx_norm
   double *f = reinterpret_cast<double *>(base + p->off_f);
   double *A = reinterpret_cast<double *>(base + p->off_A);
   EvalDev e = make_eval(*p, sys, x, f, A, base);
-  SolveDev v = make_solve(p->sl, p->n, p->d, base);
+  SolveDev v = make_solve(p->sl, p->N, p->n, p->d, base);
   v.A = A;
   v.b = f;
   v.sgn = -1.0;
@@ -954,23 +985,30 @@ md_status md_rcond_a0(const md_system *sys, void *ws, size_t ws_bytes, int flags
   md_status st = prepare(sys, ws, ws_bytes, s, p, flags);
   if (st != MD_OK) return st;
   char *base = static_cast<char *>(ws);
-  SolveDev v = make_solve(p->sl, p->n, p->d, base);
+  SolveDev v = make_solve(p->sl, p->N, p->n, p->d, base);
   v.A = reinterpret_cast<const double *>(base + p->off_A);
   v.rcond = rcond;
   return cuda_status(dispatch(p->K, p->P, 9, &v, s));
 }
 
-md_status md_linsolve_rcond(int limbs, int is_complex, int n, int degree, const double *A, void *ws,
-                            size_t ws_bytes, int flags, double *rcond, void *stream) {
-  if (!valid_limbs(limbs) || n < 1 || degree < 0 || !A || !rcond) return MD_ERR_ARG;
+md_status md_lstsq_rcond(int limbs, int is_complex, int neq, int n, int degree, const double *A, void *ws,
+                          size_t ws_bytes, int flags, double *rcond, void *stream) {
+  if (!valid_limbs(limbs) || n < 1 || neq < n || degree < 0 || !A || !rcond) return MD_ERR_ARG;
+  md_status st = flags_for_shape(neq, n, flags);
+  if (st != MD_OK) return st;
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return MD_ERR_WORKSPACE;
   const int P = is_complex ? 2 : 1;
-  SolveLayout L = solve_layout(limbs, P, n, degree, 256, flags);
+  SolveLayout L = solve_layout(limbs, P, neq, n, degree, 256, flags);
   if (256 + L.bytes > ws_bytes) return MD_ERR_WORKSPACE;
-  SolveDev v = make_solve(L, n, degree, static_cast<char *>(ws));
+  SolveDev v = make_solve(L, neq, n, degree, static_cast<char *>(ws));
   v.A = A;
   v.rcond = rcond;
   return cuda_status(dispatch(limbs, P, 9, &v, static_cast<cudaStream_t>(stream)));
+}
+
+md_status md_linsolve_rcond(int limbs, int is_complex, int n, int degree, const double *A, void *ws,
+                            size_t ws_bytes, int flags, double *rcond, void *stream) {
+  return md_lstsq_rcond(limbs, is_complex, n, n, degree, A, ws, ws_bytes, flags, rcond, stream);
 }
 
 size_t md_newton_run_workspace_bytes(const md_system *sys, const md_newton_schedule *sched, int flags) {

@@ -32,6 +32,7 @@ constexpr int kTargetLanes = 152 * 4 * 2 * 32;
 
 struct EvalDev {
   int n = 0, d = 0, nmono = 0;
+  int N = 0;  // polynomials (rows of f and A), N >= n
   const double *x = nullptr;
   double *f = nullptr;
   double *A = nullptr;
@@ -57,8 +58,9 @@ struct EvalDev {
 
 struct SolveDev {
   int n = 0, d = 0;
-  const double *A = nullptr;  // caller layout [P][K][d+1][n][n]
-  const double *b = nullptr;  // caller layout [P][K][n][d+1]
+  int N = 0;                  // rows of A_0 (N >= n; N > n: least squares)
+  const double *A = nullptr;  // caller layout [P][K][d+1][n][N]
+  const double *b = nullptr;  // caller layout [P][K][N][d+1]
   double sgn = 1.0;           // r_k = sgn * b_k - ...
   double *dx_out = nullptr;   // caller layout, may be null
   double *x = nullptr;        // x += dx when not null
@@ -77,14 +79,16 @@ struct SolveDev {
   float *oz_C = nullptr;
 };
 
-__host__ __device__ inline void rhs_chunking(int n, int k, int &C, int &nchunk) {
+// Terms j*n + col (j < k) of one of the N rows of r_k, cut into nchunk
+// chunks of C so that N * nchunk is about kTargetLanes.
+__host__ __device__ inline void rhs_chunking(int N, int n, int k, int &C, int &nchunk) {
   const long long terms = (long long)k * n;
   if (terms == 0) {
     C = 1;
     nchunk = 0;
     return;
   }
-  long long c = (terms * n + kTargetLanes - 1) / kTargetLanes;
+  long long c = (terms * N + kTargetLanes - 1) / kTargetLanes;
   if (c < 1) c = 1;
   C = (int)c;
   nchunk = (int)((terms + c - 1) / c);

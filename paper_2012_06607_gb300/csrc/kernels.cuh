@@ -293,16 +293,22 @@ __global__ void __launch_bounds__(64) conv_stage_kernel(const int *__restrict__ 
   conv_pair<K, P>(pool, d, t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z);
 }
 
-// Same work with a fixed grid of kConvResidentThreads-thread CTAs (one per SM)
+// Same work with a fixed grid of CTAs (one per SM)
 // that stride over the tasks, so that a grid of SMs - R CTAs leaves R SMs to
 // kernels that run concurrently on another stream.  Thread numbering is
 // interleaved across CTAs (t = tid * grid + cta): all tasks cost the same, and
 // the last, partial round of tasks is then spread over every SM instead of
 // going whole to the first CTAs, so the SMs end together.
-constexpr int kConvResidentThreads = 384;
+// Up to five limbs a task fits in the 168 registers a 384-thread CTA leaves
+// per thread; eight and ten limbs get 256 threads and up to 255 registers
+// (two warps per SM sub-partition still keep the FP64 pipe busy).
+template <int K>
+constexpr int conv_resident_threads() {
+  return K <= 5 ? 384 : 256;
+}
 
 template <int K, int P>
-__global__ void __launch_bounds__(kConvResidentThreads, 1)
+__global__ void __launch_bounds__(conv_resident_threads<K>(), 1)
     conv_stage_resident_kernel(const int *__restrict__ tasks, int ntask, double *pool, int d) {
   for (int t = threadIdx.x * gridDim.x + blockIdx.x; t < ntask; t += gridDim.x * blockDim.x) {
     const int4 t0 = __ldg(reinterpret_cast<const int4 *>(tasks) + 2 * t);
@@ -332,14 +338,15 @@ __device__ __forceinline__ void accum_contrib_value(const int4 C, const double *
   }
 }
 
+// f: [P][K][N][d+1]; A: [P][K][d+1][n][N] (column-major N x n blocks).
 template <int K, int P>
-__device__ __forceinline__ void accum_store(const int4 G, const mdv<K, P> &acc, double *f, double *A, int n, int d,
-                                            int k) {
+__device__ __forceinline__ void accum_store(const int4 G, const mdv<K, P> &acc, double *f, double *A, int N, int n,
+                                            int d, int k) {
   if (G.y < 0) {
-    st_soa<K, P>(f + (long long)G.x * (d + 1) + k, (long long)n * (d + 1), acc);
+    st_soa<K, P>(f + (long long)G.x * (d + 1) + k, (long long)N * (d + 1), acc);
   } else {
-    const long long nn = (long long)n * n;
-    st_soa<K, P>(A + (long long)k * nn + (long long)G.y * n + G.x, (long long)(d + 1) * nn, acc);
+    const long long nn = (long long)N * n;
+    st_soa<K, P>(A + (long long)k * nn + (long long)G.y * N + G.x, (long long)(d + 1) * nn, acc);
   }
 }
 
@@ -349,29 +356,29 @@ template <int K, int P>
 __device__ __forceinline__ void accum_entry(const int4 *groups, const int4 *contrib,
                                             const double *pool, const double *scal,
                                             const double *cst, double *f,
-                                            double *A, int n, int d, int g, int k) {
+                                            double *A, int N, int n, int d, int g, int k) {
   const int4 G = groups[g];
   mdv<K, P> acc, v;
   c_zero<K, P>(acc);
-  if (G.y < 0 && k == 0) ld_soa<K, P>(cst + G.x, n, acc);
+  if (G.y < 0 && k == 0) ld_soa<K, P>(cst + G.x, N, acc);
   for (int q = 0; q < G.w; ++q) {
     accum_contrib_value<K, P>(contrib[G.z + q], pool, scal, d, k, v);
     c_add<K, P>(acc, v, acc);
   }
-  accum_store<K, P>(G, acc, f, A, n, d, k);
+  accum_store<K, P>(G, acc, f, A, N, n, d, k);
 }
 
 // Entries (group, k) for k in [k0, k0 + nk); only_A: skip the f rows.
 template <int K, int P>
 __global__ void accum_kernel(const int4 *__restrict__ groups, int ngroups, const int4 *__restrict__ contrib,
                              const double *__restrict__ pool, const double *__restrict__ scal,
-                             const double *__restrict__ cst, double *__restrict__ f, double *__restrict__ A, int n,
-                             int d, int k0, int nk, int only_A) {
+                             const double *__restrict__ cst, double *__restrict__ f, double *__restrict__ A, int N,
+                             int n, int d, int k0, int nk, int only_A) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= (long long)ngroups * nk) return;
   const int g = (int)(e / nk);
   if (only_A && groups[g].y < 0) return;
-  accum_entry<K, P>(groups, contrib, pool, scal, cst, f, A, n, d, g, k0 + (int)(e % nk));
+  accum_entry<K, P>(groups, contrib, pool, scal, cst, f, A, N, n, d, g, k0 + (int)(e % nk));
 }
 
 // The same accumulation in two passes, so that long groups (the f rows sum
@@ -395,7 +402,7 @@ __global__ void accum_prod_kernel(const int4 *__restrict__ contrib, int ncontrib
 template <int K, int P>
 __global__ void accum_sum_kernel(const int4 *__restrict__ groups, int ngroups, const double *__restrict__ prod,
                                  const double *__restrict__ cst, double *__restrict__ f, double *__restrict__ A,
-                                 int n, int d, int skip_A0) {
+                                 int N, int n, int d, int skip_A0) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= (long long)ngroups * (d + 1)) return;
   const int g = (int)(e / (d + 1)), k = (int)(e % (d + 1));
@@ -404,37 +411,42 @@ __global__ void accum_sum_kernel(const int4 *__restrict__ groups, int ngroups, c
   const long long VS = P * K;
   mdv<K, P> acc, v;
   c_zero<K, P>(acc);
-  if (G.y < 0 && k == 0) ld_soa<K, P>(cst + G.x, n, acc);
+  if (G.y < 0 && k == 0) ld_soa<K, P>(cst + G.x, N, acc);
   for (int q = 0; q < G.w; ++q) {
     ld_aos<K, P>(prod + ((long long)(G.z + q) * (d + 1) + k) * VS, v);
     c_add<K, P>(acc, v, acc);
   }
-  accum_store<K, P>(G, acc, f, A, n, d, k);
+  accum_store<K, P>(G, acc, f, A, N, n, d, k);
 }
 
 // ------------------------------------------------------------------- solve
-// Work matrices are AoS, column-major: element (r, c) at M[(c*n + r)*P*K].
-// Every body below is shared by the one-launch-per-step kernels and by the
-// batched kernel (one CTA per system); the reduction trees are the same in both.
+// A_0 is N x n (N >= n equations; N > n: least squares).  Work matrices are
+// AoS, column-major with N rows: element (r, c) of M (N x n, becomes R and the
+// reflectors) and of Y (N x N, becomes Q^H) at [(c*N + r)*P*K]; W (n x N) is
+// row-major.  Every body below is shared by the one-launch-per-step kernels and
+// by the batched kernel (one CTA per system, N = n); the reduction trees are the
+// same in both.
 template <int K, int P>
-__device__ __forceinline__ void solve_init_entry(const double *A, double *M,
-                                                 double *Y, int n, int d, long long e) {
-  const long long nn = (long long)n * n;
+__device__ __forceinline__ void solve_init_entry(const double *A, double *M, double *Y, int N, int n, int d,
+                                                 long long e) {
+  const long long nn = (long long)N * n;
   mdv<K, P> v;
-  ld_soa<K, P>(A + e, (long long)(d + 1) * nn, v);  // A_0, column-major, e = c*n + r
-  st_aos<K, P>(M + e * (P * K), v);
+  if (e < nn) {
+    ld_soa<K, P>(A + e, (long long)(d + 1) * nn, v);  // A_0, column-major, e = c*N + r
+    st_aos<K, P>(M + e * (P * K), v);
+  }
   c_zero<K, P>(v);
-  const long long r = e % n, c = e / n;
+  const long long r = e % N, c = e / N;
   if (r == c) v.v[0][0] = 1.0;
   st_aos<K, P>(Y + e * (P * K), v);
 }
 
 template <int K, int P>
-__global__ void solve_init_kernel(const double *__restrict__ A, double *__restrict__ M, double *__restrict__ Y, int n,
-                                  int d) {
+__global__ void solve_init_kernel(const double *__restrict__ A, double *__restrict__ M, double *__restrict__ Y, int N,
+                                  int n, int d) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (e >= (long long)n * n) return;
-  solve_init_entry<K, P>(A, M, Y, n, d, e);
+  if (e >= (long long)N * N) return;
+  solve_init_entry<K, P>(A, M, Y, N, n, d, e);
 }
 
 constexpr int kHouseThreads = 128;
@@ -444,7 +456,7 @@ constexpr int kHouseThreads = 128;
 // Block-level body for kHouseThreads threads.
 template <int K, int P>
 __device__ __forceinline__ void house_block(double *M, double *vd,
-                                            double *beta, int *status, int n, int j) {
+                                            double *beta, int *status, int N, int j) {
   __shared__ mdv<K, 1> red[kHouseThreads / 32];
   __shared__ double s_alpha[K], s_a0[K], s_beta[K];
   __shared__ mdv<K, P> s_ph;
@@ -453,9 +465,9 @@ __device__ __forceinline__ void house_block(double *M, double *vd,
   mdv<K, 1> acc;
   c_zero<K, 1>(acc);
   bool have = false;
-  for (int i = j + tid; tid < kHouseThreads && i < n; i += kHouseThreads) {
+  for (int i = j + tid; tid < kHouseThreads && i < N; i += kHouseThreads) {
     mdv<K, P> x;
-    ld_aos<K, P>(M + ((long long)j * n + i) * VS, x);
+    ld_aos<K, P>(M + ((long long)j * N + i) * VS, x);
     double a2[K];
     c_abs2<K, P>(x, a2);
     if (!have) {
@@ -469,7 +481,7 @@ __device__ __forceinline__ void house_block(double *M, double *vd,
   }
   block_sum<K, 1>(acc, red, kHouseThreads);
   mdv<K, P> x0;
-  ld_aos<K, P>(M + ((long long)j * n + j) * VS, x0);
+  ld_aos<K, P>(M + ((long long)j * N + j) * VS, x0);
   if (tid == 0) {
     double al[K];
     md_sqrt<K>(acc.v[0], al);
@@ -541,7 +553,7 @@ __device__ __forceinline__ void house_block(double *M, double *vd,
 #pragma unroll
     for (int p = 0; p < P; ++p) md_neg<K>(pa.v[p], rjj.v[p]);
     st_aos<K, P>(vd + (long long)j * VS, v0);
-    st_aos<K, P>(M + ((long long)j * n + j) * VS, rjj);
+    st_aos<K, P>(M + ((long long)j * N + j) * VS, rjj);
 #pragma unroll
     for (int l = 0; l < K; ++l) beta[(long long)j * K + l] = s_beta[l];
   }
@@ -551,8 +563,8 @@ __device__ __forceinline__ void house_block(double *M, double *vd,
 template <int K, int P>
 __global__ void __launch_bounds__(kHouseThreads) house_kernel(double *__restrict__ M, double *__restrict__ vd,
                                                               double *__restrict__ beta, int *__restrict__ status,
-                                                              int n, int j) {
-  house_block<K, P>(M, vd, beta, status, n, j);
+                                                              int N, int j) {
+  house_block<K, P>(M, vd, beta, status, N, j);
 }
 
 // Apply H_j = I - beta_j v v^H to target column w: w < n-j-1 is column j+1+w of
@@ -560,8 +572,8 @@ __global__ void __launch_bounds__(kHouseThreads) house_kernel(double *__restrict
 // Warp-level body.
 template <int K, int P>
 __device__ __forceinline__ void house_apply_col(double *M, double *Y,
-                                                const double *vd, const double *beta, int n,
-                                                int j, int w, int lane) {
+                                                const double *vd, const double *beta, int N,
+                                                int n, int j, int w, int lane) {
   const int nm = n - j - 1;
   double *T;
   int c;
@@ -576,13 +588,13 @@ __device__ __forceinline__ void house_apply_col(double *M, double *Y,
   mdv<K, P> acc, v, cv, t, prod;
   c_zero<K, P>(acc);
   bool have = false;
-  for (int i = j + lane; i < n; i += 32) {
+  for (int i = j + lane; i < N; i += 32) {
     if (i == j)
       ld_aos<K, P>(vd + (long long)j * VS, v);
     else
-      ld_aos<K, P>(M + ((long long)j * n + i) * VS, v);
+      ld_aos<K, P>(M + ((long long)j * N + i) * VS, v);
     c_conj<K, P>(v, cv);
-    ld_aos<K, P>(T + ((long long)c * n + i) * VS, t);
+    ld_aos<K, P>(T + ((long long)c * N + i) * VS, t);
     c_mul<K, P>(cv, t, prod);
     if (!have) {
       acc = prod;
@@ -597,25 +609,25 @@ __device__ __forceinline__ void house_apply_col(double *M, double *Y,
   for (int l = 0; l < K; ++l) bt[l] = beta[(long long)j * K + l];
   mdv<K, P> tau;
   c_mul_real<K, P>(acc, bt, tau);
-  for (int i = j + lane; i < n; i += 32) {
+  for (int i = j + lane; i < N; i += 32) {
     if (i == j)
       ld_aos<K, P>(vd + (long long)j * VS, v);
     else
-      ld_aos<K, P>(M + ((long long)j * n + i) * VS, v);
-    ld_aos<K, P>(T + ((long long)c * n + i) * VS, t);
+      ld_aos<K, P>(M + ((long long)j * N + i) * VS, v);
+    ld_aos<K, P>(T + ((long long)c * N + i) * VS, t);
     c_mul<K, P>(tau, v, prod);
     c_sub<K, P>(t, prod, t);
-    st_aos<K, P>(T + ((long long)c * n + i) * VS, t);
+    st_aos<K, P>(T + ((long long)c * N + i) * VS, t);
   }
 }
 
 template <int K, int P>
 __global__ void __launch_bounds__(128) house_apply_kernel(double *__restrict__ M, double *__restrict__ Y,
                                                           const double *__restrict__ vd,
-                                                          const double *__restrict__ beta, int n, int j) {
+                                                          const double *__restrict__ beta, int N, int n, int j) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= (n - j - 1) + n) return;
-  house_apply_col<K, P>(M, Y, vd, beta, n, j, warp, lane);
+  if (warp >= (n - j - 1) + N) return;
+  house_apply_col<K, P>(M, Y, vd, beta, N, n, j, warp, lane);
 }
 
 // The same application by a whole CTA over kRowLanes virtual lanes (plane,
@@ -623,30 +635,30 @@ __global__ void __launch_bounds__(128) house_apply_kernel(double *__restrict__ M
 // shared-memory tree, tau = beta * dot, then t_i -= tau v_i plane by plane
 // (each element updated exactly as in house_apply_col).  CTA body.
 template <int K, int P>
-__device__ __forceinline__ void house_apply_col_cta(double *M, double *Y, const double *vd, const double *beta, int n,
-                                                    int j, int w, double (*sm)[K]) {
+__device__ __forceinline__ void house_apply_col_cta(double *M, double *Y, const double *vd, const double *beta, int N,
+                                                    int n, int j, int w, double (*sm)[K]) {
   constexpr int Vc = kRowLanes / P;
   const int nm = n - j - 1;
   double *T = (w < nm) ? M : Y;
   const int c = (w < nm) ? j + 1 + w : w - nm;
   const long long VS = P * K;
-  const int nleaf = min(n - j, Vc);
+  const int nleaf = min(N - j, Vc);
   auto ld_v = [&](int i, mdv<K, P> &v) {
     if (i == j)
       ld_aos<K, P>(vd + (long long)j * VS, v);
     else
-      ld_aos<K, P>(M + ((long long)j * n + i) * VS, v);
+      ld_aos<K, P>(M + ((long long)j * N + i) * VS, v);
   };
   for (int q = threadIdx.x; q < kRowLanes; q += blockDim.x) {
     const int p = q / Vc, cs = q % Vc;
     if (cs < nleaf) {
       double acc[K], t[K];
       bool have = false;
-      for (int i = j + cs; i < n; i += Vc) {
+      for (int i = j + cs; i < N; i += Vc) {
         mdv<K, P> v, cv, x;
         ld_v(i, v);
         c_conj<K, P>(v, cv);
-        ld_aos<K, P>(T + ((long long)c * n + i) * VS, x);
+        ld_aos<K, P>(T + ((long long)c * N + i) * VS, x);
         if (!have) {
           plane_prod_v<K, P>(cv, x, p, acc);
           have = true;
@@ -673,12 +685,12 @@ __device__ __forceinline__ void house_apply_col_cta(double *M, double *Y, const 
   for (int p = 0; p < P; ++p) ld_limbs<K>(sm[p * Vc], tau.v[p]);
   for (int q = threadIdx.x; q < kRowLanes; q += blockDim.x) {
     const int p = q / Vc, cs = q % Vc;
-    for (int i = j + cs; i < n; i += Vc) {
+    for (int i = j + cs; i < N; i += Vc) {
       mdv<K, P> v;
       ld_v(i, v);
       double pr[K], t[K];
       plane_prod_v<K, P>(tau, v, p, pr);
-      double *dst = T + ((long long)c * n + i) * VS + p * K;
+      double *dst = T + ((long long)c * N + i) * VS + p * K;
       ld_limbs<K>(dst, t);
       md_sub<K>(t, pr, t);
       st_limbs<K>(dst, t);
@@ -695,28 +707,28 @@ __device__ __forceinline__ void house_apply_col_cta(double *M, double *Y, const 
 // not their sum.
 template <int K, int P>
 __global__ void __launch_bounds__(kHouseThreads) house_step_kernel(double *M, double *Y, double *vd, double *beta,
-                                                                   int *status, int n, int j) {
+                                                                   int *status, int N, int n, int j) {
   __shared__ double sm[kRowLanes][K];
   const bool ahead = j + 1 < n;
   if (blockIdx.x == 0) {
     if (ahead) {
-      house_apply_col_cta<K, P>(M, Y, vd, beta, n, j, 0, sm);
-      house_block<K, P>(M, vd, beta, status, n, j + 1);
+      house_apply_col_cta<K, P>(M, Y, vd, beta, N, n, j, 0, sm);
+      house_block<K, P>(M, vd, beta, status, N, j + 1);
     }
     return;
   }
   const int warp = ((blockIdx.x - 1) * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   const int w = warp + (ahead ? 1 : 0);
-  if (w >= (n - j - 1) + n) return;
-  house_apply_col<K, P>(M, Y, vd, beta, n, j, w, lane);
+  if (w >= (n - j - 1) + N) return;
+  house_apply_col<K, P>(M, Y, vd, beta, N, n, j, w, lane);
 }
 
 // rinv[j] = 1 / R_jj
 template <int K, int P>
-__device__ __forceinline__ void rinv_entry(const double *M, double *rinv, int n, int j) {
+__device__ __forceinline__ void rinv_entry(const double *M, double *rinv, int N, int j) {
   const long long VS = P * K;
   mdv<K, P> r, one, z;
-  ld_aos<K, P>(M + ((long long)j * n + j) * VS, r);
+  ld_aos<K, P>(M + ((long long)j * N + j) * VS, r);
   c_zero<K, P>(one);
   one.v[0][0] = 1.0;
   c_div<K, P>(one, r, z);
@@ -724,42 +736,43 @@ __device__ __forceinline__ void rinv_entry(const double *M, double *rinv, int n,
 }
 
 template <int K, int P>
-__global__ void rinv_kernel(const double *__restrict__ M, double *__restrict__ rinv, int n) {
+__global__ void rinv_kernel(const double *__restrict__ M, double *__restrict__ rinv, int N, int n) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  rinv_entry<K, P>(M, rinv, n, j);
+  rinv_entry<K, P>(M, rinv, N, j);
 }
 
-// Column-oriented back substitution step c of R W = Y (all n right-hand sides):
-// W[c][:] = Y[c][:] / R_cc; Y[i][:] -= R_ic W[c][:] for i < c.  W is row-major.
+// Column-oriented back substitution step c of R W = Y[0:n, :] (all N
+// right-hand sides; R is the top n x n block): W[c][:] = Y[c][:] / R_cc;
+// Y[i][:] -= R_ic W[c][:] for i < c.  W (n x N) is row-major.
 template <int K, int P>
 __device__ __forceinline__ void backsub_entry(const double *M, double *Y,
-                                              double *W, const double *rinv, int n, int c,
+                                              double *W, const double *rinv, int N, int c,
                                               long long e) {
-  const int i = (int)(e / n), col = (int)(e % n);
+  const int i = (int)(e / N), col = (int)(e % N);
   const long long VS = P * K;
   mdv<K, P> y, ri, w;
-  ld_aos<K, P>(Y + ((long long)col * n + c) * VS, y);
+  ld_aos<K, P>(Y + ((long long)col * N + c) * VS, y);
   ld_aos<K, P>(rinv + (long long)c * VS, ri);
   c_mul<K, P>(y, ri, w);
   if (i == c) {
-    st_aos<K, P>(W + ((long long)c * n + col) * VS, w);
+    st_aos<K, P>(W + ((long long)c * N + col) * VS, w);
   } else {
     mdv<K, P> rc, t, yi;
-    ld_aos<K, P>(M + ((long long)c * n + i) * VS, rc);
-    ld_aos<K, P>(Y + ((long long)col * n + i) * VS, yi);
+    ld_aos<K, P>(M + ((long long)c * N + i) * VS, rc);
+    ld_aos<K, P>(Y + ((long long)col * N + i) * VS, yi);
     c_mul<K, P>(rc, w, t);
     c_sub<K, P>(yi, t, yi);
-    st_aos<K, P>(Y + ((long long)col * n + i) * VS, yi);
+    st_aos<K, P>(Y + ((long long)col * N + i) * VS, yi);
   }
 }
 
 template <int K, int P>
 __global__ void backsub_kernel(const double *__restrict__ M, double *__restrict__ Y, double *__restrict__ W,
-                               const double *__restrict__ rinv, int n, int c) {
+                               const double *__restrict__ rinv, int N, int c) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (e >= (long long)(c + 1) * n) return;
-  backsub_entry<K, P>(M, Y, W, rinv, n, c, e);
+  if (e >= (long long)(c + 1) * N) return;
+  backsub_entry<K, P>(M, Y, W, rinv, N, c, e);
 }
 
 // ------------------------------------------------------------ LU (N = n)
@@ -874,27 +887,33 @@ __global__ void lu_forward_kernel(const double *__restrict__ M, double *__restri
 }
 
 // 1 / (||A_0||_1 ||W||_1) from the leading limbs (moduli in double): the
-// reciprocal condition number of A_0 in the 1-norm, W = A_0^-1 being formed by
-// the solve.  A: caller layout [P][K][d+1][n][n] (coefficient 0, column-major);
-// W: row-major AoS.  One CTA.
+// reciprocal condition number of A_0 in the 1-norm, W = A_0^-1 (the
+// pseudo-inverse when N > n) being formed by the solve.  A: caller layout
+// [P][K][d+1][n][N] (coefficient 0, column-major); W: n x N row-major AoS.
+// One CTA.
 template <int K, int P>
 __global__ void __launch_bounds__(256) rcond_kernel(const double *__restrict__ A, const double *__restrict__ W,
-                                                    double *__restrict__ out, int n, int d) {
+                                                    double *__restrict__ out, int N, int n, int d) {
   __shared__ double s_max[2][256];
   const int tid = threadIdx.x;
-  const long long nn = (long long)n * n, pstride = (long long)K * (d + 1) * nn, VS = P * K;
+  const long long nn = (long long)N * n, pstride = (long long)K * (d + 1) * nn, VS = P * K;
   double ma = 0.0, mw = 0.0;
-  for (int c = tid; c < n; c += blockDim.x) {
-    double sa = 0.0, sw = 0.0;
-    for (int r = 0; r < n; ++r) {
-      const double are = A[(long long)c * n + r];
-      const double aim = P == 2 ? A[pstride + (long long)c * n + r] : 0.0;
+  for (int c = tid; c < n; c += blockDim.x) {  // ||A_0||_1: N rows of column c
+    double sa = 0.0;
+    for (int r = 0; r < N; ++r) {
+      const double are = A[(long long)c * N + r];
+      const double aim = P == 2 ? A[pstride + (long long)c * N + r] : 0.0;
       sa += sqrt(are * are + aim * aim);
-      const double *w = W + ((long long)r * n + c) * VS;
+    }
+    ma = fmax(ma, sa);
+  }
+  for (int c = tid; c < N; c += blockDim.x) {  // ||W||_1: n rows of column c
+    double sw = 0.0;
+    for (int r = 0; r < n; ++r) {
+      const double *w = W + ((long long)r * N + c) * VS;
       const double wre = w[0], wim = P == 2 ? w[K] : 0.0;
       sw += sqrt(wre * wre + wim * wim);
     }
-    ma = fmax(ma, sa);
     mw = fmax(mw, sw);
   }
   s_max[0][tid] = ma;
@@ -915,16 +934,16 @@ __global__ void __launch_bounds__(256) rcond_kernel(const double *__restrict__ A
 // SoA [P][K][d+1][n][n] (column-major blocks); dx is AoS [k][i].
 template <int K, int P>
 __device__ __forceinline__ void rhs_partial_item(const double *A, const double *dx,
-                                                 double *part, int n, int d, int k, int C, int nchunk,
+                                                 double *part, int N, int n, int d, int k, int C, int nchunk,
                                                  long long e) {
-  const int row = (int)(e % n), chunk = (int)(e / n);
-  const long long nn = (long long)n * n, VS = P * K, stride = (long long)(d + 1) * nn;
+  const int row = (int)(e % N), chunk = (int)(e / N);
+  const long long nn = (long long)N * n, VS = P * K, stride = (long long)(d + 1) * nn;
   const int t0 = chunk * C, t1 = min(t0 + C, k * n);
   mdv<K, P> acc, a, x, prod;
   c_zero<K, P>(acc);
   for (int t = t0; t < t1; ++t) {
     const int j = t / n, col = t % n;
-    ld_soa<K, P>(A + (long long)(k - j) * nn + (long long)col * n + row, stride, a);
+    ld_soa<K, P>(A + (long long)(k - j) * nn + (long long)col * N + row, stride, a);
     ld_aos<K, P>(dx + ((long long)j * n + col) * VS, x);
     c_mul<K, P>(a, x, prod);
     if (t == t0)
@@ -937,15 +956,16 @@ __device__ __forceinline__ void rhs_partial_item(const double *A, const double *
 
 template <int K, int P>
 __global__ void rhs_partial_kernel(const double *__restrict__ A, const double *__restrict__ dx,
-                                   double *__restrict__ part, int n, int d, int k, int C, int nchunk) {
+                                   double *__restrict__ part, int N, int n, int d, int k, int C, int nchunk) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (e >= (long long)n * nchunk) return;
-  rhs_partial_item<K, P>(A, dx, part, n, d, k, C, nchunk, e);
+  if (e >= (long long)N * nchunk) return;
+  rhs_partial_item<K, P>(A, dx, part, N, n, d, k, C, nchunk, e);
 }
 
-// r_k[row] = sgn * b_k[row] - (sum of the row's nchunk partials).  CTA body.
+// r_k[row] = sgn * b_k[row] - (sum of the row's nchunk partials), row < N.
+// b: [P][K][N][d+1].  CTA body.
 template <int K, int P>
-__device__ __forceinline__ void rhs_finish_row(const double *b, double sgn, const double *part, double *r, int n,
+__device__ __forceinline__ void rhs_finish_row(const double *b, double sgn, const double *part, double *r, int N,
                                                int d, int k, int nchunk, int row, double (*sm)[K]) {
   constexpr int Vc = kRowLanes / P;
   const long long VS = P * K;
@@ -966,7 +986,7 @@ __device__ __forceinline__ void rhs_finish_row(const double *b, double sgn, cons
   row_tree<K, P>(sm, nleaf);
   for (int p = threadIdx.x; p < P; p += blockDim.x) {
     double bv[K], a[K], z[K];
-    const long long stride = (long long)n * (d + 1);
+    const long long stride = (long long)N * (d + 1);
 #pragma unroll
     for (int l = 0; l < K; ++l) bv[l] = b[(long long)row * (d + 1) + k + (long long)(p * K + l) * stride];
     if (sgn < 0.0) md_neg<K>(bv, bv);
@@ -977,7 +997,7 @@ __device__ __forceinline__ void rhs_finish_row(const double *b, double sgn, cons
 #pragma unroll
       for (int l = 0; l < K; ++l) z[l] = bv[l];
     }
-    st_limbs<K>(r + ((long long)k * n + row) * VS + p * K, z);
+    st_limbs<K>(r + ((long long)k * N + row) * VS + p * K, z);
   }
   __syncthreads();
 }
@@ -985,26 +1005,26 @@ __device__ __forceinline__ void rhs_finish_row(const double *b, double sgn, cons
 template <int K, int P>
 __global__ void __launch_bounds__(kRowLanes) rhs_finish_kernel(const double *__restrict__ b, double sgn,
                                                                const double *__restrict__ part,
-                                                               double *__restrict__ r, int n, int d, int k,
+                                                               double *__restrict__ r, int N, int d, int k,
                                                                int nchunk) {
   __shared__ double sm[kRowLanes][K];
-  rhs_finish_row<K, P>(b, sgn, part, r, n, d, k, nchunk, blockIdx.x, sm);
+  rhs_finish_row<K, P>(b, sgn, part, r, N, d, k, nchunk, blockIdx.x, sm);
 }
 
-// dx_k[row] = sum_col W[row][col] r_k[col].  CTA body.
+// dx_k[row] = sum_{col < N} W[row][col] r_k[col], row < n.  CTA body.
 template <int K, int P>
-__device__ __forceinline__ void wmv_row(const double *W, const double *r, double *dx, int n, int k, int row,
+__device__ __forceinline__ void wmv_row(const double *W, const double *r, double *dx, int N, int n, int k, int row,
                                         double (*sm)[K]) {
   constexpr int Vc = kRowLanes / P;
   const long long VS = P * K;
-  const int nleaf = min(n, Vc);
+  const int nleaf = min(N, Vc);
   for (int v = threadIdx.x; v < kRowLanes; v += blockDim.x) {
     const int p = v / Vc, cs = v % Vc;
     if (cs < nleaf) {
       double acc[K], t[K];
-      plane_prod<K, P>(W + ((long long)row * n + cs) * VS, r + ((long long)k * n + cs) * VS, p, acc);
-      for (int c = cs + Vc; c < n; c += Vc) {
-        plane_prod<K, P>(W + ((long long)row * n + c) * VS, r + ((long long)k * n + c) * VS, p, t);
+      plane_prod<K, P>(W + ((long long)row * N + cs) * VS, r + ((long long)k * N + cs) * VS, p, acc);
+      for (int c = cs + Vc; c < N; c += Vc) {
+        plane_prod<K, P>(W + ((long long)row * N + c) * VS, r + ((long long)k * N + c) * VS, p, t);
         md_add<K>(acc, t, acc);
       }
       st_limbs<K>(sm[v], acc);
@@ -1022,9 +1042,9 @@ __device__ __forceinline__ void wmv_row(const double *W, const double *r, double
 
 template <int K, int P>
 __global__ void __launch_bounds__(kRowLanes) wmv_kernel(const double *__restrict__ W, const double *__restrict__ r,
-                                                        double *__restrict__ dx, int n, int k) {
+                                                        double *__restrict__ dx, int N, int n, int k) {
   __shared__ double sm[kRowLanes][K];
-  wmv_row<K, P>(W, r, dx, n, k, blockIdx.x, sm);
+  wmv_row<K, P>(W, r, dx, N, n, k, blockIdx.x, sm);
 }
 
 // dx (AoS [k][i]) -> SoA [P][K][n][d+1]; optionally x += dx and the norms

@@ -66,7 +66,7 @@ cudaError_t Impl<K, P>::eval0(const EvalDev &e, cudaStream_t s) {
     ProfScope prof(PK_SCAL, s);
     prep_scal_kernel<K, P><<<blocks_for(e.nscal, 64), 64, 0, s>>>(e.scal_src, e.nscal, e.coef, e.nmono, e.scal);
   }
-  const size_t Abytes = sizeof(double) * P * K * (size_t)(d + 1) * n * n;
+  const size_t Abytes = sizeof(double) * P * K * (size_t)(d + 1) * e.N * n;
   if ((err = cudaMemsetAsync(e.A, 0, Abytes, s)) != cudaSuccess) return err;
   // coefficient 0 of every product is the single product of the inputs' coefficients 0
   for (int st = 0; st < e.nstages; ++st) {
@@ -81,7 +81,7 @@ cudaError_t Impl<K, P>::eval0(const EvalDev &e, cudaStream_t s) {
     ProfScope prof(PK_ACCUM, s);
     accum_kernel<K, P><<<blocks_for(e.ngroups, 128), 128, 0, s>>>(reinterpret_cast<const int4 *>(e.groups), e.ngroups,
                                                                   reinterpret_cast<const int4 *>(e.contrib), e.pool,
-                                                                  e.scal, e.cst, e.f, e.A, n, d, 0, 1, 1);
+                                                                  e.scal, e.cst, e.f, e.A, e.N, n, d, 0, 1, 1);
   }
   return cudaGetLastError();
 }
@@ -104,7 +104,7 @@ cudaError_t Impl<K, P>::eval_rest(const EvalDev &e, cudaStream_t s) {
         (void)cudaGetLastError();
         smem = 0;
       }
-      conv_stage_resident_kernel<K, P><<<e.resident_ctas, kConvResidentThreads, smem, s>>>(e.tasks + 8LL * t0,
+      conv_stage_resident_kernel<K, P><<<e.resident_ctas, conv_resident_threads<K>(), smem, s>>>(e.tasks + 8LL * t0,
                                                                                            t1 - t0, e.pool, d);
     } else {
       conv_stage_kernel<K, P><<<blocks_for(t1 - t0, 64), 64, 0, s>>>(e.tasks + 8LL * t0, t1 - t0, e.pool, d);
@@ -120,7 +120,7 @@ cudaError_t Impl<K, P>::eval_rest(const EvalDev &e, cudaStream_t s) {
     ProfScope prof(PK_ACCUM, s);
     const long long work = (long long)e.ngroups * (d + 1);
     accum_sum_kernel<K, P><<<blocks_for(work, 128), 128, 0, s>>>(reinterpret_cast<const int4 *>(e.groups),
-                                                                 e.ngroups, e.prod, e.cst, e.f, e.A, n, d, 1);
+                                                                 e.ngroups, e.prod, e.cst, e.f, e.A, e.N, n, d, 1);
   }
   return cudaGetLastError();
 }
@@ -141,13 +141,12 @@ cudaError_t Impl<K, P>::solve(const SolveDev &v, cudaStream_t s) {
 
 template <int K, int P>
 cudaError_t Impl<K, P>::factor(const SolveDev &v, cudaStream_t s) {
-  const int n = v.n, d = v.d;
-  const long long nn = (long long)n * n;
+  const int n = v.n, N = v.N, d = v.d;
   {
     ProfScope prof(PK_QR_HOUSE, s);
-    solve_init_kernel<K, P><<<blocks_for(nn, 128), 128, 0, s>>>(v.A, v.M, v.Y, n, d);
+    solve_init_kernel<K, P><<<blocks_for((long long)N * N, 128), 128, 0, s>>>(v.A, v.M, v.Y, N, n, d);
   }
-  if (v.lu) {
+  if (v.lu) {  // N = n
     // LU with partial pivoting, L Z = P, then the shared back substitution
     for (int j = 0; j < n; ++j) {
       ProfScope prof(PK_LU, s);
@@ -168,35 +167,35 @@ cudaError_t Impl<K, P>::factor(const SolveDev &v, cudaStream_t s) {
   }
   {
     ProfScope prof(PK_QR_HOUSE, s);
-    house_kernel<K, P><<<1, kHouseThreads, 0, s>>>(v.M, v.vd, v.beta, v.status, n, 0);
+    house_kernel<K, P><<<1, kHouseThreads, 0, s>>>(v.M, v.vd, v.beta, v.status, N, 0);
   }
   for (int j = 0; j < n; ++j) {
     // H_j on every target, and the Householder vector of column j+1 (lookahead)
     ProfScope prof(PK_QR_APPLY, s);
-    const int rest = (n - j - 1) + n - (j + 1 < n ? 1 : 0);
+    const int rest = (n - j - 1) + N - (j + 1 < n ? 1 : 0);
     house_step_kernel<K, P><<<1 + (int)blocks_for((long long)rest * 32, kHouseThreads), kHouseThreads, 0, s>>>(
-        v.M, v.Y, v.vd, v.beta, v.status, n, j);
+        v.M, v.Y, v.vd, v.beta, v.status, N, n, j);
   }
   {
     ProfScope prof(PK_RINV, s);
-    rinv_kernel<K, P><<<blocks_for(n, 64), 64, 0, s>>>(v.M, v.rinv, n);
+    rinv_kernel<K, P><<<blocks_for(n, 64), 64, 0, s>>>(v.M, v.rinv, N, n);
   }
   for (int c = n - 1; c >= 0; --c) {
     ProfScope prof(PK_BACKSUB, s);
-    backsub_kernel<K, P><<<blocks_for((long long)(c + 1) * n, 64), 64, 0, s>>>(v.M, v.Y, v.W, v.rinv, n, c);
+    backsub_kernel<K, P><<<blocks_for((long long)(c + 1) * N, 64), 64, 0, s>>>(v.M, v.Y, v.W, v.rinv, N, c);
   }
   return cudaGetLastError();
 }
 
 template <int K, int P>
 cudaError_t Impl<K, P>::rcond(const SolveDev &v, cudaStream_t s) {
-  rcond_kernel<K, P><<<1, 256, 0, s>>>(v.A, v.W, v.rcond, v.n, v.d);
+  rcond_kernel<K, P><<<1, 256, 0, s>>>(v.A, v.W, v.rcond, v.N, v.n, v.d);
   return cudaGetLastError();
 }
 
 template <int K, int P>
 cudaError_t Impl<K, P>::degrees(const SolveDev &v, cudaStream_t s) {
-  const int n = v.n, d = v.d;
+  const int n = v.n, N = v.N, d = v.d;  // the split-product form needs N = n
   constexpr int S = oz_slices(K);
   __nv_bfloat16 *As = static_cast<__nv_bfloat16 *>(v.oz_As), *Xs = static_cast<__nv_bfloat16 *>(v.oz_Xs);
   if (v.ozaki && d >= 1) {
@@ -220,22 +219,22 @@ cudaError_t Impl<K, P>::degrees(const SolveDev &v, cudaStream_t s) {
                                                                                      v.sgn, v.r, n, d, k);
       }
       ProfScope prof(PK_WMV, s);
-      wmv_kernel<K, P><<<n, kRowLanes, 0, s>>>(v.W, v.r, v.dxw, n, k);
+      wmv_kernel<K, P><<<n, kRowLanes, 0, s>>>(v.W, v.r, v.dxw, n, n, k);
       continue;
     }
     int C, nchunk;
-    rhs_chunking(n, k, C, nchunk);
+    rhs_chunking(N, n, k, C, nchunk);
     if (nchunk > 0) {
       ProfScope prof(PK_RHS_PARTIAL, s);
-      rhs_partial_kernel<K, P><<<blocks_for((long long)n * nchunk, 64), 64, 0, s>>>(v.A, v.dxw, v.part, n, d, k, C,
-                                                                                    nchunk);
+      rhs_partial_kernel<K, P><<<blocks_for((long long)N * nchunk, 64), 64, 0, s>>>(v.A, v.dxw, v.part, N, n, d, k,
+                                                                                    C, nchunk);
     }
     {
       ProfScope prof(PK_RHS_FINISH, s);
-      rhs_finish_kernel<K, P><<<n, kRowLanes, 0, s>>>(v.b, v.sgn, v.part, v.r, n, d, k, nchunk);
+      rhs_finish_kernel<K, P><<<N, kRowLanes, 0, s>>>(v.b, v.sgn, v.part, v.r, N, d, k, nchunk);
     }
     ProfScope prof(PK_WMV, s);
-    wmv_kernel<K, P><<<n, kRowLanes, 0, s>>>(v.W, v.r, v.dxw, n, k);
+    wmv_kernel<K, P><<<n, kRowLanes, 0, s>>>(v.W, v.r, v.dxw, N, n, k);
   }
   const long long nx = (long long)n * (d + 1);
   ProfScope prof(PK_FINISH, s);

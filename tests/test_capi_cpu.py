@@ -159,3 +159,32 @@ def test_newton_run_host_checks(mdlib):
     assert mdlib.md_newton_series_run(ctypes.byref(c), 256, ctypes.byref(good), None, 256, wb - 1, 0, None) == 2
     assert mdlib.md_newton_series_run(ctypes.byref(c), 256, ctypes.byref(good), None, 257, wb, 0, None) == 2
     assert mdlib.md_newton_series_run(ctypes.byref(c), None, ctypes.byref(good), None, 256, wb, 0, None) == 1
+
+
+def test_lstsq_host_checks(mdlib):
+    """N > n: workspace sizes grow with N; shapes and flags are checked on the host."""
+    import paper_2012_06607_gb300 as md
+
+    K, n, d = 4, 8, 6
+    sq = mdlib.md_lstsq_workspace_bytes(K, 1, n, n, d, 0)
+    assert sq == mdlib.md_linsolve_workspace_bytes(K, 1, n, d, 0) > 0
+    assert mdlib.md_lstsq_workspace_bytes(K, 1, n + 5, n, d, 0) > sq
+    assert mdlib.md_lstsq_workspace_bytes(K, 1, n - 1, n, d, 0) == 0          # N < n
+    assert mdlib.md_lstsq_workspace_bytes(K, 1, n + 1, n, d, md.FLAG_LU) == 0  # LU needs N = n
+    assert mdlib.md_lstsq_workspace_bytes(K, 1, n + 1, n, d, md.FLAG_OZAKI) == 0
+    assert mdlib.md_lstsq_series(K, 1, n - 1, n, d, 256, 256, 256, 256, 1 << 30, 0, None) == 1
+    assert mdlib.md_lstsq_series(K, 1, n + 1, n, d, 256, 256, 256, 256, 1 << 30, md.FLAG_LU, None) == 1
+    assert mdlib.md_lstsq_series(K, 1, n + 1, n, d, 256, 256, 256, 256, 1 << 30, md.FLAG_OZAKI, None) == 8
+    # systems: neq rows
+    s = mdgen.config_system(0, seed=1)
+    sa = s.augmented([0, 1], [2.0, 0.5])
+    c, keep = _csys(s)
+    ca, keepa = _csys(sa)
+    ca.neq = sa.N
+    assert mdlib.md_workspace_bytes(ctypes.byref(ca), 0) > mdlib.md_workspace_bytes(ctypes.byref(c), 0)
+    assert mdlib.md_workspace_bytes(ctypes.byref(ca), md.FLAG_LU) == 0
+    ca.neq = s.n - 1  # fewer equations than unknowns
+    assert mdlib.md_workspace_bytes(ctypes.byref(ca), 0) == 0
+    ca.neq = sa.N
+    arr = (md.md_system * 1)(ca)
+    assert mdlib.md_batched_workspace_bytes(1, arr, 0) == 0  # the batched form is square only

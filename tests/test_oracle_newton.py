@@ -368,3 +368,78 @@ def test_rcond_within_norm_equivalence_of_cond2(orc):
     for method in (0, 1):
         rc = orc.rcond(K, False, A, method)
         assert 1e-8 / n / 1.001 <= rc <= n * 1e-8 * 1.001, (method, rc)
+
+
+# ------------------------------------------------------- least squares N > n
+@pytest.mark.parametrize("seed,n,N,d,K", [(1, 2, 3, 3, 2), (2, 2, 4, 2, 3), (3, 3, 5, 2, 2)])
+def test_lstsq_step_exact_brute_force(orc, seed, n, N, d, K):
+    """Whole step of an overdetermined system (N > n, Section 4: least squares)
+    against exact rationals: naive AD and each degree's normal equations."""
+    s = mdgen.random_system(seed, n=n, K=K, cplx=True, d=d, monos=3, maxvars=2, maxdeg=3, neq=N)
+    assert s.N == N
+    rng = np.random.default_rng(seed)
+    x = s.x0.copy()
+    x[:, 0, :, 1:] = rng.uniform(-0.5, 0.5, size=x[:, 0, :, 1:].shape)
+    xn, _ = orc.newton_step(s, x)
+    xe, dxe, fe, Ae = exact.newton_step_exact(s, x)
+    f, A = orc.eval_diff(s, x)
+    assert f.shape[2] == N and A.shape[3:] == (n, N)
+    for i in range(N):
+        for k in range(d + 1):
+            a, b = val(f, i, k), fe[i][k]
+            sc = 1 + abs(b[0]) + abs(b[1])
+            assert abs(a[0] - b[0]) <= 5e4 * eps(K) * sc and abs(a[1] - b[1]) <= 5e4 * eps(K) * sc
+    for j in range(n):
+        for k in range(d + 1):
+            a, b = val(xn, j, k), xe[j][k]
+            sc = 1 + abs(b[0]) + abs(b[1])
+            assert abs(a[0] - b[0]) <= 1e5 * eps(K) * sc, (j, k, float(a[0] - b[0]))
+            assert abs(a[1] - b[1]) <= 1e5 * eps(K) * sc
+
+
+def test_lstsq_consistent_rows_give_the_square_solution(orc):
+    """Appending scaled copies of equations keeps the system consistent: its
+    least squares Newton iterates are those of the square system."""
+    s = mdgen.config_system(0, 2)
+    sa = s.augmented([0, 2, 1], [2.0, -0.5, 4.0])
+    assert sa.N == s.n + 3
+    x1, n1 = orc.newton(s, 4)
+    x2, n2 = orc.newton(sa, 4)
+    for j in range(s.n):
+        for k in range(s.degree + 1):
+            a, b = val(x2, j, k), val(x1, j, k)
+            sc = 1 + abs(b[0]) + abs(b[1])
+            assert abs(a[0] - b[0]) <= 1e3 * eps(2) * sc and abs(a[1] - b[1]) <= 1e3 * eps(2) * sc
+
+
+def test_lstsq_linsolve_exact(orc):
+    """Block least squares solve (N = 5, n = 3, d = 3) against the exact
+    per-degree normal equations."""
+    K, N, n, d = 3, 5, 3, 3
+    rng = np.random.default_rng(17)
+    A = np.zeros((2, K, d + 1, n, N))
+    b = np.zeros((2, K, N, d + 1))
+    A[:, 0] = rng.standard_normal((2, d + 1, n, N))
+    b[:, 0] = rng.standard_normal((2, N, d + 1))
+    dx = orc.linsolve(K, True, A, b)
+    assert dx.shape == (2, K, n, d + 1)
+    dxe = exact.block_lstsq(exact.mat_series_exact(A), exact.vec_series_exact(b))
+    for k in range(d + 1):
+        for j in range(n):
+            a, w = val(dx, j, k), dxe[k][j]
+            sc = 1 + abs(w[0]) + abs(w[1])
+            assert abs(a[0] - w[0]) <= 1e4 * eps(K) * sc and abs(a[1] - w[1]) <= 1e4 * eps(K) * sc, (k, j)
+
+
+def test_lstsq_rcond_of_stacked_diagonal(orc):
+    """A_0 = [D; 0] (N x n): A_0^+ = [D^-1 0], rcond = min |d_i| / max |d_i|."""
+    K = 2
+    rows = [[4, 0], [0, -0.5], [0, 0], [0, 0]]
+    n, N = 2, 4
+    A = np.zeros((1, K, 1, n, N))
+    for r in range(N):
+        for c in range(n):
+            A[0, 0, 0, c, r] = rows[r][c]
+    assert orc.rcond(K, False, A) == 0.125
+    with pytest.raises(RuntimeError):  # LU needs a square A_0
+        orc.rcond(K, False, A, method=1)
