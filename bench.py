@@ -333,6 +333,32 @@ def run_product(args):
     line["e2e"] = {"value": world * args.steps / (e_total / 1e3), "unit": "steps/s",
                    "h2d_bytes_per_step": int(xh.numel() * 8), "d2h_bytes_per_step": int(outh.numel() * 8 + 16)}
 
+    # the other update form on the same GPU, same workload and timing (context,
+    # not the headline): the split-product update against md arithmetic
+    if args.update == "md" and not args.no_other_form:
+        oflags = md.FLAG_OZAKI
+        ows = md.workspace(sysd.workspace_bytes(oflags), device=dev)
+        xo = md.to_device(s.x0, dev)
+        for _ in range(args.warmup):
+            md.newton_step(sysd, xo, ows, nrm, flags=oflags)
+        torch.cuda.synchronize(dev)
+        o_ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            md.newton_step(sysd, xo, ows, nrm, flags=oflags)
+            b.record(stream)
+            o_ms.append((a, b))
+        torch.cuda.synchronize(dev)
+        assert md.device_status(ows) == 0
+        o_total = reduce_max(dist, sum(a.elapsed_time(b) for a, b in o_ms))
+        line["other_forms"] = {"split_product_update": {
+            "value": world * args.steps / (o_total / 1e3), "unit": "steps/s", "ms_per_step": o_total / args.steps,
+            "speedup_vs_md": total_ms / o_total}}
+        del ows, xo
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, dt = oracle_steps_per_s(s, 1, 0)
         line["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
@@ -399,7 +425,7 @@ def run_solve3(args):
                 e.append(diff / scale)
             err[name] = max(e)
     upd = {name: sum(v for k, v in res[name]["kernel_ms_per_solve"].items()
-                     if k in ("rhs_partial", "rhs_finish", "oz_split", "oz_gemm", "oz_accum")) for name in res}
+                     if k in ("rhs_partial", "rhs_finish", "oz_split", "oz_update")) for name in res}
     line = {"metric": "linearized block Toeplitz solves/s (qd real, n=256, d=16, cond(A_0)=1e8)",
             "unit": "solves/s", "form": "plain vs split-product",
             "value_plain": 1e3 / res["plain"]["ms_per_solve"], "value_ozaki": 1e3 / res["ozaki"]["ms_per_solve"],
@@ -548,6 +574,7 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--impl", default="product", choices=["product", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-form", action="store_true", help="skip timing the split-product update beside md")
     ap.add_argument("--form", default="plain", choices=["plain", "solve3", "batched", "ladder"],
                     help="plain: the Newton-step benchmark; solve3: plain vs split-product solve; "
                          "batched: 2048-system batched step vs a per-system loop; ladder: the headline step at every precision")

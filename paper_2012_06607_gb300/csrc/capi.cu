@@ -79,7 +79,7 @@ cudaError_t dispatch(int K, int P, int what, const void *a, cudaStream_t s, int 
 // ---------------------------------------------------------- solve layout
 struct SolveLayout {
   size_t off_M, off_Y, off_W, off_vd, off_beta, off_rinv, off_r, off_dxw, off_part, bytes;
-  size_t off_As = 0, off_Xs = 0, off_eA = 0, off_ex = 0, off_C = 0;
+  size_t off_As = 0, off_Xs = 0, off_eA = 0, off_ex = 0;
   int maxchunk;
   int ozaki = 0;
 };
@@ -111,13 +111,12 @@ SolveLayout solve_layout(int K, int P, int N, int n, int d, size_t base, int fla
   L.off_dxw = o; o = align256(o + (size_t)(d + 1) * n * VS);
   L.off_part = o; o = align256(o + (size_t)N * maxchunk * VS);
   if (flags & MD_FLAG_OZAKI) {
-    const size_t S = oz_slices_host(K), kp = oz_kpad_host(n), M = (size_t)n * P * S, N = (size_t)P * S;
+    const size_t S = oz_slices_host(K), kp = oz_kpad_host(n), MA = (size_t)n * P * S, NX = (size_t)P * S;
     L.ozaki = 1;
-    L.off_As = o; o = align256(o + (size_t)(d + 1) * M * kp * 2);
-    L.off_Xs = o; o = align256(o + (size_t)(d + 1) * N * kp * 2);
+    L.off_As = o; o = align256(o + (size_t)(d + 1) * MA * kp * 2);
+    L.off_Xs = o; o = align256(o + (size_t)(d + 1) * NX * kp * 2);
     L.off_eA = o; o = align256(o + sizeof(int) * (size_t)(d + 1) * n);
     L.off_ex = o; o = align256(o + sizeof(int) * (size_t)(d + 1));
-    L.off_C = o; o = align256(o + sizeof(float) * (size_t)std::max(d, 1) * M * N);
   }
   L.bytes = o - base;
   return L;
@@ -724,7 +723,6 @@ SolveDev make_solve(const SolveLayout &L, int N, int n, int d, char *base) {
     v.oz_Xs = base + L.off_Xs;
     v.oz_eA = reinterpret_cast<int *>(base + L.off_eA);
     v.oz_ex = reinterpret_cast<int *>(base + L.off_ex);
-    v.oz_C = reinterpret_cast<float *>(base + L.off_C);
   }
   return v;
 }
@@ -805,7 +803,7 @@ void prof_end(int id, cudaStream_t s) {
 namespace {
 const char *kProfNames[mdk::PK_COUNT] = {"pool_load_x", "prep_scal", "conv_stage", "accum", "qr_house", "qr_apply",
                                          "rinv", "backsub", "rhs_partial", "rhs_finish", "wmv", "finish_dx",
-                                         "elementwise", "series_conv", "oz_split", "oz_gemm", "oz_accum", "lu"};
+                                         "elementwise", "series_conv", "oz_split", "oz_update", "lu"};
 
 md_status check_schedule(const md_system *s, const md_newton_schedule *sc) {
   if (!sc || sc->nlevels < 1 || sc->nlevels > MD_MAX_LEVELS) return MD_ERR_ARG;

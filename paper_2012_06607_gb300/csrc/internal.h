@@ -11,8 +11,8 @@ enum : int { ST_SINGULAR = 1, ST_NONFINITE = 2 };
 // Kernel classes for the optional per-launch timing (md_profile_*).
 enum ProfKind : int {
   PK_POOL = 0, PK_SCAL, PK_CONV, PK_ACCUM, PK_QR_HOUSE, PK_QR_APPLY, PK_RINV, PK_BACKSUB,
-  PK_RHS_PARTIAL, PK_RHS_FINISH, PK_WMV, PK_FINISH, PK_ELEMENTWISE, PK_SERIES, PK_OZ_SPLIT, PK_OZ_GEMM,
-  PK_OZ_ACCUM, PK_LU, PK_COUNT
+  PK_RHS_PARTIAL, PK_RHS_FINISH, PK_WMV, PK_FINISH, PK_ELEMENTWISE, PK_SERIES, PK_OZ_SPLIT, PK_OZ_UPDATE,
+  PK_LU, PK_COUNT
 };
 bool prof_enabled();
 int prof_begin(int kind, cudaStream_t s);
@@ -76,7 +76,6 @@ struct SolveDev {
   int ozaki = 0;
   void *oz_As = nullptr, *oz_Xs = nullptr;  // bf16 slices
   int *oz_eA = nullptr, *oz_ex = nullptr;
-  float *oz_C = nullptr;
 };
 
 // Terms j*n + col (j < k) of one of the N rows of r_k, cut into nchunk

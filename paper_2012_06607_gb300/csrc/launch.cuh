@@ -196,8 +196,14 @@ cudaError_t Impl<K, P>::rcond(const SolveDev &v, cudaStream_t s) {
 template <int K, int P>
 cudaError_t Impl<K, P>::degrees(const SolveDev &v, cudaStream_t s) {
   const int n = v.n, N = v.N, d = v.d;  // the split-product form needs N = n
-  constexpr int S = oz_slices(K);
   __nv_bfloat16 *As = static_cast<__nv_bfloat16 *>(v.oz_As), *Xs = static_cast<__nv_bfloat16 *>(v.oz_Xs);
+  constexpr int oz_smem = oz_update_smem(K);
+  static_assert(oz_smem <= 200 * 1024, "staged slices exceed the shared memory of an SM");
+  if (v.ozaki) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(oz_update_kernel<K, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, oz_smem);
+    if (e != cudaSuccess) return e;
+  }
   if (v.ozaki && d >= 1) {
     ProfScope prof(PK_OZ_SPLIT, s);
     oz_split_rows_kernel<K, P><<<blocks_for((long long)d * n * 32, 128), 128, 0, s>>>(v.A, As, v.oz_eA, n, d);
@@ -205,18 +211,13 @@ cudaError_t Impl<K, P>::degrees(const SolveDev &v, cudaStream_t s) {
   for (int k = 0; k <= d; ++k) {
     if (v.ozaki) {
       if (k >= 1) {
-        {
-          ProfScope prof(PK_OZ_SPLIT, s);
-          oz_split_vec_kernel<K, P><<<1, 128, 0, s>>>(v.dxw, Xs, v.oz_ex, n, k - 1);
-        }
-        ProfScope prof(PK_OZ_GEMM, s);
-        const long long tiles = (long long)k * (n * P * S / 16) * (P * S / 8);
-        oz_gemm_kernel<S, P><<<blocks_for(tiles * 32, 128), 128, 0, s>>>(As, Xs, v.oz_C, n, k);
+        ProfScope prof(PK_OZ_SPLIT, s);
+        oz_split_vec_kernel<K, P><<<1, 128, 0, s>>>(v.dxw, Xs, v.oz_ex, n, k - 1);
       }
       {
-        ProfScope prof(PK_OZ_ACCUM, s);
-        oz_accum_kernel<K, P><<<blocks_for((long long)n * P * 32, 128), 128, 0, s>>>(v.oz_C, v.oz_eA, v.oz_ex, v.b,
-                                                                                     v.sgn, v.r, n, d, k);
+        ProfScope prof(PK_OZ_UPDATE, s);
+        oz_update_kernel<K, P><<<n * P, kOzWarps * 32, oz_smem, s>>>(As, Xs, v.oz_eA, v.oz_ex, v.b, v.sgn, v.r, n, d,
+                                                                 k);
       }
       ProfScope prof(PK_WMV, s);
       wmv_kernel<K, P><<<n, kRowLanes, 0, s>>>(v.W, v.r, v.dxw, n, n, k);

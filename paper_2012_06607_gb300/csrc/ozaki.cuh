@@ -8,11 +8,11 @@
 // below 2^(e - 8S), i.e. 2^-8S relative to the largest entry.  Products of
 // slices are integers below 2^14; K <= 1024 of them sum below 2^24, so the
 // tensor core's fp32 accumulation of a BF16 mma is exact.  For each pair
-// (block A_{k-j}, vector dx_j) one GEMM gives C[row, s][t] = sum_col A_s x_t for
-// all slice pairs at once (M = n P S, N = P S, K = n).  The terms of r_k -- the
-// C values with their power-of-two weights and the limbs of b_k -- are then
-// added exactly into a fixed-point integer (int64 digits of 32 bits in shared
-// memory) and converted to K limbs once.  The only rounding is the slicing
+// (row of block A_{k-j}, vector dx_j) the S x S slice products
+// C[s][t] = sum_col A_s x_t (K = n) are formed on the tensor pipe inside the
+// update kernel.  The terms of r_k -- the C values with their power-of-two
+// weights and the limbs of b_k -- are added exactly into a fixed-point integer
+// (int64 digits of 32 bits in shared memory) and converted to K limbs once.  The only rounding is the slicing
 // (normwise 2^(12 - 8S) relative to the largest term) and the final K-limb
 // truncation; the plain path rounds at every md multiply-add.
 #pragma once
@@ -268,137 +268,145 @@ __global__ void oz_split_vec_kernel(const double *__restrict__ dxw, __nv_bfloat1
   }
 }
 
-// C[j][m][nn] = sum_c As_{k-j}[m][c] * Xs_j[nn][c]  for j < k (exact fp32).
-// One warp per 16 x 8 tile; grid covers (j, m tiles, n tiles).
 __device__ __forceinline__ unsigned oz_pack(const __nv_bfloat16 *p) {
   return *reinterpret_cast<const unsigned *>(p);
 }
 
-template <int S, int P>
-__global__ void oz_gemm_kernel(const __nv_bfloat16 *__restrict__ As, const __nv_bfloat16 *__restrict__ Xs,
-                               float *__restrict__ C, int n, int k) {
-  const int M = n * P * S, N = P * S, kp = oz_kpad(n);
-  const int mt = M / 16, nt = N / 8;
-  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= (long long)k * mt * nt) return;
-  const int j = (int)(warp / ((long long)mt * nt));
-  const int rem = (int)(warp % ((long long)mt * nt));
-  const int tm = rem / nt, tn = rem % nt;
-  const int i = k - j;
-  const __nv_bfloat16 *Ab = As + ((long long)i * M + tm * 16) * kp;
-  const __nv_bfloat16 *Bb = Xs + ((long long)j * N + tn * 8) * kp;
-  const int g = lane >> 2, t = lane & 3;
-  float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
-  for (int k0 = 0; k0 < kp; k0 += 16) {
-    const unsigned a0 = oz_pack(Ab + (long long)g * kp + k0 + 2 * t);
-    const unsigned a1 = oz_pack(Ab + (long long)(g + 8) * kp + k0 + 2 * t);
-    const unsigned a2 = oz_pack(Ab + (long long)g * kp + k0 + 2 * t + 8);
-    const unsigned a3 = oz_pack(Ab + (long long)(g + 8) * kp + k0 + 2 * t + 8);
-    const unsigned b0 = oz_pack(Bb + (long long)g * kp + k0 + 2 * t);
-    const unsigned b1 = oz_pack(Bb + (long long)g * kp + k0 + 2 * t + 8);
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(c0), "+f"(c1), "+f"(c2), "+f"(c3)
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-  }
-  float *Cb = C + ((long long)j * M + tm * 16) * N + tn * 8;
-  Cb[(long long)g * N + 2 * t] = c0;
-  Cb[(long long)g * N + 2 * t + 1] = c1;
-  Cb[(long long)(g + 8) * N + 2 * t] = c2;
-  Cb[(long long)(g + 8) * N + 2 * t + 1] = c3;
+// The update of one degree k on the tensor pipe; no slice product leaves the
+// SM.  One CTA of kOzWarps warps per (row, plane q); warp w takes
+// j = w, w + kOzWarps, ... < k.  For each j and each plane pair (pa, px) of the
+// complex product the warp stages the slices of (row of A_{k-j}, plane pa) and
+// of (dx_j, plane px) in shared memory, 64 columns at a time (rows padded to 72
+// bf16 so that fragment loads hit 32 distinct banks), forms the S x S slice
+// products with m16n8k16 BF16 mma (exact in fp32: at most 64 terms of < 2^14
+// per chunk), sums them by level L = s + t into shared int32 bins (at most
+// S * kpad terms of < 2^14: below 2^31 for kpad <= 1024), and adds each nonzero
+// level, weighted 2^(eA + ex - 8(L+2)), into the CTA's fixed-point
+// accumulator.  Integer additions are exact in any order, so neither the split
+// over warps nor the chunking changes the result: the exact sum of the terms,
+// rounded once to K limbs.
+constexpr int kOzWarps = 8;
+constexpr int kOzChunk = 64;             // columns staged per step
+constexpr int kOzPitch = kOzChunk + 8;   // bf16 per staged row
+
+__host__ __device__ constexpr int oz_update_smem(int K) {
+  return kOzWarps * 2 * oz_slices(K) * kOzPitch * 2;  // bytes: A and X slices per warp
 }
 
-// r_k[row] (plane q) = sgn b_k[row] - sum_{j<k} A_{k-j}[row,:] dx_j, exactly into a
-// fixed-point accumulator, then to K limbs.  One warp per (row, q).
 template <int K, int P>
-__global__ void __launch_bounds__(128) oz_accum_kernel(const float *__restrict__ C, const int *__restrict__ eA,
-                                                       const int *__restrict__ ex, const double *__restrict__ b,
-                                                       double sgn, double *__restrict__ r, int n, int d, int k) {
+__global__ void __launch_bounds__(kOzWarps * 32) oz_update_kernel(const __nv_bfloat16 *__restrict__ As,
+                                                                  const __nv_bfloat16 *__restrict__ Xs,
+                                                                  const int *__restrict__ eA,
+                                                                  const int *__restrict__ ex,
+                                                                  const double *__restrict__ b, double sgn,
+                                                                  double *__restrict__ r, int n, int d, int k) {
   constexpr int S = oz_slices(K), W = oz_digits(K);
-  __shared__ long long acc[4][W];
-  __shared__ int s_top[4];
+  extern __shared__ __align__(16) unsigned char oz_smem[];
+  __shared__ long long acc[W];
+  __shared__ int bins[kOzWarps][2 * S];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int warp = blockIdx.x * 4 + wib;
-  const bool active = warp < n * P;
-  const int row = active ? warp / P : 0, q = active ? warp % P : 0;
-  const int M = n * P * S, N = P * S;
+  __nv_bfloat16 *sA = reinterpret_cast<__nv_bfloat16 *>(oz_smem) + (long long)wib * 2 * S * kOzPitch;
+  __nv_bfloat16 *sX = sA + S * kOzPitch;
+  const int row = blockIdx.x / P, q = blockIdx.x % P;
+  const int kp = oz_kpad(n);
+  const int g = lane >> 2, t4 = lane & 3;
+  for (int i = threadIdx.x; i < W; i += blockDim.x) acc[i] = 0;
+  for (int i = lane; i < 2 * S; i += 32) bins[wib][i] = 0;
   // top of the accumulator: 64 bits above the largest term and above b_k
   int etop = -4000;
-  if (active) {
-    for (int j = lane; j < k; j += 32) etop = max(etop, eA[(k - j) * n + row] + ex[j]);
-  }
+  for (int j = lane; j < k; j += 32) etop = max(etop, eA[(k - j) * n + row] + ex[j]);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) etop = max(etop, __shfl_xor_sync(0xffffffffu, etop, off));
   double bl[K];
-  if (active) {
 #pragma unroll
-    for (int l = 0; l < K; ++l) bl[l] = b[((long long)(q * K + l) * n + row) * (d + 1) + k];
-    etop = max(etop, oz_exp_bound(bl[0]));
-  }
+  for (int l = 0; l < K; ++l) bl[l] = b[((long long)(q * K + l) * n + row) * (d + 1) + k];
+  etop = max(etop, oz_exp_bound(bl[0]));
   const int top = etop + 64;
-  for (int w = lane; w < W; w += 32) acc[wib][w] = 0;
-  __syncwarp();
-  if (active) {
-    // products: C-values of slice pair (s, t) have weight 2^(eA + ex - 8(s+1) - 8(t+1))
-    // real part: (re,re) - (im,im); imaginary part: (re,im) + (im,re)
-    const int npairs = (P == 2) ? 2 : 1;
-    for (int j = 0; j < k; ++j) {
-      const int base = eA[(k - j) * n + row] + ex[j];
-      for (int pr = 0; pr < npairs; ++pr) {
-        int pa, px, sg;
-        if (P == 1) {
-          pa = 0; px = 0; sg = 1;
-        } else if (q == 0) {
-          pa = pr; px = pr; sg = pr == 0 ? 1 : -1;
-        } else {
-          pa = pr; px = 1 - pr; sg = 1;
+  __syncthreads();
+  const int npairs = (P == 2) ? 2 : 1;
+  for (int j = wib; j < k; j += kOzWarps) {
+    const int base = eA[(k - j) * n + row] + ex[j];
+    for (int pr = 0; pr < npairs; ++pr) {
+      int pa, px, sg;
+      if (P == 1) {
+        pa = 0; px = 0; sg = 1;
+      } else if (q == 0) {  // real part: (re, re) - (im, im)
+        pa = pr; px = pr; sg = pr == 0 ? 1 : -1;
+      } else {  // imaginary part: (re, im) + (im, re)
+        pa = pr; px = 1 - pr; sg = 1;
+      }
+      const __nv_bfloat16 *Ab = As + ((((long long)(k - j) * n + row) * P + pa) * S) * kp;
+      const __nv_bfloat16 *Bb = Xs + (((long long)j * P + px) * S) * kp;
+      for (int c0 = 0; c0 < kp; c0 += kOzChunk) {
+        const int cw = min(kOzChunk, kp - c0);  // a multiple of 16
+        // stage S rows x cw columns of both operands (16-byte pieces)
+        const int pieces = cw / 8;
+        for (int e = lane; e < S * pieces; e += 32) {
+          const int rr = e / pieces, cc = (e % pieces) * 8;
+          *reinterpret_cast<uint4 *>(sA + rr * kOzPitch + cc) =
+              *reinterpret_cast<const uint4 *>(Ab + (long long)rr * kp + c0 + cc);
+          *reinterpret_cast<uint4 *>(sX + rr * kOzPitch + cc) =
+              *reinterpret_cast<const uint4 *>(Bb + (long long)rr * kp + c0 + cc);
         }
-        const float *Crow = C + ((long long)j * M + ((long long)row * P + pa) * S) * N + px * S;
-        // level sums over s + t = L, then one exact add per level
-        for (int L = lane; L <= 2 * S - 2; L += 32) {
-          long long lv = 0;
-          const int s0 = max(0, L - (S - 1)), s1 = min(S - 1, L);
-          for (int s = s0; s <= s1; ++s) lv += (long long)Crow[(long long)s * N + (L - s)];
-          if (lv == 0) continue;
-          // lv * 2^(base - 8(L+2)) subtracted (sg * -1 for r = b - sum)
-          const int lsb_below = top - (base - 8 * (L + 2));
-          const bool neg = (lv < 0) != (sg < 0);  // sign of the term before the minus
-          unsigned long long mag = (unsigned long long)(lv < 0 ? -lv : lv);
-          // place mag (< 2^40) in 32-bit chunks
-          for (int piece = 0; piece < 2 && mag; ++piece) {
-            const unsigned long long chunk = mag & 0xffffffffULL;
-            mag >>= 32;
-            const int lb = lsb_below - 32 * piece;
-            if (lb <= 0) continue;
-            int qd = (lb + 31) / 32 - 1;
-            unsigned long long v;
-            if (qd >= W) {
-              const int drop = lb - 32 * W;
-              if (drop >= 64) continue;
-              v = chunk >> drop;
-              qd = W - 1;
-              const long long sv = (long long)v;
-              atomicAdd((unsigned long long *)&acc[wib][qd], (unsigned long long)(neg ? sv : -sv));
-              continue;
+        __syncwarp();
+        for (int mt = 0; mt < S / 16; ++mt) {
+          for (int nt = 0; nt < S / 8; ++nt) {
+            float c0f = 0.f, c1f = 0.f, c2f = 0.f, c3f = 0.f;
+            const __nv_bfloat16 *Am = sA + (mt * 16) * kOzPitch, *Bn = sX + (nt * 8) * kOzPitch;
+            for (int k0 = 0; k0 < cw; k0 += 16) {
+              const unsigned a0 = oz_pack(Am + g * kOzPitch + k0 + 2 * t4);
+              const unsigned a1 = oz_pack(Am + (g + 8) * kOzPitch + k0 + 2 * t4);
+              const unsigned a2 = oz_pack(Am + g * kOzPitch + k0 + 2 * t4 + 8);
+              const unsigned a3 = oz_pack(Am + (g + 8) * kOzPitch + k0 + 2 * t4 + 8);
+              const unsigned b0 = oz_pack(Bn + g * kOzPitch + k0 + 2 * t4);
+              const unsigned b1 = oz_pack(Bn + g * kOzPitch + k0 + 2 * t4 + 8);
+              asm volatile(
+                  "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                  "{%0,%1,%2,%3};"
+                  : "+f"(c0f), "+f"(c1f), "+f"(c2f), "+f"(c3f)
+                  : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
             }
-            const int rr = 32 * (qd + 1) - lb;
-            v = chunk << rr;
-            const long long lo = (long long)(v & 0xffffffffULL), hi = (long long)(v >> 32);
-            // r = b - term: add -term
-            atomicAdd((unsigned long long *)&acc[wib][qd], (unsigned long long)(neg ? lo : -lo));
-            if (qd > 0) atomicAdd((unsigned long long *)&acc[wib][qd - 1], (unsigned long long)(neg ? hi : -hi));
+            // (s, t) of the four values: (16 mt + g, 8 nt + 2 t4) and neighbours
+            const int L = mt * 16 + g + nt * 8 + 2 * t4;
+            if (c0f != 0.f) atomicAdd(&bins[wib][L], __float2int_rn(c0f));
+            if (c1f != 0.f) atomicAdd(&bins[wib][L + 1], __float2int_rn(c1f));
+            if (c2f != 0.f) atomicAdd(&bins[wib][L + 8], __float2int_rn(c2f));
+            if (c3f != 0.f) atomicAdd(&bins[wib][L + 9], __float2int_rn(c3f));
           }
         }
+        __syncwarp();
       }
+      for (int Lv = lane; Lv <= 2 * S - 2; Lv += 32) {
+        const long long lv = bins[wib][Lv];
+        bins[wib][Lv] = 0;
+        if (lv == 0) continue;
+        // r = b - term: the term lv 2^(base - 8(Lv+2)) enters with sign -sg
+        const int lsb_below = top - (base - 8 * (Lv + 2));
+        const bool neg = (lv < 0) != (sg < 0);
+        const unsigned long long mag = (unsigned long long)(lv < 0 ? -lv : lv);  // < 2^31
+        if (lsb_below <= 0) continue;
+        int qd = (lsb_below + 31) / 32 - 1;
+        if (qd >= W) {
+          const int drop = lsb_below - 32 * W;
+          if (drop >= 64) continue;
+          const long long sv = (long long)(mag >> drop);
+          atomicAdd((unsigned long long *)&acc[W - 1], (unsigned long long)(neg ? sv : -sv));
+          continue;
+        }
+        const int rr = 32 * (qd + 1) - lsb_below;
+        const unsigned long long v = mag << rr;
+        const long long lo = (long long)(v & 0xffffffffULL), hi = (long long)(v >> 32);
+        atomicAdd((unsigned long long *)&acc[qd], (unsigned long long)(neg ? lo : -lo));
+        if (qd > 0) atomicAdd((unsigned long long *)&acc[qd - 1], (unsigned long long)(neg ? hi : -hi));
+      }
+      __syncwarp();
     }
   }
-  __syncwarp();
-  if (active && lane == 0) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
     oz_fix<W> a;
 #pragma unroll
-    for (int w = 0; w < W; ++w) a.d[w] = acc[wib][w];
+    for (int w = 0; w < W; ++w) a.d[w] = acc[w];
 #pragma unroll
     for (int l = 0; l < K; ++l) oz_add_double<W>(a, top, bl[l], sgn < 0.0 ? -1 : 1);
     double z[K];
@@ -407,7 +415,6 @@ __global__ void __launch_bounds__(128) oz_accum_kernel(const float *__restrict__
 #pragma unroll
     for (int l = 0; l < K; ++l) r[((long long)k * n + row) * VS + q * K + l] = z[l];
   }
-  (void)s_top;
 }
 
 }  // namespace mdk
