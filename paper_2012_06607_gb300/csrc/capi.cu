@@ -79,7 +79,7 @@ cudaError_t dispatch(int K, int P, int what, const void *a, cudaStream_t s, int 
 // ---------------------------------------------------------- solve layout
 struct SolveLayout {
   size_t off_M, off_Y, off_W, off_vd, off_beta, off_rinv, off_r, off_dxw, off_part, bytes;
-  size_t off_As = 0, off_Xs = 0, off_eA = 0, off_ex = 0;
+  size_t off_As = 0, off_Xs = 0, off_eA = 0, off_ex = 0, off_acc = 0;
   int maxchunk;
   int ozaki = 0;
 };
@@ -117,6 +117,8 @@ SolveLayout solve_layout(int K, int P, int N, int n, int d, size_t base, int fla
     L.off_Xs = o; o = align256(o + (size_t)(d + 1) * NX * kp * 2);
     L.off_eA = o; o = align256(o + sizeof(int) * (size_t)(d + 1) * n);
     L.off_ex = o; o = align256(o + sizeof(int) * (size_t)(d + 1));
+    const size_t W = (53 * K + 24 + 128 + 31) / 32 + 1;  // digits per output, as oz_digits
+    L.off_acc = o; o = align256(o + sizeof(unsigned long long) * (size_t)n * P * W);
   }
   L.bytes = o - base;
   return L;
@@ -723,6 +725,7 @@ SolveDev make_solve(const SolveLayout &L, int N, int n, int d, char *base) {
     v.oz_Xs = base + L.off_Xs;
     v.oz_eA = reinterpret_cast<int *>(base + L.off_eA);
     v.oz_ex = reinterpret_cast<int *>(base + L.off_ex);
+    v.oz_acc = reinterpret_cast<unsigned long long *>(base + L.off_acc);
   }
   return v;
 }

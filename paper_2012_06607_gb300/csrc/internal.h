@@ -76,6 +76,7 @@ struct SolveDev {
   int ozaki = 0;
   void *oz_As = nullptr, *oz_Xs = nullptr;  // bf16 slices
   int *oz_eA = nullptr, *oz_ex = nullptr;
+  unsigned long long *oz_acc = nullptr;     // fixed-point accumulators, n P outputs
 };
 
 // Terms j*n + col (j < k) of one of the N rows of r_k, cut into nchunk

@@ -2,6 +2,8 @@
 #pragma once
 #include "internal.h"
 #include "kernels.cuh"
+#include <algorithm>
+
 #include "ozaki.cuh"
 #include "batched.cuh"
 
@@ -198,10 +200,11 @@ cudaError_t Impl<K, P>::degrees(const SolveDev &v, cudaStream_t s) {
   const int n = v.n, N = v.N, d = v.d;  // the split-product form needs N = n
   __nv_bfloat16 *As = static_cast<__nv_bfloat16 *>(v.oz_As), *Xs = static_cast<__nv_bfloat16 *>(v.oz_Xs);
   constexpr int oz_smem = oz_update_smem(K);
-  static_assert(oz_smem <= 200 * 1024, "staged slices exceed the shared memory of an SM");
+  static_assert(oz_smem <= kOzSmemBudget, "staged slices exceed the shared memory of an SM");
   if (v.ozaki) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(oz_update_kernel<K, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, oz_smem);
+    cudaError_t e = cudaFuncSetAttribute(oz_update_kernel<K, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, oz_smem);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(v.oz_acc, 0, sizeof(unsigned long long) * (size_t)n * P * oz_digits(K), s);
     if (e != cudaSuccess) return e;
   }
   if (v.ozaki && d >= 1) {
@@ -216,8 +219,12 @@ cudaError_t Impl<K, P>::degrees(const SolveDev &v, cudaStream_t s) {
       }
       {
         ProfScope prof(PK_OZ_UPDATE, s);
-        oz_update_kernel<K, P><<<n * P, kOzWarps * 32, oz_smem, s>>>(As, Xs, v.oz_eA, v.oz_ex, v.b, v.sgn, v.r, n, d,
-                                                                 k);
+        // G CTAs per output so that about 2048 warps share the j range
+        const int nw = oz_warps(K), outs = n * P;
+        const int G = std::max(1, std::min((k + nw - 1) / nw, (2048 + outs * nw - 1) / (outs * nw)));
+        oz_update_kernel<K, P><<<outs * G, nw * 32, oz_smem, s>>>(As, Xs, v.oz_eA, v.oz_ex, v.b, v.oz_acc, n, d, k,
+                                                                   G);
+        oz_finish_kernel<K, P><<<outs, 32, 0, s>>>(v.oz_eA, v.oz_ex, v.b, v.sgn, v.oz_acc, v.r, n, d, k);
       }
       ProfScope prof(PK_WMV, s);
       wmv_kernel<K, P><<<n, kRowLanes, 0, s>>>(v.W, v.r, v.dxw, n, n, k);

@@ -273,109 +273,170 @@ __device__ __forceinline__ unsigned oz_pack(const __nv_bfloat16 *p) {
 }
 
 // The update of one degree k on the tensor pipe; no slice product leaves the
-// SM.  One CTA of kOzWarps warps per (row, plane q); warp w takes
-// j = w, w + kOzWarps, ... < k.  For each j and each plane pair (pa, px) of the
-// complex product the warp stages the slices of (row of A_{k-j}, plane pa) and
-// of (dx_j, plane px) in shared memory, 64 columns at a time (rows padded to 72
-// bf16 so that fragment loads hit 32 distinct banks), forms the S x S slice
-// products with m16n8k16 BF16 mma (exact in fp32: at most 64 terms of < 2^14
-// per chunk), sums them by level L = s + t into shared int32 bins (at most
-// S * kpad terms of < 2^14: below 2^31 for kpad <= 1024), and adds each nonzero
-// level, weighted 2^(eA + ex - 8(L+2)), into the CTA's fixed-point
-// accumulator.  Integer additions are exact in any order, so neither the split
-// over warps nor the chunking changes the result: the exact sum of the terms,
-// rounded once to K limbs.
-constexpr int kOzWarps = 8;
+// SM.  For each output (row, plane q), G CTAs of oz_warps(K) warps share the
+// j range (warp number gw = group * warps + w takes j = gw, gw + G warps, ...).
+// For each j and each plane pair (pa, px) of the complex product a warp stages
+// the slices of (row of A_{k-j}, plane pa) and of (dx_j, plane px) in shared
+// memory, 64 columns at a time (rows padded to 72 bf16 so that fragment loads
+// hit 32 distinct banks), with cp.async into two buffers so that the next
+// stage loads while the current one is multiplied.  It forms the S x S slice
+// products with m16n8k16 BF16 mma, eight independent tiles at a time (exact in
+// fp32: at most 64 terms of < 2^14 per chunk), sums each lane's values of
+// equal level L = s + t in registers and then in shared int32 bins (at most
+// S * kpad terms of < 2^14: below 2^31 for kpad <= 1024), and adds each
+// nonzero level, weighted 2^(eA + ex - 8(L+2)), into a fixed-point
+// accumulator: the CTA's in shared memory, then (atomically, in int64 digits
+// of 32 bits) the output's in global memory.  Integer additions are exact in
+// any order, so neither the split over warps and CTAs nor the chunking
+// changes the result: the exact sum of the terms, rounded once to K limbs by
+// oz_finish_kernel.
 constexpr int kOzChunk = 64;             // columns staged per step
 constexpr int kOzPitch = kOzChunk + 8;   // bf16 per staged row
+constexpr int kOzSmemBudget = 96 * 1024;  // per CTA, so that two CTAs share an SM
 
-__host__ __device__ constexpr int oz_update_smem(int K) {
-  return kOzWarps * 2 * oz_slices(K) * kOzPitch * 2;  // bytes: A and X slices per warp
+__host__ __device__ constexpr int oz_warp_smem(int K) {
+  return 2 * 2 * oz_slices(K) * kOzPitch * 2;  // bytes: two buffers of A and X slices
+}
+__host__ __device__ constexpr int oz_warps(int K) {
+  return kOzSmemBudget / oz_warp_smem(K) < 1 ? 1 : (kOzSmemBudget / oz_warp_smem(K) < 4 ? kOzSmemBudget / oz_warp_smem(K) : 4);
+}
+__host__ __device__ constexpr int oz_update_smem(int K) { return oz_warps(K) * oz_warp_smem(K); }
+
+// the largest divisor of nt that is at most 8 (tiles multiplied together)
+__host__ __device__ constexpr int oz_tiles_in_flight(int nt, int t = 8) {
+  return t <= 1 ? 1 : (nt % t == 0 ? t : oz_tiles_in_flight(nt, t - 1));
 }
 
+__device__ __forceinline__ void oz_cp16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// top of the accumulator of (row, q) at degree k: 64 bits above the largest
+// term and above b_k (the same in every CTA and in the finish).
 template <int K, int P>
-__global__ void __launch_bounds__(kOzWarps * 32) oz_update_kernel(const __nv_bfloat16 *__restrict__ As,
-                                                                  const __nv_bfloat16 *__restrict__ Xs,
-                                                                  const int *__restrict__ eA,
-                                                                  const int *__restrict__ ex,
-                                                                  const double *__restrict__ b, double sgn,
-                                                                  double *__restrict__ r, int n, int d, int k) {
-  constexpr int S = oz_slices(K), W = oz_digits(K);
-  extern __shared__ __align__(16) unsigned char oz_smem[];
-  __shared__ long long acc[W];
-  __shared__ int bins[kOzWarps][2 * S];
-  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __nv_bfloat16 *sA = reinterpret_cast<__nv_bfloat16 *>(oz_smem) + (long long)wib * 2 * S * kOzPitch;
-  __nv_bfloat16 *sX = sA + S * kOzPitch;
-  const int row = blockIdx.x / P, q = blockIdx.x % P;
-  const int kp = oz_kpad(n);
-  const int g = lane >> 2, t4 = lane & 3;
-  for (int i = threadIdx.x; i < W; i += blockDim.x) acc[i] = 0;
-  for (int i = lane; i < 2 * S; i += 32) bins[wib][i] = 0;
-  // top of the accumulator: 64 bits above the largest term and above b_k
+__device__ __forceinline__ int oz_top(const int *eA, const int *ex, const double *b, int n, int d, int k, int row,
+                                      int q, int lane) {
   int etop = -4000;
   for (int j = lane; j < k; j += 32) etop = max(etop, eA[(k - j) * n + row] + ex[j]);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) etop = max(etop, __shfl_xor_sync(0xffffffffu, etop, off));
-  double bl[K];
-#pragma unroll
-  for (int l = 0; l < K; ++l) bl[l] = b[((long long)(q * K + l) * n + row) * (d + 1) + k];
-  etop = max(etop, oz_exp_bound(bl[0]));
-  const int top = etop + 64;
-  __syncthreads();
+  etop = max(etop, oz_exp_bound(b[((long long)(q * K) * n + row) * (d + 1) + k]));
+  return etop + 64;
+}
+
+template <int K, int P>
+__global__ void __launch_bounds__(4 * 32) oz_update_kernel(const __nv_bfloat16 *__restrict__ As,
+                                                           const __nv_bfloat16 *__restrict__ Xs,
+                                                           const int *__restrict__ eA, const int *__restrict__ ex,
+                                                           const double *__restrict__ b,
+                                                           unsigned long long *__restrict__ gacc, int n, int d,
+                                                           int k, int G) {
+  constexpr int S = oz_slices(K), W = oz_digits(K), NW = oz_warps(K);
+  constexpr int NT = (S / 16) * (S / 8);  // 16 x 8 tiles of the S x S products
+  constexpr int TB = oz_tiles_in_flight(NT);
+  constexpr int NU = 2 * (S / 16) + S / 8;  // slots u = 2 mt + nt (+1)
+  static_assert(NW >= 1 && S % 16 == 0 && NT % TB == 0, "split sizes");
+  extern __shared__ __align__(16) unsigned char oz_smem[];
+  __shared__ long long acc[W];
+  __shared__ int bins[NW][2 * S];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __nv_bfloat16 *buf = reinterpret_cast<__nv_bfloat16 *>(oz_smem) + (long long)wib * 4 * S * kOzPitch;
+  const int out = blockIdx.x / G, grp = blockIdx.x % G;
+  const int row = out / P, q = out % P;
+  const int kp = oz_kpad(n), nchunk = kp / kOzChunk + (kp % kOzChunk ? 1 : 0);
   const int npairs = (P == 2) ? 2 : 1;
-  for (int j = wib; j < k; j += kOzWarps) {
-    const int base = eA[(k - j) * n + row] + ex[j];
-    for (int pr = 0; pr < npairs; ++pr) {
+  const int g = lane >> 2, t4 = lane & 3;
+  for (int i = threadIdx.x; i < W; i += blockDim.x) acc[i] = 0;
+  for (int i = lane; i < 2 * S; i += 32) bins[wib][i] = 0;
+  const int top = oz_top<K, P>(eA, ex, b, n, d, k, row, q, lane);
+  __syncthreads();
+  const int gw = grp * NW + wib, TW = G * NW;
+  const int myj = (k > gw) ? (k - gw + TW - 1) / TW : 0;
+  const int nstage = myj * npairs * nchunk;
+  auto plane_pair = [&](int pr, int &pa, int &px, int &sg) {
+    if (P == 1) {
+      pa = 0; px = 0; sg = 1;
+    } else if (q == 0) {  // real part: (re, re) - (im, im)
+      pa = pr; px = pr; sg = pr == 0 ? 1 : -1;
+    } else {  // imaginary part: (re, im) + (im, re)
+      pa = pr; px = 1 - pr; sg = 1;
+    }
+  };
+  auto issue = [&](int st) {  // start loading stage st into buffer st & 1
+    const int c = st % nchunk, pr = (st / nchunk) % npairs, j = gw + TW * (st / (nchunk * npairs));
+    int pa, px, sg;
+    plane_pair(pr, pa, px, sg);
+    const __nv_bfloat16 *Ab = As + ((((long long)(k - j) * n + row) * P + pa) * S) * kp;
+    const __nv_bfloat16 *Bb = Xs + (((long long)j * P + px) * S) * kp;
+    __nv_bfloat16 *sA = buf + (st & 1) * 2 * S * kOzPitch, *sX = sA + S * kOzPitch;
+    const int c0 = c * kOzChunk, pieces = min(kOzChunk, kp - c0) / 8;
+    for (int e = lane; e < S * pieces; e += 32) {
+      const int rr = e / pieces, cc = (e % pieces) * 8;
+      oz_cp16(sA + rr * kOzPitch + cc, Ab + (long long)rr * kp + c0 + cc);
+      oz_cp16(sX + rr * kOzPitch + cc, Bb + (long long)rr * kp + c0 + cc);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if (nstage > 0) issue(0);
+  for (int st = 0; st < nstage; ++st) {
+    if (st + 1 < nstage) {
+      issue(st + 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncwarp();
+    const int c = st % nchunk, pr = (st / nchunk) % npairs, j = gw + TW * (st / (nchunk * npairs));
+    const __nv_bfloat16 *sA = buf + (st & 1) * 2 * S * kOzPitch, *sX = sA + S * kOzPitch;
+    const int cw = min(kOzChunk, kp - c * kOzChunk);  // a multiple of 16
+    // per-lane sums of equal levels: slot u holds L = g + 2 t4 + 8u (e0) and +1 (e1)
+    int e0[NU + 1], e1[NU + 1];
+#pragma unroll
+    for (int u = 0; u <= NU; ++u) e0[u] = e1[u] = 0;
+#pragma unroll
+    for (int tb = 0; tb < NT; tb += TB) {
+      float cf[TB][4];
+#pragma unroll
+      for (int t = 0; t < TB; ++t) cf[t][0] = cf[t][1] = cf[t][2] = cf[t][3] = 0.f;
+      for (int k0 = 0; k0 < cw; k0 += 16) {
+#pragma unroll
+        for (int t = 0; t < TB; ++t) {
+          const int mt = (tb + t) / (S / 8), nt = (tb + t) % (S / 8);
+          const __nv_bfloat16 *Am = sA + (mt * 16) * kOzPitch, *Bn = sX + (nt * 8) * kOzPitch;
+          const unsigned a0 = oz_pack(Am + g * kOzPitch + k0 + 2 * t4);
+          const unsigned a1 = oz_pack(Am + (g + 8) * kOzPitch + k0 + 2 * t4);
+          const unsigned a2 = oz_pack(Am + g * kOzPitch + k0 + 2 * t4 + 8);
+          const unsigned a3 = oz_pack(Am + (g + 8) * kOzPitch + k0 + 2 * t4 + 8);
+          const unsigned b0 = oz_pack(Bn + g * kOzPitch + k0 + 2 * t4);
+          const unsigned b1 = oz_pack(Bn + g * kOzPitch + k0 + 2 * t4 + 8);
+          asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+              "{%0,%1,%2,%3};"
+              : "+f"(cf[t][0]), "+f"(cf[t][1]), "+f"(cf[t][2]), "+f"(cf[t][3])
+              : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < TB; ++t) {
+        const int mt = (tb + t) / (S / 8), nt = (tb + t) % (S / 8), u = 2 * mt + nt;
+        // values at (16 mt + g, 8 nt + 2 t4) + {(0,0), (0,1), (8,0), (8,1)}: L = g + 2 t4 + 8u + {0, 1, 8, 9}
+        e0[u] += __float2int_rn(cf[t][0]);
+        e1[u] += __float2int_rn(cf[t][1]);
+        e0[u + 1] += __float2int_rn(cf[t][2]);
+        e1[u + 1] += __float2int_rn(cf[t][3]);
+      }
+    }
+    const int Lb = g + 2 * t4;
+#pragma unroll
+    for (int u = 0; u <= NU; ++u) {
+      if (e0[u] != 0) atomicAdd(&bins[wib][Lb + 8 * u], e0[u]);
+      if (e1[u] != 0) atomicAdd(&bins[wib][Lb + 8 * u + 1], e1[u]);
+    }
+    __syncwarp();  // the buffer is free and the bins are complete for this chunk
+    if (c == nchunk - 1) {  // last chunk of (j, pr): add the levels
       int pa, px, sg;
-      if (P == 1) {
-        pa = 0; px = 0; sg = 1;
-      } else if (q == 0) {  // real part: (re, re) - (im, im)
-        pa = pr; px = pr; sg = pr == 0 ? 1 : -1;
-      } else {  // imaginary part: (re, im) + (im, re)
-        pa = pr; px = 1 - pr; sg = 1;
-      }
-      const __nv_bfloat16 *Ab = As + ((((long long)(k - j) * n + row) * P + pa) * S) * kp;
-      const __nv_bfloat16 *Bb = Xs + (((long long)j * P + px) * S) * kp;
-      for (int c0 = 0; c0 < kp; c0 += kOzChunk) {
-        const int cw = min(kOzChunk, kp - c0);  // a multiple of 16
-        // stage S rows x cw columns of both operands (16-byte pieces)
-        const int pieces = cw / 8;
-        for (int e = lane; e < S * pieces; e += 32) {
-          const int rr = e / pieces, cc = (e % pieces) * 8;
-          *reinterpret_cast<uint4 *>(sA + rr * kOzPitch + cc) =
-              *reinterpret_cast<const uint4 *>(Ab + (long long)rr * kp + c0 + cc);
-          *reinterpret_cast<uint4 *>(sX + rr * kOzPitch + cc) =
-              *reinterpret_cast<const uint4 *>(Bb + (long long)rr * kp + c0 + cc);
-        }
-        __syncwarp();
-        for (int mt = 0; mt < S / 16; ++mt) {
-          for (int nt = 0; nt < S / 8; ++nt) {
-            float c0f = 0.f, c1f = 0.f, c2f = 0.f, c3f = 0.f;
-            const __nv_bfloat16 *Am = sA + (mt * 16) * kOzPitch, *Bn = sX + (nt * 8) * kOzPitch;
-            for (int k0 = 0; k0 < cw; k0 += 16) {
-              const unsigned a0 = oz_pack(Am + g * kOzPitch + k0 + 2 * t4);
-              const unsigned a1 = oz_pack(Am + (g + 8) * kOzPitch + k0 + 2 * t4);
-              const unsigned a2 = oz_pack(Am + g * kOzPitch + k0 + 2 * t4 + 8);
-              const unsigned a3 = oz_pack(Am + (g + 8) * kOzPitch + k0 + 2 * t4 + 8);
-              const unsigned b0 = oz_pack(Bn + g * kOzPitch + k0 + 2 * t4);
-              const unsigned b1 = oz_pack(Bn + g * kOzPitch + k0 + 2 * t4 + 8);
-              asm volatile(
-                  "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                  "{%0,%1,%2,%3};"
-                  : "+f"(c0f), "+f"(c1f), "+f"(c2f), "+f"(c3f)
-                  : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-            }
-            // (s, t) of the four values: (16 mt + g, 8 nt + 2 t4) and neighbours
-            const int L = mt * 16 + g + nt * 8 + 2 * t4;
-            if (c0f != 0.f) atomicAdd(&bins[wib][L], __float2int_rn(c0f));
-            if (c1f != 0.f) atomicAdd(&bins[wib][L + 1], __float2int_rn(c1f));
-            if (c2f != 0.f) atomicAdd(&bins[wib][L + 8], __float2int_rn(c2f));
-            if (c3f != 0.f) atomicAdd(&bins[wib][L + 9], __float2int_rn(c3f));
-          }
-        }
-        __syncwarp();
-      }
+      plane_pair(pr, pa, px, sg);
+      const int base = eA[(k - j) * n + row] + ex[j];
       for (int Lv = lane; Lv <= 2 * S - 2; Lv += 32) {
         const long long lv = bins[wib][Lv];
         bins[wib][Lv] = 0;
@@ -403,18 +464,35 @@ __global__ void __launch_bounds__(kOzWarps * 32) oz_update_kernel(const __nv_bfl
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    oz_fix<W> a;
+  for (int w = threadIdx.x; w < W; w += blockDim.x)
+    if (acc[w] != 0) atomicAdd(gacc + (long long)out * W + w, (unsigned long long)acc[w]);
+}
+
+// r_k[row] (plane q) from the output's fixed-point accumulator and b_k; the
+// accumulator is cleared for the next degree.  One thread per (row, q).
+template <int K, int P>
+__global__ void oz_finish_kernel(const int *__restrict__ eA, const int *__restrict__ ex,
+                                 const double *__restrict__ b, double sgn, unsigned long long *__restrict__ gacc,
+                                 double *__restrict__ r, int n, int d, int k) {
+  constexpr int W = oz_digits(K);
+  const int out = blockIdx.x, lane = threadIdx.x;  // one warp per output
+  const int row = out / P, q = out % P;
+  const int top = oz_top<K, P>(eA, ex, b, n, d, k, row, q, lane);
+  if (lane != 0) return;
+  oz_fix<W> a;
 #pragma unroll
-    for (int w = 0; w < W; ++w) a.d[w] = acc[w];
-#pragma unroll
-    for (int l = 0; l < K; ++l) oz_add_double<W>(a, top, bl[l], sgn < 0.0 ? -1 : 1);
-    double z[K];
-    oz_to_md<W, K>(a, top, z);
-    const long long VS = P * K;
-#pragma unroll
-    for (int l = 0; l < K; ++l) r[((long long)k * n + row) * VS + q * K + l] = z[l];
+  for (int w = 0; w < W; ++w) {
+    a.d[w] = (long long)gacc[(long long)out * W + w];
+    gacc[(long long)out * W + w] = 0ULL;
   }
+#pragma unroll
+  for (int l = 0; l < K; ++l)
+    oz_add_double<W>(a, top, b[((long long)(q * K + l) * n + row) * (d + 1) + k], sgn < 0.0 ? -1 : 1);
+  double z[K];
+  oz_to_md<W, K>(a, top, z);
+  const long long VS = P * K;
+#pragma unroll
+  for (int l = 0; l < K; ++l) r[((long long)k * n + row) * VS + q * K + l] = z[l];
 }
 
 }  // namespace mdk
