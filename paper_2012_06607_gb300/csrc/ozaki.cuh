@@ -109,8 +109,10 @@ __device__ __forceinline__ void oz_normalize(oz_fix<W> &a) {
   }
 }
 
-// K-limb md value of the normalised fixed-point number (top as in oz_add_double):
-// limbs are consecutive 53-bit chunks of the magnitude (truncated).
+// K-limb md value of the fixed-point number (top as in oz_add_double): limbs
+// are consecutive 53-bit chunks of the magnitude (truncated), each starting at
+// the first set bit after the previous one.  Word operations only: the
+// magnitude is a stream of 32-bit words, MSB first.
 template <int W, int K>
 __device__ __forceinline__ void oz_to_md(oz_fix<W> a, int top, double (&z)[K]) {
   oz_normalize<W>(a);
@@ -125,41 +127,41 @@ __device__ __forceinline__ void oz_to_md(oz_fix<W> a, int top, double (&z)[K]) {
     }
     a.d[0] = -a.d[0] - 1 + carry;
   }
-  // magnitude digits: d[0] may exceed 32 bits; handle it as a 64-bit head
 #pragma unroll
   for (int l = 0; l < K; ++l) z[l] = 0.0;
-  // find the leading set bit
-  int lead = -1;  // bit index counted from the top: position p has weight 2^(top - 1 - p) for p >= 0
-  // head digit (possibly > 32 bits): weight 2^(top-32) per unit
+  // stream words: the 64-bit head d[0] (units of 2^(top-32)) as two words, then d[1..W-1]
+  constexpr int NWD = W + 1;
+  unsigned wd[NWD];
   const unsigned long long head = (unsigned long long)a.d[0];
-  int hb = head ? 64 - __clzll((long long)head) : 0;  // bits in head
-  // bit stream: head bits (hb of them, MSB first) then W-1 digits of 32 bits
-  // value = sum of bits; emit 53-bit chunks
-  auto bit_at = [&](int p) -> unsigned {  // p = 0 is the MSB of the stream
-    if (p < hb) return (unsigned)((head >> (hb - 1 - p)) & 1ULL);
-    const int q = 1 + (p - hb) / 32, o = (p - hb) % 32;
-    if (q >= W) return 0u;
-    return (unsigned)(((unsigned long long)a.d[q] >> (31 - o)) & 1ULL);
-  };
-  const int nbits = hb + 32 * (W - 1);
-  for (int p = 0; p < nbits; ++p)
-    if (bit_at(p)) {
-      lead = p;
-      break;
+  wd[0] = (unsigned)(head >> 32);
+  wd[1] = (unsigned)head;
+#pragma unroll
+  for (int q = 1; q < W; ++q) wd[q + 1] = (unsigned)a.d[q];
+  // stream bit p (p = 0 is the MSB of wd[0]) has weight 2^(top - 32 + 63 - p)
+  auto first_set = [&](int p) -> int {  // first set bit at or after p, or -1
+    for (int w = p >> 5; w < NWD; ++w) {
+      unsigned v = wd[w];
+      if (w == (p >> 5)) v &= 0xffffffffu >> (p & 31);
+      if (v) return 32 * w + __clz((int)v);
     }
-  if (lead < 0) return;
-  // weight of stream bit p: 2^(top - 32 + hb - 1 - p)
-  int p = lead;
+    return -1;
+  };
+  auto bits53 = [&](int p) -> unsigned long long {  // stream bits [p, p + 53), zero past the end
+    unsigned long long win = 0;  // 64 bits starting at p
+    const int w = p >> 5, o = p & 31;
+    const unsigned w0 = w < NWD ? wd[w] : 0u, w1 = w + 1 < NWD ? wd[w + 1] : 0u, w2 = w + 2 < NWD ? wd[w + 2] : 0u;
+    win = ((unsigned long long)w0 << 32 | w1) << o;
+    if (o) win |= (unsigned long long)w2 >> (32 - o);
+    return win >> 11;
+  };
+  int p = first_set(0);
 #pragma unroll 1
-  for (int l = 0; l < K && p < nbits; ++l) {
-    unsigned long long m = 0;
-    const int first = p;
-    for (int i = 0; i < 53; ++i) m = (m << 1) | (p + i < nbits ? bit_at(p + i) : 0u);
-    const int lsb_weight = top - 32 + hb - 1 - (first + 52);
+  for (int l = 0; l < K && p >= 0; ++l) {
+    const unsigned long long m = bits53(p);
+    const int lsb_weight = top - 32 + 63 - (p + 52);
     const double v = scalbn((double)m, lsb_weight);
     z[l] = neg ? -v : v;
-    p = first + 53;
-    while (p < nbits && !bit_at(p)) ++p;  // next limb starts at the next set bit
+    p = (p + 53 < 32 * NWD) ? first_set(p + 53) : -1;
   }
 }
 
@@ -280,8 +282,9 @@ __device__ __forceinline__ unsigned oz_pack(const __nv_bfloat16 *p) {
 // memory, 64 columns at a time (rows padded to 72 bf16 so that fragment loads
 // hit 32 distinct banks), with cp.async into two buffers so that the next
 // stage loads while the current one is multiplied.  It forms the S x S slice
-// products with m16n8k16 BF16 mma, eight independent tiles at a time (exact in
-// fp32: at most 64 terms of < 2^14 per chunk), sums each lane's values of
+// products with m16n8k16 BF16 mma on ldmatrix fragments, a 32-row (S <= 32) or
+// 16-row band of tiles at a time (exact in fp32: at most 64 terms of < 2^14
+// per chunk), sums each lane's values of
 // equal level L = s + t in registers and then in shared int32 bins (at most
 // S * kpad terms of < 2^14: below 2^31 for kpad <= 1024), and adds each
 // nonzero level, weighted 2^(eA + ex - 8(L+2)), into a fixed-point
@@ -301,11 +304,6 @@ __host__ __device__ constexpr int oz_warps(int K) {
   return kOzSmemBudget / oz_warp_smem(K) < 1 ? 1 : (kOzSmemBudget / oz_warp_smem(K) < 4 ? kOzSmemBudget / oz_warp_smem(K) : 4);
 }
 __host__ __device__ constexpr int oz_update_smem(int K) { return oz_warps(K) * oz_warp_smem(K); }
-
-// the largest divisor of nt that is at most 8 (tiles multiplied together)
-__host__ __device__ constexpr int oz_tiles_in_flight(int nt, int t = 8) {
-  return t <= 1 ? 1 : (nt % t == 0 ? t : oz_tiles_in_flight(nt, t - 1));
-}
 
 __device__ __forceinline__ void oz_cp16(void *smem, const void *gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -333,10 +331,9 @@ __global__ void __launch_bounds__(4 * 32) oz_update_kernel(const __nv_bfloat16 *
                                                            unsigned long long *__restrict__ gacc, int n, int d,
                                                            int k, int G) {
   constexpr int S = oz_slices(K), W = oz_digits(K), NW = oz_warps(K);
-  constexpr int NT = (S / 16) * (S / 8);  // 16 x 8 tiles of the S x S products
-  constexpr int TB = oz_tiles_in_flight(NT);
+  constexpr int MB = S <= 32 ? S / 16 : 1;  // 16-row bands multiplied together
   constexpr int NU = 2 * (S / 16) + S / 8;  // slots u = 2 mt + nt (+1)
-  static_assert(NW >= 1 && S % 16 == 0 && NT % TB == 0, "split sizes");
+  static_assert(NW >= 1 && S % 16 == 0, "split sizes");
   extern __shared__ __align__(16) unsigned char oz_smem[];
   __shared__ long long acc[W];
   __shared__ int bins[NW][2 * S];
@@ -394,37 +391,54 @@ __global__ void __launch_bounds__(4 * 32) oz_update_kernel(const __nv_bfloat16 *
     int e0[NU + 1], e1[NU + 1];
 #pragma unroll
     for (int u = 0; u <= NU; ++u) e0[u] = e1[u] = 0;
+    // tile groups: all tiles when S <= 32, else one 16-row band (S/8 tiles)
 #pragma unroll
-    for (int tb = 0; tb < NT; tb += TB) {
-      float cf[TB][4];
+    for (int mg = 0; mg < S / 16; mg += MB) {
+      float cf[MB][S / 8][4];
 #pragma unroll
-      for (int t = 0; t < TB; ++t) cf[t][0] = cf[t][1] = cf[t][2] = cf[t][3] = 0.f;
+      for (int a = 0; a < MB; ++a)
+#pragma unroll
+        for (int t = 0; t < S / 8; ++t) cf[a][t][0] = cf[a][t][1] = cf[a][t][2] = cf[a][t][3] = 0.f;
       for (int k0 = 0; k0 < cw; k0 += 16) {
+        // fragments with ldmatrix: A rows 16 (mg + a) + (lane & 15), columns k0 + 8 (lane >> 4);
+        // B rows 8 t + (lane & 7), columns k0 + 8 ((lane >> 3) & 1)
+        unsigned af[MB][4], bf[S / 8][2];
 #pragma unroll
-        for (int t = 0; t < TB; ++t) {
-          const int mt = (tb + t) / (S / 8), nt = (tb + t) % (S / 8);
-          const __nv_bfloat16 *Am = sA + (mt * 16) * kOzPitch, *Bn = sX + (nt * 8) * kOzPitch;
-          const unsigned a0 = oz_pack(Am + g * kOzPitch + k0 + 2 * t4);
-          const unsigned a1 = oz_pack(Am + (g + 8) * kOzPitch + k0 + 2 * t4);
-          const unsigned a2 = oz_pack(Am + g * kOzPitch + k0 + 2 * t4 + 8);
-          const unsigned a3 = oz_pack(Am + (g + 8) * kOzPitch + k0 + 2 * t4 + 8);
-          const unsigned b0 = oz_pack(Bn + g * kOzPitch + k0 + 2 * t4);
-          const unsigned b1 = oz_pack(Bn + g * kOzPitch + k0 + 2 * t4 + 8);
-          asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-              "{%0,%1,%2,%3};"
-              : "+f"(cf[t][0]), "+f"(cf[t][1]), "+f"(cf[t][2]), "+f"(cf[t][3])
-              : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+        for (int a = 0; a < MB; ++a) {
+          const __nv_bfloat16 *pa = sA + (16 * (mg + a) + (lane & 15)) * kOzPitch + k0 + 8 * (lane >> 4);
+          const unsigned sa = (unsigned)__cvta_generic_to_shared(pa);
+          asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                       : "=r"(af[a][0]), "=r"(af[a][1]), "=r"(af[a][2]), "=r"(af[a][3])
+                       : "r"(sa));
         }
+#pragma unroll
+        for (int t = 0; t < S / 8; ++t) {
+          const __nv_bfloat16 *pb = sX + (8 * t + (lane & 7)) * kOzPitch + k0 + 8 * ((lane >> 3) & 1);
+          const unsigned sb = (unsigned)__cvta_generic_to_shared(pb);
+          asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];"
+                       : "=r"(bf[t][0]), "=r"(bf[t][1])
+                       : "r"(sb));
+        }
+#pragma unroll
+        for (int a = 0; a < MB; ++a)
+#pragma unroll
+          for (int t = 0; t < S / 8; ++t)
+            asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                "{%0,%1,%2,%3};"
+                : "+f"(cf[a][t][0]), "+f"(cf[a][t][1]), "+f"(cf[a][t][2]), "+f"(cf[a][t][3])
+                : "r"(af[a][0]), "r"(af[a][1]), "r"(af[a][2]), "r"(af[a][3]), "r"(bf[t][0]), "r"(bf[t][1]));
       }
 #pragma unroll
-      for (int t = 0; t < TB; ++t) {
-        const int mt = (tb + t) / (S / 8), nt = (tb + t) % (S / 8), u = 2 * mt + nt;
-        // values at (16 mt + g, 8 nt + 2 t4) + {(0,0), (0,1), (8,0), (8,1)}: L = g + 2 t4 + 8u + {0, 1, 8, 9}
-        e0[u] += __float2int_rn(cf[t][0]);
-        e1[u] += __float2int_rn(cf[t][1]);
-        e0[u + 1] += __float2int_rn(cf[t][2]);
-        e1[u + 1] += __float2int_rn(cf[t][3]);
-      }
+      for (int a = 0; a < MB; ++a)
+#pragma unroll
+        for (int t = 0; t < S / 8; ++t) {
+          const int u = 2 * (mg + a) + t;
+          // values at (16 mt + g, 8 nt + 2 t4) + {(0,0), (0,1), (8,0), (8,1)}: L = g + 2 t4 + 8u + {0, 1, 8, 9}
+          e0[u] += __float2int_rn(cf[a][t][0]);
+          e1[u] += __float2int_rn(cf[a][t][1]);
+          e0[u + 1] += __float2int_rn(cf[a][t][2]);
+          e1[u + 1] += __float2int_rn(cf[a][t][3]);
+        }
     }
     const int Lb = g + 2 * t4;
 #pragma unroll
