@@ -201,9 +201,17 @@ cudaError_t Impl<K, P>::degrees(const SolveDev &v, cudaStream_t s) {
   __nv_bfloat16 *As = static_cast<__nv_bfloat16 *>(v.oz_As), *Xs = static_cast<__nv_bfloat16 *>(v.oz_Xs);
   constexpr int oz_smem = oz_update_smem(K);
   static_assert(oz_smem <= kOzSmemBudget, "staged slices exceed the shared memory of an SM");
+  int oz_slots = 0;  // update CTAs resident on the whole GPU
   if (v.ozaki) {
     cudaError_t e = cudaFuncSetAttribute(oz_update_kernel<K, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, oz_smem);
     if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, oz_update_kernel<K, P>, oz_warps(K) * 32,
+                                                           oz_smem)) != cudaSuccess)
+      return e;
+    oz_slots = std::max(1, sms * per_sm);
     e = cudaMemsetAsync(v.oz_acc, 0, sizeof(unsigned long long) * (size_t)n * P * oz_digits(K), s);
     if (e != cudaSuccess) return e;
   }
@@ -219,9 +227,9 @@ cudaError_t Impl<K, P>::degrees(const SolveDev &v, cudaStream_t s) {
       }
       {
         ProfScope prof(PK_OZ_UPDATE, s);
-        // G CTAs per output so that about 2048 warps share the j range
+        // G CTAs per output: as many as fit on the GPU at once (one wave)
         const int nw = oz_warps(K), outs = n * P;
-        const int G = std::max(1, std::min((k + nw - 1) / nw, (2048 + outs * nw - 1) / (outs * nw)));
+        const int G = std::max(1, std::min((k + nw - 1) / nw, oz_slots / outs));
         oz_update_kernel<K, P><<<outs * G, nw * 32, oz_smem, s>>>(As, Xs, v.oz_eA, v.oz_ex, v.b, v.oz_acc, n, d, k,
                                                                    G);
         oz_finish_kernel<K, P><<<outs, 32, 0, s>>>(v.oz_eA, v.oz_ex, v.b, v.sgn, v.oz_acc, v.r, n, d, k);

@@ -368,10 +368,19 @@ __global__ void __launch_bounds__(4 * 32) oz_update_kernel(const __nv_bfloat16 *
     const __nv_bfloat16 *Bb = Xs + (((long long)j * P + px) * S) * kp;
     __nv_bfloat16 *sA = buf + (st & 1) * 2 * S * kOzPitch, *sX = sA + S * kOzPitch;
     const int c0 = c * kOzChunk, pieces = min(kOzChunk, kp - c0) / 8;
-    for (int e = lane; e < S * pieces; e += 32) {
-      const int rr = e / pieces, cc = (e % pieces) * 8;
-      oz_cp16(sA + rr * kOzPitch + cc, Ab + (long long)rr * kp + c0 + cc);
-      oz_cp16(sX + rr * kOzPitch + cc, Bb + (long long)rr * kp + c0 + cc);
+    if (pieces == kOzChunk / 8) {  // full chunk: lane = (row mod 4, 16-byte piece)
+      const int cc = (lane & 7) * 8;
+#pragma unroll 4
+      for (int rr = lane >> 3; rr < S; rr += 4) {
+        oz_cp16(sA + rr * kOzPitch + cc, Ab + (long long)rr * kp + c0 + cc);
+        oz_cp16(sX + rr * kOzPitch + cc, Bb + (long long)rr * kp + c0 + cc);
+      }
+    } else {
+      for (int e = lane; e < S * pieces; e += 32) {
+        const int rr = e / pieces, cc = (e % pieces) * 8;
+        oz_cp16(sA + rr * kOzPitch + cc, Ab + (long long)rr * kp + c0 + cc);
+        oz_cp16(sX + rr * kOzPitch + cc, Bb + (long long)rr * kp + c0 + cc);
+      }
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
