@@ -453,7 +453,9 @@ constexpr int kHouseThreads = 128;
 
 // Householder vector of column j (Golub-Van Loan): alpha = ||x||, phase
 // e = x_0/|x_0|, v = x + e alpha e_1, beta = 1/(alpha (alpha + |x_0|)), R_jj = -e alpha.
-// Block-level body for kHouseThreads threads.
+// The square roots and the reciprocal use the precision-doubling iterations
+// (this chain bounds the factorisation).  Block-level body for kHouseThreads
+// threads.
 template <int K, int P>
 __device__ __forceinline__ void house_block(double *M, double *vd,
                                             double *beta, int *status, int N, int j) {
@@ -484,7 +486,7 @@ __device__ __forceinline__ void house_block(double *M, double *vd,
   ld_aos<K, P>(M + ((long long)j * N + j) * VS, x0);
   if (tid == 0) {
     double al[K];
-    md_sqrt<K>(acc.v[0], al);
+    md_sqrt_pd<K>(acc.v[0], al);
 #pragma unroll
     for (int l = 0; l < K; ++l) s_alpha[l] = al[l];
   }
@@ -497,25 +499,23 @@ __device__ __forceinline__ void house_block(double *M, double *vd,
     } else {
       double s2[K];
       c_abs2<K, P>(x0, s2);
-      md_sqrt<K>(s2, a0);
+      md_sqrt_pd<K>(s2, a0);
     }
 #pragma unroll
     for (int l = 0; l < K; ++l) s_a0[l] = a0[l];
   }
   __syncthreads();
   if (tid == 0) {
-    double al[K], a0[K], t[K], den[K], one[K], bt[K];
+    double al[K], a0[K], t[K], den[K], bt[K];
 #pragma unroll
     for (int l = 0; l < K; ++l) {
       al[l] = s_alpha[l];
       a0[l] = s_a0[l];
-      one[l] = 0.0;
     }
-    one[0] = 1.0;
     if (!nonzero(al[0])) atomicOr(status, ST_SINGULAR);
     md_add<K>(al, a0, t);
     md_mul<K>(al, t, den);
-    md_div<K>(one, den, bt);
+    md_recip_pd<K>(den, bt);
 #pragma unroll
     for (int l = 0; l < K; ++l) s_beta[l] = bt[l];
   }

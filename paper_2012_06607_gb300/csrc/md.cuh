@@ -306,6 +306,83 @@ __device__ __forceinline__ void md_sqrt(const double (&a)[K], double (&z)[K]) {
   }
 }
 
+// ------------------------------------------ precision-doubling iterations
+// For the latency-bound chain of Householder vectors: Newton iterations whose
+// early steps run at 2, 4, 8 limbs (each step doubles the correct bits, so a
+// step needs only the precision it produces) and whose last step runs at K
+// limbs.  Same accuracy as md_sqrt / md_div, about a third of the sequential
+// FP64 instructions for the square root; not bit-identical to them.
+
+// s <- (s + a/s) / 2 on the leading L limbs (s's limbs from L on are zero).
+template <int L, int K>
+__device__ __forceinline__ void heron_step(const double (&a)[K], double (&s)[K]) {
+  double aL[L], sL[L], q[L], t[L];
+#pragma unroll
+  for (int l = 0; l < L; ++l) {
+    aL[l] = a[l];
+    sL[l] = s[l];
+  }
+  md_div<L>(aL, sL, q);
+  md_add<L>(sL, q, t);
+#pragma unroll
+  for (int l = 0; l < L; ++l) s[l] = dmul(t[l], 0.5);  // exact halving
+}
+
+template <int K>
+__device__ __forceinline__ void md_sqrt_pd(const double (&a)[K], double (&z)[K]) {
+  if constexpr (K == 1) {
+    z[0] = __dsqrt_rn(a[0]);
+  } else {
+    double s[K];
+#pragma unroll
+    for (int l = 0; l < K; ++l) s[l] = 0.0;
+    if (nonzero(a[0])) {
+      s[0] = __dsqrt_rn(a[0]);
+      heron_step<2, K>(a, s);
+      if constexpr (K > 2) heron_step<(K < 4 ? K : 4), K>(a, s);
+      if constexpr (K > 4) heron_step<(K < 8 ? K : 8), K>(a, s);
+      if constexpr (K > 8) heron_step<K, K>(a, s);
+    }
+#pragma unroll
+    for (int l = 0; l < K; ++l) z[l] = s[l];
+  }
+}
+
+// y <- y + y (1 - a y) on the leading L limbs.
+template <int L, int K>
+__device__ __forceinline__ void recip_step(const double (&a)[K], double (&y)[K]) {
+  double aL[L], yL[L], t[L], e[L], u[L], one[L];
+#pragma unroll
+  for (int l = 0; l < L; ++l) {
+    aL[l] = a[l];
+    yL[l] = y[l];
+    one[l] = l == 0 ? 1.0 : 0.0;
+  }
+  md_mul<L>(aL, yL, t);
+  md_sub<L>(one, t, e);
+  md_mul<L>(yL, e, u);
+  md_add<L>(yL, u, t);
+#pragma unroll
+  for (int l = 0; l < L; ++l) y[l] = t[l];
+}
+
+// 1 / a (a != 0) by Newton steps at 2, 4, 8 and K limbs from 1 / a_0.
+template <int K>
+__device__ __forceinline__ void md_recip_pd(const double (&a)[K], double (&z)[K]) {
+  double y[K];
+#pragma unroll
+  for (int l = 0; l < K; ++l) y[l] = 0.0;
+  y[0] = ddiv(1.0, a[0]);
+  if constexpr (K > 1) {
+    recip_step<2, K>(a, y);
+    if constexpr (K > 2) recip_step<(K < 4 ? K : 4), K>(a, y);
+    if constexpr (K > 4) recip_step<(K < 8 ? K : 8), K>(a, y);
+    if constexpr (K > 8) recip_step<K, K>(a, y);
+  }
+#pragma unroll
+  for (int l = 0; l < K; ++l) z[l] = y[l];
+}
+
 // ----------------------------------------------------------------- complex
 // P = 1: real, P = 2: complex (v[0] real part, v[1] imaginary part).
 template <int K, int P>
