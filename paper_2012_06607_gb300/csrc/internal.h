@@ -141,6 +141,7 @@ struct Impl {
   static cudaError_t factor(const SolveDev &v, cudaStream_t s);    // QR, Q^H, W = R^-1 Q^H
   static cudaError_t degrees(const SolveDev &v, cudaStream_t s);   // degree loop and update
   static cudaError_t rcond(const SolveDev &v, cudaStream_t s);     // 1-norm rcond of A_0 from A_0 and W
+  static cudaError_t backsub(const SolveDev &v, int N, cudaStream_t s);  // W = R^-1 Y[0:n, :]
 };
 
 }  // namespace mdk

@@ -929,6 +929,56 @@ __global__ void __launch_bounds__(256) rcond_kernel(const double *__restrict__ A
   if (tid == 0) out[0] = 1.0 / (s_max[0][0] * s_max[1][0]);
 }
 
+// The same back substitution with lookahead: row c of W is known when step c
+// starts (W[c][:] = Y[c][:] / R_cc).  The first gA CTAs update row c-1 of Y
+// with it and form row c-1 of W (the next step's row); the other CTAs update
+// rows 0..c-2.  Each element gets the same operations as in backsub_entry, so
+// W is the same; the chain per step is one row instead of the whole step.
+template <int K, int P>
+__global__ void backsub_row0_kernel(const double *__restrict__ Y, double *__restrict__ W,
+                                    const double *__restrict__ rinv, int N, int c) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= N) return;
+  const long long VS = P * K;
+  mdv<K, P> y, ri, w;
+  ld_aos<K, P>(Y + ((long long)col * N + c) * VS, y);
+  ld_aos<K, P>(rinv + (long long)c * VS, ri);
+  c_mul<K, P>(y, ri, w);
+  st_aos<K, P>(W + ((long long)c * N + col) * VS, w);
+}
+
+template <int K, int P>
+__global__ void backsub_step_kernel(const double *__restrict__ M, double *__restrict__ Y, double *__restrict__ W,
+                                    const double *__restrict__ rinv, int N, int c, int gA) {
+  const long long VS = P * K;
+  if ((int)blockIdx.x < gA) {  // row c-1, then W[c-1][:]
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= N) return;
+    mdv<K, P> w, rc, t, yi, ri;
+    ld_aos<K, P>(W + ((long long)c * N + col) * VS, w);
+    ld_aos<K, P>(M + ((long long)c * N + (c - 1)) * VS, rc);
+    ld_aos<K, P>(Y + ((long long)col * N + (c - 1)) * VS, yi);
+    c_mul<K, P>(rc, w, t);
+    c_sub<K, P>(yi, t, yi);
+    st_aos<K, P>(Y + ((long long)col * N + (c - 1)) * VS, yi);
+    ld_aos<K, P>(rinv + (long long)(c - 1) * VS, ri);
+    c_mul<K, P>(yi, ri, w);
+    st_aos<K, P>(W + ((long long)(c - 1) * N + col) * VS, w);
+    return;
+  }
+  // rows 0..c-2: e = col * (c-1) + i
+  const long long e = (blockIdx.x - gA) * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)(c - 1) * N) return;
+  const int i = (int)(e % (c - 1)), col = (int)(e / (c - 1));
+  mdv<K, P> w, rc, t, yi;
+  ld_aos<K, P>(W + ((long long)c * N + col) * VS, w);
+  ld_aos<K, P>(M + ((long long)c * N + i) * VS, rc);
+  ld_aos<K, P>(Y + ((long long)col * N + i) * VS, yi);
+  c_mul<K, P>(rc, w, t);
+  c_sub<K, P>(yi, t, yi);
+  st_aos<K, P>(Y + ((long long)col * N + i) * VS, yi);
+}
+
 // Partial sums of sum_{j<k} A_{k-j} dx_j for item e = (row, chunk); term index
 // t = j*n + col over [chunk*C, min((chunk+1)*C, k*n)).  A is the caller's
 // SoA [P][K][d+1][n][n] (column-major blocks); dx is AoS [k][i].

@@ -161,11 +161,7 @@ cudaError_t Impl<K, P>::factor(const SolveDev &v, cudaStream_t s) {
       const long long m = n - j - 1;
       lu_forward_kernel<K, P><<<blocks_for(m * n, 128), 128, 0, s>>>(v.M, v.Y, n, j);
     }
-    for (int c = n - 1; c >= 0; --c) {
-      ProfScope prof(PK_BACKSUB, s);
-      backsub_kernel<K, P><<<blocks_for((long long)(c + 1) * n, 64), 64, 0, s>>>(v.M, v.Y, v.W, v.rinv, n, c);
-    }
-    return cudaGetLastError();
+    return backsub(v, n, s);
   }
   {
     ProfScope prof(PK_QR_HOUSE, s);
@@ -182,9 +178,23 @@ cudaError_t Impl<K, P>::factor(const SolveDev &v, cudaStream_t s) {
     ProfScope prof(PK_RINV, s);
     rinv_kernel<K, P><<<blocks_for(n, 64), 64, 0, s>>>(v.M, v.rinv, N, n);
   }
-  for (int c = n - 1; c >= 0; --c) {
+  return backsub(v, N, s);
+}
+
+// W = R^-1 Y[0:n, :] (N columns), lookahead form: row c of W is ready when
+// step c starts.
+template <int K, int P>
+cudaError_t Impl<K, P>::backsub(const SolveDev &v, int N, cudaStream_t s) {
+  const int n = v.n;
+  {
     ProfScope prof(PK_BACKSUB, s);
-    backsub_kernel<K, P><<<blocks_for((long long)(c + 1) * N, 64), 64, 0, s>>>(v.M, v.Y, v.W, v.rinv, N, c);
+    backsub_row0_kernel<K, P><<<blocks_for(N, 64), 64, 0, s>>>(v.Y, v.W, v.rinv, N, n - 1);
+  }
+  for (int c = n - 1; c >= 1; --c) {
+    ProfScope prof(PK_BACKSUB, s);
+    const int gA = (int)blocks_for(N, 64);
+    const long long rest = (long long)(c - 1) * N;
+    backsub_step_kernel<K, P><<<gA + (int)blocks_for(rest, 64), 64, 0, s>>>(v.M, v.Y, v.W, v.rinv, N, c, gA);
   }
   return cudaGetLastError();
 }
