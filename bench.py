@@ -103,7 +103,26 @@ def conv_schedule_counts(s) -> int:
     return total
 
 
-# ------------------------------------------------------------------ clocks
+def step_fp64_model(s) -> dict:
+    """FP64 instructions of one Newton step of system s: the series products
+    exactly (the md algorithms' counts), the rest from the operation counts of
+    the accumulation, the QR with Q^H, the back substitution, the block
+    Toeplitz update and W r_k (complex multiply-adds; reductions as adds)."""
+    P, K, n, d = s.planes, s.limbs, s.n, s.degree
+    cm, ca = complex_mac_instr(K, P)
+    mac = cm + ca
+    D1 = d + 1
+    conv = conv_schedule_counts(s) * (D1 * (D1 + 1) // 2 * cm + d * D1 // 2 * ca)
+    contrib = sum(1 + len([v for v, _ in pairs if v != n]) for i in range(s.N) for _, pairs in s.monomials(i))
+    accum = contrib * D1 * mac
+    qr = sum(((n - j - 1) + n) * (n - j) * 2 * mac for j in range(n))
+    backsub = sum((c + 1) * n for c in range(n)) * (2 * cm + ca)
+    update = n * n * d * D1 // 2 * mac + D1 * n * n * mac
+    return {"conv": conv, "accum": accum, "qr": qr, "backsub": backsub, "update": update,
+            "total": conv + accum + qr + backsub + update}
+
+
+# ------------------------------------------------------------------ clocks# ------------------------------------------------------------------ clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -499,6 +518,57 @@ def run_ladder(args):
     return 0
 
 
+def run_elementwise(args):
+    """Elementwise md add and mul on arrays far larger than L2 (512 MB per
+    input limb set), at every precision: HBM GB/s and FP64 instruction rate,
+    each against its peak, to show where the md arithmetic stops being
+    memory-bound."""
+    import torch
+
+    import paper_2012_06607_gb300 as md
+
+    peaks = {}
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except (OSError, ValueError):
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    res = {}
+    for K in (1, 2, 3, 4, 8, 10):
+        count = (512 << 20) // (8 * K)
+        x = torch.rand((1, K, count), dtype=torch.float64, device="cuda")
+        y = torch.rand((1, K, count), dtype=torch.float64, device="cuda")
+        x[:, 1:] *= 2.0 ** -60
+        y[:, 1:] *= 2.0 ** -60
+        z = torch.empty_like(x)
+        c = fp64_instr_counts(K)
+        for op in ("add", "mul"):
+            for _ in range(2):
+                md.elementwise(op, K, False, x, y, out=z)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 5
+            e0.record()
+            for _ in range(reps):
+                md.elementwise(op, K, False, x, y, out=z)
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            gbs = 3 * 8 * K * count / (ms / 1e3) / 1e9
+            instr = c[op] * count / (ms / 1e3)
+            res[f"K{K}_{op}"] = {"ms": ms, "gb_per_s": gbs, "hbm_frac": gbs / hbm, "fp64_instr_per_s": instr,
+                                 "fp64_frac": instr / FP64_PEAK_INSTR,
+                                 "bound": "hbm" if gbs / hbm > instr / FP64_PEAK_INSTR else "alu"}
+        del x, y, z
+        torch.cuda.empty_cache()
+    line = {"metric": "elementwise md add / mul, real, 512 MB per input limb set", "form": "elementwise",
+            "per_op": res, "hbm_peak_gbs": hbm, "hbm_peak_source": "measured" if peaks else "fallback",
+            "fp64_peak_instr_per_s": FP64_PEAK_INSTR, "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batched(args):
     """2048 complex systems, n ~ U{8..64}, d ~ U{8..32}, double double / quad
     double: one persistent launch per precision class per Newton iteration
@@ -553,6 +623,8 @@ def run_batched(args):
     kinds = {}
     for s in systems:
         kinds[s.limbs] = kinds.get(s.limbs, 0) + 1
+    models = [step_fp64_model(s) for s in systems]
+    fp64 = {k: sum(m[k] for m in models) for k in models[0]}
     line = {"metric": "batched Newton iterations/s (2048 systems, n~U{8..64}, d~U{8..32}, dd/qd, complex)",
             "unit": "iterations/s", "value": 1e3 / it_ms, "ms_per_iteration": it_ms,
             "system_steps_per_s": len(systems) * 1e3 / it_ms,
@@ -560,6 +632,11 @@ def run_batched(args):
             "loop_ms_per_iteration": loop_ms,
             "speedup_vs_loop": (loop_ms / it_ms) if loop_ms else None,
             "systems": len(systems), "limb_counts": kinds, "workspace_gib": ws.numel() / 2 ** 30,
+            "roofline": {"bound": "alu", "achieved": fp64["total"] / (it_ms / 1e3) / 1e12,
+                         "peak": FP64_PEAK_INSTR / 1e12, "unit": "TFLOP/s",
+                         "frac": fp64["total"] / (it_ms / 1e3) / FP64_PEAK_INSTR,
+                         "counted": "FP64 instructions per iteration: series products exact, solve modelled",
+                         "fp64_instr_per_iteration": fp64},
             "steps": args.steps, "warmup": args.warmup, "flags": "autotune+graph", "data": "synthetic",
             "dtype": "f64 (double double / quad double)"}
     print(json.dumps(line), flush=True)
@@ -575,9 +652,9 @@ def main():
     ap.add_argument("--impl", default="product", choices=["product", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other-form", action="store_true", help="skip timing the split-product update beside md")
-    ap.add_argument("--form", default="plain", choices=["plain", "solve3", "batched", "ladder"],
+    ap.add_argument("--form", default="plain", choices=["plain", "solve3", "batched", "ladder", "elementwise"],
                     help="plain: the Newton-step benchmark; solve3: plain vs split-product solve; "
-                         "batched: 2048-system batched step vs a per-system loop; ladder: the headline step at every precision")
+                         "batched: 2048-system batched step vs a per-system loop; ladder: the headline step at every precision; elementwise: md add/mul HBM vs FP64 bound")
     ap.add_argument("--update", default="md", choices=["md", "split"],
                     help="block Toeplitz update of the plain form: md arithmetic or split-product")
     ap.add_argument("--batch", type=int, default=2048)
@@ -593,6 +670,8 @@ def main():
         return run_batched(args)
     if args.form == "ladder":
         return run_ladder(args)
+    if args.form == "elementwise":
+        return run_elementwise(args)
     return run_product(args)
 
 
