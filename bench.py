@@ -629,6 +629,7 @@ def run_batched(args):
             "unit": "iterations/s", "value": 1e3 / it_ms, "ms_per_iteration": it_ms,
             "system_steps_per_s": len(systems) * 1e3 / it_ms,
             "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+            "latency_ms_max": float(lat.max()),
             "loop_ms_per_iteration": loop_ms,
             "speedup_vs_loop": (loop_ms / it_ms) if loop_ms else None,
             "systems": len(systems), "limb_counts": kinds, "workspace_gib": ws.numel() / 2 ** 30,

@@ -493,6 +493,10 @@ md_status batch_prepare(int nsys, const md_system *sys, double *const *x, BatchP
   for (BatchClass &c : bp->classes)
     std::stable_sort(c.order.begin(), c.order.end(),
                      [&](int a, int b) { return job_cost(*plans[a]) > job_cost(*plans[b]); });
+  // the class holding the most expensive job first (it starts on the caller's stream)
+  std::stable_sort(bp->classes.begin(), bp->classes.end(), [&](const BatchClass &a, const BatchClass &b) {
+    return job_cost(*plans[a.order.front()]) > job_cost(*plans[b.order.front()]);
+  });
   // layout
   size_t o = 256;
   bp->off_jobs = o;
@@ -618,17 +622,42 @@ mdk::BatchDev batch_dev(const BatchPlan &bp, const BatchClass &c, int ci, char *
   return b;
 }
 
+struct DevAux;
+DevAux *aux_for_current_device();
+std::mutex *aux_mutex(DevAux *a);
+cudaStream_t aux_stream(DevAux *a);
+cudaEvent_t aux_event(DevAux *a, int i);
+
+// Class 0 (the one with the most expensive job, see batch_prepare) runs on
+// the caller's stream; the other classes run on the library's second stream,
+// concurrently: their CTAs take the SMs that class 0's CTAs release while its
+// longest jobs finish.
 cudaError_t batch_enqueue(const BatchPlan &bp, char *base, double *nrm, unsigned long long *times, cudaStream_t s,
                           int sms) {
   cudaError_t e = cudaMemcpyAsync(base + bp.off_jobs, bp.pinned, bp.image_bytes, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(base, 0, 256, s)) != cudaSuccess) return e;
+  DevAux *ax = bp.classes.size() > 1 ? aux_for_current_device() : nullptr;
+  if (!ax) {
+    for (size_t ci = 0; ci < bp.classes.size(); ++ci) {
+      const BatchClass &c = bp.classes[ci];
+      mdk::BatchDev b = batch_dev(bp, c, (int)ci, base, nrm, times, 1, sms);
+      if ((e = dispatch(c.K, c.P, 4, &b, s)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  std::lock_guard<std::mutex> lk(*aux_mutex(ax));
+  cudaStream_t s2 = aux_stream(ax);
+  if ((e = cudaEventRecord(aux_event(ax, 0), s)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(s2, aux_event(ax, 0), 0)) != cudaSuccess)
+    return e;
   for (size_t ci = 0; ci < bp.classes.size(); ++ci) {
     const BatchClass &c = bp.classes[ci];
     mdk::BatchDev b = batch_dev(bp, c, (int)ci, base, nrm, times, 1, sms);
-    if ((e = dispatch(c.K, c.P, 4, &b, s)) != cudaSuccess) return e;
+    if ((e = dispatch(c.K, c.P, 4, &b, ci == 0 ? s : s2)) != cudaSuccess) return e;
   }
-  return cudaSuccess;
+  if ((e = cudaEventRecord(aux_event(ax, 1), s2)) != cudaSuccess) return e;
+  return cudaStreamWaitEvent(s, aux_event(ax, 1), 0);
 }
 
 // Picks (threads per CTA, CTAs per SM) per precision class by timing trial
@@ -755,6 +784,10 @@ DevAux *aux_for_current_device() {
   }
   return &a;
 }
+
+std::mutex *aux_mutex(DevAux *a) { return &a->mu; }
+cudaStream_t aux_stream(DevAux *a) { return a->s2; }
+cudaEvent_t aux_event(DevAux *a, int i) { return i == 0 ? a->e0 : a->e1; }
 
 // SMs left to the factorisation while the evaluation runs resident.
 #ifndef MDK_FACTOR_SMS
