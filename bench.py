@@ -603,6 +603,16 @@ def run_batched(args):
             t = times.cpu().numpy()
             lat.append((t[:, 1] - t[:, 0]) / 1e6)
         torch.cuda.synchronize()
+        # the same step with every CTA sharing SMs, one class after another
+        # (no whole-SM systems, one stream)
+        sflags = flags | md.FLAG_SERIAL
+        md.newton_step_batched(sds, xs, ws, nrm, None, flags=sflags, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        md.newton_step_batched(sds, xs, ws, nrm, None, flags=sflags, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        serial_ms = e0.elapsed_time(e1)
     assert md.device_status(ws) == 0
     lat = np.concatenate(lat)
     it_ms = sum(ms) / len(ms)
@@ -630,6 +640,7 @@ def run_batched(args):
             "system_steps_per_s": len(systems) * 1e3 / it_ms,
             "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
             "latency_ms_max": float(lat.max()),
+            "shared_sm_only_ms_per_iteration": serial_ms,
             "loop_ms_per_iteration": loop_ms,
             "speedup_vs_loop": (loop_ms / it_ms) if loop_ms else None,
             "systems": len(systems), "limb_counts": kinds, "workspace_gib": ws.numel() / 2 ** 30,

@@ -103,8 +103,9 @@ typedef struct md_system {
  * workspace reported for this flag.
  */
 #define MD_FLAG_OZAKI 0x1
-/* batched form: pick CTAs per SM per precision class by timing trial steps
-   (first call only; trial steps do not update x) */
+/* batched form: pick threads per CTA and CTAs per SM per precision class, and
+   the threads of the whole-SM CTAs, by timing trial steps (first call only;
+   trial steps do not update x) */
 #define MD_FLAG_AUTOTUNE 0x2
 /* batched form: capture the step (plan upload + persistent launches) in a CUDA
    graph on the first call and replay it on later calls with the same arguments
@@ -113,7 +114,9 @@ typedef struct md_system {
 /* single-system step: run every phase on `stream` in order.  By default the
    factorisation of A_0 runs on a second (library-owned, highest-priority)
    stream on a few SMs while the higher coefficients are evaluated on the rest;
-   results are identical either way. */
+   results are identical either way.  Batched form: no whole-SM systems (every
+   launch on `stream`, see md_newton_series_step_batched); results are
+   identical either way. */
 #define MD_FLAG_SERIAL 0x8
 /* factor A_0 by LU with partial pivoting (Section 4: for N = n "an LU
    factorization can be applied") instead of Householder QR.  Pivot: the first
@@ -220,6 +223,12 @@ md_status md_newton_series_step(const md_system *sys, double *x, double *dx_norm
  * precision class: each CTA takes the next system from an atomic job counter
  * (most expensive first) and runs its whole step; there are no waits between
  * CTAs.  Every system gets the same bits as md_newton_series_step on it alone.
+ * The classes run one after another; a class runs at most a set number of
+ * CTAs per SM (autotuned, else 2).  When that number is above one, the
+ * systems of the first class whose step on a shared SM would outlast an even
+ * share of the batch over the SMs each run in a CTA that holds a whole SM, on
+ * `stream`, while the others share the remaining SMs from a second
+ * (library-owned) stream that `stream` waits for.
  *   sys:     HOST array of nsys systems (structure host, values device)
  *   x:       HOST array of nsys DEVICE pointers, each [P][K][n][d+1], updated
  *   dx_norm: DEVICE double[nsys][2] or NULL (per system, as in the single step)
@@ -227,7 +236,7 @@ md_status md_newton_series_step(const md_system *sys, double *x, double *dx_norm
  *            nanoseconds at the start and end of each system's step
  *   ws:      DEVICE workspace of md_batched_workspace_bytes() bytes; the status
  *            word covers the whole batch
- *   flags:   MD_FLAG_AUTOTUNE, MD_FLAG_GRAPH
+ *   flags:   MD_FLAG_AUTOTUNE, MD_FLAG_GRAPH, MD_FLAG_SERIAL
  */
 size_t md_batched_workspace_bytes(int nsys, const md_system *sys, int flags);
 md_status md_newton_series_step_batched(int nsys, const md_system *sys, double *const *x, double *dx_norm,

@@ -1,13 +1,16 @@
 // Batched form: many independent systems of uneven dimension n and degree d,
-// one Newton step each, in one persistent launch per precision class.
+// one Newton step each, in persistent launches per precision class.
 //
-// Every CTA (128 threads) takes the next system from an atomic job counter
-// (systems listed longest first) and runs that system's whole step: series
-// products stage by stage, accumulation of f and A, Householder QR of A_0 with
-// Q^H, W = R^-1 Q^H, the degree loop of the block Toeplitz solve and the update
-// of x -- with __syncthreads between phases and no waiting on other CTAs, so
-// nothing can hang.  The per-item bodies and reduction trees are those of the
-// one-system kernels, so every system gets the same bits as a single-system step.
+// Every CTA (128 to 384 threads) takes the next system from an atomic job
+// counter (systems listed longest first) and runs that system's whole step:
+// series products stage by stage, accumulation of f and A, Householder QR of
+// A_0 with Q^H, W = R^-1 Q^H, the degree loop of the block Toeplitz solve and
+// the update of x -- with __syncthreads between phases and no waiting on other
+// CTAs, so nothing can hang.  The per-item bodies and reduction trees are
+// those of the one-system kernels, so every system gets the same bits as a
+// single-system step.  The most expensive systems may run in a launch whose
+// CTAs each hold a whole SM (see batched_cap_bytes); the others share SMs.
+
 #pragma once
 #include "kernels.cuh"
 
@@ -24,16 +27,44 @@ constexpr int kBatchThreads = 128;
 constexpr int kBatchMaxThreads = 384;
 
 template <int K, int P>
+__global__ void batched_step_kernel(const BatchJob *__restrict__ jobs, const int *__restrict__ order, int njobs,
+                                    int *__restrict__ counter, const int *ibase, double *dbase,
+                                    double *__restrict__ nrm, unsigned long long *__restrict__ times,
+                                    int *__restrict__ status, int update_x, int *__restrict__ resident);
+
+// Dynamic shared memory per CTA of the batched kernel that lets at most
+// `cps` CTAs share an SM: the SM's shared memory split cps ways, less the
+// per-CTA reserve and the kernel's static shared memory (cps = 1: the CTA
+// holds a whole SM).  The kernel does not use it; it only bounds residency,
+// which registers alone would leave at up to four CTAs per SM.
+template <int K, int P>
+inline int batched_cap_bytes(int cps) {
+  int dev = 0, per_sm = 0, resv = 0, optin = 0;
+  cudaFuncAttributes fa;
+  if (cps < 1 || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, batched_step_kernel<K, P>) != cudaSuccess)
+    return 0;
+  const int room = optin - (int)fa.sharedSizeBytes;
+  const int b = per_sm / cps - resv - (int)fa.sharedSizeBytes;
+  return b <= 0 ? 0 : (b < room ? b : room);
+}
+
+template <int K, int P>
 __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const BatchJob *__restrict__ jobs,
                                                                      const int *__restrict__ order, int njobs,
                                                                      int *__restrict__ counter,
                                                                      const int *ibase, double *dbase,
                                                                      double *__restrict__ nrm,
                                                                      unsigned long long *__restrict__ times,
-                                                                     int *__restrict__ status, int update_x) {
+                                                                     int *__restrict__ status, int update_x,
+                                                                     int *__restrict__ resident) {
   __shared__ int s_job;
   __shared__ double s_row[kRowLanes][K];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NT = blockDim.x, nwarp = NT / 32;
+  if (resident && tid == 0) atomicAdd(resident, 1);
   for (;;) {
     if (tid == 0) s_job = atomicAdd(counter, 1);
     __syncthreads();
@@ -69,10 +100,10 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
       for (long long it = tid; it < items; it += NT) {
         const int o = o0 + (int)(it / npairs), p = (int)(it % npairs);
         const int out = ops[3 * o], a = ops[3 * o + 1], b = ops[3 * o + 2];
-        if (2 * p < d)
-          conv_pair<K, P, false>(pool, d, out, a, b, p, out, a, b);
-        else
-          conv_pair<K, P, false>(pool, d, out, a, b, p, -1, -1, -1);
+        // one call for both kinds of item: two inlined copies would run one
+        // after the other in a warp that holds both
+        const bool pair = 2 * p < d;
+        conv_pair<K, P, false>(pool, d, out, a, b, p, pair ? out : -1, pair ? a : -1, pair ? b : -1);
       }
       __syncthreads();
     }

@@ -42,6 +42,9 @@ cudaError_t dispatch_p(int P, int what, const void *a, cudaStream_t s, int op = 
       case 7: return mdk::Impl<K, 1>::factor(*static_cast<const SolveDev *>(a), s);
       case 8: return mdk::Impl<K, 1>::degrees(*static_cast<const SolveDev *>(a), s);
       case 9: return mdk::Impl<K, 1>::rcond(*static_cast<const SolveDev *>(a), s);
+      case 10:
+        if constexpr (K <= mdk::kBatchMaxLimbs) return mdk::Impl<K, 1>::batched_setup();
+        return cudaErrorNotSupported;
     }
   } else {
     switch (what) {
@@ -57,6 +60,9 @@ cudaError_t dispatch_p(int P, int what, const void *a, cudaStream_t s, int op = 
       case 7: return mdk::Impl<K, 2>::factor(*static_cast<const SolveDev *>(a), s);
       case 8: return mdk::Impl<K, 2>::degrees(*static_cast<const SolveDev *>(a), s);
       case 9: return mdk::Impl<K, 2>::rcond(*static_cast<const SolveDev *>(a), s);
+      case 10:
+        if constexpr (K <= mdk::kBatchMaxLimbs) return mdk::Impl<K, 2>::batched_setup();
+        return cudaErrorNotSupported;
     }
   }
   return cudaErrorInvalidValue;
@@ -156,18 +162,43 @@ uint64_t fnv(uint64_t h, const void *p, size_t bytes) {
 // Number of polynomials N >= n (neq = 0 means N = n).
 int neq_of(const md_system *s) { return s->neq ? s->neq : s->n; }
 
+// Hash of a byte range, eight bytes at a time in four independent
+// multiply-xorshift lanes (the FNV prime as multiplier), folded with the
+// length: the structure of a large batch is hashed on every call, and byte-wise
+// FNV took tenths of a second there.
+uint64_t hash_bytes(uint64_t h, const void *p, size_t bytes) {
+  const unsigned char *c = static_cast<const unsigned char *>(p);
+  const uint64_t prime = 1099511628211ULL;
+  uint64_t l[4] = {h, h ^ 0x9e3779b97f4a7c15ULL, h ^ 0xbf58476d1ce4e5b9ULL, h ^ 0x94d049bb133111ebULL};
+  size_t i = 0;
+  for (; i + 32 <= bytes; i += 32)
+    for (int k = 0; k < 4; ++k) {
+      uint64_t w;
+      std::memcpy(&w, c + i + 8 * k, 8);
+      l[k] = (l[k] ^ w) * prime;
+      l[k] ^= l[k] >> 29;
+    }
+  uint64_t r = fnv(l[0], c + i, bytes - i);
+  for (int k = 1; k < 4; ++k) {
+    r = (r ^ l[k]) * prime;
+    r ^= r >> 29;
+  }
+  return (r ^ (uint64_t)bytes) * prime;
+}
+
 uint64_t structure_checksum(const md_system *s) {
   uint64_t h = 1469598103934665603ULL;
   const int hdr[6] = {s->limbs, s->is_complex, s->n, s->degree, s->nmono, neq_of(s)};
   h = fnv(h, hdr, sizeof(hdr));
-  h = fnv(h, s->poly_ptr, sizeof(int) * (neq_of(s) + 1));
-  h = fnv(h, s->nvar, sizeof(int) * s->nmono);
-  h = fnv(h, s->idx, sizeof(int) * s->nmono * MD_MAXV);
-  h = fnv(h, s->expo, sizeof(int) * s->nmono * MD_MAXV);
+  h = hash_bytes(h, s->poly_ptr, sizeof(int) * (neq_of(s) + 1));
+  h = hash_bytes(h, s->nvar, sizeof(int) * s->nmono);
+  h = hash_bytes(h, s->idx, sizeof(int) * s->nmono * MD_MAXV);
+  h = hash_bytes(h, s->expo, sizeof(int) * s->nmono * MD_MAXV);
   return h;
 }
 
-md_status check_system(const md_system *s) {
+// Sizes, pointers and polynomial offsets (what the structure hash needs).
+md_status check_system_header(const md_system *s) {
   if (!s || !valid_limbs(s->limbs) || s->n < 1 || s->degree < 0 || s->nmono < 0) return MD_ERR_ARG;
   if (s->neq != 0 && s->neq < s->n) return MD_ERR_ARG;
   if (!s->poly_ptr || (s->nmono > 0 && (!s->nvar || !s->idx || !s->expo || !s->coef)) || !s->cst) return MD_ERR_ARG;
@@ -175,6 +206,12 @@ md_status check_system(const md_system *s) {
   if (s->poly_ptr[0] != 0 || s->poly_ptr[N] != s->nmono) return MD_ERR_ARG;
   for (int i = 0; i < N; ++i)
     if (s->poly_ptr[i + 1] < s->poly_ptr[i]) return MD_ERR_ARG;
+  return MD_OK;
+}
+
+md_status check_system(const md_system *s) {
+  const md_status st = check_system_header(s);
+  if (st != MD_OK) return st;
   for (int m = 0; m < s->nmono; ++m) {
     if (s->nvar[m] < 0 || s->nvar[m] > MD_MAXV) return MD_ERR_ARG;
     for (int q = 0; q < s->nvar[m]; ++q) {
@@ -407,13 +444,16 @@ md_status prepare(const md_system *s, void *ws, size_t ws_bytes, cudaStream_t st
 
 // ------------------------------------------------------------ batched form
 // Host plans of single systems, cached by structure checksum (no pinned image).
+// A structure already in the cache passed the full check when it was planned:
+// only the header is checked again.
 Plan *plan_of(const md_system *s, md_status &st) {
-  st = check_system(s);
+  st = check_system_header(s);
   if (st != MD_OK) return nullptr;
   const uint64_t cs = structure_checksum(s);
   std::lock_guard<std::mutex> lk(g_mu);
   auto it = g_plans.find(cs);
   if (it != g_plans.end()) return &it->second->plan;
+  if ((st = check_system(s)) != MD_OK) return nullptr;
   std::unique_ptr<PlanEntry> e(new PlanEntry);
   st = build_plan(s, e->plan, 0);
   if (st != MD_OK) return nullptr;
@@ -424,14 +464,17 @@ Plan *plan_of(const md_system *s, md_status &st) {
 
 struct BatchClass {
   int K = 0, P = 0;
-  std::vector<int> order;  // job indices, most expensive first
-  size_t order_off = 0;    // int offset from off_orders
-  int cps = 2;             // CTAs per SM (autotuned)
-  int threads = 128;       // threads per CTA (autotuned)
+  std::vector<int> order;    // job indices, most expensive first
+  std::vector<double> cost;  // job_cost of order[q]
+  size_t order_off = 0;      // int offset from off_orders
+  int cps = 2;               // CTAs per SM (autotuned)
+  int threads = 128;         // threads per CTA (autotuned)
+  int big_threads = 384;     // threads of the whole-SM CTAs (autotuned)
 };
 
 struct BatchPlan {
   int nsys = 0;
+  double total_cost = 0;  // sum of job_cost over the batch
   std::vector<mdk::BatchJob> jobs;
   std::vector<BatchClass> classes;
   size_t off_jobs = 0, off_orders = 0, off_ibase = 0, off_dbase = 0, total = 0;
@@ -441,6 +484,7 @@ struct BatchPlan {
   cudaGraphExec_t exec = nullptr;
   const void *exec_ws = nullptr, *exec_nrm = nullptr, *exec_times = nullptr;
   cudaStream_t exec_stream = nullptr;
+  bool exec_split = false;
 };
 std::map<uint64_t, BatchPlan *> g_batch;
 
@@ -490,10 +534,15 @@ md_status batch_prepare(int nsys, const md_system *sys, double *const *x, BatchP
     }
     bp->classes[cls_of[key2]].order.push_back(i);
   }
-  for (BatchClass &c : bp->classes)
+  for (BatchClass &c : bp->classes) {
     std::stable_sort(c.order.begin(), c.order.end(),
                      [&](int a, int b) { return job_cost(*plans[a]) > job_cost(*plans[b]); });
-  // the class holding the most expensive job first (it starts on the caller's stream)
+    for (int j : c.order) {
+      c.cost.push_back(job_cost(*plans[j]));
+      bp->total_cost += c.cost.back();
+    }
+  }
+  // the class holding the most expensive job first (its largest systems start first; only it gets whole-SM CTAs)
   std::stable_sort(bp->classes.begin(), bp->classes.end(), [&](const BatchClass &a, const BatchClass &b) {
     return job_cost(*plans[a.order.front()]) > job_cost(*plans[b.order.front()]);
   });
@@ -603,23 +652,58 @@ int device_smem_optin() {
   return v;
 }
 
-mdk::BatchDev batch_dev(const BatchPlan &bp, const BatchClass &c, int ci, char *base, double *nrm,
-                        unsigned long long *times, int update_x, int sms, int njobs_cap = -1) {
+// Job counters of the batched launches: ints at base + 64 (cleared with the
+// status word by the 256-byte memset of every step).  Class ci's shared-SM
+// launch counts at [ci] (at most 20 classes), the whole-SM launch at
+// [kBigCounter]; its CTAs count themselves in at [kResidentCounter].
+constexpr int kBigCounter = 24, kResidentCounter = 25;
+
+// Launch of class c over its jobs order[first, first + count): `grid` CTAs
+// of `threads`, at most `cps` of them on one SM.
+mdk::BatchDev batch_dev(const BatchPlan &bp, const BatchClass &c, int ctr, int first, int count, char *base,
+                        double *nrm, unsigned long long *times, int update_x, int grid, int threads, int cps) {
   mdk::BatchDev b;
   b.jobs = reinterpret_cast<const mdk::BatchJob *>(base + bp.off_jobs);
-  b.order = reinterpret_cast<const int *>(base + bp.off_orders) + c.order_off;
-  b.njobs = (int)c.order.size();
-  if (njobs_cap >= 0) b.njobs = std::min(b.njobs, njobs_cap);
-  b.counter = reinterpret_cast<int *>(base + 64) + ci;
+  b.order = reinterpret_cast<const int *>(base + bp.off_orders) + c.order_off + first;
+  b.njobs = count;
+  b.counter = reinterpret_cast<int *>(base + 64) + ctr;
   b.ibase = reinterpret_cast<const int *>(base + bp.off_ibase);
   b.dbase = reinterpret_cast<double *>(base + bp.off_dbase);
   b.nrm = nrm;
   b.times = times;
   b.status = reinterpret_cast<int *>(base);
   b.update_x = update_x;
-  b.grid = sms * c.cps;
-  b.threads = c.threads;
+  b.grid = grid;
+  b.threads = threads;
+  b.ctas_per_sm = cps;
   return b;
+}
+
+// Systems of the first class (the one holding the most expensive system)
+// that get a whole SM each: the leading ones whose step on a shared SM
+// (cps CTAs) would take longer than an even share of the whole batch over
+// the SMs, cps * cost > total / sms.  At most sms - 1, so that one SM stays
+// for the gate and the shared CTAs; none when the class runs one CTA per SM
+// anyway.
+int big_jobs(const BatchPlan &bp, int sms) {
+  const BatchClass &c = bp.classes[0];
+  if (c.cps <= 1) return 0;
+  const double share = bp.total_cost / sms;
+  int nb = 0;
+  while (nb < (int)c.order.size() && nb < sms - 1 && c.cps * c.cost[nb] > share) ++nb;
+  return nb;
+}
+
+// Holds back the launches after it on its stream until `target` CTAs have
+// counted themselves in at `resident`, so that the whole-SM CTAs are placed
+// before CTAs that share SMs take the rest.  It only orders placement (no
+// result depends on it) and gives up after about a tenth of a second.
+__global__ void batch_gate_kernel(const int *resident, int target) {
+  if (threadIdx.x != 0) return;
+  for (int it = 0; it < 100000; ++it) {
+    if (*reinterpret_cast<const volatile int *>(resident) >= target) return;
+    __nanosleep(1000);
+  }
 }
 
 struct DevAux;
@@ -628,20 +712,24 @@ std::mutex *aux_mutex(DevAux *a);
 cudaStream_t aux_stream(DevAux *a);
 cudaEvent_t aux_event(DevAux *a, int i);
 
-// Class 0 (the one with the most expensive job, see batch_prepare) runs on
-// the caller's stream; the other classes run on the library's second stream,
-// concurrently: their CTAs take the SMs that class 0's CTAs release while its
-// longest jobs finish.
+// One step of the batch.  Every class runs in turn, in launches of
+// sms x cps CTAs with at most cps of them on one SM.  With `split` and
+// whole-SM systems in the first class (big_jobs), those run on the caller's
+// stream in CTAs that each hold a whole SM, and on the library's second
+// stream a gate waits until those CTAs are placed before the shared-SM
+// launches take the other SMs (and each SM a whole-SM CTA leaves).
 cudaError_t batch_enqueue(const BatchPlan &bp, char *base, double *nrm, unsigned long long *times, cudaStream_t s,
-                          int sms) {
+                          int sms, bool split) {
   cudaError_t e = cudaMemcpyAsync(base + bp.off_jobs, bp.pinned, bp.image_bytes, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(base, 0, 256, s)) != cudaSuccess) return e;
-  DevAux *ax = bp.classes.size() > 1 ? aux_for_current_device() : nullptr;
+  const int nbig = split ? big_jobs(bp, sms) : 0;
+  DevAux *ax = nbig > 0 ? aux_for_current_device() : nullptr;
   if (!ax) {
     for (size_t ci = 0; ci < bp.classes.size(); ++ci) {
       const BatchClass &c = bp.classes[ci];
-      mdk::BatchDev b = batch_dev(bp, c, (int)ci, base, nrm, times, 1, sms);
+      mdk::BatchDev b =
+          batch_dev(bp, c, (int)ci, 0, (int)c.order.size(), base, nrm, times, 1, sms * c.cps, c.threads, c.cps);
       if ((e = dispatch(c.K, c.P, 4, &b, s)) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -651,44 +739,70 @@ cudaError_t batch_enqueue(const BatchPlan &bp, char *base, double *nrm, unsigned
   if ((e = cudaEventRecord(aux_event(ax, 0), s)) != cudaSuccess ||
       (e = cudaStreamWaitEvent(s2, aux_event(ax, 0), 0)) != cudaSuccess)
     return e;
+  {
+    const BatchClass &c = bp.classes[0];
+    int *ctr = reinterpret_cast<int *>(base + 64);
+    mdk::BatchDev b = batch_dev(bp, c, kBigCounter, 0, nbig, base, nrm, times, 1, nbig, c.big_threads, 1);
+    b.resident = ctr + kResidentCounter;
+    if ((e = dispatch(c.K, c.P, 4, &b, s)) != cudaSuccess) return e;
+    batch_gate_kernel<<<1, 32, 0, s2>>>(ctr + kResidentCounter, nbig);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   for (size_t ci = 0; ci < bp.classes.size(); ++ci) {
     const BatchClass &c = bp.classes[ci];
-    mdk::BatchDev b = batch_dev(bp, c, (int)ci, base, nrm, times, 1, sms);
-    if ((e = dispatch(c.K, c.P, 4, &b, ci == 0 ? s : s2)) != cudaSuccess) return e;
+    const int first = ci == 0 ? nbig : 0;
+    mdk::BatchDev b = batch_dev(bp, c, (int)ci, first, (int)c.order.size() - first, base, nrm, times, 1, sms * c.cps,
+                                c.threads, c.cps);
+    if ((e = dispatch(c.K, c.P, 4, &b, s2)) != cudaSuccess) return e;
   }
   if ((e = cudaEventRecord(aux_event(ax, 1), s2)) != cudaSuccess) return e;
   return cudaStreamWaitEvent(s, aux_event(ax, 1), 0);
 }
 
-// Picks (threads per CTA, CTAs per SM) per precision class by timing trial
-// steps that do not update x, on the first 3 x grid jobs of the class.  Only
-// shapes whose registers fit on an SM are tried.
-md_status batch_autotune(BatchPlan &bp, char *base, cudaStream_t s, int sms) {
+// Per precision class, picks the shape (threads per CTA, CTAs per SM) by
+// timing trial steps that do not update x on the same 4 x SMs of the class's
+// jobs (after any whole-SM ones) for every shape, and the threads of the whole-SM CTAs by timing one
+// launch over those.  Only shapes whose registers fit on an SM are tried.
+// Shapes are tried from the fewest CTAs per SM (the shortest time per
+// system, hence the shortest tail); one with more CTAs per SM must be 3%
+// faster per system to be taken.
+md_status batch_autotune(BatchPlan &bp, char *base, cudaStream_t s, int sms, bool split) {
   cudaEvent_t a, b;
   if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return MD_ERR_CUDA;
   if (cudaMemcpyAsync(base + bp.off_jobs, bp.pinned, bp.image_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return MD_ERR_CUDA;
-  const int shapes[][2] = {{128, 1}, {128, 2}, {128, 3}, {256, 1}, {384, 1}};
+  auto trial = [&](const BatchClass &c, mdk::BatchDev &d, float &ms) -> md_status {
+    ms = -1.f;
+    if (cudaMemsetAsync(base, 0, 256, s) != cudaSuccess) return MD_ERR_CUDA;
+    cudaEventRecord(a, s);
+    if (dispatch(c.K, c.P, 4, &d, s) != cudaSuccess) {  // shape does not fit: skip it
+      cudaGetLastError();
+      return MD_OK;
+    }
+    cudaEventRecord(b, s);
+    if (cudaEventSynchronize(b) != cudaSuccess) return MD_ERR_CUDA;
+    cudaEventElapsedTime(&ms, a, b);
+    return MD_OK;
+  };
+  const int nbig = split ? big_jobs(bp, sms) : 0;
+  const int shapes[][2] = {{384, 1}, {256, 1}, {128, 1}, {128, 2}, {128, 3}};
   for (size_t ci = 0; ci < bp.classes.size(); ++ci) {
     BatchClass &c = bp.classes[ci];
+    const int first = ci == 0 ? nbig : 0;
+    const int avail = (int)c.order.size() - first;
     float best = 1e30f;
-    int best_t = 128, best_cps = 2;
+    int best_t = c.threads, best_cps = c.cps;
     for (const auto &sh : shapes) {
+      if (avail <= 0) break;
       c.threads = sh[0];
       c.cps = sh[1];
-      if (cudaMemsetAsync(base, 0, 256, s) != cudaSuccess) return MD_ERR_CUDA;
-      mdk::BatchDev d = batch_dev(bp, c, (int)ci, base, nullptr, nullptr, 0, sms, 3 * sms * c.cps);
-      cudaEventRecord(a, s);
-      if (dispatch(c.K, c.P, 4, &d, s) != cudaSuccess) {  // shape does not fit: skip it
-        cudaGetLastError();
-        continue;
-      }
-      cudaEventRecord(b, s);
-      if (cudaEventSynchronize(b) != cudaSuccess) return MD_ERR_CUDA;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, a, b);
+      mdk::BatchDev d = batch_dev(bp, c, (int)ci, first, std::min(avail, 4 * sms), base, nullptr, nullptr, 0,
+                                  sms * c.cps, c.threads, c.cps);
+      float ms;
+      if (trial(c, d, ms) != MD_OK) return MD_ERR_CUDA;
+      if (ms < 0.f) continue;
       const float per_job = ms / (float)std::max(1, d.njobs);
-      if (per_job < best) {
+      if (per_job < (c.cps > best_cps ? 0.97f : 1.0f) * best) {
         best = per_job;
         best_t = c.threads;
         best_cps = c.cps;
@@ -696,6 +810,23 @@ md_status batch_autotune(BatchPlan &bp, char *base, cudaStream_t s, int sms) {
     }
     c.threads = best_t;
     c.cps = best_cps;
+  }
+  const int nbig2 = split ? big_jobs(bp, sms) : 0;
+  if (nbig2 > 0) {
+    BatchClass &c = bp.classes[0];
+    float best = 1e30f;
+    int best_t = c.big_threads;
+    for (int t : {256, 384}) {
+      c.big_threads = t;
+      mdk::BatchDev d = batch_dev(bp, c, kBigCounter, 0, nbig2, base, nullptr, nullptr, 0, nbig2, t, 1);
+      float ms;
+      if (trial(c, d, ms) != MD_OK) return MD_ERR_CUDA;
+      if (ms >= 0.f && ms < best) {
+        best = ms;
+        best_t = t;
+      }
+    }
+    c.big_threads = best_t;
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
@@ -1121,17 +1252,22 @@ md_status md_newton_series_step_batched(int nsys, const md_system *sys, double *
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   char *base = static_cast<char *>(ws);
   const int sms = device_sms();
+  const bool split = !(flags & MD_FLAG_SERIAL);
+  // shared-memory attributes of the batched kernels (not stream operations: kept out of any capture)
+  for (const BatchClass &c : bp->classes)
+    if (dispatch(c.K, c.P, 10, nullptr, s) != cudaSuccess) return MD_ERR_CUDA;
   if ((flags & MD_FLAG_AUTOTUNE) && !bp->tuned) {
-    st = batch_autotune(*bp, base, s, sms);
+    st = batch_autotune(*bp, base, s, sms, split);
     if (st != MD_OK) return st;
   }
   if ((flags & MD_FLAG_GRAPH) && s != nullptr) {
-    if (!bp->exec || bp->exec_ws != ws || bp->exec_nrm != dx_norm || bp->exec_times != times || bp->exec_stream != s) {
+    if (!bp->exec || bp->exec_ws != ws || bp->exec_nrm != dx_norm || bp->exec_times != times || bp->exec_stream != s ||
+        bp->exec_split != split) {
       if (bp->exec) cudaGraphExecDestroy(bp->exec);
       bp->exec = nullptr;
       cudaGraph_t g = nullptr;
       if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MD_ERR_CUDA;
-      const cudaError_t e = batch_enqueue(*bp, base, dx_norm, times, s, sms);
+      const cudaError_t e = batch_enqueue(*bp, base, dx_norm, times, s, sms, split);
       if (cudaStreamEndCapture(s, &g) != cudaSuccess || e != cudaSuccess) return MD_ERR_CUDA;
       if (cudaGraphInstantiate(&bp->exec, g, 0) != cudaSuccess) {
         cudaGraphDestroy(g);
@@ -1143,10 +1279,11 @@ md_status md_newton_series_step_batched(int nsys, const md_system *sys, double *
       bp->exec_nrm = dx_norm;
       bp->exec_times = times;
       bp->exec_stream = s;
+      bp->exec_split = split;
     }
     return cuda_status(cudaGraphLaunch(bp->exec, s));
   }
-  return cuda_status(batch_enqueue(*bp, base, dx_norm, times, s, sms));
+  return cuda_status(batch_enqueue(*bp, base, dx_norm, times, s, sms, split));
 }
 
 void md_profile_enable(int on) {

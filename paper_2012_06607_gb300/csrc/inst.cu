@@ -19,4 +19,5 @@ template cudaError_t mdk::Impl<MDK_K, MDK_P>::degrees(const mdk::SolveDev &, cud
 template cudaError_t mdk::Impl<MDK_K, MDK_P>::rcond(const mdk::SolveDev &, cudaStream_t);
 #elif MDK_PART == 3
 template cudaError_t mdk::Impl<MDK_K, MDK_P>::batched(const mdk::BatchDev &, cudaStream_t);
+template cudaError_t mdk::Impl<MDK_K, MDK_P>::batched_setup();
 #endif

@@ -125,11 +125,14 @@ struct BatchDev {
   int update_x = 1;
   int grid = 1;
   int threads = 128;
+  int ctas_per_sm = 0;      // > 0: dynamic shared memory lets at most this many CTAs share an SM
+  int *resident = nullptr;  // if set, every CTA adds 1 here when it starts
 };
 
 template <int K, int P>
 struct Impl {
   static cudaError_t batched(const BatchDev &b, cudaStream_t s);
+  static cudaError_t batched_setup();  // shared-memory attributes of the batched kernel (outside stream capture)
   static cudaError_t elementwise(int op, long long count, const double *x, const double *y, double *z,
                                  cudaStream_t s);
   static cudaError_t series_conv(int d, long long count, const double *x, const double *y, double *z,

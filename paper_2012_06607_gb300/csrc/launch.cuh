@@ -49,9 +49,25 @@ cudaError_t Impl<K, P>::batched(const BatchDev &b, cudaStream_t s) {
     return cudaErrorNotSupported;
   } else {
     if (b.njobs <= 0) return cudaSuccess;
-    batched_step_kernel<K, P><<<b.grid, b.threads, 0, s>>>(b.jobs, b.order, b.njobs, b.counter, b.ibase, b.dbase,
-                                                               b.nrm, b.times, b.status, b.update_x);
+    const int smem = b.ctas_per_sm > 0 ? batched_cap_bytes<K, P>(b.ctas_per_sm) : 0;
+    batched_step_kernel<K, P><<<b.grid, b.threads, smem, s>>>(b.jobs, b.order, b.njobs, b.counter, b.ibase, b.dbase,
+                                                                  b.nrm, b.times, b.status, b.update_x, b.resident);
     return cudaGetLastError();
+  }
+}
+
+template <int K, int P>
+cudaError_t Impl<K, P>::batched_setup() {
+  if constexpr (K > kBatchMaxLimbs) {
+    return cudaErrorNotSupported;
+  } else {
+    // room for the largest cap (one CTA per SM), and the largest shared-memory
+    // carveout, so that cps CTAs with their share fit on one SM
+    const cudaError_t e = cudaFuncSetAttribute(batched_step_kernel<K, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               batched_cap_bytes<K, P>(1));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(batched_step_kernel<K, P>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
   }
 }
 

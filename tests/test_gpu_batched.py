@@ -101,3 +101,35 @@ def test_batched_rejects_large_limbs(md):
     with pytest.raises(md.MdError) as e:
         md.newton_step_batched([sd], [x], ws)
     assert e.value.code == 8  # MD_ERR_UNSUPPORTED
+
+
+def _skewed_systems():
+    """A few systems much larger than the rest, so that the most expensive ones
+    get a whole SM while the rest of the same precision class share SMs."""
+    rng = np.random.default_rng(91)
+    out = [mdgen.small_system_fast(rng, 24, 12, 2, monos=24, name="big0"),
+           mdgen.small_system_fast(rng, 20, 10, 2, monos=20, name="big1")]
+    out += [mdgen.small_system_fast(rng, 8, 6, 2, monos=8, name=f"mid{b}") for b in range(4)]
+    out += [mdgen.small_system_fast(rng, int(rng.integers(2, 5)), int(rng.integers(1, 4)), 2, monos=4,
+                                    name=f"tiny{b}") for b in range(300)]
+    out += [mdgen.small_system_fast(rng, 4, 3, 4, monos=4, name=f"qd{b}") for b in range(40)]
+    return out
+
+
+def test_batched_whole_sm_split_equals_shared_and_single(md):
+    import torch
+
+    systems = _skewed_systems()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        split_x, split_n, times = _batched_steps(md, systems, 2, flags=md.FLAG_AUTOTUNE | md.FLAG_GRAPH, stream=stream)
+        shared_x, shared_n, _ = _batched_steps(md, systems, 2, flags=md.FLAG_SERIAL, stream=stream)
+    pick = [0, 1, 2, 5, 6, 100, 305, len(systems) - 1]
+    want_x, want_n = _single_steps(md, [systems[i] for i in pick], 2)
+    for i in range(len(systems)):
+        assert np.array_equal(split_x[i], shared_x[i]), (i, systems[i].name)
+        assert np.array_equal(split_n[i], shared_n[i]), (i, systems[i].name)
+    for j, i in enumerate(pick):
+        assert np.array_equal(split_x[i], want_x[j]), (i, systems[i].name)
+        assert np.array_equal(split_n[i], want_n[j]), (i, systems[i].name)
+    assert (times[:, 1] >= times[:, 0]).all() and (times[:, 0] > 0).all()
