@@ -613,9 +613,30 @@ def run_batched(args):
         e1.record(stream)
         e1.synchronize()
         serial_ms = e0.elapsed_time(e1)
+        # one more step (not timed) with a global-timer stamp after every phase
+        ptimes = torch.zeros((len(systems), md.PHASE_STAMPS), dtype=torch.int64, device="cuda")
+        md.newton_step_batched(sds, xs, ws, nrm, ptimes, flags=flags | md.FLAG_PHASE_TIMES, stream=stream)
+        torch.cuda.synchronize()
     assert md.device_status(ws) == 0
     lat = np.concatenate(lat)
     it_ms = sum(ms) / len(ms)
+    # phases of the slowest system, against the SM's share of the FP64 peak
+    pt = ptimes.cpu().numpy().astype(np.float64)
+    plat = pt[:, -1] - pt[:, 0]
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    slow = int(np.argmax(plat))
+    ph = dict(zip(md.PHASE_NAMES, np.diff(pt[slow]) / 1e6))
+    m = step_fp64_model(systems[slow])
+    per_sm = FP64_PEAK_INSTR / sms
+    spans = {"products": (m["conv"], ph["products"]), "accumulation": (m["accum"], ph["accumulation"]),
+             "qr": (m["qr"], ph["qr_setup"] + ph["householder_qr"]), "w": (m["backsub"], ph["rinv"] + ph["w"]),
+             "degree_loop": (m["update"], ph["degree_loop"])}
+    phases = {"system": {"index": slow, "n": systems[slow].n, "d": systems[slow].degree, "limbs": systems[slow].limbs},
+              "ms": {k: round(float(v), 3) for k, v in ph.items()},
+              "fraction_of_sm_fp64_peak": {k: round(float(c / (t / 1e3) / per_sm), 3) for k, (c, t) in spans.items()
+                                           if t > 0},
+              "sm_busy_fraction": float(plat.sum() / (sms * (pt[:, -1].max() - pt[:, 0].min()))),
+              "counted": "FP64 instructions of the bench's model per phase; stamps from MD_FLAG_PHASE_TIMES"}
     # per-system launch loop on the same systems (plain single-system steps)
     loop_ms = None
     if not args.no_loop:
@@ -641,6 +662,7 @@ def run_batched(args):
             "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
             "latency_ms_max": float(lat.max()),
             "shared_sm_only_ms_per_iteration": serial_ms,
+            "phases_of_slowest_system": phases,
             "loop_ms_per_iteration": loop_ms,
             "speedup_vs_loop": (loop_ms / it_ms) if loop_ms else None,
             "systems": len(systems), "limb_counts": kinds, "workspace_gib": ws.numel() / 2 ** 30,

@@ -124,6 +124,13 @@ typedef struct md_system {
    reciprocal of the pivot.  Single-system calls only (the batched form
    returns MD_ERR_UNSUPPORTED). */
 #define MD_FLAG_LU 0x10
+/* batched form: `times` holds MD_PHASE_STAMPS global-timer stamps per system
+   instead of 2: the start of its step, then the end of each phase -- x loaded
+   and coefficients scaled, series products, accumulation of f and A, QR
+   set-up, Householder QR, reciprocals of R's diagonal, W = R^-1 Q^H, degree
+   loop -- and the end (x updated).  Adds a few barriers per system. */
+#define MD_FLAG_PHASE_TIMES 0x20
+#define MD_PHASE_STAMPS 10
 
 /* Version of this ABI (major*100 + minor). */
 int md_version(void);
@@ -234,9 +241,10 @@ md_status md_newton_series_step(const md_system *sys, double *x, double *dx_norm
  *   dx_norm: DEVICE double[nsys][2] or NULL (per system, as in the single step)
  *   times:   DEVICE unsigned long long[nsys][2] or NULL: global-timer
  *            nanoseconds at the start and end of each system's step
+ *            ([nsys][MD_PHASE_STAMPS] with MD_FLAG_PHASE_TIMES)
  *   ws:      DEVICE workspace of md_batched_workspace_bytes() bytes; the status
  *            word covers the whole batch
- *   flags:   MD_FLAG_AUTOTUNE, MD_FLAG_GRAPH, MD_FLAG_SERIAL
+ *   flags:   MD_FLAG_AUTOTUNE, MD_FLAG_GRAPH, MD_FLAG_SERIAL, MD_FLAG_PHASE_TIMES
  */
 size_t md_batched_workspace_bytes(int nsys, const md_system *sys, int flags);
 md_status md_newton_series_step_batched(int nsys, const md_system *sys, double *const *x, double *dx_norm,

@@ -237,6 +237,10 @@ def newton_step(sysd: DeviceSystem, x, ws, dx_norm=None, flags: int = 0, stream=
 
 
 FLAG_OZAKI, FLAG_AUTOTUNE, FLAG_GRAPH, FLAG_SERIAL, FLAG_LU = 0x1, 0x2, 0x4, 0x8, 0x10
+FLAG_PHASE_TIMES = 0x20  # batched form: times is [nsys, PHASE_STAMPS]
+PHASE_STAMPS = 10
+PHASE_NAMES = ("load", "products", "accumulation", "qr_setup", "householder_qr", "rinv", "w", "degree_loop",
+               "finish")
 
 
 def rcond_a0(sysd: DeviceSystem, ws, flags: int = 0, out=None, stream=None):
@@ -325,7 +329,9 @@ def batched_workspace_bytes(systems, flags: int = 0) -> int:
 def newton_step_batched(systems, xs, ws, dx_norm=None, times=None, flags: int = 0, stream=None):
     """One Newton step for every system (DeviceSystem list) on its series xs[i]
     (CUDA tensors, updated in place).  dx_norm: CUDA double [nsys, 2] or None;
-    times: CUDA int64 [nsys, 2] (global-timer ns at start/end) or None."""
+    times: CUDA int64 [nsys, 2] (global-timer ns at start/end) or None;
+    [nsys, PHASE_STAMPS] with FLAG_PHASE_TIMES (start, the end of each phase
+    of PHASE_NAMES)."""
     arr = _sys_array(systems)
     xp = (ctypes.c_void_p * len(xs))(*[_ptr(x) for x in xs])
     _check(lib().md_newton_series_step_batched(len(systems), arr, xp, _ptr(dx_norm), _ptr(times), _ptr(ws),

@@ -22,6 +22,12 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
+// Called by every thread of the CTA at a phase boundary that all of them have
+// passed (after a __syncthreads); thread 0 writes the global timer.
+__device__ __forceinline__ void phase_stamp(bool on, unsigned long long *times, long long at) {
+  if (on && threadIdx.x == 0) times[at] = global_ns();
+}
+
 // CTA sizes of the batched kernel: kBatchThreads (default) up to kBatchMaxThreads.
 constexpr int kBatchThreads = 128;
 constexpr int kBatchMaxThreads = 384;
@@ -30,7 +36,7 @@ template <int K, int P>
 __global__ void batched_step_kernel(const BatchJob *__restrict__ jobs, const int *__restrict__ order, int njobs,
                                     int *__restrict__ counter, const int *ibase, double *dbase,
                                     double *__restrict__ nrm, unsigned long long *__restrict__ times,
-                                    int *__restrict__ status, int update_x, int *__restrict__ resident);
+                                    int *__restrict__ status, int update_x, int *__restrict__ resident, int tstride);
 
 // Dynamic shared memory per CTA of the batched kernel that lets at most
 // `cps` CTAs share an SM: the SM's shared memory split cps ways, less the
@@ -60,11 +66,13 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
                                                                      double *__restrict__ nrm,
                                                                      unsigned long long *__restrict__ times,
                                                                      int *__restrict__ status, int update_x,
-                                                                     int *__restrict__ resident) {
+                                                                     int *__restrict__ resident, int tstride) {
   __shared__ int s_job;
   __shared__ double s_row[kRowLanes][K];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NT = blockDim.x, nwarp = NT / 32;
   if (resident && tid == 0) atomicAdd(resident, 1);
+  // times: tstride stamps per system; with kPhaseStamps, one after each phase
+  const bool phases = times && tstride == kPhaseStamps;
   for (;;) {
     if (tid == 0) s_job = atomicAdd(counter, 1);
     __syncthreads();
@@ -75,7 +83,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
     const BatchJob J = jobs[job];
     const int n = J.n, d = J.d;
     if (tid == 0) {
-      if (times) times[2 * job] = global_ns();
+      if (times) times[(long long)tstride * job] = global_ns();
       if (nrm) {
         nrm[2 * job] = 0.0;
         nrm[2 * job + 1] = 0.0;
@@ -91,6 +99,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
     const long long Awords = (long long)P * K * (d + 1) * n * n;
     for (long long e = tid; e < Awords; e += NT) A[e] = 0.0;
     __syncthreads();
+    phase_stamp(phases, times, (long long)tstride * job + 1);
     const int *ops = ibase + J.ops;
     const int *soff = ibase + J.stage_off;
     const int npairs = (d + 2) / 2;  // coefficient pairs (k, d-k); the middle one alone when d is even
@@ -107,17 +116,20 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
       }
       __syncthreads();
     }
+    phase_stamp(phases, times, (long long)tstride * job + 2);
     const int4 *groups = reinterpret_cast<const int4 *>(ibase + J.groups);
     const int4 *contrib = reinterpret_cast<const int4 *>(ibase + J.contrib);
     for (long long e = tid; e < (long long)J.ngroups * (d + 1); e += NT)
       accum_entry<K, P>(groups, contrib, pool, scal, J.cst, f, A, n, n, d, (int)(e / (d + 1)), (int)(e % (d + 1)));
     __syncthreads();
+    phase_stamp(phases, times, (long long)tstride * job + 3);
     // ---- solve A(t) dx(t) = -f(t)
     double *M = dbase + J.M, *Y = dbase + J.Y, *W = dbase + J.W;
     double *vd = dbase + J.vd, *beta = dbase + J.beta, *rinv = dbase + J.rinv;
     double *r = dbase + J.r, *dxw = dbase + J.dxw, *part = dbase + J.part;
     for (long long e = tid; e < (long long)n * n; e += NT) solve_init_entry<K, P>(A, M, Y, n, n, d, e);
     __syncthreads();
+    phase_stamp(phases, times, (long long)tstride * job + 4);
     // QR in the order of the lookahead form (same arithmetic per column): H_j
     // on column j+1 by the whole CTA, on the other targets by warps, then the
     // Householder vector of column j+1
@@ -130,12 +142,16 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
       __syncthreads();
       if (ahead) house_block<K, P>(M, vd, beta, status, n, j + 1);
     }
+    if (phases) __syncthreads();
+    phase_stamp(phases, times, (long long)tstride * job + 5);
     for (int j = tid; j < n; j += NT) rinv_entry<K, P>(M, rinv, n, j);
     __syncthreads();
+    phase_stamp(phases, times, (long long)tstride * job + 6);
     for (int c = n - 1; c >= 0; --c) {
       for (long long e = tid; e < (long long)(c + 1) * n; e += NT) backsub_entry<K, P>(M, Y, W, rinv, n, c, e);
       __syncthreads();
     }
+    phase_stamp(phases, times, (long long)tstride * job + 7);
     for (int k = 0; k <= d; ++k) {
       int C, nchunk;
       rhs_chunking(n, n, k, C, nchunk);
@@ -145,10 +161,11 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
       for (int row = 0; row < n; ++row) rhs_finish_row<K, P>(f, -1.0, part, r, n, d, k, nchunk, row, s_row);
       for (int row = 0; row < n; ++row) wmv_row<K, P>(W, r, dxw, n, n, k, row, s_row);
     }
+    phase_stamp(phases, times, (long long)tstride * job + 8);
     for (long long e = tid; e < (long long)n * (d + 1); e += NT)
       finish_entry<K, P>(dxw, nullptr, update_x ? J.x : nullptr, nrm ? nrm + 2 * job : nullptr, status, n, d, e);
     __syncthreads();
-    if (tid == 0 && times) times[2 * job + 1] = global_ns();
+    if (tid == 0 && times) times[(long long)tstride * job + tstride - 1] = global_ns();
   }
 }
 

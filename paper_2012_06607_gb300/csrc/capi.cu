@@ -485,6 +485,7 @@ struct BatchPlan {
   const void *exec_ws = nullptr, *exec_nrm = nullptr, *exec_times = nullptr;
   cudaStream_t exec_stream = nullptr;
   bool exec_split = false;
+  int exec_tstride = 2;
 };
 std::map<uint64_t, BatchPlan *> g_batch;
 
@@ -657,6 +658,7 @@ int device_smem_optin() {
 // launch counts at [ci] (at most 20 classes), the whole-SM launch at
 // [kBigCounter]; its CTAs count themselves in at [kResidentCounter].
 constexpr int kBigCounter = 24, kResidentCounter = 25;
+static_assert(MD_PHASE_STAMPS == mdk::kPhaseStamps, "phase stamps of the ABI and the kernel differ");
 
 // Launch of class c over its jobs order[first, first + count): `grid` CTAs
 // of `threads`, at most `cps` of them on one SM.
@@ -719,7 +721,7 @@ cudaEvent_t aux_event(DevAux *a, int i);
 // stream a gate waits until those CTAs are placed before the shared-SM
 // launches take the other SMs (and each SM a whole-SM CTA leaves).
 cudaError_t batch_enqueue(const BatchPlan &bp, char *base, double *nrm, unsigned long long *times, cudaStream_t s,
-                          int sms, bool split) {
+                          int sms, bool split, int tstride) {
   cudaError_t e = cudaMemcpyAsync(base + bp.off_jobs, bp.pinned, bp.image_bytes, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(base, 0, 256, s)) != cudaSuccess) return e;
@@ -730,6 +732,7 @@ cudaError_t batch_enqueue(const BatchPlan &bp, char *base, double *nrm, unsigned
       const BatchClass &c = bp.classes[ci];
       mdk::BatchDev b =
           batch_dev(bp, c, (int)ci, 0, (int)c.order.size(), base, nrm, times, 1, sms * c.cps, c.threads, c.cps);
+      b.times_stride = tstride;
       if ((e = dispatch(c.K, c.P, 4, &b, s)) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -744,6 +747,7 @@ cudaError_t batch_enqueue(const BatchPlan &bp, char *base, double *nrm, unsigned
     int *ctr = reinterpret_cast<int *>(base + 64);
     mdk::BatchDev b = batch_dev(bp, c, kBigCounter, 0, nbig, base, nrm, times, 1, nbig, c.big_threads, 1);
     b.resident = ctr + kResidentCounter;
+    b.times_stride = tstride;
     if ((e = dispatch(c.K, c.P, 4, &b, s)) != cudaSuccess) return e;
     batch_gate_kernel<<<1, 32, 0, s2>>>(ctr + kResidentCounter, nbig);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -753,6 +757,7 @@ cudaError_t batch_enqueue(const BatchPlan &bp, char *base, double *nrm, unsigned
     const int first = ci == 0 ? nbig : 0;
     mdk::BatchDev b = batch_dev(bp, c, (int)ci, first, (int)c.order.size() - first, base, nrm, times, 1, sms * c.cps,
                                 c.threads, c.cps);
+    b.times_stride = tstride;
     if ((e = dispatch(c.K, c.P, 4, &b, s2)) != cudaSuccess) return e;
   }
   if ((e = cudaEventRecord(aux_event(ax, 1), s2)) != cudaSuccess) return e;
@@ -1253,6 +1258,7 @@ md_status md_newton_series_step_batched(int nsys, const md_system *sys, double *
   char *base = static_cast<char *>(ws);
   const int sms = device_sms();
   const bool split = !(flags & MD_FLAG_SERIAL);
+  const int tstride = (flags & MD_FLAG_PHASE_TIMES) ? mdk::kPhaseStamps : 2;
   // shared-memory attributes of the batched kernels (not stream operations: kept out of any capture)
   for (const BatchClass &c : bp->classes)
     if (dispatch(c.K, c.P, 10, nullptr, s) != cudaSuccess) return MD_ERR_CUDA;
@@ -1262,12 +1268,12 @@ md_status md_newton_series_step_batched(int nsys, const md_system *sys, double *
   }
   if ((flags & MD_FLAG_GRAPH) && s != nullptr) {
     if (!bp->exec || bp->exec_ws != ws || bp->exec_nrm != dx_norm || bp->exec_times != times || bp->exec_stream != s ||
-        bp->exec_split != split) {
+        bp->exec_split != split || bp->exec_tstride != tstride) {
       if (bp->exec) cudaGraphExecDestroy(bp->exec);
       bp->exec = nullptr;
       cudaGraph_t g = nullptr;
       if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MD_ERR_CUDA;
-      const cudaError_t e = batch_enqueue(*bp, base, dx_norm, times, s, sms, split);
+      const cudaError_t e = batch_enqueue(*bp, base, dx_norm, times, s, sms, split, tstride);
       if (cudaStreamEndCapture(s, &g) != cudaSuccess || e != cudaSuccess) return MD_ERR_CUDA;
       if (cudaGraphInstantiate(&bp->exec, g, 0) != cudaSuccess) {
         cudaGraphDestroy(g);
@@ -1280,10 +1286,11 @@ md_status md_newton_series_step_batched(int nsys, const md_system *sys, double *
       bp->exec_times = times;
       bp->exec_stream = s;
       bp->exec_split = split;
+      bp->exec_tstride = tstride;
     }
     return cuda_status(cudaGraphLaunch(bp->exec, s));
   }
-  return cuda_status(batch_enqueue(*bp, base, dx_norm, times, s, sms, split));
+  return cuda_status(batch_enqueue(*bp, base, dx_norm, times, s, sms, split, tstride));
 }
 
 void md_profile_enable(int on) {

@@ -94,6 +94,12 @@ __host__ __device__ inline void rhs_chunking(int N, int n, int k, int &C, int &n
   nchunk = (int)((terms + c - 1) / c);
 }
 
+// Stamps per system of the batched form with phase times: start, then after
+// loading x, the series products, the accumulation of f and A, the QR set-up,
+// the Householder QR, the reciprocals of R's diagonal, W = R^-1 Q^H and the
+// degree loop, then the end.  Without phase times: start and end.
+constexpr int kPhaseStamps = 10;
+
 // Largest limb count of the batched form (larger ones use the per-system step).
 constexpr int kBatchMaxLimbs = 5;
 
@@ -127,6 +133,7 @@ struct BatchDev {
   int threads = 128;
   int ctas_per_sm = 0;      // > 0: dynamic shared memory lets at most this many CTAs share an SM
   int *resident = nullptr;  // if set, every CTA adds 1 here when it starts
+  int times_stride = 2;     // stamps per system in times: 2 or kPhaseStamps
 };
 
 template <int K, int P>

@@ -51,7 +51,8 @@ cudaError_t Impl<K, P>::batched(const BatchDev &b, cudaStream_t s) {
     if (b.njobs <= 0) return cudaSuccess;
     const int smem = b.ctas_per_sm > 0 ? batched_cap_bytes<K, P>(b.ctas_per_sm) : 0;
     batched_step_kernel<K, P><<<b.grid, b.threads, smem, s>>>(b.jobs, b.order, b.njobs, b.counter, b.ibase, b.dbase,
-                                                                  b.nrm, b.times, b.status, b.update_x, b.resident);
+                                                                  b.nrm, b.times, b.status, b.update_x, b.resident,
+                                                                  b.times_stride);
     return cudaGetLastError();
   }
 }

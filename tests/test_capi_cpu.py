@@ -188,3 +188,15 @@ def test_lstsq_host_checks(mdlib):
     ca.neq = sa.N
     arr = (md.md_system * 1)(ca)
     assert mdlib.md_batched_workspace_bytes(1, arr, 0) == 0  # the batched form is square only
+
+
+def test_python_flags_match_header():
+    import re
+
+    import paper_2012_06607_gb300 as md
+
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "mdnewton.h")).read()
+    defs = {k: int(v, 0) for k, v in re.findall(r"#define\s+(MD_\w+)\s+(0x[0-9a-fA-F]+|\d+)\b", hdr)}
+    for name in ("OZAKI", "AUTOTUNE", "GRAPH", "SERIAL", "LU", "PHASE_TIMES"):
+        assert getattr(md, "FLAG_" + name) == defs["MD_FLAG_" + name], name
+    assert md.PHASE_STAMPS == defs["MD_PHASE_STAMPS"] == len(md.PHASE_NAMES) + 1

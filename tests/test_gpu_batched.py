@@ -133,3 +133,24 @@ def test_batched_whole_sm_split_equals_shared_and_single(md):
         assert np.array_equal(split_x[i], want_x[j]), (i, systems[i].name)
         assert np.array_equal(split_n[i], want_n[j]), (i, systems[i].name)
     assert (times[:, 1] >= times[:, 0]).all() and (times[:, 0] > 0).all()
+
+
+def test_batched_phase_times(md):
+    """MD_FLAG_PHASE_TIMES: ten ordered stamps per system, results unchanged."""
+    import torch
+
+    systems = _mixed_systems()[:10]
+    ref_x, ref_n, _ = _batched_steps(md, systems, 1)
+    sds = [md.DeviceSystem(s) for s in systems]
+    ws = md.workspace(md.batched_workspace_bytes(sds))
+    xs = [md.to_device(s.x0) for s in systems]
+    nrm = torch.zeros((len(systems), 2), dtype=torch.float64, device="cuda")
+    times = torch.zeros((len(systems), md.PHASE_STAMPS), dtype=torch.int64, device="cuda")
+    md.newton_step_batched(sds, xs, ws, nrm, times, flags=md.FLAG_PHASE_TIMES)
+    torch.cuda.synchronize()
+    assert md.device_status(ws) == 0
+    t = times.cpu().numpy()
+    assert (t[:, 0] > 0).all() and (np.diff(t, axis=1) >= 0).all()
+    for i in range(len(systems)):
+        assert np.array_equal(xs[i].cpu().numpy(), ref_x[i]), i
+        assert np.array_equal(nrm.cpu().numpy()[i], ref_n[i]), i
