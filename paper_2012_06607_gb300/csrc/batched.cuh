@@ -68,8 +68,12 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
                                                                      int *__restrict__ status, int update_x,
                                                                      int *__restrict__ resident, int tstride) {
   __shared__ int s_job;
-  __shared__ double s_row[kRowLanes][K];
+  // one reduction buffer per group of kRowLanes threads: the degree loop
+  // reduces that many rows at once
+  __shared__ double s_rows[kBatchMaxThreads / kRowLanes][kRowLanes][K];
+  double(*s_row)[K] = s_rows[0];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NT = blockDim.x, nwarp = NT / 32;
+  const int G = NT / kRowLanes, grp = tid / kRowLanes, gt = tid % kRowLanes;
   if (resident && tid == 0) atomicAdd(resident, 1);
   // times: tstride stamps per system; with kPhaseStamps, one after each phase
   const bool phases = times && tstride == kPhaseStamps;
@@ -158,8 +162,16 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
       for (long long e = tid; e < (long long)n * nchunk; e += NT)
         rhs_partial_item<K, P>(A, dxw, part, n, n, d, k, C, nchunk, e);
       __syncthreads();
-      for (int row = 0; row < n; ++row) rhs_finish_row<K, P>(f, -1.0, part, r, n, d, k, nchunk, row, s_row);
-      for (int row = 0; row < n; ++row) wmv_row<K, P>(W, r, dxw, n, n, k, row, s_row);
+      // G rows at a time, one per group; every row's tree is the one-row tree
+      for (int row0 = 0; row0 < n; row0 += G) {
+        const bool act = grp < G && row0 + grp < n;
+        rhs_finish_row<K, P>(f, -1.0, part, r, n, d, k, nchunk, act ? row0 + grp : 0, s_rows[act ? grp : 0], gt,
+                             kRowLanes, act);
+      }
+      for (int row0 = 0; row0 < n; row0 += G) {
+        const bool act = grp < G && row0 + grp < n;
+        wmv_row<K, P>(W, r, dxw, n, n, k, act ? row0 + grp : 0, s_rows[act ? grp : 0], gt, kRowLanes, act);
+      }
     }
     phase_stamp(phases, times, (long long)tstride * job + 8);
     for (long long e = tid; e < (long long)n * (d + 1); e += NT)

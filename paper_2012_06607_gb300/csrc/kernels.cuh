@@ -96,12 +96,14 @@ __device__ __forceinline__ void st_limbs(double *dst, const double (&z)[K]) {
   for (int l = 0; l < K; ++l) dst[l] = z[l];
 }
 
-// Pairwise sum of the first nleaf slots of every plane; all threads call it.
+// Pairwise sum of the first nleaf slots of every plane.  All threads of the
+// CTA call it; the gn threads of a group (gt = index in the group) work on
+// the group's sm, and groups with act false only take the barriers.
 template <int K, int P>
-__device__ __forceinline__ void row_tree(double (*sm)[K], int nleaf) {
+__device__ __forceinline__ void row_tree(double (*sm)[K], int nleaf, int gt, int gn, bool act) {
   constexpr int Vc = kRowLanes / P;
   for (int s = 1; s < nleaf; s <<= 1) {
-    for (int v = threadIdx.x; v < kRowLanes; v += blockDim.x) {
+    for (int v = gt; act && v < kRowLanes; v += gn) {
       const int cs = v % Vc;
       if ((cs & (2 * s - 1)) == 0 && cs + s < nleaf) {
         double a[K], b[K], z[K];
@@ -113,6 +115,11 @@ __device__ __forceinline__ void row_tree(double (*sm)[K], int nleaf) {
     }
     __syncthreads();
   }
+}
+
+template <int K, int P>
+__device__ __forceinline__ void row_tree(double (*sm)[K], int nleaf) {
+  row_tree<K, P>(sm, nleaf, threadIdx.x, blockDim.x, true);
 }
 
 // Plane p of the product a * b, computed as the complex product does it:
@@ -1013,14 +1020,16 @@ __global__ void rhs_partial_kernel(const double *__restrict__ A, const double *_
 }
 
 // r_k[row] = sgn * b_k[row] - (sum of the row's nchunk partials), row < N.
-// b: [P][K][N][d+1].  CTA body.
+// b: [P][K][N][d+1].  CTA body: a group of gn threads (gt = index in the
+// group) per row, as in row_tree.
 template <int K, int P>
 __device__ __forceinline__ void rhs_finish_row(const double *b, double sgn, const double *part, double *r, int N,
-                                               int d, int k, int nchunk, int row, double (*sm)[K]) {
+                                               int d, int k, int nchunk, int row, double (*sm)[K], int gt, int gn,
+                                               bool act) {
   constexpr int Vc = kRowLanes / P;
   const long long VS = P * K;
   const int nleaf = min(nchunk, Vc);
-  for (int v = threadIdx.x; v < kRowLanes; v += blockDim.x) {
+  for (int v = gt; act && v < kRowLanes; v += gn) {
     const int p = v / Vc, cs = v % Vc;
     if (cs < nleaf) {
       double acc[K], t[K];
@@ -1033,8 +1042,8 @@ __device__ __forceinline__ void rhs_finish_row(const double *b, double sgn, cons
     }
   }
   __syncthreads();
-  row_tree<K, P>(sm, nleaf);
-  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+  row_tree<K, P>(sm, nleaf, gt, gn, act);
+  for (int p = gt; act && p < P; p += gn) {
     double bv[K], a[K], z[K];
     const long long stride = (long long)N * (d + 1);
 #pragma unroll
@@ -1053,6 +1062,12 @@ __device__ __forceinline__ void rhs_finish_row(const double *b, double sgn, cons
 }
 
 template <int K, int P>
+__device__ __forceinline__ void rhs_finish_row(const double *b, double sgn, const double *part, double *r, int N,
+                                               int d, int k, int nchunk, int row, double (*sm)[K]) {
+  rhs_finish_row<K, P>(b, sgn, part, r, N, d, k, nchunk, row, sm, threadIdx.x, blockDim.x, true);
+}
+
+template <int K, int P>
 __global__ void __launch_bounds__(kRowLanes) rhs_finish_kernel(const double *__restrict__ b, double sgn,
                                                                const double *__restrict__ part,
                                                                double *__restrict__ r, int N, int d, int k,
@@ -1061,14 +1076,15 @@ __global__ void __launch_bounds__(kRowLanes) rhs_finish_kernel(const double *__r
   rhs_finish_row<K, P>(b, sgn, part, r, N, d, k, nchunk, blockIdx.x, sm);
 }
 
-// dx_k[row] = sum_{col < N} W[row][col] r_k[col], row < n.  CTA body.
+// dx_k[row] = sum_{col < N} W[row][col] r_k[col], row < n.  CTA body, with
+// groups as in rhs_finish_row.
 template <int K, int P>
 __device__ __forceinline__ void wmv_row(const double *W, const double *r, double *dx, int N, int n, int k, int row,
-                                        double (*sm)[K]) {
+                                        double (*sm)[K], int gt, int gn, bool act) {
   constexpr int Vc = kRowLanes / P;
   const long long VS = P * K;
   const int nleaf = min(N, Vc);
-  for (int v = threadIdx.x; v < kRowLanes; v += blockDim.x) {
+  for (int v = gt; act && v < kRowLanes; v += gn) {
     const int p = v / Vc, cs = v % Vc;
     if (cs < nleaf) {
       double acc[K], t[K];
@@ -1081,13 +1097,19 @@ __device__ __forceinline__ void wmv_row(const double *W, const double *r, double
     }
   }
   __syncthreads();
-  row_tree<K, P>(sm, nleaf);
-  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+  row_tree<K, P>(sm, nleaf, gt, gn, act);
+  for (int p = gt; act && p < P; p += gn) {
     double z[K];
     ld_limbs<K>(sm[p * Vc], z);
     st_limbs<K>(dx + ((long long)k * n + row) * VS + p * K, z);
   }
   __syncthreads();
+}
+
+template <int K, int P>
+__device__ __forceinline__ void wmv_row(const double *W, const double *r, double *dx, int N, int n, int k, int row,
+                                        double (*sm)[K]) {
+  wmv_row<K, P>(W, r, dx, N, n, k, row, sm, threadIdx.x, blockDim.x, true);
 }
 
 template <int K, int P>

@@ -49,6 +49,9 @@ cudaError_t Impl<K, P>::batched(const BatchDev &b, cudaStream_t s) {
     return cudaErrorNotSupported;
   } else {
     if (b.njobs <= 0) return cudaSuccess;
+    // the kernel splits its threads into groups of kRowLanes
+    if (b.threads < kRowLanes || b.threads % kRowLanes != 0 || b.threads > kBatchMaxThreads)
+      return cudaErrorInvalidValue;
     const int smem = b.ctas_per_sm > 0 ? batched_cap_bytes<K, P>(b.ctas_per_sm) : 0;
     batched_step_kernel<K, P><<<b.grid, b.threads, smem, s>>>(b.jobs, b.order, b.njobs, b.counter, b.ibase, b.dbase,
                                                                   b.nrm, b.times, b.status, b.update_x, b.resident,
