@@ -201,7 +201,7 @@ def reduce_max(dist, v: float) -> float:
 
 
 # ---------------------------------------------------------------- oracle leg
-def oracle_steps_per_s(s, steps: int, warmup: int):
+def oracle_steps_per_s(s, steps: int, warmup: int, want_x: bool = False):
     import oracle
 
     orc = oracle.Oracle(threads=os.cpu_count() or 1)
@@ -212,7 +212,28 @@ def oracle_steps_per_s(s, steps: int, warmup: int):
     for _ in range(steps):
         x, _ = orc.newton_step(s, x)
     dt = time.perf_counter() - t0
+    if want_x:
+        return steps / dt, orc.threads(), dt, x
     return steps / dt, orc.threads(), dt
+
+
+def err_vs_oracle(got, want) -> float:
+    """max over degrees k of max_i |got_ik - want_ik| / max_i |want_ik|, each
+    md number summed exactly over its limbs ([P][K][n][d+1] arrays)."""
+    from math import fsum
+
+    P, _, n, D1 = want.shape
+    worst = 0.0
+    for k in range(D1):
+        diff = scale = 0.0
+        for i in range(n):
+            dd = [fsum(list(got[p, :, i, k]) + [-v for v in want[p, :, i, k]]) for p in range(P)]
+            ww = [fsum(want[p, :, i, k]) for p in range(P)]
+            diff = max(diff, sum(v * v for v in dd) ** 0.5)
+            scale = max(scale, sum(v * v for v in ww) ** 0.5)
+        if scale > 0:
+            worst = max(worst, diff / scale)
+    return worst
 
 
 def run_reference(args):
@@ -379,9 +400,17 @@ def run_product(args):
         del ows, xo
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, dt = oracle_steps_per_s(s, 1, 0)
+        v, cores, dt, x_orc = oracle_steps_per_s(s, 1, 0, want_x=True)
         line["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
                                 "sample": "1 full Newton step of the workload from x0 (host cores, OpenMP)"}
+        # the same step on the GPU (outside the timed region), against the oracle's
+        x1 = md.to_device(s.x0, dev)
+        md.newton_step(sysd, x1, ws, nrm, flags=flags)
+        torch.cuda.synchronize()
+        e = err_vs_oracle(x1.cpu().numpy(), x_orc)
+        eps = 2.0 ** (-53 * s.limbs)
+        line["err_vs_oracle"] = {"max_rel": e, "max_rel_over_eps": e / eps, "eps": eps,
+                                 "measure": "one step from x0; per degree, max_i |x_gpu - x_oracle| / max_i |x_oracle|"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
