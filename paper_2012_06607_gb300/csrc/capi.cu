@@ -765,15 +765,22 @@ cudaError_t batch_enqueue(const BatchPlan &bp, char *base, double *nrm, unsigned
 }
 
 // Per precision class, picks the shape (threads per CTA, CTAs per SM) by
-// timing trial steps that do not update x on the same 4 x SMs of the class's
-// jobs (after any whole-SM ones) for every shape, and the threads of the whole-SM CTAs by timing one
-// launch over those.  Only shapes whose registers fit on an SM are tried.
-// Shapes are tried from the fewest CTAs per SM (the shortest time per
-// system, hence the shortest tail); one with more CTAs per SM must be 3%
-// faster per system to be taken.
+// timing trial steps that do not update x on the same first 4 x SMs of the
+// class's jobs (the most expensive ones) for every shape, then, if whole-SM
+// systems result, their threads by timing one launch over those.  Only
+// shapes whose registers fit on an SM are tried.  Shapes are tried from the
+// fewest CTAs per SM (the shortest time per system, hence the shortest
+// tail); one with more CTAs per SM must be 3% faster per system to be taken.
 md_status batch_autotune(BatchPlan &bp, char *base, cudaStream_t s, int sms, bool split) {
-  cudaEvent_t a, b;
-  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return MD_ERR_CUDA;
+  struct Events {  // destroyed on every return
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~Events() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } ev;
+  if (cudaEventCreate(&ev.a) != cudaSuccess || cudaEventCreate(&ev.b) != cudaSuccess) return MD_ERR_CUDA;
+  cudaEvent_t a = ev.a, b = ev.b;
   if (cudaMemcpyAsync(base + bp.off_jobs, bp.pinned, bp.image_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return MD_ERR_CUDA;
   auto trial = [&](const BatchClass &c, mdk::BatchDev &d, float &ms) -> md_status {
@@ -789,12 +796,11 @@ md_status batch_autotune(BatchPlan &bp, char *base, cudaStream_t s, int sms, boo
     cudaEventElapsedTime(&ms, a, b);
     return MD_OK;
   };
-  const int nbig = split ? big_jobs(bp, sms) : 0;
   const int shapes[][2] = {{384, 1}, {256, 1}, {128, 1}, {128, 2}, {128, 3}};
   for (size_t ci = 0; ci < bp.classes.size(); ++ci) {
     BatchClass &c = bp.classes[ci];
-    const int first = ci == 0 ? nbig : 0;
-    const int avail = (int)c.order.size() - first;
+    const int first = 0;
+    const int avail = (int)c.order.size();
     float best = 1e30f;
     int best_t = c.threads, best_cps = c.cps;
     for (const auto &sh : shapes) {
@@ -833,8 +839,6 @@ md_status batch_autotune(BatchPlan &bp, char *base, cudaStream_t s, int sms, boo
     }
     c.big_threads = best_t;
   }
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
   bp.tuned = true;
   bp.exec_ws = nullptr;  // configuration changed: recapture any graph
   return MD_OK;
