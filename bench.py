@@ -598,17 +598,38 @@ def run_elementwise(args):
     return 0
 
 
+def batched_shard(systems, rank: int, world: int):
+    """This rank's systems of the batch: the LPT partition of the host cost
+    estimates over the ranks (every rank computes the same partition; no
+    communication).  Returns (indices of this rank, the whole partition)."""
+    import paper_2012_06607_gb300 as md
+
+    if world <= 1:
+        return list(range(len(systems))), [list(range(len(systems)))]
+    parts = md.shard_lpt(md.batched_job_costs(systems), world)
+    return sorted(parts[rank]), parts
+
+
 def run_batched(args):
     """2048 complex systems, n ~ U{8..64}, d ~ U{8..32}, double double / quad
     double: one persistent launch per precision class per Newton iteration
-    (autotuned, replayed from a CUDA graph) against a per-system launch loop."""
+    (autotuned, replayed from a CUDA graph) against a per-system launch loop.
+    With N ranks the batch is split by LPT over the GPUs (strong scaling; no
+    collective on the data path) and the iteration time is the slowest
+    rank's."""
     import numpy as np
     import torch
 
     import mdgen
     import paper_2012_06607_gb300 as md
 
-    systems = mdgen.batch_systems(args.seed, count=args.batch)
+    rank, world, local = dist_env()
+    dist = dist_init(world)
+    if world > 1:
+        torch.cuda.set_device(local)
+    all_systems = mdgen.batch_systems(args.seed, count=args.batch)
+    mine, _ = batched_shard(all_systems, rank, world)
+    systems = [all_systems[i] for i in mine]
     sds = [md.DeviceSystem(s) for s in systems]
     flags = md.FLAG_AUTOTUNE | md.FLAG_GRAPH
     ws = md.workspace(md.batched_workspace_bytes(sds, flags))
@@ -623,6 +644,8 @@ def run_batched(args):
         ms = []
         lat = []
         for _ in range(args.steps):
+            if dist is not None:
+                dist.barrier()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             md.newton_step_batched(sds, xs, ws, nrm, times, flags=flags, stream=stream)
@@ -648,7 +671,7 @@ def run_batched(args):
         torch.cuda.synchronize()
     assert md.device_status(ws) == 0
     lat = np.concatenate(lat)
-    it_ms = sum(ms) / len(ms)
+    it_ms = reduce_max(dist, sum(ms) / len(ms))
     # phases of the slowest system, against the SM's share of the FP64 peak
     pt = ptimes.cpu().numpy().astype(np.float64)
     plat = pt[:, -1] - pt[:, 0]
@@ -668,7 +691,7 @@ def run_batched(args):
               "counted": "FP64 instructions of the bench's model per phase; stamps from MD_FLAG_PHASE_TIMES"}
     # per-system launch loop on the same systems (plain single-system steps)
     loop_ms = None
-    if not args.no_loop:
+    if not args.no_loop and world == 1:
         wmax = max(sd.workspace_bytes() for sd in sds)
         ws1 = md.workspace(wmax)
         xs1 = [md.to_device(s.x0) for s in systems]
@@ -681,28 +704,34 @@ def run_batched(args):
         torch.cuda.synchronize()
         loop_ms = (time.perf_counter() - t0) * 1e3
     kinds = {}
-    for s in systems:
+    for s in all_systems:
         kinds[s.limbs] = kinds.get(s.limbs, 0) + 1
-    models = [step_fp64_model(s) for s in systems]
+    models = [step_fp64_model(s) for s in all_systems]
     fp64 = {k: sum(m[k] for m in models) for k in models[0]}
     line = {"metric": "batched Newton iterations/s (2048 systems, n~U{8..64}, d~U{8..32}, dd/qd, complex)",
             "unit": "iterations/s", "value": 1e3 / it_ms, "ms_per_iteration": it_ms,
-            "system_steps_per_s": len(systems) * 1e3 / it_ms,
+            "system_steps_per_s": len(all_systems) * 1e3 / it_ms, "n_gpus": world,
+            "scaling": "strong" if world > 1 else "weak",
+            "parallelism": f"LPT shards of the batch x{world}" if world > 1 else "one GPU",
             "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
             "latency_ms_max": float(lat.max()),
             "shared_sm_only_ms_per_iteration": serial_ms,
             "phases_of_slowest_system": phases,
             "loop_ms_per_iteration": loop_ms,
             "speedup_vs_loop": (loop_ms / it_ms) if loop_ms else None,
-            "systems": len(systems), "limb_counts": kinds, "workspace_gib": ws.numel() / 2 ** 30,
+            "systems": len(all_systems), "systems_on_rank0": len(systems), "limb_counts": kinds,
+            "workspace_gib": ws.numel() / 2 ** 30,
             "roofline": {"bound": "alu", "achieved": fp64["total"] / (it_ms / 1e3) / 1e12,
-                         "peak": FP64_PEAK_INSTR / 1e12, "unit": "TFLOP/s",
-                         "frac": fp64["total"] / (it_ms / 1e3) / FP64_PEAK_INSTR,
+                         "peak": world * FP64_PEAK_INSTR / 1e12, "unit": "TFLOP/s",
+                         "frac": fp64["total"] / (it_ms / 1e3) / (world * FP64_PEAK_INSTR),
                          "counted": "FP64 instructions per iteration: series products exact, solve modelled",
                          "fp64_instr_per_iteration": fp64},
             "steps": args.steps, "warmup": args.warmup, "flags": "autotune+graph", "data": "synthetic",
             "dtype": "f64 (double double / quad double)"}
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
     return 0
 
 

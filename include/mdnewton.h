@@ -252,6 +252,20 @@ md_status md_newton_series_step_batched(int nsys, const md_system *sys, double *
                                         void *stream);
 
 /*
+ * Host-side cost estimate of each system's Newton step: the estimate the
+ * batched form orders its job queue by (most expensive first) and the one to
+ * partition a batch across GPUs by (longest processing time first).  It
+ * counts multiply-adds: series products (d+1)(d+2)/2 per product, 2 n^3 for
+ * the QR and W, n^2 d (d+1)/2 for the block Toeplitz update, one per
+ * coefficient and contribution for the accumulation; times K^2, and times 4
+ * for complex.  Host only (no device work); plans structures not seen before.
+ *   cost: HOST double[nsys], written
+ * Returns MD_ERR_ARG for nsys < 1, NULL pointers or an invalid system (cost
+ * is then unspecified).
+ */
+md_status md_batched_job_costs(int nsys, const md_system *sys, double *cost);
+
+/*
  * Synchronise `stream`, read the sticky device status word of `ws` (written by
  * the calls above that used this workspace), clear it and return it
  * (MD_OK, MD_ERR_SINGULAR or MD_ERR_NONFINITE).

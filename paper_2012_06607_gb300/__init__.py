@@ -76,6 +76,8 @@ def lib():
         L.md_get_device_status.argtypes = [vp, vp]
         L.md_batched_workspace_bytes.argtypes = [i, ctypes.POINTER(md_system), i]
         L.md_batched_workspace_bytes.restype = sz
+        L.md_batched_job_costs.argtypes = [i, ctypes.POINTER(md_system), ctypes.c_void_p]
+        L.md_batched_job_costs.restype = i
         L.md_newton_series_step_batched.argtypes = [i, ctypes.POINTER(md_system), ctypes.POINTER(vp), vp, vp, vp, sz,
                                                     i, vp]
         L.md_newton_series_step_batched.restype = i
@@ -111,7 +113,8 @@ def exported_symbols():
             "md_newton_series_step", "md_get_device_status", "md_batched_workspace_bytes",
             "md_newton_series_step_batched", "md_linsolve_series_static", "md_profile_enable",
             "md_profile_read", "md_profile_kind_name", "md_newton_run_workspace_bytes", "md_newton_series_run",
-            "md_rcond_a0", "md_linsolve_rcond", "md_lstsq_workspace_bytes", "md_lstsq_series", "md_lstsq_rcond"]
+            "md_rcond_a0", "md_linsolve_rcond", "md_lstsq_workspace_bytes", "md_lstsq_series", "md_lstsq_rcond",
+            "md_batched_job_costs"]
 
 
 # --------------------------------------------------------------- helpers
@@ -320,6 +323,54 @@ def _sys_array(systems):
     for i, sd in enumerate(systems):
         arr[i] = sd._c
     return arr
+
+
+def _host_md_system(s, keep) -> "md_system":
+    """md_system over host arrays of any object with its fields (the host
+    planning reads the structure only; coef and cst are never read there)."""
+    pp = np.ascontiguousarray(s.poly_ptr, dtype=np.int32)
+    nv = np.ascontiguousarray(s.nvar, dtype=np.int32)
+    ix = np.ascontiguousarray(s.idx, dtype=np.int32)
+    ex = np.ascontiguousarray(s.expo, dtype=np.int32)
+    cf = np.ascontiguousarray(s.coef, dtype=np.float64)
+    cs = np.ascontiguousarray(s.cst, dtype=np.float64)
+    keep += [pp, nv, ix, ex, cf, cs]
+    nm = int(nv.shape[0])
+    return md_system(int(s.limbs), int(bool(s.is_complex)), int(s.n), int(s.degree), nm, pp.ctypes.data,
+                     nv.ctypes.data if nm else None, ix.ctypes.data if nm else None, ex.ctypes.data if nm else None,
+                     cf.ctypes.data if nm else None, cs.ctypes.data, int(getattr(s, "neq", 0) or 0))
+
+
+def batched_job_costs(systems) -> np.ndarray:
+    """md_batched_job_costs: the host cost estimate of each system's step
+    (DeviceSystem, or any object with the md_system fields as arrays)."""
+    keep = []
+    arr = (md_system * len(systems))()
+    for i, sd in enumerate(systems):
+        arr[i] = sd._c if hasattr(sd, "_c") else _host_md_system(sd, keep)
+    out = np.zeros(len(systems), dtype=np.float64)
+    _check(lib().md_batched_job_costs(len(systems), arr, out.ctypes.data), "md_batched_job_costs")
+    return out
+
+
+def shard_lpt(costs, world: int):
+    """Partition of a batch over `world` GPUs, longest processing time first:
+    systems in decreasing cost (ties: lower index), each to the rank with the
+    least total cost so far (ties: lower rank).  Returns per rank its system
+    indices in that order.  Deterministic, so every rank computes the same
+    partition without communicating."""
+    import heapq
+
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    order = sorted(range(len(costs)), key=lambda i: (-float(costs[i]), i))
+    heap = [(0.0, r) for r in range(world)]
+    out = [[] for _ in range(world)]
+    for i in order:
+        load, r = heapq.heappop(heap)
+        out[r].append(i)
+        heapq.heappush(heap, (load + float(costs[i]), r))
+    return out
 
 
 def batched_workspace_bytes(systems, flags: int = 0) -> int:

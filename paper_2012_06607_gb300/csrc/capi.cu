@@ -1237,6 +1237,17 @@ md_status md_newton_series_run(const md_system *sys, double *x, const md_newton_
   return MD_OK;
 }
 
+md_status md_batched_job_costs(int nsys, const md_system *sys, double *cost) {
+  if (nsys < 1 || !sys || !cost) return MD_ERR_ARG;
+  for (int i = 0; i < nsys; ++i) {
+    md_status st;
+    const Plan *p = plan_of(&sys[i], st);
+    if (!p) return st;
+    cost[i] = job_cost(*p);
+  }
+  return MD_OK;
+}
+
 size_t md_batched_workspace_bytes(int nsys, const md_system *sys, int flags) {
   (void)flags;
   BatchPlan *bp = nullptr;

@@ -200,3 +200,21 @@ def test_python_flags_match_header():
     for name in ("OZAKI", "AUTOTUNE", "GRAPH", "SERIAL", "LU", "PHASE_TIMES"):
         assert getattr(md, "FLAG_" + name) == defs["MD_FLAG_" + name], name
     assert md.PHASE_STAMPS == defs["MD_PHASE_STAMPS"] == len(md.PHASE_NAMES) + 1
+
+
+def test_batched_job_costs_host_only():
+    """md_batched_job_costs needs no device: K^2 and complex x4 scaling, growth
+    with the degree, and argument errors."""
+    import paper_2012_06607_gb300 as md
+
+    base = mdgen.config_system(0, 1)  # double double complex, n = 3, d = 8
+    c2 = md.batched_job_costs([base])[0]
+    c4 = md.batched_job_costs([base.with_limbs(4)])[0]
+    assert c2 > 0 and c4 == pytest.approx(4.0 * c2)
+    rng = np.random.default_rng(3)
+    lo = mdgen.small_system_fast(rng, 6, 4, 2, monos=6)
+    hi = mdgen.small_system_fast(np.random.default_rng(3), 6, 12, 2, monos=6)
+    cl, ch = md.batched_job_costs([lo, hi])
+    assert ch > cl
+    arr = (md.md_system * 1)()
+    assert md.lib().md_batched_job_costs(0, arr, None) == 1  # MD_ERR_ARG

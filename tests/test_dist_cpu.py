@@ -66,3 +66,56 @@ def test_reference_arm_under_torchrun():
     line = json.loads(lines[0])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def _shard_worker(rank, world, port, out_dir):
+    import torch.distributed as dist
+
+    sys.path.insert(0, ROOT)
+    import bench
+    import mdgen
+
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank), MASTER_ADDR="127.0.0.1",
+                      MASTER_PORT=str(port))
+    r, w, _ = bench.dist_env()
+    d = bench.dist_init(w)
+    systems = mdgen.batch_systems(1, count=200)
+    mine, parts = bench.batched_shard(systems, r, w)
+    got = [None] * w
+    d.all_gather_object(got, {"mine": mine, "parts": parts})
+    if r == 0:
+        with open(os.path.join(out_dir, "shards.json"), "w") as fh:
+            json.dump(got, fh)
+    d.barrier()
+    d.destroy_process_group()
+
+
+def test_batched_lpt_shards_over_two_gloo_ranks(tmp_path):
+    """The batched form's multi-GPU split: every rank computes the same LPT
+    partition of the host cost estimates on its own; the shards are disjoint,
+    cover the batch, and their costs differ by at most the largest system's."""
+    import torch.multiprocessing as mp
+
+    import mdgen
+    import paper_2012_06607_gb300 as md
+
+    port = _free_port()
+    mp.start_processes(_shard_worker, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    got = json.load(open(tmp_path / "shards.json"))
+    assert got[0]["parts"] == got[1]["parts"]  # same partition on both ranks, no communication needed
+    mine = [set(g["mine"]) for g in got]
+    assert not (mine[0] & mine[1]) and (mine[0] | mine[1]) == set(range(200))
+    costs = md.batched_job_costs(mdgen.batch_systems(1, count=200))
+    loads = [sum(costs[i] for i in m) for m in mine]
+    assert abs(loads[0] - loads[1]) <= costs.max()
+
+
+def test_shard_lpt_small_cases():
+    import paper_2012_06607_gb300 as md
+
+    assert md.shard_lpt([5.0, 4.0, 3.0, 3.0, 3.0], 2) == [[0, 3], [1, 2, 4]]  # 8 and 10
+    assert md.shard_lpt([1.0, 1.0, 1.0], 1) == [[0, 1, 2]]
+    assert md.shard_lpt([], 3) == [[], [], []]
+    assert md.shard_lpt([2.0, 2.0], 4) == [[0], [1], [], []]
+    with pytest.raises(ValueError):
+        md.shard_lpt([1.0], 0)
