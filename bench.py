@@ -12,7 +12,8 @@ from x0 (the work per step does not depend on x).
 Timing: W untimed warm-up steps, then exactly K steps, each bracketed by CUDA
 events on the launching stream, L2 flushed (256 MB write) between steps outside
 the events; barrier + synchronize around the timed region; max over ranks.
-For N > 1 every rank runs its own replica (the single system does not shard).
+For N > 1 every rank runs its own replica (the single system does not shard);
+--form batched instead splits its batch over the ranks by LPT cost.
 
 --impl reference times the CPU oracle (oracle/, plain C, OpenMP over the
 paper's jobs) on the host cores for the same workload and metric.
