@@ -7,6 +7,7 @@
 #include <atomic>
 #include <cstdint>
 #include <cstring>
+#include <list>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -486,8 +487,40 @@ struct BatchPlan {
   cudaStream_t exec_stream = nullptr;
   bool exec_split = false;
   int exec_tstride = 2;
+  ~BatchPlan() {
+    // a step in flight may still read the pinned image, directly or from the graph
+    if (exec || pinned) cudaDeviceSynchronize();
+    if (exec) cudaGraphExecDestroy(exec);
+    if (pinned) cudaFreeHost(pinned);
+  }
 };
-std::map<uint64_t, BatchPlan *> g_batch;
+
+// Batch plans, keyed by the structures and the coefficient and x pointers.
+// Beyond kBatchPlanCache the least recently used are dropped, so that callers
+// who pass new buffers on every call do not accumulate pinned images; a call
+// holds its plan by shared_ptr.  Dropping a plan with a pinned image or a
+// graph synchronises the device, so it is skipped while the calling stream
+// is being captured (the cache may then exceed the bound for a while).
+constexpr size_t kBatchPlanCache = 16;
+std::map<uint64_t, std::shared_ptr<BatchPlan>> g_batch;
+std::list<uint64_t> g_batch_lru;  // most recently used first
+
+// Under g_mu.
+void batch_touch(uint64_t key) {
+  g_batch_lru.remove(key);
+  g_batch_lru.push_front(key);
+}
+
+// Under g_mu.
+void batch_evict(bool may_sync) {
+  for (auto it = g_batch_lru.end(); g_batch.size() > kBatchPlanCache && it != g_batch_lru.begin();) {
+    --it;
+    auto e = g_batch.find(*it);
+    if (!may_sync && (e->second->pinned || e->second->exec)) continue;
+    g_batch.erase(e);
+    it = g_batch_lru.erase(it);
+  }
+}
 
 double job_cost(const Plan &p) {
   const double n = p.n, d = p.d, D1 = d + 1;
@@ -497,7 +530,8 @@ double job_cost(const Plan &p) {
   return macs * per;
 }
 
-md_status batch_prepare(int nsys, const md_system *sys, double *const *x, BatchPlan *&out, bool need_image) {
+md_status batch_prepare(int nsys, const md_system *sys, double *const *x, std::shared_ptr<BatchPlan> &out,
+                        bool need_image, bool may_sync) {
   if (nsys < 1 || !sys) return MD_ERR_ARG;
   std::vector<Plan *> plans(nsys);
   uint64_t key = 1469598103934665603ULL;
@@ -516,10 +550,11 @@ md_status batch_prepare(int nsys, const md_system *sys, double *const *x, BatchP
     auto it = g_batch.find(key);
     if (it != g_batch.end() && (!need_image || it->second->pinned)) {
       out = it->second;
+      batch_touch(key);
       return MD_OK;
     }
   }
-  std::unique_ptr<BatchPlan> bp(new BatchPlan);
+  std::shared_ptr<BatchPlan> bp = std::make_shared<BatchPlan>();
   bp->nsys = nsys;
   bp->jobs.resize(nsys);
   // classes by (K, P), jobs ordered by decreasing cost
@@ -626,14 +661,11 @@ md_status batch_prepare(int nsys, const md_system *sys, double *const *x, BatchP
   }
   std::lock_guard<std::mutex> lk(g_mu);
   auto it = g_batch.find(key);
-  if (it != g_batch.end()) {
-    if (!it->second->pinned && bp->pinned) {
-      g_batch[key] = bp.release();  // the earlier size-only plan is replaced (leaked: tiny)
-    }
-  } else {
-    g_batch[key] = bp.release();
-  }
+  if (it == g_batch.end() || (!it->second->pinned && bp->pinned))
+    g_batch[key] = bp;  // new, or replaces a size-only plan
   out = g_batch[key];
+  batch_touch(key);
+  batch_evict(may_sync);
   return MD_OK;
 }
 
@@ -1250,8 +1282,8 @@ md_status md_batched_job_costs(int nsys, const md_system *sys, double *cost) {
 
 size_t md_batched_workspace_bytes(int nsys, const md_system *sys, int flags) {
   (void)flags;
-  BatchPlan *bp = nullptr;
-  if (batch_prepare(nsys, sys, nullptr, bp, false) != MD_OK) return 0;
+  std::shared_ptr<BatchPlan> bp;
+  if (batch_prepare(nsys, sys, nullptr, bp, false, false) != MD_OK) return 0;
   return bp->total;
 }
 
@@ -1265,11 +1297,13 @@ md_status md_newton_series_step_batched(int nsys, const md_system *sys, double *
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return MD_ERR_WORKSPACE;
   for (int i = 0; i < nsys; ++i)
     if (sys[i].limbs > mdk::kBatchMaxLimbs) return MD_ERR_UNSUPPORTED;
-  BatchPlan *bp = nullptr;
-  md_status st = batch_prepare(nsys, sys, x, bp, true);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return MD_ERR_CUDA;
+  std::shared_ptr<BatchPlan> bp;
+  md_status st = batch_prepare(nsys, sys, x, bp, true, cap == cudaStreamCaptureStatusNone);
   if (st != MD_OK) return st;
   if (bp->total > ws_bytes) return MD_ERR_WORKSPACE;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   char *base = static_cast<char *>(ws);
   const int sms = device_sms();
   const bool split = !(flags & MD_FLAG_SERIAL);

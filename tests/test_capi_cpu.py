@@ -218,3 +218,19 @@ def test_batched_job_costs_host_only():
     assert ch > cl
     arr = (md.md_system * 1)()
     assert md.lib().md_batched_job_costs(0, arr, None) == 1  # MD_ERR_ARG
+
+
+def test_batched_plan_cache_bound_host_only():
+    """Workspace queries over many distinct batches (new coefficient pointers
+    each time) stay correct while the batch plan cache drops old entries."""
+    import paper_2012_06607_gb300 as md
+
+    systems = [mdgen.config_system(0, 1), mdgen.small_system_fast(np.random.default_rng(2), 5, 4, 2, monos=5)]
+    keep = []
+    sizes = []
+    for _ in range(40):
+        arr = (md.md_system * len(systems))()
+        for i, s in enumerate(systems):
+            arr[i] = md._host_md_system(s, keep)  # fresh host copies: new pointers, new key
+        sizes.append(md.lib().md_batched_workspace_bytes(len(systems), arr, 0))
+    assert sizes[0] > 0 and len(set(sizes)) == 1

@@ -154,3 +154,27 @@ def test_batched_phase_times(md):
     for i in range(len(systems)):
         assert np.array_equal(xs[i].cpu().numpy(), ref_x[i]), i
         assert np.array_equal(nrm.cpu().numpy()[i], ref_n[i]), i
+
+
+def test_batched_fresh_buffers_every_call(md):
+    """A caller that passes new x buffers on every call gets a new plan each
+    time; the plan cache drops the least recently used ones (pinned images and
+    graphs freed after a device synchronisation) and every result stays the
+    same."""
+    import torch
+
+    systems = _mixed_systems()[:6]
+    ref_x, ref_n, _ = _batched_steps(md, systems, 1)
+    sds = [md.DeviceSystem(s) for s in systems]
+    ws = md.workspace(md.batched_workspace_bytes(sds))
+    stream = torch.cuda.Stream()
+    for it in range(24):  # more than the cache holds
+        xs = [md.to_device(s.x0) for s in systems]
+        nrm = torch.zeros((len(systems), 2), dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(stream):
+            md.newton_step_batched(sds, xs, ws, nrm, None, flags=md.FLAG_GRAPH if it % 2 else 0, stream=stream)
+        stream.synchronize()
+        for i in range(len(systems)):
+            assert np.array_equal(xs[i].cpu().numpy(), ref_x[i]), (it, i)
+            assert np.array_equal(nrm.cpu().numpy()[i], ref_n[i]), (it, i)
+    assert md.device_status(ws) == 0
