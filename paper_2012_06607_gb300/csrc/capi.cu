@@ -388,33 +388,101 @@ md_status build_plan(const md_system *s, Plan &p, int flags = 0) {
 // Plans are cached per system structure (checksum) together with a pinned host
 // image of their integer tables; every call copies that image into its
 // workspace with one asynchronous copy, so a workspace needs no state between
-// calls.  Cached images live until the process exits (in-flight copies may
-// still read them).
+// calls.  Beyond kPlanCache structures the least recently used plans are
+// dropped; a call holds its plan by shared_ptr, and a dropped image is freed
+// after a device synchronisation (in-flight copies may still read it), which
+// is skipped while the calling stream is being captured.
 struct PlanEntry {
   Plan plan;
   int *pinned = nullptr;  // tables laid out exactly as in the workspace, from off_tasks
   size_t image_bytes = 0;
+  ~PlanEntry() {
+    if (pinned) {
+      cudaDeviceSynchronize();
+      cudaFreeHost(pinned);
+    }
+  }
 };
+constexpr size_t kPlanCache = 4096;  // a batch plans one structure per system
 std::mutex g_mu;
-std::map<uint64_t, PlanEntry *> g_plans;
 
-md_status prepare(const md_system *s, void *ws, size_t ws_bytes, cudaStream_t stream, Plan *&out, int flags = 0) {
+// A cache of shared values by 64-bit key with least-recently-used order
+// (touch and insert in O(log n)); not locked itself.
+template <class V>
+struct LruCache {
+  struct Slot {
+    std::shared_ptr<V> v;
+    std::list<uint64_t>::iterator pos;
+  };
+  std::map<uint64_t, Slot> map;
+  std::list<uint64_t> order;  // most recently used first
+
+  std::shared_ptr<V> find(uint64_t key) const {
+    auto it = map.find(key);
+    return it == map.end() ? nullptr : it->second.v;
+  }
+  void put(uint64_t key, std::shared_ptr<V> v) {
+    auto it = map.find(key);
+    if (it != map.end()) {
+      it->second.v = std::move(v);
+    } else {
+      order.push_front(key);
+      map.emplace(key, Slot{std::move(v), order.begin()});
+    }
+  }
+  void touch(uint64_t key) {
+    auto it = map.find(key);
+    if (it != map.end()) order.splice(order.begin(), order, it->second.pos);
+  }
+  // drops the least recently used entries beyond `bound`, except `keep` and
+  // those `pinned(v)` says must stay
+  template <class Pinned>
+  void evict(size_t bound, uint64_t keep, Pinned pinned) {
+    for (auto it = order.end(); map.size() > bound && it != order.begin();) {
+      --it;
+      auto e = map.find(*it);
+      if (*it == keep || pinned(*e->second.v)) continue;
+      map.erase(e);
+      it = order.erase(it);
+    }
+  }
+};
+
+LruCache<PlanEntry> g_plans;
+
+// Under g_mu: mark `key` used, then drop the least recently used plans beyond
+// the bound (those with a pinned image only if may_sync).
+void plans_touch(uint64_t key, bool may_sync) {
+  g_plans.touch(key);
+  g_plans.evict(kPlanCache, key, [&](const PlanEntry &e) { return !may_sync && e.pinned; });
+}
+
+bool not_capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone;
+}
+
+// Plan of `s` (cached), its tables uploaded into ws on `stream`.  `hold`
+// keeps the plan alive for the caller; `out` points into it.
+md_status prepare(const md_system *s, void *ws, size_t ws_bytes, cudaStream_t stream, Plan *&out,
+                  std::shared_ptr<PlanEntry> &hold, int flags = 0) {
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return MD_ERR_WORKSPACE;
-  md_status st = check_system(s);
+  md_status st = check_system_header(s);
   if (st != MD_OK) return st;
   const uint64_t cs = structure_checksum(s) ^ (0x9e3779b97f4a7c15ULL * (uint64_t)(flags & MD_FLAG_OZAKI));
+  const bool may_sync = not_capturing(stream);
   std::lock_guard<std::mutex> lk(g_mu);
-  PlanEntry *pe = nullptr;
-  auto it = g_plans.find(cs);
-  if (it != g_plans.end()) {
-    pe = it->second;
-  } else {
-    std::unique_ptr<PlanEntry> e(new PlanEntry);
+  hold = g_plans.find(cs);
+  if (!hold) {
+    if ((st = check_system(s)) != MD_OK) return st;  // a cached structure passed it when it was planned
+    std::shared_ptr<PlanEntry> e = std::make_shared<PlanEntry>();
     st = build_plan(s, e->plan, flags);
     if (st != MD_OK) return st;
-    pe = e.release();
-    g_plans[cs] = pe;
+    g_plans.put(cs, e);
+    hold = e;
   }
+  plans_touch(cs, may_sync);
+  PlanEntry *pe = hold.get();
   const Plan &p = pe->plan;
   // the cached plan does not depend on MD_FLAG_LU: check the shape every call
   if ((st = flags_for_shape(p.N, p.n, flags)) != MD_OK) return st;
@@ -446,21 +514,24 @@ md_status prepare(const md_system *s, void *ws, size_t ws_bytes, cudaStream_t st
 // ------------------------------------------------------------ batched form
 // Host plans of single systems, cached by structure checksum (no pinned image).
 // A structure already in the cache passed the full check when it was planned:
-// only the header is checked again.
-Plan *plan_of(const md_system *s, md_status &st) {
+// only the header is checked again.  `hold` keeps the plan alive.
+Plan *plan_of(const md_system *s, md_status &st, std::shared_ptr<PlanEntry> &hold, bool may_sync) {
   st = check_system_header(s);
   if (st != MD_OK) return nullptr;
   const uint64_t cs = structure_checksum(s);
   std::lock_guard<std::mutex> lk(g_mu);
-  auto it = g_plans.find(cs);
-  if (it != g_plans.end()) return &it->second->plan;
+  if ((hold = g_plans.find(cs))) {
+    plans_touch(cs, may_sync);
+    return &hold->plan;
+  }
   if ((st = check_system(s)) != MD_OK) return nullptr;
-  std::unique_ptr<PlanEntry> e(new PlanEntry);
+  std::shared_ptr<PlanEntry> e = std::make_shared<PlanEntry>();
   st = build_plan(s, e->plan, 0);
   if (st != MD_OK) return nullptr;
-  PlanEntry *pe = e.release();
-  g_plans[cs] = pe;
-  return &pe->plan;
+  g_plans.put(cs, e);
+  hold = e;
+  plans_touch(cs, may_sync);
+  return &hold->plan;
 }
 
 struct BatchClass {
@@ -502,24 +573,13 @@ struct BatchPlan {
 // graph synchronises the device, so it is skipped while the calling stream
 // is being captured (the cache may then exceed the bound for a while).
 constexpr size_t kBatchPlanCache = 16;
-std::map<uint64_t, std::shared_ptr<BatchPlan>> g_batch;
-std::list<uint64_t> g_batch_lru;  // most recently used first
+LruCache<BatchPlan> g_batch;
 
-// Under g_mu.
-void batch_touch(uint64_t key) {
-  g_batch_lru.remove(key);
-  g_batch_lru.push_front(key);
-}
-
-// Under g_mu.
-void batch_evict(bool may_sync) {
-  for (auto it = g_batch_lru.end(); g_batch.size() > kBatchPlanCache && it != g_batch_lru.begin();) {
-    --it;
-    auto e = g_batch.find(*it);
-    if (!may_sync && (e->second->pinned || e->second->exec)) continue;
-    g_batch.erase(e);
-    it = g_batch_lru.erase(it);
-  }
+// Under g_mu: mark `key` used and drop the least recently used batch plans
+// beyond the bound (those with a pinned image or a graph only if may_sync).
+void batch_touch(uint64_t key, bool may_sync) {
+  g_batch.touch(key);
+  g_batch.evict(kBatchPlanCache, key, [&](const BatchPlan &b) { return !may_sync && (b.pinned || b.exec); });
 }
 
 double job_cost(const Plan &p) {
@@ -534,10 +594,11 @@ md_status batch_prepare(int nsys, const md_system *sys, double *const *x, std::s
                         bool need_image, bool may_sync) {
   if (nsys < 1 || !sys) return MD_ERR_ARG;
   std::vector<Plan *> plans(nsys);
+  std::vector<std::shared_ptr<PlanEntry>> holds(nsys);
   uint64_t key = 1469598103934665603ULL;
   for (int i = 0; i < nsys; ++i) {
     md_status st;
-    plans[i] = plan_of(&sys[i], st);
+    plans[i] = plan_of(&sys[i], st, holds[i], may_sync);
     if (!plans[i]) return st;
     if (plans[i]->N != plans[i]->n) return MD_ERR_UNSUPPORTED;  // the batched form is for square systems
     const uint64_t cs = plans[i]->checksum;
@@ -547,10 +608,10 @@ md_status batch_prepare(int nsys, const md_system *sys, double *const *x, std::s
   }
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    auto it = g_batch.find(key);
-    if (it != g_batch.end() && (!need_image || it->second->pinned)) {
-      out = it->second;
-      batch_touch(key);
+    std::shared_ptr<BatchPlan> hit = g_batch.find(key);
+    if (hit && (!need_image || hit->pinned)) {
+      out = hit;
+      batch_touch(key, may_sync);
       return MD_OK;
     }
   }
@@ -660,12 +721,14 @@ md_status batch_prepare(int nsys, const md_system *sys, double *const *x, std::s
     }
   }
   std::lock_guard<std::mutex> lk(g_mu);
-  auto it = g_batch.find(key);
-  if (it == g_batch.end() || (!it->second->pinned && bp->pinned))
-    g_batch[key] = bp;  // new, or replaces a size-only plan
-  out = g_batch[key];
-  batch_touch(key);
-  batch_evict(may_sync);
+  std::shared_ptr<BatchPlan> old = g_batch.find(key);
+  if (!old || (!old->pinned && bp->pinned)) {
+    g_batch.put(key, bp);  // new, or replaces a size-only plan
+    out = bp;
+  } else {
+    out = old;
+  }
+  batch_touch(key, may_sync);
   return MD_OK;
 }
 
@@ -1109,7 +1172,8 @@ md_status md_eval_diff(const md_system *sys, const double *x, double *f, double 
   if (!x || !f || !A) return MD_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Plan *p = nullptr;
-  md_status st = prepare(sys, ws, ws_bytes, s, p);
+  std::shared_ptr<PlanEntry> hold;
+  md_status st = prepare(sys, ws, ws_bytes, s, p, hold);
   if (st != MD_OK) return st;
   char *base = static_cast<char *>(ws);
   if (cudaMemsetAsync(base, 0, 256, s) != cudaSuccess) return MD_ERR_CUDA;
@@ -1148,7 +1212,8 @@ md_status md_newton_series_step(const md_system *sys, double *x, double *dx_norm
   if (!x) return MD_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Plan *p = nullptr;
-  md_status st = prepare(sys, ws, ws_bytes, s, p, flags);
+  std::shared_ptr<PlanEntry> hold;
+  md_status st = prepare(sys, ws, ws_bytes, s, p, hold, flags);
   if (st != MD_OK) return st;
   char *base = static_cast<char *>(ws);
   if (cudaMemsetAsync(base, 0, 256, s) != cudaSuccess) return MD_ERR_CUDA;
@@ -1188,7 +1253,8 @@ md_status md_rcond_a0(const md_system *sys, void *ws, size_t ws_bytes, int flags
   if (!rcond) return MD_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Plan *p = nullptr;
-  md_status st = prepare(sys, ws, ws_bytes, s, p, flags);
+  std::shared_ptr<PlanEntry> hold;
+  md_status st = prepare(sys, ws, ws_bytes, s, p, hold, flags);
   if (st != MD_OK) return st;
   char *base = static_cast<char *>(ws);
   SolveDev v = make_solve(p->sl, p->N, p->n, p->d, base);
@@ -1273,7 +1339,8 @@ md_status md_batched_job_costs(int nsys, const md_system *sys, double *cost) {
   if (nsys < 1 || !sys || !cost) return MD_ERR_ARG;
   for (int i = 0; i < nsys; ++i) {
     md_status st;
-    const Plan *p = plan_of(&sys[i], st);
+    std::shared_ptr<PlanEntry> hold;
+    const Plan *p = plan_of(&sys[i], st, hold, false);
     if (!p) return st;
     cost[i] = job_cost(*p);
   }
