@@ -629,6 +629,8 @@ def run_batched(args):
     if world > 1:
         torch.cuda.set_device(local)
     all_systems = mdgen.batch_systems(args.seed, count=args.batch)
+    if len(all_systems) < world:
+        raise SystemExit(f"--batch {args.batch} leaves ranks without systems at {world} GPUs")
     mine, _ = batched_shard(all_systems, rank, world)
     systems = [all_systems[i] for i in mine]
     sds = [md.DeviceSystem(s) for s in systems]
