@@ -11,6 +11,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "../../include/mdnewton.h"
@@ -195,7 +196,7 @@ uint64_t structure_checksum(const md_system *s) {
   h = hash_bytes(h, s->nvar, sizeof(int) * s->nmono);
   h = hash_bytes(h, s->idx, sizeof(int) * s->nmono * MD_MAXV);
   h = hash_bytes(h, s->expo, sizeof(int) * s->nmono * MD_MAXV);
-  return h;
+  return h | 1;  // never 0 (0 marks "not computed")
 }
 
 // Sizes, pointers and polynomial offsets (what the structure hash needs).
@@ -515,10 +516,13 @@ md_status prepare(const md_system *s, void *ws, size_t ws_bytes, cudaStream_t st
 // Host plans of single systems, cached by structure checksum (no pinned image).
 // A structure already in the cache passed the full check when it was planned:
 // only the header is checked again.  `hold` keeps the plan alive.
-Plan *plan_of(const md_system *s, md_status &st, std::shared_ptr<PlanEntry> &hold, bool may_sync) {
-  st = check_system_header(s);
-  if (st != MD_OK) return nullptr;
-  const uint64_t cs = structure_checksum(s);
+// cs: the structure checksum if already computed (the header then checked), else 0.
+Plan *plan_of(const md_system *s, md_status &st, std::shared_ptr<PlanEntry> &hold, bool may_sync, uint64_t cs = 0) {
+  if (!cs) {
+    st = check_system_header(s);
+    if (st != MD_OK) return nullptr;
+    cs = structure_checksum(s);
+  }
   std::lock_guard<std::mutex> lk(g_mu);
   if ((hold = g_plans.find(cs))) {
     plans_touch(cs, may_sync);
@@ -595,10 +599,25 @@ md_status batch_prepare(int nsys, const md_system *sys, double *const *x, std::s
   if (nsys < 1 || !sys) return MD_ERR_ARG;
   std::vector<Plan *> plans(nsys);
   std::vector<std::shared_ptr<PlanEntry>> holds(nsys);
+  // the structures are hashed on every call: on several host threads
+  for (int i = 0; i < nsys; ++i)
+    if (check_system_header(&sys[i]) != MD_OK) return MD_ERR_ARG;
+  std::vector<uint64_t> sums(nsys);
+  {
+    const int nt = nsys < 64 ? 1 : std::max(1, std::min(8, (int)std::thread::hardware_concurrency()));
+    std::atomic<int> next{0};
+    auto work = [&] {
+      for (int i; (i = next.fetch_add(1)) < nsys;) sums[i] = structure_checksum(&sys[i]);
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) pool.emplace_back(work);
+    work();
+    for (std::thread &t : pool) t.join();
+  }
   uint64_t key = 1469598103934665603ULL;
   for (int i = 0; i < nsys; ++i) {
     md_status st;
-    plans[i] = plan_of(&sys[i], st, holds[i], may_sync);
+    plans[i] = plan_of(&sys[i], st, holds[i], may_sync, sums[i]);
     if (!plans[i]) return st;
     if (plans[i]->N != plans[i]->n) return MD_ERR_UNSUPPORTED;  // the batched form is for square systems
     const uint64_t cs = plans[i]->checksum;
