@@ -46,7 +46,8 @@ typedef enum md_status {
   MD_ERR_NONFINITE = 5,   /* an update contains Inf or NaN                      */
   MD_ERR_NOCONV = 6,      /* reserved for drivers that iterate to a tolerance   */
   MD_ERR_TIMEOUT = 7,     /* reserved: a bounded device wait ran out            */
-  MD_ERR_UNSUPPORTED = 8  /* valid request this build does not implement        */
+  MD_ERR_UNSUPPORTED = 8, /* valid request this build does not implement        */
+  MD_ERR_CHECK = 9        /* MD_FLAG_CHECK: a plan table or layout out of bounds */
 } md_status;
 
 /* Maximum number of (variable, exponent) pairs per monomial. */
@@ -131,6 +132,15 @@ typedef struct md_system {
    loop -- and the end (x updated).  Adds a few barriers per system. */
 #define MD_FLAG_PHASE_TIMES 0x20
 #define MD_PHASE_STAMPS 10
+/* Bounds mode: before any launch, check on the host every index the kernels
+   follow from the plan's tables and the workspace layout: each product's
+   operands are series made before it, and each product and coefficient index
+   is in range. Each accumulation group and contribution points inside its
+   tables, and every workspace region lies in order within the workspace.
+   Failure returns MD_ERR_CHECK without device work.  The kernels compute
+   every other address from (N, n, d, K, P).  Costs one pass over the tables
+   per call. */
+#define MD_FLAG_CHECK 0x40
 
 /* Version of this ABI (major*100 + minor). */
 int md_version(void);
@@ -250,6 +260,13 @@ size_t md_batched_workspace_bytes(int nsys, const md_system *sys, int flags);
 md_status md_newton_series_step_batched(int nsys, const md_system *sys, double *const *x, double *dx_norm,
                                         unsigned long long *times, void *ws, size_t ws_bytes, int flags,
                                         void *stream);
+
+/*
+ * The bounds mode's checks of MD_FLAG_CHECK on the plan of one system, host
+ * only (no device work): MD_OK, MD_ERR_CHECK, or MD_ERR_ARG for an invalid
+ * system.  flags: MD_FLAG_OZAKI selects that form's workspace layout.
+ */
+md_status md_plan_check(const md_system *sys, int flags);
 
 /*
  * Host-side cost estimate of each system's Newton step: the estimate the

@@ -78,6 +78,8 @@ def lib():
         L.md_batched_workspace_bytes.restype = sz
         L.md_batched_job_costs.argtypes = [i, ctypes.POINTER(md_system), ctypes.c_void_p]
         L.md_batched_job_costs.restype = i
+        L.md_plan_check.argtypes = [ctypes.POINTER(md_system), i]
+        L.md_plan_check.restype = i
         L.md_newton_series_step_batched.argtypes = [i, ctypes.POINTER(md_system), ctypes.POINTER(vp), vp, vp, vp, sz,
                                                     i, vp]
         L.md_newton_series_step_batched.restype = i
@@ -114,7 +116,7 @@ def exported_symbols():
             "md_newton_series_step_batched", "md_linsolve_series_static", "md_profile_enable",
             "md_profile_read", "md_profile_kind_name", "md_newton_run_workspace_bytes", "md_newton_series_run",
             "md_rcond_a0", "md_linsolve_rcond", "md_lstsq_workspace_bytes", "md_lstsq_series", "md_lstsq_rcond",
-            "md_batched_job_costs"]
+            "md_batched_job_costs", "md_plan_check"]
 
 
 # --------------------------------------------------------------- helpers
@@ -241,6 +243,7 @@ def newton_step(sysd: DeviceSystem, x, ws, dx_norm=None, flags: int = 0, stream=
 
 FLAG_OZAKI, FLAG_AUTOTUNE, FLAG_GRAPH, FLAG_SERIAL, FLAG_LU = 0x1, 0x2, 0x4, 0x8, 0x10
 FLAG_PHASE_TIMES = 0x20  # batched form: times is [nsys, PHASE_STAMPS]
+FLAG_CHECK = 0x40  # bounds mode: plan tables and workspace layout checked on the host (MD_ERR_CHECK)
 PHASE_STAMPS = 10
 PHASE_NAMES = ("load", "products", "accumulation", "qr_setup", "householder_qr", "rinv", "w", "degree_loop",
                "finish")
@@ -339,6 +342,14 @@ def _host_md_system(s, keep) -> "md_system":
     return md_system(int(s.limbs), int(bool(s.is_complex)), int(s.n), int(s.degree), nm, pp.ctypes.data,
                      nv.ctypes.data if nm else None, ix.ctypes.data if nm else None, ex.ctypes.data if nm else None,
                      cf.ctypes.data if nm else None, cs.ctypes.data, int(getattr(s, "neq", 0) or 0))
+
+
+def plan_check(system, flags: int = 0) -> int:
+    """md_plan_check: the bounds mode's host checks on one system's plan
+    (DeviceSystem, or any object with the md_system fields); returns the status."""
+    keep = []
+    c = system._c if hasattr(system, "_c") else _host_md_system(system, keep)
+    return int(lib().md_plan_check(ctypes.byref(c), flags))
 
 
 def batched_job_costs(systems) -> np.ndarray:

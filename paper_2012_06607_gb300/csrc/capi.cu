@@ -386,6 +386,76 @@ md_status build_plan(const md_system *s, Plan &p, int flags = 0) {
   return MD_OK;
 }
 
+// MD_FLAG_CHECK: every index the kernels follow from the plan's tables, and
+// the workspace layout, checked on the host before any launch.  The kernels
+// compute all other addresses from (N, n, d, K, P), which the parity tests
+// cover shape by shape.
+md_status check_plan(const Plan &p) {
+  const int ns = p.nslots, n = p.n, N = p.N, d = p.d;
+  const int nscal = (int)p.scal_src.size() / 2, ncon = (int)p.contrib.size() / 4;
+  auto in = [](long long v, long long lo, long long hi) { return v >= lo && v < hi; };
+  // a product's operands are series made before it (slots are numbered in order)
+  auto product = [&](int out, int a, int b) { return in(out, n, ns) && in(a, 0, out) && in(b, 0, out); };
+  auto stages = [&](const std::vector<int> &off, size_t count) {
+    if (off.empty() || off.front() != 0 || (size_t)off.back() != count) return false;
+    for (size_t i = 1; i < off.size(); ++i)
+      if (off[i] < off[i - 1]) return false;
+    return true;
+  };
+  if (p.tasks.size() % 8 || p.tasks0.size() % 8 || p.ops3.size() % 3 || p.scal_src.size() % 2 ||
+      p.groups.size() % 4 || p.contrib.size() % 4)
+    return MD_ERR_CHECK;
+  if (!stages(p.stage_off, p.tasks.size() / 8) || !stages(p.stage_off0, p.tasks0.size() / 8) ||
+      !stages(p.op_stage_off, p.ops3.size() / 3))
+    return MD_ERR_CHECK;
+  for (size_t t = 0; t < p.tasks.size(); t += 8) {
+    const int *q = &p.tasks[t];
+    if (!product(q[0], q[1], q[2]) || !in(q[3], 0, d + 1)) return MD_ERR_CHECK;
+    if (q[4] >= 0 ? !product(q[4], q[5], q[6]) || 2 * q[3] > d : q[5] != -1 || q[6] != -1) return MD_ERR_CHECK;
+  }
+  for (size_t t = 0; t < p.tasks0.size(); t += 8)
+    if (!product(p.tasks0[t], p.tasks0[t + 1], p.tasks0[t + 2]) || p.tasks0[t + 3] != 0 || p.tasks0[t + 4] != -1)
+      return MD_ERR_CHECK;
+  for (size_t t = 0; t < p.ops3.size(); t += 3)
+    if (!product(p.ops3[t], p.ops3[t + 1], p.ops3[t + 2])) return MD_ERR_CHECK;
+  for (int i = 0; i < nscal; ++i)
+    if (!in(p.scal_src[2 * i], 0, p.nmono) || p.scal_src[2 * i + 1] < 1) return MD_ERR_CHECK;
+  for (size_t g = 0; g < p.groups.size(); g += 4) {
+    const int *q = &p.groups[g];
+    if (!in(q[0], 0, N) || !in(q[1], -1, n) || q[2] < 0 || q[3] < 0 || (long long)q[2] + q[3] > ncon)
+      return MD_ERR_CHECK;
+  }
+  for (int c = 0; c < ncon; ++c) {
+    const int *q = &p.contrib[4 * c];
+    if (!in(q[0], -1, ns) || !in(q[1], 0, nscal) || q[2] < 0) return MD_ERR_CHECK;
+  }
+  // regions in order, each within the next offset, the solve area last
+  const size_t VS = sizeof(double) * p.P * p.K;
+  const size_t ends[][2] = {
+      {p.off_pool, (size_t)ns * (d + 1) * VS},
+      {p.off_scal, (size_t)std::max(nscal, 1) * VS},
+      {p.off_tasks, sizeof(int) * std::max<size_t>(p.tasks.size(), 8)},
+      {p.off_scalsrc, sizeof(int) * std::max<size_t>(p.scal_src.size(), 2)},
+      {p.off_groups, sizeof(int) * std::max<size_t>(p.groups.size(), 4)},
+      {p.off_contrib, sizeof(int) * std::max<size_t>(p.contrib.size(), 4)},
+      {p.off_tasks0, sizeof(int) * std::max<size_t>(p.tasks0.size(), 8)},
+      {p.off_f, (size_t)N * (d + 1) * VS},
+      {p.off_A, (size_t)(d + 1) * N * n * VS},
+      {p.off_prod, (size_t)ncon * (d + 1) * VS},
+      {p.off_solve, p.sl.bytes}};
+  size_t prev_end = 256;  // the status header
+  for (const auto &r : ends) {
+    if (r[0] < prev_end || r[0] % 256) return MD_ERR_CHECK;
+    prev_end = r[0] + r[1];
+  }
+  if (prev_end > p.total) return MD_ERR_CHECK;
+  const SolveLayout &L = p.sl;
+  const size_t solve[] = {L.off_M, L.off_Y, L.off_W, L.off_vd, L.off_beta, L.off_rinv, L.off_r, L.off_dxw, L.off_part};
+  for (size_t i = 0; i < sizeof(solve) / sizeof(solve[0]); ++i)
+    if (solve[i] < (i ? solve[i - 1] + 1 : p.off_solve) || solve[i] >= p.off_solve + L.bytes) return MD_ERR_CHECK;
+  return MD_OK;
+}
+
 // Plans are cached per system structure (checksum) together with a pinned host
 // image of their integer tables; every call copies that image into its
 // workspace with one asynchronous copy, so a workspace needs no state between
@@ -484,6 +554,7 @@ md_status prepare(const md_system *s, void *ws, size_t ws_bytes, cudaStream_t st
   }
   plans_touch(cs, may_sync);
   PlanEntry *pe = hold.get();
+  if ((flags & MD_FLAG_CHECK) && (st = check_plan(pe->plan)) != MD_OK) return st;
   const Plan &p = pe->plan;
   // the cached plan does not depend on MD_FLAG_LU: check the shape every call
   if ((st = flags_for_shape(p.N, p.n, flags)) != MD_OK) return st;
@@ -595,7 +666,7 @@ double job_cost(const Plan &p) {
 }
 
 md_status batch_prepare(int nsys, const md_system *sys, double *const *x, std::shared_ptr<BatchPlan> &out,
-                        bool need_image, bool may_sync) {
+                        bool need_image, bool may_sync, bool check = false) {
   if (nsys < 1 || !sys) return MD_ERR_ARG;
   std::vector<Plan *> plans(nsys);
   std::vector<std::shared_ptr<PlanEntry>> holds(nsys);
@@ -619,6 +690,7 @@ md_status batch_prepare(int nsys, const md_system *sys, double *const *x, std::s
     md_status st;
     plans[i] = plan_of(&sys[i], st, holds[i], may_sync, sums[i]);
     if (!plans[i]) return st;
+    if (check && (st = check_plan(*plans[i])) != MD_OK) return st;
     if (plans[i]->N != plans[i]->n) return MD_ERR_UNSUPPORTED;  // the batched form is for square systems
     const uint64_t cs = plans[i]->checksum;
     key = fnv(key, &cs, sizeof(cs));
@@ -1151,8 +1223,15 @@ const char *md_status_string(md_status st) {
     case MD_ERR_NOCONV: return "no convergence";
     case MD_ERR_TIMEOUT: return "device wait timed out";
     case MD_ERR_UNSUPPORTED: return "unsupported";
+    case MD_ERR_CHECK: return "bounds check failed";
   }
   return "unknown status";
+}
+
+md_status md_plan_check(const md_system *sys, int flags) {
+  Plan p;
+  const md_status st = build_plan(sys, p, flags);
+  return st != MD_OK ? st : check_plan(p);
 }
 
 size_t md_workspace_bytes(const md_system *sys, int flags) {
@@ -1387,7 +1466,7 @@ md_status md_newton_series_step_batched(int nsys, const md_system *sys, double *
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return MD_ERR_CUDA;
   std::shared_ptr<BatchPlan> bp;
-  md_status st = batch_prepare(nsys, sys, x, bp, true, cap == cudaStreamCaptureStatusNone);
+  md_status st = batch_prepare(nsys, sys, x, bp, true, cap == cudaStreamCaptureStatusNone, flags & MD_FLAG_CHECK);
   if (st != MD_OK) return st;
   if (bp->total > ws_bytes) return MD_ERR_WORKSPACE;
   char *base = static_cast<char *>(ws);

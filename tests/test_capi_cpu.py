@@ -197,7 +197,7 @@ def test_python_flags_match_header():
 
     hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "mdnewton.h")).read()
     defs = {k: int(v, 0) for k, v in re.findall(r"#define\s+(MD_\w+)\s+(0x[0-9a-fA-F]+|\d+)\b", hdr)}
-    for name in ("OZAKI", "AUTOTUNE", "GRAPH", "SERIAL", "LU", "PHASE_TIMES"):
+    for name in ("OZAKI", "AUTOTUNE", "GRAPH", "SERIAL", "LU", "PHASE_TIMES", "CHECK"):
         assert getattr(md, "FLAG_" + name) == defs["MD_FLAG_" + name], name
     assert md.PHASE_STAMPS == defs["MD_PHASE_STAMPS"] == len(md.PHASE_NAMES) + 1
 
@@ -234,3 +234,38 @@ def test_batched_plan_cache_bound_host_only():
             arr[i] = md._host_md_system(s, keep)  # fresh host copies: new pointers, new key
         sizes.append(md.lib().md_batched_workspace_bytes(len(systems), arr, 0))
     assert sizes[0] > 0 and len(set(sizes)) == 1
+
+
+def test_plan_check_fuzz_host_only():
+    """Bounds mode on the host: the plans of many seeded systems (shapes,
+    degrees, limbs, real and complex, N > n, the split-product layout) pass
+    every table and layout check; an invalid system is an argument error."""
+    import paper_2012_06607_gb300 as md
+
+    rng = np.random.default_rng(11)
+    count = 0
+    for seed in range(40):
+        n = int(rng.integers(1, 12))
+        K = int(rng.choice([1, 2, 3, 4, 5, 8, 10]))
+        d = int(rng.integers(0, 12))
+        maxvars = min(int(rng.integers(1, 5)), n + 1)
+        try:
+            s = mdgen.random_system(seed, n=n, K=K, cplx=bool(seed % 2), d=d, monos=int(rng.integers(1, 4)),
+                                    maxvars=maxvars, maxdeg=maxvars + int(rng.integers(0, 3)), coef_kind="uniform",
+                                    cond_max=1e30, neq=n + int(rng.integers(0, 3)) if seed % 3 == 0 else 0)
+        except RuntimeError:  # no regular Jacobian for this shape: nothing to plan
+            continue
+        flags = md.FLAG_OZAKI if (seed % 4 == 1 and s.N == s.n) else 0
+        assert md.plan_check(s, flags) == 0, (seed, n, K, d)
+        count += 1
+    for cfg in range(5):
+        s = mdgen.config_system(cfg, 1) if cfg != 3 and cfg != 4 else None
+        if s is not None:
+            assert md.plan_check(s) == 0, cfg
+    assert count >= 20  # 23 of the 40 seeded shapes are regular
+    bad = mdgen.config_system(0, 1)
+    keep = []
+    c = md._host_md_system(bad, keep)
+    c.n = 0  # invalid
+    assert md.lib().md_plan_check(ctypes.byref(c), 0) == 1  # MD_ERR_ARG
+    assert md.lib().md_status_string(9) == b"bounds check failed"
