@@ -36,6 +36,23 @@ METRIC = "power-series Newton steps/s (qd, n=64, d=64); FP64-pipe % of peak; err
 WORKLOAD = ("quad double complex, n=64 polynomials (+t), 64 monomials each of degree <= 4 over <= 4 variables, "
             "truncation degree d=64, seed 1")
 CFG = 1
+# the other seeded workloads (--config): the small double double case and the
+# octo double real n = 128 case (the shape of the paper's 128-dimensional runs)
+OTHER_WORKLOADS = {
+    0: ("power-series Newton steps/s (dd, n=3, d=8); FP64-pipe % of peak; err vs oracle",
+        "double double complex, n=3 polynomials (+t), 4 monomials each of degree <= 2 over 1-2 variables, "
+        "truncation degree d=8, seed {seed}"),
+    2: ("power-series Newton steps/s (od, n=128, d=32); FP64-pipe % of peak; err vs oracle",
+        "octo double real, n=128 polynomials (+t), 32 monomials each of degree <= 3 over <= 3 variables, "
+        "truncation degree d=32, seed {seed}"),
+}
+
+
+def metric_and_workload(cfg: int, seed: int):
+    if cfg == CFG:
+        return METRIC, WORKLOAD.replace("seed 1", f"seed {seed}")
+    m, w = OTHER_WORKLOADS[cfg]
+    return m, w.format(seed=seed)
 
 # Table 1 of the paper: double operations per md add / mul (sum of the +,-,*,/ columns)
 TABLE1 = {2: (20, 23), 3: (35, 209), 4: (89, 336), 5: (122, 554), 8: (269, 1742), 10: (397, 3089)}
@@ -243,12 +260,13 @@ def run_reference(args):
         return 0
     import mdgen
 
-    s = mdgen.config_system(CFG, args.seed)
+    s = mdgen.config_system(args.config, args.seed)
+    metric, workload = metric_and_workload(args.config, args.seed)
     v, cores, dt = oracle_steps_per_s(s, args.steps, args.warmup)
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": metric, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "arm": "CPU oracle (plain C, OpenMP over polynomials and RHS updates)"},
+            "config": {"workload": workload, "arm": "CPU oracle (plain C, OpenMP over polynomials and RHS updates)"},
             "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
                              "sample": f"{args.steps} full Newton steps of the workload after {args.warmup} warm-up"},
             "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -268,7 +286,8 @@ def run_product(args):
     torch.cuda.set_device(local)
     dist = dist_init(world)
     dev = torch.device("cuda", local)
-    s = mdgen.config_system(CFG, args.seed)
+    s = mdgen.config_system(args.config, args.seed)
+    metric, workload = metric_and_workload(args.config, args.seed)
     P, K, n, d = s.planes, s.limbs, s.n, s.degree
     sysd = md.DeviceSystem(s, device=dev)
     flags = md.FLAG_OZAKI if args.update == "split" else 0
@@ -330,17 +349,17 @@ def run_product(args):
     achieved = args.steps * conv_instr / (conv_ms / 1e3) if conv_ms > 0 else None
     roofline = {"bound": "alu", "kernel": "conv_stage", "achieved": achieved / 1e12 if achieved else None,
                 "peak": FP64_PEAK_INSTR / 1e12, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_INSTR if achieved else None,
-                "traffic": CONV_TRAFFIC_BYTES_PER_LAUNCH if args.update == "md" else None,
+                "traffic": CONV_TRAFFIC_BYTES_PER_LAUNCH if args.update == "md" and args.config == CFG else None,
                 "traffic_unit": "bytes per launch (ncu DRAM read + write)",
                 "counted": "FP64 instructions of the md algorithms (an fma counts once)",
                 "launches_in_timed_region": conv_launches, "avg_launch_ms": conv_ms / max(conv_launches, 1),
                 "dominant_by_time": dom_name,
                 "paper_ops_per_s": args.steps * conv_paper / (conv_ms / 1e3) if conv_ms > 0 else None,
                 "algorithmic_fp64_per_step": conv_instr}
-    line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+    line = {"metric": metric, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "l2": "flushed between steps (256 MB write outside the events)",
+            "config": {"workload": workload, "l2": "flushed between steps (256 MB write outside the events)",
                        "parallelism": f"replicas x{world}", "workspace_bytes": wsb,
                        "update": "split-product (BF16 tensor pipe)" if flags else "md arithmetic"},
             "roofline": roofline, "gpu_launches": launches, "clocks": clk, "device_status": status,
@@ -753,6 +772,8 @@ def main():
     ap.add_argument("--update", default="md", choices=["md", "split"],
                     help="block Toeplitz update of the plain form: md arithmetic or split-product")
     ap.add_argument("--batch", type=int, default=2048)
+    ap.add_argument("--config", type=int, default=CFG, choices=[0, 1, 2],
+                    help="workload of the plain and reference forms: 1 (default, the headline), 0 or 2")
     ap.add_argument("--no-loop", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
