@@ -290,7 +290,7 @@ def run_product(args):
     metric, workload = metric_and_workload(args.config, args.seed)
     P, K, n, d = s.planes, s.limbs, s.n, s.degree
     sysd = md.DeviceSystem(s, device=dev)
-    flags = md.FLAG_OZAKI if args.update == "split" else 0
+    flags = (md.FLAG_OZAKI if args.update == "split" else 0) | (md.FLAG_LU if args.factor == "lu" else 0)
     wsb = sysd.workspace_bytes(flags)
     ws = md.workspace(wsb, device=dev)
     x = md.to_device(s.x0, dev)
@@ -361,7 +361,8 @@ def run_product(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload, "l2": "flushed between steps (256 MB write outside the events)",
                        "parallelism": f"replicas x{world}", "workspace_bytes": wsb,
-                       "update": "split-product (BF16 tensor pipe)" if flags else "md arithmetic"},
+                       "update": "split-product (BF16 tensor pipe)" if args.update == "split" else "md arithmetic",
+                       "factor": "LU with partial pivoting" if args.factor == "lu" else "Householder QR"},
             "roofline": roofline, "gpu_launches": launches, "clocks": clk, "device_status": status,
             "kernel_ms": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
             "wall_s_timed_region": wall, "dx_norm_last": float(nrm[0].item()),
@@ -396,7 +397,7 @@ def run_product(args):
     # the other update form on the same GPU, same workload and timing (context,
     # not the headline): the split-product update against md arithmetic
     if args.update == "md" and not args.no_other_form:
-        oflags = md.FLAG_OZAKI
+        oflags = md.FLAG_OZAKI | (flags & md.FLAG_LU)
         ows = md.workspace(sysd.workspace_bytes(oflags), device=dev)
         xo = md.to_device(s.x0, dev)
         for _ in range(args.warmup):
@@ -772,6 +773,7 @@ def main():
     ap.add_argument("--update", default="md", choices=["md", "split"],
                     help="block Toeplitz update of the plain form: md arithmetic or split-product")
     ap.add_argument("--batch", type=int, default=2048)
+    ap.add_argument("--factor", default="qr", choices=["qr", "lu"], help="factorisation of A_0 in the plain form")
     ap.add_argument("--config", type=int, default=CFG, choices=[0, 1, 2],
                     help="workload of the plain and reference forms: 1 (default, the headline), 0 or 2")
     ap.add_argument("--no-loop", action="store_true")
