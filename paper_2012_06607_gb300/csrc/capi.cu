@@ -519,7 +519,9 @@ struct LruCache {
   }
 };
 
-LruCache<PlanEntry> g_plans;
+// Never destroyed: entries free pinned memory with CUDA calls, which must not
+// run from static destructors after the runtime has unloaded.
+LruCache<PlanEntry> &g_plans = *new LruCache<PlanEntry>;
 
 // Under g_mu: mark `key` used, then drop the least recently used plans beyond
 // the bound (those with a pinned image only if may_sync).
@@ -648,7 +650,7 @@ struct BatchPlan {
 // graph synchronises the device, so it is skipped while the calling stream
 // is being captured (the cache may then exceed the bound for a while).
 constexpr size_t kBatchPlanCache = 16;
-LruCache<BatchPlan> g_batch;
+LruCache<BatchPlan> &g_batch = *new LruCache<BatchPlan>;  // never destroyed (as g_plans)
 
 // Under g_mu: mark `key` used and drop the least recently used batch plans
 // beyond the bound (those with a pinned image or a graph only if may_sync).
