@@ -230,6 +230,7 @@ md_status md_lstsq_series(int limbs, int is_complex, int neq, int n, int degree,
  *            of Section 6), [1] = max over all coefficients; both from the
  *            leading limbs.
  *   ws:      DEVICE workspace of md_workspace_bytes(sys, flags) bytes.
+ *   flags:   MD_FLAG_OZAKI, MD_FLAG_LU, MD_FLAG_SERIAL, MD_FLAG_CHECK
  */
 md_status md_newton_series_step(const md_system *sys, double *x, double *dx_norm, void *ws, size_t ws_bytes,
                                 int flags, void *stream);
@@ -254,7 +255,8 @@ md_status md_newton_series_step(const md_system *sys, double *x, double *dx_norm
  *            ([nsys][MD_PHASE_STAMPS] with MD_FLAG_PHASE_TIMES)
  *   ws:      DEVICE workspace of md_batched_workspace_bytes() bytes; the status
  *            word covers the whole batch
- *   flags:   MD_FLAG_AUTOTUNE, MD_FLAG_GRAPH, MD_FLAG_SERIAL, MD_FLAG_PHASE_TIMES
+ *   flags:   MD_FLAG_AUTOTUNE, MD_FLAG_GRAPH, MD_FLAG_SERIAL, MD_FLAG_PHASE_TIMES,
+ *            MD_FLAG_CHECK
  */
 size_t md_batched_workspace_bytes(int nsys, const md_system *sys, int flags);
 md_status md_newton_series_step_batched(int nsys, const md_system *sys, double *const *x, double *dx_norm,
