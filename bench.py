@@ -429,7 +429,7 @@ def run_product(args):
         md.newton_step(sysd, x1, ws, nrm, flags=flags)
         torch.cuda.synchronize()
         e = err_vs_oracle(x1.cpu().numpy(), x_orc)
-        eps = 2.0 ** (-53 * s.limbs)
+        eps = 2.0 ** (-52 * s.limbs)
         line["err_vs_oracle"] = {"max_rel": e, "max_rel_over_eps": e / eps, "eps": eps,
                                  "measure": "one step from x0; per degree, max_i |x_gpu - x_oracle| / max_i |x_oracle|"}
     if rank == 0:

@@ -490,8 +490,10 @@ def solve_config3(seed: int = 1, n: int = 256, d: int = 16, K: int = 4, cond: fl
 
     A_0 = U diag(sigma) V^T with seeded orthogonal U, V (QR of Gaussian matrices,
     in double) and sigma log-spaced on [1/cond, 1]; its double entries are the
-    leading limbs (lower limbs zero).  A_1..A_d and b have N(0,1) leading limbs;
-    each lower limb is uniform within half an ulp of the limb above it.
+    leading limbs.  A_1..A_d and b have N(0,1) leading limbs.  In every matrix
+    and vector each lower limb is uniform within half an ulp of the limb above
+    it, so every limb is in use; the lower limbs of A_0 move its singular
+    values by about 1e-16 times its norm, far below sigma_min = 1/cond.
     Returns (A [1][K][d+1][n][n] column-major blocks, b [1][K][n][d+1]).
     """
     rng = np.random.default_rng([seed, 3])
@@ -500,12 +502,13 @@ def solve_config3(seed: int = 1, n: int = 256, d: int = 16, K: int = 4, cond: fl
     sig = np.logspace(0.0, -np.log10(cond), n)
     A0 = (U * sig) @ V.T
     A = np.zeros((1, K, d + 1, n, n))
-    A[0, 0, 0] = A0.T  # column-major: [col][row]
-    def lifted(shape):
-        # leading limb N(0,1); limb l uniform in (-ulp/2, ulp/2) of limb l-1, so the
-        # expansion is non-overlapping by construction (about 2^-53 per limb)
+
+    def lifted(shape, lead=None):
+        # leading limb N(0,1) (or `lead`); limb l uniform in (-ulp/2, ulp/2) of
+        # limb l-1, so the expansion is non-overlapping by construction (about
+        # 2^-53 per limb)
         out = np.zeros((K,) + shape)
-        out[0] = rng.standard_normal(shape)
+        out[0] = rng.standard_normal(shape) if lead is None else lead
         for l in range(1, K):
             _, e = np.frexp(out[l - 1])
             out[l] = rng.uniform(-0.5, 0.5, size=shape) * np.ldexp(1.0, e - 53)
@@ -513,6 +516,7 @@ def solve_config3(seed: int = 1, n: int = 256, d: int = 16, K: int = 4, cond: fl
         return out
 
     A[0, :, 1:] = lifted((d, n, n))
+    A[0, :, 0] = lifted((n, n), lead=A0.T)  # column-major: [col][row]
     b = np.zeros((1, K, n, d + 1))
     b[0] = lifted((n, d + 1))
     return A, b

@@ -1,11 +1,14 @@
 """Batched form: many systems of uneven size and precision in one persistent
 launch per precision class.  Each system must get exactly the bits of the
 single-system step (same per-item bodies and reduction trees), with and
-without the autotuner and the CUDA graph."""
+without the autotuner and the CUDA graph, and every system of a mixed batch
+of full-width inputs must agree with the oracle's Newton step within the
+per-degree tolerance (1e3 eps_K)."""
 import numpy as np
 import pytest
 
 import mdgen
+from mdcompare import TOL, worst_in_eps
 
 pytestmark = pytest.mark.gpu
 
@@ -178,3 +181,78 @@ def test_batched_fresh_buffers_every_call(md):
             assert np.array_equal(xs[i].cpu().numpy(), ref_x[i]), (it, i)
             assert np.array_equal(nrm.cpu().numpy()[i], ref_n[i]), (it, i)
     assert md.device_status(ws) == 0
+
+
+def _full_width_batch():
+    """Double double and quad double complex systems of uneven n and d built by
+    mdgen.random_system: unit-modulus coefficients and x0 whose every limb is
+    in use, constants fixed exactly so that x0 solves at t = 0."""
+    out = []
+    specs = [(2, 8, 8), (4, 6, 12), (2, 13, 5), (4, 9, 9), (2, 16, 16), (4, 3, 20), (2, 24, 10), (4, 20, 6),
+             (2, 5, 31), (4, 12, 17), (2, 1, 9), (4, 32, 8)]
+    for i, (K, n, d) in enumerate(specs):
+        out.append(mdgen.random_system(300 + i, n=n, K=K, cplx=True, d=d, monos=max(n, 3), minvars=1, maxvars=2,
+                                       maxdeg=3, coef_kind="unit", name=f"fw{i}"))
+    return out
+
+
+def _oracle_steps(orc, s, steps):
+    xo = s.x0.copy()
+    norms = []
+    for _ in range(steps):
+        xo, nr = orc.newton_step(s, xo)
+        norms.append(nr)
+    return xo, norms
+
+
+def _assert_batch_matches_oracle(orc, systems, got_x, got_n, steps):
+    worst_all = 0.0
+    for i, s in enumerate(systems):
+        xo, norms = _oracle_steps(orc, s, steps)
+        worst = worst_in_eps(got_x[i], xo, s.limbs)
+        worst_all = max(worst_all, worst)
+        assert worst <= TOL, (i, s.name, s.limbs, s.n, s.degree, worst)
+        # the norm of the last coefficient's update, within the same tolerance
+        scale = max(float(np.abs(xo[:, 0]).max()), 1.0)
+        assert abs(got_n[i][0] - norms[-1][0]) <= 1e-6 * norms[-1][0] + TOL * 2.0 ** (-52 * s.limbs) * scale, (
+            i, got_n[i][0], norms[-1][0])
+    return worst_all
+
+
+def test_batched_against_oracle_full_width(md, orc):
+    """One mixed batch (dd and qd, n from 1 to 32, d from 5 to 31), two Newton
+    steps, every system against two oracle steps."""
+    systems = _full_width_batch()
+    got_x, got_n, _ = _batched_steps(md, systems, 2)
+    worst = _assert_batch_matches_oracle(orc, systems, got_x, got_n, 2)
+    print("batched vs oracle, full-width mixed batch: worst rel/eps", worst)
+
+
+def _skewed_full_width():
+    """A few large double-double systems among many small ones and some quad
+    double ones, all full width: the autotuner then runs the small ones
+    several CTAs per SM and gives the largest whole SMs."""
+    out = [mdgen.random_system(400, n=24, K=2, cplx=True, d=12, monos=24, maxvars=2, maxdeg=3, name="big0"),
+           mdgen.random_system(401, n=20, K=2, cplx=True, d=10, monos=20, maxvars=2, maxdeg=3, name="big1")]
+    out += [mdgen.random_system(410 + b, n=8, K=2, cplx=True, d=6, monos=8, maxvars=2, maxdeg=3, name=f"mid{b}")
+            for b in range(4)]
+    rng = np.random.default_rng(5)
+    out += [mdgen.random_system(500 + b, n=int(rng.integers(2, 5)), K=2, cplx=True, d=int(rng.integers(1, 4)),
+                                monos=4, maxvars=2, maxdeg=3, name=f"tiny{b}") for b in range(300)]
+    out += [mdgen.random_system(900 + b, n=4, K=4, cplx=True, d=3, monos=4, maxvars=2, maxdeg=3, name=f"qd{b}")
+            for b in range(40)]
+    return out
+
+
+def test_batched_skewed_against_oracle(md, orc):
+    """The skewed batch through the autotuner and the graph (whole-SM CTAs for
+    the largest systems when the tuner shares SMs), every system against the
+    oracle."""
+    import torch
+
+    systems = _skewed_full_width()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        got_x, got_n, _ = _batched_steps(md, systems, 2, flags=md.FLAG_AUTOTUNE | md.FLAG_GRAPH, stream=stream)
+    worst = _assert_batch_matches_oracle(orc, systems, got_x, got_n, 2)
+    print("batched vs oracle, skewed full-width batch: worst rel/eps", worst)

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import mdgen
-from mdcompare import md_diff, md_value, modulus
+from mdcompare import TOL, eps, worst_in_eps
 
 pytestmark = pytest.mark.gpu
 
@@ -34,17 +34,11 @@ def _run(md, s, x0, degrees, max_iter, tol, too_large, flags=0):
     return x.cpu().numpy(), rep
 
 
-def _rel(got, want):
-    diff = modulus(md_diff(got, want))
-    scale = np.maximum(modulus(md_value(want)).max(axis=0), 1e-300)
-    return float((diff.max(axis=0) / scale).max())
-
-
-def _margin_ok(rep, tol, too_large):
-    """Every decision value is at least 100x away from its threshold."""
+def _margin_ok(rep, tol, too_large, factor=1e2):
+    """Every decision value is at least `factor` times away from its threshold."""
     for v in rep["dx_norm"]:
         for th in (tol, too_large):
-            if th > 0 and v > 0 and 1e-2 < v / th < 1e2:
+            if th > 0 and v > 0 and 1.0 / factor < v / th < factor:
                 return False
     return True
 
@@ -58,7 +52,7 @@ def test_sqrt_ladder(md, orc, K, tol):
     xo, ro = orc.newton_run(s, [8, 16], [8, 8], tol, 1.0, x0)
     assert rg["iterations"] == ro["iterations"] == [4, 2]
     assert rg["levels_done"] == 2 and rg["converged"]
-    assert _rel(xg, xo) <= 1e3 * 2.0 ** (-52 * K)
+    assert worst_in_eps(xg, xo, K) <= TOL
 
 
 def test_too_large_stops(md, orc):
@@ -72,19 +66,23 @@ def test_too_large_stops(md, orc):
     assert np.array_equal(xg[..., 9:], x0[..., 9:])
 
 
-@pytest.mark.parametrize("seed", [1, 2])
+@pytest.mark.parametrize("seed", [1, 2, 6])
 def test_random_system_ladder(md, orc, seed):
-    """dd complex n=3, degrees 2 -> 4 -> 8 (the paper's 8/8/12-style limits)."""
+    """dd complex n=3, degrees 2 -> 4 -> 8 (the paper's 8/8/12-style limits).
+    The seeds are chosen so that every stop decision of the oracle's run is at
+    least three decades away from its threshold (asserted): rounding
+    differences between the GPU and the oracle cannot flip one."""
     s = mdgen.config_system(0, seed)
     degrees, max_iter, tol, tl = [2, 4, 8], [6, 6, 8], 1e-26, 1e3
     xo, ro = orc.newton_run(s, degrees, max_iter, tol, tl)
-    if not _margin_ok(ro, tol, tl):
-        pytest.skip("a stop decision of this seed is too close to its threshold")
+    assert _margin_ok(ro, tol, tl, 1e3), ro["dx_norm"]
     xg, rg = _run(md, s, s.x0, degrees, max_iter, tol, tl)
     assert rg["levels_done"] == ro["levels_done"]
     assert rg["iterations"] == ro["iterations"]
     assert rg["converged"] == ro["converged"]
-    assert _rel(xg, xo) <= 1e6 * 2.0 ** -104
+    worst = worst_in_eps(xg, xo, 2)
+    print("driver seed", seed, "worst rel/eps:", worst)
+    assert worst <= TOL
 
 
 def test_one_level_equals_steps(md):

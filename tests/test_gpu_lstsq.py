@@ -6,13 +6,9 @@ import numpy as np
 import pytest
 
 import mdgen
-from mdcompare import md_diff, md_value, modulus
+from mdcompare import TOL, eps, rel_by_degree, worst_in_eps
 
 pytestmark = pytest.mark.gpu
-
-
-def eps(K):
-    return 2.0 ** (-52 * K)
 
 
 @pytest.fixture(scope="module")
@@ -27,12 +23,6 @@ def md():
     import paper_2012_06607_gb300 as m
 
     return m
-
-
-def _rel_by_degree(got, want):
-    diff = modulus(md_diff(got, want))
-    scale = np.maximum(modulus(md_value(want)).max(axis=0), 1e-300)
-    return diff.max(axis=0) / scale
 
 
 def _tall(K, cplx, N, n, d, seed):
@@ -55,10 +45,10 @@ def test_lstsq_close_to_oracle(md, orc, K, cplx, N, n, d):
     assert dx.shape == (2 if cplx else 1, K, n, d + 1)
     want = orc.linsolve(K, cplx, A, b)
     rc = orc.rcond(K, cplx, A)
-    rel = _rel_by_degree(dx, want)
+    rel = rel_by_degree(dx, want)
     print("lstsq", K, cplx, N, n, d, "rcond", rc, "max rel/eps", float((rel / eps(K)).max()))
     for k in range(d + 1):
-        assert rel[k] <= 1e3 * eps(K) * (k + 1) / rc ** 2, (k, rel[k] / eps(K))
+        assert rel[k] <= TOL * eps(K) * (k + 1), (k, rel[k] / eps(K))
     r = md.lstsq_rcond(K, cplx, Ad, ws)
     assert float(r.item()) == pytest.approx(rc, rel=1e-8)
 
@@ -78,8 +68,9 @@ def test_consistent_overdetermined_newton(md, orc):
             assert md.device_status(ws) == 0
         xs[sys_.N] = x.cpu().numpy()
     xo, _ = orc.newton(sa, 4)
-    assert float((_rel_by_degree(xs[sa.N], xo) / eps(2)).max()) <= 1e6
-    assert float((_rel_by_degree(xs[sa.N], xs[s.n]) / eps(2)).max()) <= 1e6
+    w1, w2 = worst_in_eps(xs[sa.N], xo, 2), worst_in_eps(xs[sa.N], xs[s.n], 2)
+    print("consistent ls newton worst rel/eps: vs oracle", w1, "vs square system", w2)
+    assert w1 <= TOL and w2 <= TOL
 
 
 @pytest.mark.parametrize("seed,n,N,cplx,K,d", [(1, 3, 5, True, 2, 8), (2, 6, 9, False, 4, 6), (3, 16, 20, True, 4, 12)])
@@ -93,9 +84,9 @@ def test_overdetermined_newton_steps(md, orc, seed, n, N, cplx, K, d):
         md.newton_step(sysd, x, ws)
         assert md.device_status(ws) == 0
         xo, _ = orc.newton_step(s, xo)
-    rel = _rel_by_degree(x.cpu().numpy(), xo)
+    rel = rel_by_degree(x.cpu().numpy(), xo)
     print("ls newton", seed, n, N, "worst rel/eps", float((rel / eps(K)).max()))
-    assert float((rel / eps(K)).max()) <= 1e8
+    assert float((rel / eps(K)).max()) <= TOL
     # eval_diff shapes with N rows
     f, A = md.eval_diff(sysd, x, ws)
     assert tuple(f.shape) == (s.planes, K, N, d + 1) and tuple(A.shape) == (s.planes, K, d + 1, n, N)

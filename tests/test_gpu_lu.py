@@ -9,14 +9,10 @@ import numpy as np
 import pytest
 
 import mdgen
-from mdcompare import md_diff, md_value, modulus
+from mdcompare import TOL, eps, rel_by_degree, worst_in_eps
 
 pytestmark = pytest.mark.gpu
 LU = 0x10
-
-
-def eps(K):
-    return 2.0 ** (-52 * K)
 
 
 @pytest.fixture(scope="module")
@@ -31,12 +27,6 @@ def md():
     import paper_2012_06607_gb300 as m
 
     return m
-
-
-def _rel_by_degree(got, want):
-    diff = modulus(md_diff(got, want))
-    scale = np.maximum(modulus(md_value(want)).max(axis=0), 1e-300)
-    return diff.max(axis=0) / scale
 
 
 def _random_linear(K, cplx, n, d, seed, diag=4.0):
@@ -59,11 +49,11 @@ def test_lu_linsolve_close_to_oracle(md, orc, K, cplx, n, d):
     dx = md.linsolve(K, cplx, Ad, bd, ws, flags=LU).cpu().numpy()
     assert md.device_status(ws) == 0
     want = orc.linsolve(K, cplx, A, b, method=1)
-    rel = _rel_by_degree(dx, want)
+    rel = rel_by_degree(dx, want)
     rc = orc.rcond(K, cplx, A, method=1)
     print("lu", K, cplx, n, d, "rcond", rc, "max rel/eps", float((rel / eps(K)).max()))
     for k in range(d + 1):
-        assert rel[k] <= 1e3 * eps(K) * (k + 1) / rc, (k, rel[k] / eps(K))
+        assert rel[k] <= TOL * eps(K) * (k + 1), (k, rel[k] / eps(K))
     # rcond of the same A_0 from the device's W
     r = md.linsolve_rcond(K, cplx, Ad, ws, flags=LU)
     assert float(r.item()) == pytest.approx(rc, rel=1e-8)
@@ -104,8 +94,9 @@ def test_lu_newton_steps(md, orc, flags):
         md.newton_step(sysd, x, ws, flags=flags)
         assert md.device_status(ws) == 0
         xo, _ = orc.newton_step(s, xo, method=1)
-    rel = _rel_by_degree(x.cpu().numpy(), xo)
-    assert float((rel / eps(2)).max()) <= 1e6
+    worst = worst_in_eps(x.cpu().numpy(), xo, 2)
+    print("lu newton cfg0 flags", flags, "worst rel/eps:", worst)
+    assert worst <= TOL
 
 
 def test_lu_full_size_step(md, orc):
@@ -117,8 +108,9 @@ def test_lu_full_size_step(md, orc):
     md.newton_step(sysd, x, ws, flags=LU)
     assert md.device_status(ws) == 0
     xo, _ = orc.newton_step(s, s.x0, method=1)
-    rel = _rel_by_degree(x.cpu().numpy(), xo)
-    assert float((rel / eps(4)).max()) <= 1e12
+    worst = worst_in_eps(x.cpu().numpy(), xo, 4)
+    print("lu newton cfg1 worst rel/eps:", worst)
+    assert worst <= TOL
     r = md.rcond_a0(sysd, ws, LU)
     A0 = _a0_of(orc, s)
     assert float(r.item()) == pytest.approx(orc.rcond(4, True, A0, method=1), rel=1e-8)

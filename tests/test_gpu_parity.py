@@ -4,7 +4,12 @@ Elementwise md operations, series products and the evaluation /
 differentiation keep the oracle's operation order: they must agree bit for
 bit (IEEE equality of every limb).  The block Toeplitz solve runs tree
 reductions and an explicit A_0^-1 = R^-1 Q^H, so the solve and the Newton
-step are compared within a tolerance (see the test docstrings).
+step are compared within a tolerance: per degree k, the largest difference
+over the unknowns is at most 1e3 eps_K times the largest modulus of the
+reference's degree-k coefficients, eps_K = 2^(-52 K).  The reference is the
+oracle in the same precision, and for whole steps also the oracle run with
+more limbs on the same exact inputs (twice the limbs; ten for octo double),
+which stands in for the exact step.
 """
 import math
 import os
@@ -13,15 +18,11 @@ import numpy as np
 import pytest
 
 import mdgen
-from mdcompare import md_diff, md_value, modulus
+from mdcompare import TOL, eps, md_diff, md_value, modulus, rel_by_degree, worst_in_eps
 
 pytestmark = pytest.mark.gpu
 
 KS = [1, 2, 3, 4, 5, 8, 10]
-
-
-def eps(K):
-    return 2.0 ** (-52 * K)
 
 
 @pytest.fixture(scope="module")
@@ -120,14 +121,6 @@ def test_eval_diff_bit_exact_full_size(md, orc, cfg):
     _eval_case(md, orc, s, _perturbed_x(s, 5, 0.2))
 
 
-def _rel_err_by_degree(got, want):
-    """max over unknowns of |got - want| / max(|want_k|) per degree k."""
-    diff = modulus(md_diff(got, want))  # [n][d+1]
-    val = modulus(md_value(want))
-    scale = np.maximum(val.max(axis=0), 1e-300)
-    return diff.max(axis=0) / scale
-
-
 def _random_linear(K, cplx, n, d, seed, diag=4.0):
     rng = np.random.default_rng(seed)
     P = 2 if cplx else 1
@@ -149,7 +142,7 @@ def test_linsolve_close_to_oracle(md, orc, K, cplx, n, d):
     got = md.linsolve(K, cplx, md.to_device(A), md.to_device(b), ws).cpu().numpy()
     assert md.device_status(ws) == 0
     want = orc.linsolve(K, cplx, A, b)
-    rel = _rel_err_by_degree(got, want)
+    rel = rel_by_degree(got, want)
     print("linsolve", K, cplx, n, d, "max rel/eps:", float((rel / eps(K)).max()))
     for k in range(d + 1):
         assert rel[k] <= 1e3 * eps(K) * (k + 1), (k, rel[k] / eps(K))
@@ -175,7 +168,10 @@ def test_nonfinite_reported(md):
     assert md.device_status(ws) == 5
 
 
-def _newton_compare(md, orc, s, steps, tol_factor):
+def _newton_compare(md, orc, s, steps, tol_factor=TOL):
+    """`steps` GPU steps and oracle steps from x0 in the same precision; after
+    every step the series agree within tol_factor eps_K per degree, and the
+    norm of the last coefficient's update agrees too."""
     import torch
 
     sysd = md.DeviceSystem(s)
@@ -188,7 +184,7 @@ def _newton_compare(md, orc, s, steps, tol_factor):
         md.newton_step(sysd, x, ws, nrm)
         assert md.device_status(ws) == 0
         xo, nr = orc.newton_step(s, xo)
-        rel = _rel_err_by_degree(x.cpu().numpy(), xo)
+        rel = rel_by_degree(x.cpu().numpy(), xo)
         worst = max(worst, float((rel / eps(s.limbs)).max()))
         g = nrm.cpu().numpy()
         assert abs(g[0] - nr[0]) <= 1e-6 * max(nr[0], 1e-300) + 1e3 * eps(s.limbs) * max(
@@ -199,17 +195,47 @@ def _newton_compare(md, orc, s, steps, tol_factor):
 
 
 def test_newton_cfg0_four_steps(md, orc):
-    _newton_compare(md, orc, mdgen.config_system(0, 1), 4, 1e6)
+    _newton_compare(md, orc, mdgen.config_system(0, 1), 4)
 
 
 def test_newton_examples(md, orc):
-    _newton_compare(md, orc, mdgen.circle_system(2, 8), 5, 1e6)
-    _newton_compare(md, orc, mdgen.sqrt_system(4, 16), 5, 1e6)
+    _newton_compare(md, orc, mdgen.circle_system(2, 8), 5)
+    _newton_compare(md, orc, mdgen.sqrt_system(4, 16), 5)
 
 
 @pytest.mark.parametrize("cfg", [1, 2])
 def test_newton_full_size_one_step(md, orc, cfg):
-    _newton_compare(md, orc, mdgen.config_system(cfg, 1), 1, 1e12)
+    _newton_compare(md, orc, mdgen.config_system(cfg, 1), 1)
+
+
+def _gpu_steps(md, s, steps):
+    import torch
+
+    sysd = md.DeviceSystem(s)
+    ws = md.workspace(sysd.workspace_bytes())
+    x = md.to_device(s.x0)
+    nrm = torch.zeros(2, dtype=torch.float64, device="cuda")
+    for _ in range(steps):
+        md.newton_step(sysd, x, ws, nrm)
+        assert md.device_status(ws) == 0
+    return x.cpu().numpy()
+
+
+@pytest.mark.parametrize("cfg,steps,Kref", [(0, 4, 4), (1, 1, 8), (2, 1, 10)])
+def test_newton_against_more_limbs(md, orc, cfg, steps, Kref):
+    """Whole steps against the oracle with more limbs on the same exact inputs
+    (the coefficients, constants and x0 of the K-limb system re-expanded into
+    Kref limbs): double double (4 steps, reference quad double), quad double
+    (the n = 64, d = 64 step, reference octo double), octo double (the
+    n = 128, d = 32 step, reference deca double).  Per degree within
+    1e3 eps_K of the reference."""
+    s = mdgen.config_system(cfg, 1)
+    got = _gpu_steps(md, s, steps)
+    ref = s.with_limbs(Kref)
+    xr, _ = orc.newton(ref, steps)
+    worst = worst_in_eps(got, xr, s.limbs)
+    print(s.name, "against", Kref, "limbs: worst rel err / eps_K:", worst)
+    assert worst <= TOL
 
 
 def test_deterministic(md):
@@ -254,10 +280,9 @@ def test_newton_other_precisions(md, orc, K, cplx):
     a random system against the oracle in the same precision."""
     s = mdgen.random_system(40 + K, n=6, K=K, cplx=cplx, d=10, monos=5, maxvars=3, maxdeg=3,
                             coef_kind="unit" if cplx else "uniform", name=f"k{K}")
-    worst = _newton_compare(md, orc, s, 4, 1e6)
-    assert worst <= 1e6
+    _newton_compare(md, orc, s, 4)
 
 
 def test_newton_octo_double_two_steps(md, orc):
     """Octo double real, n = 128, d = 32: two full steps against the oracle."""
-    _newton_compare(md, orc, mdgen.config_system(2, 1), 2, 1e12)
+    _newton_compare(md, orc, mdgen.config_system(2, 1), 2)
