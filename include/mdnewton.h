@@ -45,7 +45,8 @@ typedef enum md_status {
   MD_ERR_SINGULAR = 4,    /* A_0 is singular (a Householder column norm is 0)   */
   MD_ERR_NONFINITE = 5,   /* an update contains Inf or NaN                      */
   MD_ERR_NOCONV = 6,      /* reserved for drivers that iterate to a tolerance   */
-  MD_ERR_TIMEOUT = 7,     /* reserved: a bounded device wait ran out            */
+  MD_ERR_TIMEOUT = 7,     /* a bounded device wait ran out (md_wait_selftest, the
+                             batched form's placement gate; results unaffected) */
   MD_ERR_UNSUPPORTED = 8, /* valid request this build does not implement        */
   MD_ERR_CHECK = 9        /* MD_FLAG_CHECK: a plan table or layout out of bounds */
 } md_status;
@@ -287,9 +288,27 @@ md_status md_batched_job_costs(int nsys, const md_system *sys, double *cost);
 /*
  * Synchronise `stream`, read the sticky device status word of `ws` (written by
  * the calls above that used this workspace), clear it and return it
- * (MD_OK, MD_ERR_SINGULAR or MD_ERR_NONFINITE).
+ * (MD_OK, MD_ERR_SINGULAR, MD_ERR_NONFINITE or MD_ERR_TIMEOUT, in that order
+ * of precedence).  MD_ERR_TIMEOUT from a batched step means that its
+ * placement gate (a one-thread kernel waiting, at most about 0.1 s, until the
+ * whole-SM CTAs are resident) gave up: the step's results are unaffected, only
+ * the order in which CTAs were placed was not enforced.
  */
 md_status md_get_device_status(void *ws, void *stream);
+
+/*
+ * Failure-detection check of the library's one bounded device wait (no
+ * counterpart in the paper).  Clears the first 256 bytes of `ws` (the status
+ * word and the batched form's counters) and runs the batched form's placement
+ * gate on `stream` against a counter there that nothing increments, with the
+ * given target.  target = 0: the wait ends at once, the status stays MD_OK.
+ * target >= 1: the wait runs out after about 0.1 s and sets the timeout bit,
+ * so that md_get_device_status(ws, stream) returns MD_ERR_TIMEOUT.  The
+ * context stays usable either way.
+ *   ws: DEVICE, >= 256 bytes, 256-byte aligned (MD_ERR_WORKSPACE otherwise).
+ * Errors: MD_ERR_ARG (target < 0), MD_ERR_WORKSPACE, MD_ERR_CUDA.
+ */
+md_status md_wait_selftest(void *ws, size_t ws_bytes, int target, void *stream);
 
 /*
  * Allocation-free block Toeplitz solve.  The paper has no counterpart: this is
@@ -305,15 +324,26 @@ md_status md_get_device_status(void *ws, void *stream);
  * process exits.  Requests whose md_linsolve_workspace_bytes() exceeds it are
  * rejected with MD_ERR_WORKSPACE before any device work (16 MiB holds, e.g.,
  * n = 64, d = 64 in quad double complex).  The call allocates nothing.
+ *   - The array is claimed on a device when the CUDA runtime loads the
+ *     library's module there.  With lazy module loading (the default since
+ *     CUDA 12.2) that can be this entry point's first call on the device,
+ *     which then returns MD_ERR_CUDA if the device has no 16 MiB left.  Callers
+ *     that reserve device memory up to the limit should make one call (or set
+ *     CUDA_MODULE_LOADING=EAGER) before reserving the rest.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture on the device.
+ *     (cudaGetSymbolAddress) with that device current and keeps it; make that
+ *     first call before any stream capture on the device.  The address belongs
+ *     to the context current at that call (the runtime's primary context of
+ *     the device); after cudaDeviceReset, or from another context on the same
+ *     device, do not call this entry point again in the same process.
  *   - Every call on a device shares the one array and it keeps the last call's
  *     contents; calls whose work may overlap on the GPU (different streams,
  *     host threads) race on it and must be serialised by the caller.
  *   - The device status word lives in that array too, so device-detected
  *     conditions (singular A_0) are not readable through
- *     md_get_device_status; a singular A_0 shows as non-finite entries of dx.
+ *     md_get_device_status; a singular A_0 (QR: a zero Householder column
+ *     norm; LU: a zero pivot) shows as non-finite entries of dx, because the
+ *     reciprocal of the zero pivot spreads into every later column.
  */
 #define MD_STATIC_WS_BYTES (16u << 20)
 md_status md_linsolve_series_static(int limbs, int is_complex, int n, int degree, const double *A, const double *b,

@@ -101,9 +101,10 @@ def lib():
         L.md_lstsq_workspace_bytes.restype = sz
         L.md_lstsq_series.argtypes = [i, i, i, i, i, vp, vp, vp, vp, sz, i, vp]
         L.md_lstsq_rcond.argtypes = [i, i, i, i, i, vp, vp, sz, i, vp, vp]
+        L.md_wait_selftest.argtypes = [vp, sz, i, vp]
         for name in ("md_elementwise", "md_series_conv", "md_eval_diff", "md_linsolve_series",
                      "md_newton_series_step", "md_get_device_status", "md_newton_series_run", "md_rcond_a0",
-                     "md_linsolve_rcond", "md_lstsq_series", "md_lstsq_rcond"):
+                     "md_linsolve_rcond", "md_lstsq_series", "md_lstsq_rcond", "md_wait_selftest"):
             getattr(L, name).restype = i
         _lib = L
     return _lib
@@ -116,7 +117,7 @@ def exported_symbols():
             "md_newton_series_step_batched", "md_linsolve_series_static", "md_profile_enable",
             "md_profile_read", "md_profile_kind_name", "md_newton_run_workspace_bytes", "md_newton_series_run",
             "md_rcond_a0", "md_linsolve_rcond", "md_lstsq_workspace_bytes", "md_lstsq_series", "md_lstsq_rcond",
-            "md_batched_job_costs", "md_plan_check"]
+            "md_batched_job_costs", "md_plan_check", "md_wait_selftest"]
 
 
 # --------------------------------------------------------------- helpers
@@ -403,6 +404,12 @@ def newton_step_batched(systems, xs, ws, dx_norm=None, times=None, flags: int = 
 
 def device_status(ws, stream=None) -> int:
     return int(lib().md_get_device_status(_ptr(ws), _stream(stream)))
+
+
+def wait_selftest(ws, target: int, stream=None) -> None:
+    """Runs the library's bounded device wait on a counter nothing increments
+    (md_wait_selftest); read the outcome with device_status."""
+    _check(lib().md_wait_selftest(_ptr(ws), ws.numel(), int(target), _stream(stream)), "md_wait_selftest")
 
 
 # ------------------------------------------------------------------ profiling

@@ -887,13 +887,16 @@ int big_jobs(const BatchPlan &bp, int sms) {
 // Holds back the launches after it on its stream until `target` CTAs have
 // counted themselves in at `resident`, so that the whole-SM CTAs are placed
 // before CTAs that share SMs take the rest.  It only orders placement (no
-// result depends on it) and gives up after about a tenth of a second.
-__global__ void batch_gate_kernel(const int *resident, int target) {
+// result depends on it) and gives up after about a tenth of a second; giving
+// up sets ST_TIMEOUT in the status word (md_get_device_status then reports
+// MD_ERR_TIMEOUT: the results stand, the placement was not enforced).
+__global__ void batch_gate_kernel(const int *resident, int target, int *status) {
   if (threadIdx.x != 0) return;
   for (int it = 0; it < 100000; ++it) {
     if (*reinterpret_cast<const volatile int *>(resident) >= target) return;
     __nanosleep(1000);
   }
+  atomicOr(status, mdk::ST_TIMEOUT);
 }
 
 struct DevAux;
@@ -937,7 +940,7 @@ cudaError_t batch_enqueue(const BatchPlan &bp, char *base, double *nrm, unsigned
     b.resident = ctr + kResidentCounter;
     b.times_stride = tstride;
     if ((e = dispatch(c.K, c.P, 4, &b, s)) != cudaSuccess) return e;
-    batch_gate_kernel<<<1, 32, 0, s2>>>(ctr + kResidentCounter, nbig);
+    batch_gate_kernel<<<1, 32, 0, s2>>>(ctr + kResidentCounter, nbig, reinterpret_cast<int *>(base));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   for (size_t ci = 0; ci < bp.classes.size(); ++ci) {
@@ -1549,7 +1552,20 @@ md_status md_get_device_status(void *ws, void *stream) {
   if (cudaMemset(ws, 0, sizeof(int)) != cudaSuccess) return MD_ERR_CUDA;
   if (word & mdk::ST_SINGULAR) return MD_ERR_SINGULAR;
   if (word & mdk::ST_NONFINITE) return MD_ERR_NONFINITE;
+  if (word & mdk::ST_TIMEOUT) return MD_ERR_TIMEOUT;
   return MD_OK;
+}
+
+md_status md_wait_selftest(void *ws, size_t ws_bytes, int target, void *stream) {
+  if (!ws || ws_bytes < 256 || (reinterpret_cast<uintptr_t>(ws) & 255) != 0) return MD_ERR_WORKSPACE;
+  if (target < 0) return MD_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char *base = static_cast<char *>(ws);
+  cudaError_t e = cudaMemsetAsync(base, 0, 256, s);
+  if (e != cudaSuccess) return MD_ERR_CUDA;
+  int *ctr = reinterpret_cast<int *>(base + 64);
+  batch_gate_kernel<<<1, 32, 0, s>>>(ctr + kResidentCounter, target, reinterpret_cast<int *>(base));
+  return cuda_status(cudaGetLastError());
 }
 
 }  // extern "C"

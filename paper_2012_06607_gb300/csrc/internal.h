@@ -6,7 +6,7 @@
 
 namespace mdk {
 
-enum : int { ST_SINGULAR = 1, ST_NONFINITE = 2 };
+enum : int { ST_SINGULAR = 1, ST_NONFINITE = 2, ST_TIMEOUT = 4 };
 
 // Kernel classes for the optional per-launch timing (md_profile_*).
 enum ProfKind : int {

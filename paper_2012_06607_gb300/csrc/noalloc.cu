@@ -6,8 +6,10 @@
 // synchronise the device, and plug-in or callback contexts that forbid
 // allocation.  This entry point takes only inputs and outputs.  Its scratch
 // space is a file-scope device array of MD_STATIC_WS_BYTES that lives in the
-// library's own module: every GPU that loads the library holds it until the
-// process exits.
+// library's own module: every GPU that loads the module holds it until the
+// process exits.  With lazy module loading the module, and so the array, is
+// loaded on a device at its first use there, which may be the first call of
+// this entry point.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -25,7 +27,8 @@ std::mutex g_static_mu;
 void *g_static_addr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on the current device, looked up once
-// per device with that device current.
+// per device with that device current and kept: it is the address in the
+// context current at that first call (the runtime's primary context).
 md_status static_ws_address(void **out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MD_ERR_CUDA;

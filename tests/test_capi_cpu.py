@@ -135,6 +135,12 @@ def test_argument_errors_before_cuda(mdlib):
     assert mdlib.md_newton_series_step(ctypes.byref(c), 1, None, 256, 64, 0, None) == 2
     assert mdlib.md_eval_diff(ctypes.byref(c), None, 1, 1, 256, 1 << 30, None) == 1
     assert mdlib.md_get_device_status(None, None) == 2
+    mdlib.md_wait_selftest.restype = ctypes.c_int
+    mdlib.md_wait_selftest.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p]
+    assert mdlib.md_wait_selftest(None, 256, 1, None) == 2
+    assert mdlib.md_wait_selftest(256, 64, 1, None) == 2  # too small
+    assert mdlib.md_wait_selftest(264, 256, 1, None) == 2  # misaligned
+    assert mdlib.md_wait_selftest(256, 256, -1, None) == 1
 
 
 def test_newton_run_host_checks(mdlib):

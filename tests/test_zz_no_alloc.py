@@ -4,10 +4,12 @@ md_linsolve_series_static serves callers that cannot allocate a device
 workspace (device memory owned by another allocator or reserved to the limit,
 code where cudaMalloc/cudaFree would synchronise the device, contexts that
 forbid allocation): it runs the same solve in a static 16 MiB device array of
-the library.  Two calls in a row with different systems must each match the
-workspace entry point within the tolerance of the solve tests; oversize
-requests are refused before any device work.  Collected last on purpose, and
-self-contained so that it also passes alone in a fresh process.
+the library.  It runs the same kernels on the same workspace layout, so two
+calls in a row with different systems must each give exactly the bits of the
+workspace entry point (and so lie within the solve tests' tolerance), with the
+QR, LU and split-product forms; a singular A_0 shows as non-finite entries of
+dx; oversize requests are refused before any device work.  Collected last on
+purpose, and self-contained so that it also passes alone in a fresh process.
 """
 import ctypes
 
@@ -48,23 +50,23 @@ def _system(K, cplx, n, d, seed):
     return A, b
 
 
-def _static_solve(md, K, cplx, A, b):
+def _static_solve(md, K, cplx, A, b, flags=0):
     import torch
 
     Ad, bd = md.to_device(A), md.to_device(b)
     dx = torch.empty_like(bd)
     n, d = b.shape[2], b.shape[3] - 1
-    st = md.lib().md_linsolve_series_static(K, int(cplx), n, d, Ad.data_ptr(), bd.data_ptr(), dx.data_ptr(), 0,
+    st = md.lib().md_linsolve_series_static(K, int(cplx), n, d, Ad.data_ptr(), bd.data_ptr(), dx.data_ptr(), flags,
                                              torch.cuda.current_stream().cuda_stream)
     assert st == 0, st
     torch.cuda.synchronize()
     return dx.cpu().numpy()
 
 
-def _reference_solve(md, K, cplx, A, b):
+def _reference_solve(md, K, cplx, A, b, flags=0):
     n, d = b.shape[2], b.shape[3] - 1
-    ws = md.workspace(md.linsolve_workspace_bytes(K, cplx, n, d))
-    dx = md.linsolve(K, cplx, md.to_device(A), md.to_device(b), ws).cpu().numpy()
+    ws = md.workspace(md.linsolve_workspace_bytes(K, cplx, n, d, flags))
+    dx = md.linsolve(K, cplx, md.to_device(A), md.to_device(b), ws, flags=flags).cpu().numpy()
     assert md.device_status(ws) == 0
     return dx
 
@@ -77,13 +79,38 @@ def _check_close(got, want, K):
         assert rel[k] <= 1e3 * eps(K) * (k + 1), (k, rel[k] / eps(K))
 
 
-def test_static_matches_workspace_entry_point_twice(md):
+LU, OZAKI = 0x10, 0x1
+
+
+@pytest.mark.parametrize("flags", [0, LU, OZAKI])
+def test_static_matches_workspace_entry_point_twice(md, flags):
     cases = [(4, True, 16, 12, 1), (2, False, 24, 9, 2)]
     for K, cplx, n, d, seed in cases:  # two calls in a row, different systems
         A, b = _system(K, cplx, n, d, seed)
-        got = _static_solve(md, K, cplx, A, b)
-        want = _reference_solve(md, K, cplx, A, b)
+        got = _static_solve(md, K, cplx, A, b, flags)
+        want = _reference_solve(md, K, cplx, A, b, flags)
+        assert np.array_equal(got, want), (flags, K, n, d)
         _check_close(got, want, K)
+
+
+@pytest.mark.parametrize("flags", [0, LU])
+@pytest.mark.parametrize("col", [0, 3, 7])
+def test_static_singular_gives_nonfinite_dx(md, flags, col):
+    """A_0 with one exactly zero column (first, middle, last): the status word
+    is not readable on this path, so the header promises non-finite entries
+    in dx instead.  The workspace entry point reports MD_ERR_SINGULAR for the
+    same A_0."""
+    K, cplx, n, d = 2, True, 8, 3
+    A, b = _system(K, cplx, n, d, 11 + col)
+    A[:, :, 0, col, :] = 0.0
+    got = _static_solve(md, K, cplx, A, b, flags)
+    assert not np.isfinite(got).all(), (flags, col)
+    ws = md.workspace(md.linsolve_workspace_bytes(K, cplx, n, d, flags))
+    md.linsolve(K, cplx, md.to_device(A), md.to_device(b), ws, flags=flags)
+    assert md.device_status(ws) == 4  # MD_ERR_SINGULAR
+    # and the next call on the shared array is clean again
+    A2, b2 = _system(K, cplx, n, d, 5)
+    assert np.array_equal(_static_solve(md, K, cplx, A2, b2, flags), _reference_solve(md, K, cplx, A2, b2, flags))
 
 
 def test_static_rejects_oversize(md):
