@@ -414,6 +414,17 @@ md_status md_newton_series_run(const md_system *sys, double *x, const md_newton_
                                md_newton_report *rep, void *ws, size_t ws_bytes, int flags, void *stream);
 
 /*
+ * Test hook of the plan cache (no counterpart in the paper).  The library
+ * caches the product schedule of each system structure under a 64-bit hash of
+ * the structure and, on a hit, compares the stored structure with the
+ * caller's, so that a colliding structure gets its own plan.  To let tests
+ * exercise that path, this narrows every structure hash to `mask` (so that
+ * structures collide); 0 restores the full hash.  Results never depend on
+ * it; only the cache's hit rate does.  Host only.
+ */
+void md_plan_cache_hash_mask(unsigned long long mask);
+
+/*
  * Optional timing of the library's own kernels (tracing support; not part of
  * the computation).  While enabled, every kernel launch of every call in this
  * process is bracketed by two CUDA events on its stream.

@@ -102,6 +102,8 @@ def lib():
         L.md_lstsq_series.argtypes = [i, i, i, i, i, vp, vp, vp, vp, sz, i, vp]
         L.md_lstsq_rcond.argtypes = [i, i, i, i, i, vp, vp, sz, i, vp, vp]
         L.md_wait_selftest.argtypes = [vp, sz, i, vp]
+        L.md_plan_cache_hash_mask.argtypes = [ctypes.c_ulonglong]
+        L.md_plan_cache_hash_mask.restype = None
         for name in ("md_elementwise", "md_series_conv", "md_eval_diff", "md_linsolve_series",
                      "md_newton_series_step", "md_get_device_status", "md_newton_series_run", "md_rcond_a0",
                      "md_linsolve_rcond", "md_lstsq_series", "md_lstsq_rcond", "md_wait_selftest"):
@@ -117,7 +119,7 @@ def exported_symbols():
             "md_newton_series_step_batched", "md_linsolve_series_static", "md_profile_enable",
             "md_profile_read", "md_profile_kind_name", "md_newton_run_workspace_bytes", "md_newton_series_run",
             "md_rcond_a0", "md_linsolve_rcond", "md_lstsq_workspace_bytes", "md_lstsq_series", "md_lstsq_rcond",
-            "md_batched_job_costs", "md_plan_check", "md_wait_selftest"]
+            "md_batched_job_costs", "md_plan_check", "md_wait_selftest", "md_plan_cache_hash_mask"]
 
 
 # --------------------------------------------------------------- helpers

@@ -150,6 +150,11 @@ struct Plan {
   size_t off_f = 0, off_A = 0, off_prod = 0, off_solve = 0, total = 0;
   SolveLayout sl{};
   uint64_t checksum = 0;
+  // the planned structure itself, compared with the caller's on every cache
+  // hit (a 64-bit hash can collide)
+  int hdr[6] = {0, 0, 0, 0, 0, 0};
+  std::vector<int> s_poly, s_nvar, s_idx, s_expo;
+  int oz = 0;  // laid out for the split-product form
 };
 
 uint64_t fnv(uint64_t h, const void *p, size_t bytes) {
@@ -188,6 +193,10 @@ uint64_t hash_bytes(uint64_t h, const void *p, size_t bytes) {
   return (r ^ (uint64_t)bytes) * prime;
 }
 
+// Mask applied to every structure checksum (all ones; tests narrow it with
+// md_plan_cache_hash_mask to make different structures collide).
+std::atomic<uint64_t> g_hash_mask{~0ULL};
+
 uint64_t structure_checksum(const md_system *s) {
   uint64_t h = 1469598103934665603ULL;
   const int hdr[6] = {s->limbs, s->is_complex, s->n, s->degree, s->nmono, neq_of(s)};
@@ -196,7 +205,31 @@ uint64_t structure_checksum(const md_system *s) {
   h = hash_bytes(h, s->nvar, sizeof(int) * s->nmono);
   h = hash_bytes(h, s->idx, sizeof(int) * s->nmono * MD_MAXV);
   h = hash_bytes(h, s->expo, sizeof(int) * s->nmono * MD_MAXV);
-  return h | 1;  // never 0 (0 marks "not computed")
+  return (h & g_hash_mask.load(std::memory_order_relaxed)) | 1;  // never 0 (0 marks "not computed")
+}
+
+void structure_header(const md_system *s, int (&hdr)[6]) {
+  hdr[0] = s->limbs;
+  hdr[1] = s->is_complex;
+  hdr[2] = s->n;
+  hdr[3] = s->degree;
+  hdr[4] = s->nmono;
+  hdr[5] = neq_of(s);
+}
+
+template <class T>
+bool same_ints(const std::vector<int> &v, const T *a, size_t count) {
+  return v.size() == count && (count == 0 || std::memcmp(v.data(), a, sizeof(int) * count) == 0);
+}
+
+// Is `p` the plan of the structure of `s` (header and every structure array)?
+bool same_structure(const Plan &p, const md_system *s) {
+  int hdr[6];
+  structure_header(s, hdr);
+  if (std::memcmp(hdr, p.hdr, sizeof(hdr)) != 0) return false;
+  const size_t nm = (size_t)s->nmono;
+  return same_ints(p.s_poly, s->poly_ptr, (size_t)neq_of(s) + 1) && same_ints(p.s_nvar, s->nvar, nm) &&
+         same_ints(p.s_idx, s->idx, nm * MD_MAXV) && same_ints(p.s_expo, s->expo, nm * MD_MAXV);
 }
 
 // Sizes, pointers and polynomial offsets (what the structure hash needs).
@@ -383,6 +416,14 @@ md_status build_plan(const md_system *s, Plan &p, int flags = 0) {
   p.sl = solve_layout(p.K, p.P, N, n, d, o, flags);
   p.total = o + p.sl.bytes;
   p.checksum = structure_checksum(s);
+  p.oz = (flags & MD_FLAG_OZAKI) ? 1 : 0;
+  structure_header(s, p.hdr);
+  p.s_poly.assign(s->poly_ptr, s->poly_ptr + N + 1);
+  if (s->nmono > 0) {
+    p.s_nvar.assign(s->nvar, s->nvar + s->nmono);
+    p.s_idx.assign(s->idx, s->idx + (size_t)s->nmono * MD_MAXV);
+    p.s_expo.assign(s->expo, s->expo + (size_t)s->nmono * MD_MAXV);
+  }
   return MD_OK;
 }
 
@@ -459,17 +500,47 @@ md_status check_plan(const Plan &p) {
 // Plans are cached per system structure (checksum) together with a pinned host
 // image of their integer tables; every call copies that image into its
 // workspace with one asynchronous copy, so a workspace needs no state between
-// calls.  Beyond kPlanCache structures the least recently used plans are
-// dropped; a call holds its plan by shared_ptr, and a dropped image is freed
-// after a device synchronisation (in-flight copies may still read it), which
-// is skipped while the calling stream is being captured.
+// calls.  A hit is taken only if the stored structure equals the caller's
+// (a colliding structure gets its own plan).  Beyond kPlanCache structures
+// the least recently used plans are dropped; a call holds its plan by
+// shared_ptr, and a dropped image is freed once the copies enqueued from it
+// have run (an event per stream), which is skipped while the calling stream
+// is being captured.  A plan used inside a capture is never dropped: the
+// caller's graph copies from its image on every replay.
+// Events recorded on each stream after a use of a pinned image (one per
+// stream), so that dropping the image waits for its own copies only.
+struct UseEvents {
+  std::vector<std::pair<cudaStream_t, cudaEvent_t>> ev;
+  // after an enqueue on s (not during a capture)
+  cudaError_t record(cudaStream_t s) {
+    for (auto &p : ev)
+      if (p.first == s) return cudaEventRecord(p.second, s);
+    cudaEvent_t e = nullptr;
+    cudaError_t err = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    if (err != cudaSuccess) return err;
+    ev.emplace_back(s, e);
+    return cudaEventRecord(e, s);
+  }
+  void wait_and_release() {
+    for (auto &p : ev) {
+      cudaEventSynchronize(p.second);
+      cudaEventDestroy(p.second);
+    }
+    ev.clear();
+  }
+};
+
 struct PlanEntry {
   Plan plan;
   int *pinned = nullptr;  // tables laid out exactly as in the workspace, from off_tasks
   size_t image_bytes = 0;
+  UseEvents uses;
+  // used while a stream was being captured: a caller's graph may copy from
+  // the pinned image whenever it is replayed, so the entry is never dropped
+  bool captured = false;
   ~PlanEntry() {
     if (pinned) {
-      cudaDeviceSynchronize();
+      uses.wait_and_release();
       cudaFreeHost(pinned);
     }
   }
@@ -524,10 +595,30 @@ struct LruCache {
 LruCache<PlanEntry> &g_plans = *new LruCache<PlanEntry>;
 
 // Under g_mu: mark `key` used, then drop the least recently used plans beyond
-// the bound (those with a pinned image only if may_sync).
+// the bound (those with a pinned image only if may_sync; never one used in a
+// capture).
 void plans_touch(uint64_t key, bool may_sync) {
   g_plans.touch(key);
-  g_plans.evict(kPlanCache, key, [&](const PlanEntry &e) { return !may_sync && e.pinned; });
+  g_plans.evict(kPlanCache, key, [&](const PlanEntry &e) { return e.captured || (!may_sync && e.pinned); });
+}
+
+// Under g_mu: the cached plan of structure `s` with checksum `cs`, planned
+// (and cached under `cs`) if there is none or if the cached one belongs to a
+// different structure whose checksum collides with this one's.
+md_status plan_cached(const md_system *s, uint64_t cs, int flags, std::shared_ptr<PlanEntry> &hold) {
+  hold = g_plans.find(cs);
+  if (hold && same_structure(hold->plan, s) && hold->plan.oz == ((flags & MD_FLAG_OZAKI) ? 1 : 0)) return MD_OK;
+  md_status st = check_system(s);  // a cached structure passed it when it was planned
+  if (st != MD_OK) return st;
+  std::shared_ptr<PlanEntry> e = std::make_shared<PlanEntry>();
+  if ((st = build_plan(s, e->plan, flags)) != MD_OK) return st;
+  if (hold && hold->captured) {  // keep the captured entry alive: hold this one uncached
+    hold = e;
+    return MD_OK;
+  }
+  g_plans.put(cs, e);
+  hold = e;
+  return MD_OK;
 }
 
 bool not_capturing(cudaStream_t s) {
@@ -545,15 +636,7 @@ md_status prepare(const md_system *s, void *ws, size_t ws_bytes, cudaStream_t st
   const uint64_t cs = structure_checksum(s) ^ (0x9e3779b97f4a7c15ULL * (uint64_t)(flags & MD_FLAG_OZAKI));
   const bool may_sync = not_capturing(stream);
   std::lock_guard<std::mutex> lk(g_mu);
-  hold = g_plans.find(cs);
-  if (!hold) {
-    if ((st = check_system(s)) != MD_OK) return st;  // a cached structure passed it when it was planned
-    std::shared_ptr<PlanEntry> e = std::make_shared<PlanEntry>();
-    st = build_plan(s, e->plan, flags);
-    if (st != MD_OK) return st;
-    g_plans.put(cs, e);
-    hold = e;
-  }
+  if ((st = plan_cached(s, cs, flags, hold)) != MD_OK) return st;
   plans_touch(cs, may_sync);
   PlanEntry *pe = hold.get();
   if ((flags & MD_FLAG_CHECK) && (st = check_plan(pe->plan)) != MD_OK) return st;
@@ -580,6 +663,10 @@ md_status prepare(const md_system *s, void *ws, size_t ws_bytes, cudaStream_t st
   if (cudaMemcpyAsync(static_cast<char *>(ws) + p.off_tasks, pe->pinned, pe->image_bytes, cudaMemcpyHostToDevice,
                       stream) != cudaSuccess)
     return MD_ERR_CUDA;
+  if (!may_sync)
+    pe->captured = true;
+  else if (pe->uses.record(stream) != cudaSuccess)
+    return MD_ERR_CUDA;
   out = &pe->plan;
   return MD_OK;
 }
@@ -597,16 +684,7 @@ Plan *plan_of(const md_system *s, md_status &st, std::shared_ptr<PlanEntry> &hol
     cs = structure_checksum(s);
   }
   std::lock_guard<std::mutex> lk(g_mu);
-  if ((hold = g_plans.find(cs))) {
-    plans_touch(cs, may_sync);
-    return &hold->plan;
-  }
-  if ((st = check_system(s)) != MD_OK) return nullptr;
-  std::shared_ptr<PlanEntry> e = std::make_shared<PlanEntry>();
-  st = build_plan(s, e->plan, 0);
-  if (st != MD_OK) return nullptr;
-  g_plans.put(cs, e);
-  hold = e;
+  if ((st = plan_cached(s, cs, 0, hold)) != MD_OK) return nullptr;
   plans_touch(cs, may_sync);
   return &hold->plan;
 }
@@ -635,9 +713,12 @@ struct BatchPlan {
   cudaStream_t exec_stream = nullptr;
   bool exec_split = false;
   int exec_tstride = 2;
+  UseEvents uses;         // after each step enqueued on a stream
+  bool captured = false;  // enqueued into a caller's capture: never dropped
   ~BatchPlan() {
-    // a step in flight may still read the pinned image, directly or from the graph
-    if (exec || pinned) cudaDeviceSynchronize();
+    // a step in flight may still read the pinned image, directly or from the
+    // graph: wait for the steps enqueued with this plan, not the device
+    uses.wait_and_release();
     if (exec) cudaGraphExecDestroy(exec);
     if (pinned) cudaFreeHost(pinned);
   }
@@ -647,8 +728,9 @@ struct BatchPlan {
 // Beyond kBatchPlanCache the least recently used are dropped, so that callers
 // who pass new buffers on every call do not accumulate pinned images; a call
 // holds its plan by shared_ptr.  Dropping a plan with a pinned image or a
-// graph synchronises the device, so it is skipped while the calling stream
-// is being captured (the cache may then exceed the bound for a while).
+// graph waits for the steps enqueued with it (events), so it is skipped while
+// the calling stream is being captured (the cache may then exceed the bound
+// for a while); a plan enqueued into a caller's capture is never dropped.
 constexpr size_t kBatchPlanCache = 16;
 LruCache<BatchPlan> &g_batch = *new LruCache<BatchPlan>;  // never destroyed (as g_plans)
 
@@ -656,7 +738,8 @@ LruCache<BatchPlan> &g_batch = *new LruCache<BatchPlan>;  // never destroyed (as
 // beyond the bound (those with a pinned image or a graph only if may_sync).
 void batch_touch(uint64_t key, bool may_sync) {
   g_batch.touch(key);
-  g_batch.evict(kBatchPlanCache, key, [&](const BatchPlan &b) { return !may_sync && (b.pinned || b.exec); });
+  g_batch.evict(kBatchPlanCache, key,
+                [&](const BatchPlan &b) { return b.captured || (!may_sync && (b.pinned || b.exec)); });
 }
 
 double job_cost(const Plan &p) {
@@ -1507,10 +1590,19 @@ md_status md_newton_series_step_batched(int nsys, const md_system *sys, double *
       bp->exec_split = split;
       bp->exec_tstride = tstride;
     }
-    return cuda_status(cudaGraphLaunch(bp->exec, s));
+    if (cudaGraphLaunch(bp->exec, s) != cudaSuccess) return MD_ERR_CUDA;
+  } else if (batch_enqueue(*bp, base, dx_norm, times, s, sms, split, tstride) != cudaSuccess) {
+    return MD_ERR_CUDA;
   }
-  return cuda_status(batch_enqueue(*bp, base, dx_norm, times, s, sms, split, tstride));
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (cap != cudaStreamCaptureStatusNone) {
+    bp->captured = true;
+    return MD_OK;
+  }
+  return cuda_status(bp->uses.record(s));
 }
+
+void md_plan_cache_hash_mask(unsigned long long mask) { g_hash_mask.store(mask ? mask : ~0ULL); }
 
 void md_profile_enable(int on) {
   std::lock_guard<std::mutex> lk(g_prof_mu);

@@ -226,6 +226,30 @@ def test_batched_job_costs_host_only():
     assert md.lib().md_batched_job_costs(0, arr, None) == 1  # MD_ERR_ARG
 
 
+def test_plan_cache_collision_replans_host_only():
+    """Structures whose hashes collide (the test hook narrows every hash to one
+    value) each get their own plan: the host cost estimate of every system,
+    computed from its plan, equals its value with the full hash, whether the
+    colliding systems come in one call or in turns."""
+    import paper_2012_06607_gb300 as md
+
+    systems = [mdgen.config_system(0, 1), mdgen.config_system(0, 2),
+               mdgen.small_system_fast(np.random.default_rng(4), 6, 5, 2, monos=6),
+               mdgen.small_system_fast(np.random.default_rng(5), 9, 7, 4, monos=9)]
+    want = md.batched_job_costs(systems)
+    assert len(set(want)) == len(want)  # distinct structures, distinct costs
+    L = md.lib()
+    try:
+        L.md_plan_cache_hash_mask(1)  # every structure hashes to the same key
+        assert np.array_equal(md.batched_job_costs(systems), want)
+        for _ in range(2):
+            for s, w in zip(systems, want):
+                assert md.batched_job_costs([s])[0] == w
+    finally:
+        L.md_plan_cache_hash_mask(0)
+    assert np.array_equal(md.batched_job_costs(systems), want)
+
+
 def test_batched_plan_cache_bound_host_only():
     """Workspace queries over many distinct batches (new coefficient pointers
     each time) stay correct while the batch plan cache drops old entries."""
