@@ -533,20 +533,73 @@ def _fixed_unit(rng, size, bits=11):
     return np.round(np.cos(th) * sc) / sc + 1j * (np.round(np.sin(th) * sc) / sc)
 
 
-def small_system_fast(rng, n: int, d: int, K: int, monos: int, cond_max: float = 1e6, name: str = "") -> System:
+class UnitPool:
+    """Full-width unit complex numbers cos t + i sin t, t ~ U[0, 2 pi), made by
+    unit_complex (every limb in use, modulus 1 to about 2^(-53K)), with each
+    part also held as an exact integer over 2^B, B the finest limb bit of the
+    pool.  Draws pick uniformly from the pool: the batched workload takes its
+    coefficients from a seeded pool of `size` angles instead of one angle per
+    coefficient, which keeps its construction fast."""
+
+    def __init__(self, rng, K: int, size: int):
+        self.K = K
+        self.limbs = np.zeros((2, K, size))
+        for i in range(size):
+            re, im = unit_complex(float(rng.uniform(0.0, 2 * math.pi)), K)
+            self.limbs[0, :, i] = re
+            self.limbs[1, :, i] = im
+        # finest bit among all nonzero limbs: value * 2^B is an integer
+        nz = self.limbs[self.limbs != 0.0]
+        _, ex = np.frexp(nz)
+        self.B = int((53 - ex).max())
+        self.ints = [self._ints(self.limbs[p]) for p in range(2)]
+        self.dbl = self.limbs[0, 0] + 1j * self.limbs[1, 0]
+
+    def _ints(self, limbs):  # [K][size] -> object array of exact integers (value * 2^B)
+        out = np.zeros(limbs.shape[1], dtype=object)
+        for i in range(limbs.shape[1]):
+            v = 0
+            for l in range(self.K):
+                num, den = float(limbs[l, i]).as_integer_ratio()
+                v += num * ((1 << self.B) // den)
+            out[i] = v
+        return out
+
+
+def _cmul_obj(ar, ai, br, bi):
+    """Exact complex product of object arrays of Python integers."""
+    return ar * br - ai * bi, ar * bi + ai * br
+
+
+def small_system_fast(rng, n: int, d: int, K: int, monos: int, cond_max: float = 1e6, name: str = "",
+                      pool: Optional["UnitPool"] = None) -> System:
     """System as in the double-double n=3 configuration but of size n, built fast.
 
     Per polynomial `monos` distinct monomials of total degree <= 3 over one or two
-    variables (t included; the first monomial contains t).  Coefficients and x0
-    are cos t + i sin t with real and imaginary parts rounded to 11 fractional
-    bits: every product of a coefficient with at most three such numbers has at
-    most 44 fractional bits and every constant term (a sum of at most `monos`
-    such products, below 2^7 in modulus) is exact in double, so x0 solves the
-    system at t = 0 exactly.  Limbs below the leading one are zero.
+    variables (t included; the first monomial contains t).
+
+    With a UnitPool (`pool`, K limbs): coefficients and x0 are full-width unit
+    complex numbers drawn from the pool, as in the n = 3 configuration, and the
+    constant terms are the exact negated values of the t-free monomials at
+    (x0, t = 0), computed with Python integers on the pool's power-of-two scale
+    and rounded to K limbs, so that x0 solves the system at t = 0.
+
+    Without a pool: coefficients and x0 are cos t + i sin t with real and
+    imaginary parts rounded to 11 fractional bits; every product of a
+    coefficient with at most three such numbers has at most 44 fractional bits
+    and every constant term (a sum of at most `monos` such products, below 2^7
+    in modulus) is exact in double, so x0 solves the system at t = 0 exactly.
+    Limbs below the leading one are zero.
     """
     N = n + 1
+    if pool is not None:
+        assert pool.K == K
     for _ in range(64):
-        x0 = _fixed_unit(rng, n)
+        if pool is not None:
+            xi = rng.integers(0, pool.dbl.shape[0], n)
+            x0 = pool.dbl[xi]
+        else:
+            x0 = _fixed_unit(rng, n)
         V = np.zeros((n, monos, 2), dtype=np.int64)
         E = np.zeros((n, monos, 2), dtype=np.int64)
         Mv = np.zeros((n, monos), dtype=np.int64)
@@ -586,7 +639,11 @@ def small_system_fast(rng, n: int, d: int, K: int, monos: int, cond_max: float =
                 todo[i] = dup
         else:
             continue
-        c = _fixed_unit(rng, (n, monos))
+        if pool is not None:
+            ci = rng.integers(0, pool.dbl.shape[0], (n, monos))
+            c = pool.dbl[ci]
+        else:
+            c = _fixed_unit(rng, (n, monos))
         xt = np.concatenate([x0, [0.0]])  # t = 0
         p1 = xt[V[:, :, 0]] ** E[:, :, 0]
         p2 = np.where(Mv == 2, xt[V[:, :, 1]] ** E[:, :, 1], 1.0)
@@ -615,29 +672,79 @@ def small_system_fast(rng, n: int, d: int, K: int, monos: int, cond_max: float =
         idx[two, 1] = V[:, :, 1].ravel()[two]
         expo[two, 1] = E[:, :, 1].ravel()[two]
         coef = np.zeros((P, K, nm))
-        coef[0, 0] = c.real.ravel()
-        coef[1, 0] = c.imag.ravel()
         cs = np.zeros((P, K, n))
-        cs[0, 0] = cst.real
-        cs[1, 0] = cst.imag
         xx = np.zeros((P, K, n, d + 1))
-        xx[0, 0, :, 0] = x0.real
-        xx[1, 0, :, 0] = x0.imag
+        if pool is not None:
+            coef[:, :, :] = pool.limbs[:, :, ci.ravel()]
+            xx[:, :, :, 0] = pool.limbs[:, :, xi]
+            cs[:, :, :] = _exact_constants(pool, xi, ci, V, E, Mv, n)
+        else:
+            coef[0, 0] = c.real.ravel()
+            coef[1, 0] = c.imag.ravel()
+            cs[0, 0] = cst.real
+            cs[1, 0] = cst.imag
+            xx[0, 0, :, 0] = x0.real
+            xx[1, 0, :, 0] = x0.imag
         poly_ptr = np.arange(0, nm + 1, monos, dtype=np.int32)
         return System(K, True, n, d, poly_ptr, nvar, idx.ravel(), expo.ravel(), coef, cs, xx, name=name,
                       meta={"cond_double": float(np.linalg.cond(Jm))})
     raise RuntimeError("no regular draw found")
 
 
-def batch_systems(seed: int = 1, count: int = 2048, nmin: int = 8, nmax: int = 64, dmin: int = 8, dmax: int = 32):
+def _exact_constants(pool, xi, ci, V, E, Mv, n):
+    """Constant terms [2][K][n]: minus the exact sum, per polynomial, of the
+    t-free monomials c x_v1^e1 x_v2^e2 at x0 (t = 0), rounded to K limbs.
+    Exact integers: every pool value is an integer over 2^B; a monomial of q
+    factors is an integer over 2^(qB), brought to the common scale 2^(4B)."""
+    B, K = pool.B, pool.K
+    xr = np.append(pool.ints[0][xi], 0).astype(object)  # index n: t = 0
+    xim = np.append(pool.ints[1][xi], 0).astype(object)
+    one = np.array([1 << B] * (n + 1), dtype=object)
+    zero = np.array([0] * (n + 1), dtype=object)
+    # powers of every variable at scale 2^(3B): x^0, x^1, x^2, x^3
+    pw = [(one * (1 << (2 * B)), zero.copy())]
+    cur = (xr, xim)
+    for e in (1, 2, 3):
+        pw.append((cur[0] << ((3 - e) * B), cur[1] << ((3 - e) * B)))
+        if e < 3:
+            cur = _cmul_obj(cur[0], cur[1], xr, xim)
+    pwr = np.stack([p[0] for p in pw])  # [4][n+1] objects
+    pwi = np.stack([p[1] for p in pw])
+    v1, e1 = V[:, :, 0], E[:, :, 0]
+    v2 = np.where(Mv == 2, V[:, :, 1], n)
+    e2 = np.where(Mv == 2, E[:, :, 1], 0)
+    # f1 * f2 at scale 2^(6B), times c at 2^B: 2^(7B)
+    f1r, f1i = pwr[e1, v1], pwi[e1, v1]
+    f2r, f2i = pwr[e2, v2], pwi[e2, v2]
+    pr, pi = _cmul_obj(f1r, f1i, f2r, f2i)
+    cr, cim = pool.ints[0][ci], pool.ints[1][ci]
+    tr, ti = _cmul_obj(pr, pi, cr, cim)
+    has_t = (v1 == n) | ((Mv == 2) & (V[:, :, 1] == n))
+    tr[has_t] = 0
+    ti[has_t] = 0
+    sr, si = tr.sum(axis=1), ti.sum(axis=1)
+    out = np.zeros((2, K, n))
+    den = 1 << (7 * B)
+    for i in range(n):
+        out[0, :, i] = md_from_fraction(Fraction(-int(sr[i]), den), K)
+        out[1, :, i] = md_from_fraction(Fraction(-int(si[i]), den), K)
+    return out
+
+
+def batch_systems(seed: int = 1, count: int = 2048, nmin: int = 8, nmax: int = 64, dmin: int = 8, dmax: int = 32,
+                  pool_size: int = 8192):
     """The batched workload: `count` complex systems, n ~ U{nmin..nmax},
     d ~ U{dmin..dmax}, n monomials per polynomial of degree <= 3 over <= 2
-    variables, double double or quad double with probability 1/2 each."""
+    variables, double double or quad double with probability 1/2 each.
+    Coefficients and x0 are full-width unit complex numbers (as in the n = 3
+    configuration), drawn from a seeded pool of `pool_size` angles per
+    precision; constant terms exact (small_system_fast)."""
     rng = np.random.default_rng([seed, 4])
+    pools = {K: UnitPool(np.random.default_rng([seed, 5, K]), K, pool_size) for K in (2, 4)}
     out = []
     for b in range(count):
         n = int(rng.integers(nmin, nmax + 1))
         d = int(rng.integers(dmin, dmax + 1))
         K = 2 if rng.uniform() < 0.5 else 4
-        out.append(small_system_fast(rng, n, d, K, monos=n, name=f"batch{b}"))
+        out.append(small_system_fast(rng, n, d, K, monos=n, name=f"batch{b}", pool=pools[K]))
     return out
