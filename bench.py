@@ -22,6 +22,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -419,6 +420,19 @@ def run_product(args):
             "value": world * args.steps / (o_total / 1e3), "unit": "steps/s", "ms_per_step": o_total / args.steps,
             "speedup_vs_md": total_ms / o_total}}
         del ows, xo
+        if world == 1:
+            # the other two forms of the method on the same GPU: the n = 256
+            # quad double solve (plain vs split-product update) and the batched
+            # form with its per-system launch loop
+            line["other_forms"]["solve_qd_n256_d16_cond1e8"] = measure_solve3(args, with_err=not args.no_cpu_baseline)
+            bl = measure_batched(args, args.other_batch, 0, 1, local, None, with_loop=True,
+                                 err_sample=0 if args.no_cpu_baseline else 8)
+            line["other_forms"]["batched"] = {k: bl[k] for k in (
+                "metric", "value", "unit", "ms_per_iteration", "system_steps_per_s", "latency_ms_p50",
+                "latency_ms_p99", "latency_ms_max", "loop_ms_per_iteration", "speedup_vs_loop",
+                "shared_sm_only_ms_per_iteration", "roofline", "err_vs_oracle", "systems", "limb_counts",
+                "phases_of_slowest_system")}
+            torch.cuda.empty_cache()
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, dt, x_orc = oracle_steps_per_s(s, 1, 0, want_x=True)
@@ -443,6 +457,16 @@ def run_product(args):
 def run_solve3(args):
     """Linearized solve, quad double real n=256 d=16, cond(A_0) = 1e8: plain
     block Toeplitz update against the split-product (Ozaki) update."""
+    line = measure_solve3(args, with_err=not args.no_cpu_baseline)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def measure_solve3(args, with_err: bool) -> dict:
+    """The plain and split-product solves of the n = 256, d = 16 quad double
+    system (condition 1e8) on the same GPU: solves/s, the update's time per
+    solve, the kernels, and (with_err) each form's largest per-degree error
+    against the oracle, relative to the largest coefficient of that degree."""
     import numpy as np
     import torch
 
@@ -480,7 +504,7 @@ def run_solve3(args):
                                              sorted(prof.items(), key=lambda kv: -kv[1][0])},
                      "dx": dx.cpu().numpy()}
     err = {}
-    if not args.no_cpu_baseline:
+    if with_err:
         import oracle
 
         from math import fsum
@@ -492,20 +516,21 @@ def run_solve3(args):
                 diff = max(abs(fsum(list(got[0, :, i, k]) + [-v for v in want[0, :, i, k]])) for i in range(n))
                 scale = max(abs(want[0, 0, i, k]) for i in range(n))
                 e.append(diff / scale)
-            err[name] = max(e)
+            err[name] = {"max_rel": max(e), "max_rel_over_eps": max(e) / 2.0 ** (-52 * K)}
     upd = {name: sum(v for k, v in res[name]["kernel_ms_per_solve"].items()
                      if k in ("rhs_partial", "rhs_finish", "oz_split", "oz_update")) for name in res}
-    line = {"metric": "linearized block Toeplitz solves/s (qd real, n=256, d=16, cond(A_0)=1e8)",
+    return {"metric": "linearized block Toeplitz solves/s (qd real, n=256, d=16, cond(A_0)=1e8)",
             "unit": "solves/s", "form": "plain vs split-product",
             "value_plain": 1e3 / res["plain"]["ms_per_solve"], "value_ozaki": 1e3 / res["ozaki"]["ms_per_solve"],
             "speedup_solve": res["plain"]["ms_per_solve"] / res["ozaki"]["ms_per_solve"],
             "update_ms_plain": upd["plain"], "update_ms_ozaki": upd["ozaki"],
             "speedup_update": upd["plain"] / max(upd["ozaki"], 1e-9),
-            "max_rel_err_vs_oracle": err, "kernel_ms_plain": res["plain"]["kernel_ms_per_solve"],
+            "err_vs_oracle": err or None,
+            "err_measure": "per degree, max_i |dx_gpu - dx_oracle| / max_i |dx_oracle|; eps = 2^-208; "
+                           "cond(A_0) = 1e8 bounds both forms' forward error alike",
+            "kernel_ms_plain": res["plain"]["kernel_ms_per_solve"],
             "kernel_ms_ozaki": res["ozaki"]["kernel_ms_per_solve"], "steps": args.steps, "warmup": args.warmup,
             "data": "synthetic", "dtype": "f64 (quad double); bf16 slices for the split products"}
-    print(json.dumps(line), flush=True)
-    return 0
 
 
 def run_ladder(args):
@@ -638,19 +663,35 @@ def run_batched(args):
     With N ranks the batch is split by LPT over the GPUs (strong scaling; no
     collective on the data path) and the iteration time is the slowest
     rank's."""
+    rank, world, local = dist_env()
+    dist = dist_init(world)
+    line = measure_batched(args, args.batch, rank, world, local, dist, with_loop=not args.no_loop,
+                           err_sample=0 if args.no_cpu_baseline else 8)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_batched(args, count, rank, world, local, dist, with_loop: bool, err_sample: int) -> dict:
+    """One batched Newton iteration over `count` systems of the batched
+    workload (this rank's LPT shard): iterations/s, per-system latency, the
+    same step with every CTA sharing SMs, the phases of the slowest system
+    against the SM's FP64 rate, a per-system launch loop (with_loop), and the
+    first step from x0 of `err_sample` systems (largest n first, both
+    precisions) against the oracle's step."""
     import numpy as np
     import torch
 
     import mdgen
     import paper_2012_06607_gb300 as md
 
-    rank, world, local = dist_env()
-    dist = dist_init(world)
     if world > 1:
         torch.cuda.set_device(local)
-    all_systems = mdgen.batch_systems(args.seed, count=args.batch)
+    all_systems = mdgen.batch_systems(args.seed, count=count)
     if len(all_systems) < world:
-        raise SystemExit(f"--batch {args.batch} leaves ranks without systems at {world} GPUs")
+        raise SystemExit(f"--batch {count} leaves ranks without systems at {world} GPUs")
     mine, _ = batched_shard(all_systems, rank, world)
     systems = [all_systems[i] for i in mine]
     sds = [md.DeviceSystem(s) for s in systems]
@@ -660,9 +701,18 @@ def run_batched(args):
     nrm = torch.zeros((len(systems), 2), dtype=torch.float64, device="cuda")
     times = torch.zeros((len(systems), 2), dtype=torch.int64, device="cuda")
     stream = torch.cuda.Stream()
+    sample = []
+    if err_sample > 0 and rank == 0:
+        by_size = sorted(range(len(systems)), key=lambda i: -systems[i].n * (systems[i].degree + 1))
+        for K in (2, 4):
+            sample += [i for i in by_size if systems[i].limbs == K][:err_sample // 2]
+    first = {}
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
+        for w in range(args.warmup):
             md.newton_step_batched(sds, xs, ws, nrm, times, flags=flags, stream=stream)
+            if w == 0:
+                stream.synchronize()
+                first = {i: xs[i].cpu().numpy() for i in sample}
         torch.cuda.synchronize()
         ms = []
         lat = []
@@ -714,7 +764,7 @@ def run_batched(args):
               "counted": "FP64 instructions of the bench's model per phase; stamps from MD_FLAG_PHASE_TIMES"}
     # per-system launch loop on the same systems (plain single-system steps)
     loop_ms = None
-    if not args.no_loop and world == 1:
+    if with_loop and world == 1:
         wmax = max(sd.workspace_bytes() for sd in sds)
         ws1 = md.workspace(wmax)
         xs1 = [md.to_device(s.x0) for s in systems]
@@ -731,8 +781,30 @@ def run_batched(args):
         kinds[s.limbs] = kinds.get(s.limbs, 0) + 1
     models = [step_fp64_model(s) for s in all_systems]
     fp64 = {k: sum(m[k] for m in models) for k in models[0]}
-    line = {"metric": "batched Newton iterations/s (2048 systems, n~U{8..64}, d~U{8..32}, dd/qd, complex)",
-            "unit": "iterations/s", "value": 1e3 / it_ms, "ms_per_iteration": it_ms,
+    err = None
+    if first:
+        import oracle
+
+        from math import fsum
+        orc = oracle.Oracle(threads=os.cpu_count() or 1)
+        worst = []
+        for i, got in first.items():
+            s = systems[i]
+            want, _ = orc.newton_step(s, s.x0)
+            P, K, n, d = s.planes, s.limbs, s.n, s.degree
+            rel = 0.0
+            for k in range(d + 1):
+                diff = max(math.hypot(*[fsum(list(got[p, :, j, k]) + [-v for v in want[p, :, j, k]]) for p in range(P)])
+                           for j in range(n))
+                scale = max(math.hypot(*[fsum(want[p, :, j, k]) for p in range(P)]) for j in range(n))
+                rel = max(rel, diff / max(scale, 1e-300))
+            worst.append({"n": n, "d": d, "limbs": K, "max_rel_over_eps": rel / 2.0 ** (-52 * K)})
+        err = {"systems": worst, "max_rel_over_eps": max(w["max_rel_over_eps"] for w in worst),
+               "measure": "first step from x0; per degree, max_i |x_gpu - x_oracle| / max_i |x_oracle|, "
+                          "in units of eps_K = 2^(-52K)"}
+    line = {"metric": f"batched Newton iterations/s ({len(all_systems)} systems, n~U{{8..64}}, d~U{{8..32}}, dd/qd, "
+                      "complex)",
+            "unit": "iterations/s", "value": 1e3 / it_ms, "ms_per_iteration": it_ms, "err_vs_oracle": err,
             "system_steps_per_s": len(all_systems) * 1e3 / it_ms, "n_gpus": world,
             "scaling": "strong" if world > 1 else "weak",
             "parallelism": f"LPT shards of the batch x{world}" if world > 1 else "one GPU",
@@ -751,11 +823,7 @@ def run_batched(args):
                          "fp64_instr_per_iteration": fp64},
             "steps": args.steps, "warmup": args.warmup, "flags": "autotune+graph", "data": "synthetic",
             "dtype": "f64 (double double / quad double)"}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
-    return 0
+    return line
 
 
 def main():
@@ -773,6 +841,8 @@ def main():
     ap.add_argument("--update", default="md", choices=["md", "split"],
                     help="block Toeplitz update of the plain form: md arithmetic or split-product")
     ap.add_argument("--batch", type=int, default=2048)
+    ap.add_argument("--other-batch", type=int, default=2048,
+                    help="systems of the batched form measured beside the plain step (other_forms)")
     ap.add_argument("--factor", default="qr", choices=["qr", "lu"], help="factorisation of A_0 in the plain form")
     ap.add_argument("--config", type=int, default=CFG, choices=[0, 1, 2],
                     help="workload of the plain and reference forms: 1 (default, the headline), 0 or 2")
