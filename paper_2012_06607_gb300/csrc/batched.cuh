@@ -137,14 +137,14 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
     // QR in the order of the lookahead form (same arithmetic per column): H_j
     // on column j+1 by the whole CTA, on the other targets by warps, then the
     // Householder vector of column j+1
-    house_block<K, P>(M, vd, beta, status, n, 0);
+    qr_house<K, P>(M, vd, beta, status, n, 0);
     for (int j = 0; j < n; ++j) {
       const bool ahead = j + 1 < n;
-      if (ahead) house_apply_col_cta<K, P>(M, Y, vd, beta, n, n, j, 0, s_row);
+      if (ahead) qr_apply_cta<K, P>(M, Y, vd, beta, n, n, j, 0, s_row);
       for (int w = warp + (ahead ? 1 : 0); w < (n - j - 1) + n; w += nwarp)
-        house_apply_col<K, P>(M, Y, vd, beta, n, n, j, w, lane);
+        qr_apply_warp<K, P>(M, Y, vd, beta, n, n, j, w, lane);
       __syncthreads();
-      if (ahead) house_block<K, P>(M, vd, beta, status, n, j + 1);
+      if (ahead) qr_house<K, P>(M, vd, beta, status, n, j + 1);
     }
     if (phases) __syncthreads();
     phase_stamp(phases, times, (long long)tstride * job + 5);

@@ -8,6 +8,11 @@ namespace mdk {
 
 enum : int { ST_SINGULAR = 1, ST_NONFINITE = 2, ST_TIMEOUT = 4 };
 
+// Virtual lanes of the CTA-level row reductions, and threads of the
+// Householder-vector block (kernels.cuh, house_fx.cuh).
+constexpr int kRowLanes = 128;
+constexpr int kHouseThreads = 128;
+
 // Kernel classes for the optional per-launch timing (md_profile_*).
 enum ProfKind : int {
   PK_POOL = 0, PK_SCAL, PK_CONV, PK_ACCUM, PK_QR_HOUSE, PK_QR_APPLY, PK_RINV, PK_BACKSUB,

@@ -24,6 +24,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "house_fx.cuh"
 #include "internal.h"
 #include "md.cuh"
 
@@ -81,8 +82,7 @@ __device__ __forceinline__ void block_sum(mdv<K, P> &v, mdv<K, P> *smem, int act
 // produce the same bits.  An FP64 warp instruction costs the same with one or
 // 32 active lanes, so spreading a row over four warps (one per SM
 // sub-partition) and splitting complex products by plane is what shortens
-// these latency-bound steps.
-constexpr int kRowLanes = 128;
+// these latency-bound steps.  (kRowLanes: internal.h.)
 
 template <int K>
 __device__ __forceinline__ void ld_limbs(const double *src, double (&z)[K]) {
@@ -456,8 +456,6 @@ __global__ void solve_init_kernel(const double *__restrict__ A, double *__restri
   solve_init_entry<K, P>(A, M, Y, N, n, d, e);
 }
 
-constexpr int kHouseThreads = 128;
-
 // Householder vector of column j (Golub-Van Loan): alpha = ||x||, phase
 // e = x_0/|x_0|, v = x + e alpha e_1, beta = 1/(alpha (alpha + |x_0|)), R_jj = -e alpha.
 // The square roots and the reciprocal use the precision-doubling iterations
@@ -567,11 +565,21 @@ __device__ __forceinline__ void house_block(double *M, double *vd,
   __syncthreads();
 }
 
+// The QR steps as the kernels run them: in W-word fixed point (house_fx.cuh)
+// from two limbs on, in FP64 for plain double.
+template <int K, int P>
+__device__ __forceinline__ void qr_house(double *M, double *vd, double *beta, int *status, int N, int j) {
+  if constexpr (K >= 2)
+    house_block_fx<K, P>(M, vd, beta, status, N, j);
+  else
+    house_block<K, P>(M, vd, beta, status, N, j);
+}
+
 template <int K, int P>
 __global__ void __launch_bounds__(kHouseThreads) house_kernel(double *__restrict__ M, double *__restrict__ vd,
                                                               double *__restrict__ beta, int *__restrict__ status,
                                                               int N, int j) {
-  house_block<K, P>(M, vd, beta, status, N, j);
+  qr_house<K, P>(M, vd, beta, status, N, j);
 }
 
 // Apply H_j = I - beta_j v v^H to target column w: w < n-j-1 is column j+1+w of
@@ -713,21 +721,39 @@ __device__ __forceinline__ void house_apply_col_cta(double *M, double *Y, const 
 // the larger of (column j+1 + Householder vector) and the rest of the update,
 // not their sum.
 template <int K, int P>
+__device__ __forceinline__ void qr_apply_cta(double *M, double *Y, const double *vd, const double *beta, int N, int n,
+                                             int j, int w, double (*sm)[K]) {
+  if constexpr (K >= 2)
+    house_apply_col_cta_fx<K, P>(M, Y, vd, beta, N, n, j, w);
+  else
+    house_apply_col_cta<K, P>(M, Y, vd, beta, N, n, j, w, sm);
+}
+
+template <int K, int P>
+__device__ __forceinline__ void qr_apply_warp(double *M, double *Y, const double *vd, const double *beta, int N,
+                                              int n, int j, int w, int lane) {
+  if constexpr (K >= 2)
+    house_apply_col_fx<K, P>(M, Y, vd, beta, N, n, j, w, lane);
+  else
+    house_apply_col<K, P>(M, Y, vd, beta, N, n, j, w, lane);
+}
+
+template <int K, int P>
 __global__ void __launch_bounds__(kHouseThreads) house_step_kernel(double *M, double *Y, double *vd, double *beta,
                                                                    int *status, int N, int n, int j) {
-  __shared__ double sm[kRowLanes][K];
+  __shared__ double sm[K >= 2 ? 1 : kRowLanes][K];
   const bool ahead = j + 1 < n;
   if (blockIdx.x == 0) {
     if (ahead) {
-      house_apply_col_cta<K, P>(M, Y, vd, beta, N, n, j, 0, sm);
-      house_block<K, P>(M, vd, beta, status, N, j + 1);
+      qr_apply_cta<K, P>(M, Y, vd, beta, N, n, j, 0, sm);
+      qr_house<K, P>(M, vd, beta, status, N, j + 1);
     }
     return;
   }
   const int warp = ((blockIdx.x - 1) * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   const int w = warp + (ahead ? 1 : 0);
   if (w >= (n - j - 1) + N) return;
-  house_apply_col<K, P>(M, Y, vd, beta, N, n, j, w, lane);
+  qr_apply_warp<K, P>(M, Y, vd, beta, N, n, j, w, lane);
 }
 
 // rinv[j] = 1 / R_jj

@@ -1,0 +1,105 @@
+"""The fixed-point scalar arithmetic of the Householder chain (csrc/fixp.cuh),
+compiled for the host, against exact rationals: conversion from K limbs and
+back, products, sums (with cancellation), reciprocal square roots, square
+roots and reciprocals, each within a few units of 2^(-53K) relative to the
+exact result.  The conversion to K limbs must give non-overlapping limbs."""
+import ctypes
+import os
+import subprocess
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import mdgen
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+KS = [2, 3, 4, 5, 8, 10]
+
+
+@pytest.fixture(scope="module")
+def fx(tmp_path_factory):
+    so = str(tmp_path_factory.mktemp("fixp") / "fixp_host.so")
+    subprocess.check_call(["g++", "-O1", "-std=c++17", "-shared", "-fPIC", os.path.join(HERE, "fixp_host.cpp"),
+                           "-o", so])
+    lib = ctypes.CDLL(so)
+    P = ctypes.c_void_p
+    lib.fxp_op.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_long, P, P, P]
+    return lib
+
+
+def _call(fx, K, op, x, y=None):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros_like(x)
+    yp = None if y is None else np.ascontiguousarray(y, dtype=np.float64).ctypes.data
+    assert fx.fxp_op(K, op, x.shape[0], x.ctypes.data, yp, out.ctypes.data) == 0
+    return out
+
+
+def _val(limbs):
+    return sum((Fraction(float(v)) for v in limbs), Fraction(0))
+
+
+def _operands(K, count, seed, positive=False):
+    rng = np.random.default_rng([K, seed])
+    x = mdgen.random_md_array(rng, K, count, spread=40.0).T.copy()  # [count][K]
+    if positive:
+        x *= np.sign(x[:, :1])
+    return x
+
+
+def _nonoverlapping(limbs):
+    for a, b in zip(limbs[:-1], limbs[1:]):
+        if b != 0.0:
+            assert a != 0.0 and abs(b) < abs(a) * 2.0 ** -52 * 2, (a, b)
+
+
+def _rel(got, want):
+    return abs(got - want) / abs(want)
+
+
+@pytest.mark.parametrize("K", KS)
+def test_round_trip_and_products(fx, K):
+    x, y = _operands(K, 300, 1), _operands(K, 300, 2)
+    tol = Fraction(8) * Fraction(2) ** (-53 * K)
+    rt = _call(fx, K, 0, x)
+    pr = _call(fx, K, 1, x, y)
+    for i in range(x.shape[0]):
+        X, Y = _val(x[i]), _val(y[i])
+        assert _rel(_val(rt[i]), X) <= tol, (K, i)
+        assert _rel(_val(pr[i]), X * Y) <= tol, (K, i)
+        _nonoverlapping(rt[i])
+        _nonoverlapping(pr[i])
+
+
+@pytest.mark.parametrize("K", KS)
+def test_sums_with_cancellation(fx, K):
+    x = _operands(K, 300, 3)
+    y = _operands(K, 300, 4)
+    # a third of the pairs cancel in their leading limbs (y = -x_0 + x_tail / 2,
+    # a valid expansion), a third cancel exactly
+    y[:100, 0] = -x[:100, 0]
+    y[:100, 1:] = x[:100, 1:] * 0.5
+    y[100:200] = -x[100:200]
+    s = _call(fx, K, 2, x, y)
+    for i in range(x.shape[0]):
+        want = _val(x[i]) + _val(y[i])
+        got = _val(s[i])
+        # truncation below the last word of the larger operand
+        bound = Fraction(8) * Fraction(2) ** (-53 * K) * max(abs(_val(x[i])), abs(_val(y[i])))
+        assert abs(got - want) <= bound, (K, i)
+
+
+@pytest.mark.parametrize("K", KS)
+def test_square_roots_and_reciprocals(fx, K):
+    a = _operands(K, 200, 5, positive=True)
+    tol = Fraction(16) * Fraction(2) ** (-53 * K)
+    rs = _call(fx, K, 3, a)
+    sq = _call(fx, K, 4, a)
+    rc = _call(fx, K, 5, a)
+    for i in range(a.shape[0]):
+        A = _val(a[i])
+        assert _rel(_val(rs[i]) ** 2 * A, Fraction(1)) <= 2 * tol, (K, i, "rsqrt")
+        assert _rel(_val(sq[i]) ** 2, A) <= 2 * tol, (K, i, "sqrt")
+        assert _rel(_val(rc[i]) * A, Fraction(1)) <= tol, (K, i, "recip")
+        _nonoverlapping(sq[i])
