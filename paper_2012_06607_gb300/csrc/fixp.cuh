@@ -87,28 +87,72 @@ FXP_HD bf<W> zero() {
   return z;
 }
 
+// Funnel shift: the high 32 bits of (hi:lo) << s, 0 <= s < 32.
+FXP_HD uint32_t fshl(uint32_t hi, uint32_t lo, int s) {
+#ifdef __CUDA_ARCH__
+  return __funnelshift_l(lo, hi, s);
+#else
+  return s ? (hi << s) | (lo >> (32 - s)) : hi;
+#endif
+}
+
+// t (N words, t[0] the most significant) shifted left by s bits, 0 <= s,
+// zeros shifted in: word shifts by binary stages (selects), then a funnel
+// shift -- O(N log N) instead of a select per (word, offset) pair.
+template <int N>
+FXP_HD void shl_bits(uint32_t (&t)[N], int s) {
+  const int ws = s >> 5;
+#pragma unroll
+  for (int b = 1; b < N; b <<= 1) {
+    const bool on = (ws & b) != 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) t[i] = on ? (i + b < N ? t[i + b] : 0u) : t[i];
+  }
+  if (ws >= N) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) t[i] = 0u;
+  }
+  const int bs = s & 31;
+#pragma unroll
+  for (int i = 0; i < N; ++i) t[i] = fshl(t[i], i + 1 < N ? t[i + 1] : 0u, bs);
+}
+
+// t shifted right by s bits, 0 <= s, zeros shifted in.
+template <int N>
+FXP_HD void shr_bits(uint32_t (&t)[N], int s) {
+  const int ws = s >> 5;
+#pragma unroll
+  for (int b = 1; b < N; b <<= 1) {
+    const bool on = (ws & b) != 0;
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) t[i] = on ? (i - b >= 0 ? t[i - b] : 0u) : t[i];
+  }
+  if (ws >= N) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) t[i] = 0u;
+  }
+  const int bs = s & 31;
+  // word i gets the low bits of word i-1 on top
+#pragma unroll
+  for (int i = N - 1; i >= 0; --i) {
+    const uint32_t prev = i > 0 ? t[i - 1] : 0u;
+    t[i] = bs ? fshl(prev, t[i], 32 - bs) : t[i];
+  }
+}
+
 // Shift the (W+1)-word magnitude t left until its top bit is set and keep the
 // top W words; returns the shift (0 if t is zero, which the caller checks).
 template <int W>
 FXP_HD int normalize_words(uint32_t (&t)[W + 1], uint32_t (&out)[W]) {
-  // word shift
-  int ws = 0;
+  int lead = 32 * (W + 1);  // position of the first set bit
 #pragma unroll
-  for (int i = 0; i <= W; ++i)
-    if (t[i] == 0u && ws == i) ws = i + 1;
-  uint32_t u[W + 1];
+  for (int i = W; i >= 0; --i)
+    if (t[i]) lead = 32 * i + clz32(t[i]);
+  if (lead >= 32 * (W + 1)) lead = 0;
+  shl_bits<W + 1>(t, lead);
 #pragma unroll
-  for (int i = 0; i <= W; ++i) {
-    uint32_t v = 0u;
-#pragma unroll
-    for (int k = 0; k <= W; ++k)
-      if (k == i + ws) v = t[k];
-    u[i] = v;
-  }
-  const int bs = u[0] ? clz32(u[0]) : 0;
-#pragma unroll
-  for (int i = 0; i < W; ++i) out[i] = bs ? (u[i] << bs) | (u[i + 1] >> (32 - bs)) : u[i];
-  return 32 * ws + bs;
+  for (int i = 0; i < W; ++i) out[i] = t[i];
+  return lead;
 }
 
 // Exact value of the K-limb md number x (rounded down in magnitude below the
@@ -140,21 +184,25 @@ FXP_NI bf<W> from_md(const double (&x)[K]) {
       const int lsb = below - 32 * piece;  // chunk * 2^(T - lsb)
       if (lsb <= 0) continue;              // cannot happen: |x_l| < 2^T
       int q = (lsb + 31) / 32 - 1;
-      int r = 32 * (q + 1) - lsb;  // chunk << r sits in digits q (low part) and q-1 (high part)
-      uint64_t v;
-      if (q >= W + 2) {
+      const int r = 32 * (q + 1) - lsb;  // chunk << r sits in digits q (low part) and q-1 (high part)
+      int64_t lo, hi;
+      if (q >= W + 2) {  // below the last digit: shifted down into it (truncated)
         const int drop = lsb - 32 * (W + 2);
-        if (drop >= 64) continue;
-        v = chunk >> drop;
+        lo = drop >= 64 ? 0 : (int64_t)(chunk >> drop);
+        hi = 0;
         q = W + 1;
-        r = 0;
-        acc[q] += sgn ? -(int64_t)v : (int64_t)v;
-        continue;
+      } else {
+        const uint64_t v = chunk << r;  // < 2^64 since chunk < 2^32 and r < 32
+        lo = (int64_t)(v & 0xffffffffULL);
+        hi = (int64_t)(v >> 32);
       }
-      v = chunk << r;  // < 2^64 since chunk < 2^32 and r < 32
-      const int64_t lo = (int64_t)(v & 0xffffffffULL), hi = (int64_t)(v >> 32);
-      acc[q] += sgn ? -lo : lo;
-      if (q > 0) acc[q - 1] += sgn ? -hi : hi;
+      if (sgn) {
+        lo = -lo;
+        hi = -hi;
+      }
+      // predicated adds over the digits: no runtime index, the digits stay in registers
+#pragma unroll
+      for (int dg = 0; dg < W + 2; ++dg) acc[dg] += (dg == q ? lo : 0) + (dg == q - 1 ? hi : 0);
     }
   }
   // carries: digits 1..W+1 into [0, 2^32), digit 0 signed
@@ -300,23 +348,19 @@ FXP_NI bf<W> add(const bf<W> &a, const bf<W> &b) {
   if (d >= 32 * W + 32) return x;
   // y's mantissa shifted right by d into W+1 words (one guard word); x's words
   // shifted right by one word position as well so that a carry fits
+  // a (W+2)-word frame: word 0 takes a carry, words 1..W hold x, word W+1 is
+  // a guard word; y is shifted right by d bits into the same frame
   uint32_t xs[W + 2], ys[W + 2];
   xs[0] = 0u;
+  ys[0] = 0u;
 #pragma unroll
-  for (int i = 0; i < W; ++i) xs[i + 1] = x.m[i];
-  xs[W + 1] = 0u;
-  const int wsh = (d >> 5) + 1, bsh = d & 31;
-#pragma unroll
-  for (int i = 0; i < W + 2; ++i) {
-    // word i of y >> (32 wsh + bsh) over a (W+2)-word frame whose word 1 holds y.m[0]
-    uint32_t hi = 0u, lo = 0u;
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-      if (k == i - wsh) hi = y.m[k];
-      if (k == i - wsh - 1) lo = y.m[k];
-    }
-    ys[i] = bsh ? (hi >> bsh) | (lo << (32 - bsh)) : hi;
+  for (int i = 0; i < W; ++i) {
+    xs[i + 1] = x.m[i];
+    ys[i + 1] = y.m[i];
   }
+  xs[W + 1] = 0u;
+  ys[W + 1] = 0u;
+  shr_bits<W + 2>(ys, d);
   uint32_t r[W + 2];
   if (x.neg == y.neg) {
     uint64_t carry = 0;

@@ -176,96 +176,195 @@ __device__ __forceinline__ void house_block_fx(double *M, double *vd, double *be
   __syncthreads();
 }
 
-// H_j applied to target column w (warp body; targets as in house_apply_col).
-template <int K, int P>
-__device__ __forceinline__ void house_apply_col_fx(double *M, double *Y, const double *vd, const double *beta, int N,
-                                                   int n, int j, int w, int lane) {
+// H_j applied to target column w (targets as in house_apply_col: w < n-j-1
+// is column j+1+w of M, otherwise column w-(n-j-1) of Y) over 128 virtual
+// lanes: lane q takes rows j+q, j+q+128, ... in order and holds their partial
+// dot product p_q; the column's dot product is the xor tree over 32 values
+// u_l = (p_l + p_{l+64}) + (p_{l+32} + p_{l+96}).  CTA = true: 128 threads of
+// a CTA, one virtual lane each (all threads of the CTA call it); CTA = false:
+// one warp, lane l running virtual lanes l, l+32, l+64, l+96.  Both forms
+// perform the same additions in the same order, so they give the same bits.
+template <int K, int P, bool CTA>
+__device__ __forceinline__ void house_apply_col_v128(double *M, double *Y, const double *vd, const double *beta,
+                                                     int N, int n, int j, int w) {
   using namespace fxp;
   constexpr int W = words_for(K);
   const int nm = n - j - 1;
   double *T = (w < nm) ? M : Y;
   const int c = (w < nm) ? j + 1 + w : w - nm;
   const long long VS = P * K;
-  bf<W> dr = zero<W>(), di = zero<W>();
-  for (int i = j + lane; i < N; i += 32) {
-    bf<W> v[P], t[P];
-    fx_ld_v<W, K, P>(M, vd, N, j, i, v);
+  const int tid = CTA ? (int)threadIdx.x : (int)(threadIdx.x & 31);
+  auto partial = [&](int q, bf<W> (&d)[P]) {
 #pragma unroll
-    for (int p = 0; p < P; ++p) t[p] = fx_ld<W, K>(T + ((long long)c * N + i) * VS + p * K);
-    fx_cdot_acc<W, P>(v, t, dr, di);
+    for (int p = 0; p < P; ++p) d[p] = zero<W>();
+    for (int i = j + q; i < N; i += kRowLanes) {
+      bf<W> v[P], t[P];
+      fx_ld_v<W, K, P>(M, vd, N, j, i, v);
+#pragma unroll
+      for (int p = 0; p < P; ++p) t[p] = fx_ld<W, K>(T + ((long long)c * N + i) * VS + p * K);
+      if constexpr (P == 1) {
+        fx_cdot_acc<W, P>(v, t, d[0], d[0]);
+      } else {
+        fx_cdot_acc<W, P>(v, t, d[0], d[1]);
+      }
+    }
+  };
+  bf<W> u[P];
+  if constexpr (CTA) {
+    __shared__ bf<W> s_p[kRowLanes][P];
+    __shared__ bf<W> s_tau[P];
+    if (tid < kRowLanes) {
+      bf<W> d[P];
+      partial(tid, d);
+#pragma unroll
+      for (int p = 0; p < P; ++p) s_p[tid][p] = d[p];
+    }
+    __syncthreads();
+    if (tid < 32) {
+#pragma unroll
+      for (int p = 0; p < P; ++p)
+        u[p] = add<W>(add<W>(s_p[tid][p], s_p[tid + 64][p]), add<W>(s_p[tid + 32][p], s_p[tid + 96][p]));
+#pragma unroll
+      for (int p = 0; p < P; ++p) fx_warp_sum<W>(u[p]);
+      if (tid == 0) {
+        const bf<W> bt = fx_ld<W, K>(beta + (long long)j * K);
+#pragma unroll
+        for (int p = 0; p < P; ++p) s_tau[p] = mul<W>(bt, u[p]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < P; ++p) u[p] = s_tau[p];
+  } else {
+    bf<W> a[P], b[P], s02[P];
+    partial(tid, a);
+    partial(tid + 64, b);
+#pragma unroll
+    for (int p = 0; p < P; ++p) s02[p] = add<W>(a[p], b[p]);
+    partial(tid + 32, a);
+    partial(tid + 96, b);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      u[p] = add<W>(s02[p], add<W>(a[p], b[p]));
+      fx_warp_sum<W>(u[p]);
+    }
+    const bf<W> bt = fx_ld<W, K>(beta + (long long)j * K);
+#pragma unroll
+    for (int p = 0; p < P; ++p) u[p] = mul<W>(bt, u[p]);
   }
-  fx_warp_sum<W>(dr);
-  if constexpr (P == 2) fx_warp_sum<W>(di);
-  const bf<W> bt = fx_ld<W, K>(beta + (long long)j * K);
-  bf<W> tau[P];
-  tau[0] = mul<W>(bt, dr);
-  if constexpr (P == 2) tau[1] = mul<W>(bt, di);
-  for (int i = j + lane; i < N; i += 32) {
-    bf<W> v[P], t[P];
-    fx_ld_v<W, K, P>(M, vd, N, j, i, v);
-    double *dst = T + ((long long)c * N + i) * VS;
+  // t_i <- t_i - tau v_i on every virtual lane's rows
+  const int qs = CTA ? kRowLanes : 32;
+  for (int q = tid; q < kRowLanes; q += qs) {
+    for (int i = j + q; i < N; i += kRowLanes) {
+      bf<W> v[P], t[P];
+      fx_ld_v<W, K, P>(M, vd, N, j, i, v);
+      double *dst = T + ((long long)c * N + i) * VS;
 #pragma unroll
-    for (int p = 0; p < P; ++p) t[p] = fx_ld<W, K>(dst + p * K);
-    fx_axpy<W, P>(tau, v, t);
+      for (int p = 0; p < P; ++p) t[p] = fx_ld<W, K>(dst + p * K);
+      fx_axpy<W, P>(u, v, t);
 #pragma unroll
-    for (int p = 0; p < P; ++p) fx_st<K, W>(dst + p * K, t[p]);
+      for (int p = 0; p < P; ++p) fx_st<K, W>(dst + p * K, t[p]);
+    }
+  }
+  if constexpr (CTA) __syncthreads();
+}
+
+// ------------------------------------------------- back substitution, W = R^-1 Q^H
+// The element bodies of rinv_entry / backsub_entry / the lookahead kernels in
+// fixed point: w = y r_cc^-1, y_i <- y_i - R_ic w.  Every element takes the
+// same operations in the same order in the lookahead kernels and in the
+// batched kernel, so both get the same bits.
+
+// z = a b (complex for P = 2)
+template <int W, int P>
+__device__ __forceinline__ void fx_cmul(const fxp::bf<W> (&a)[P], const fxp::bf<W> (&b)[P], fxp::bf<W> (&z)[P]) {
+  using namespace fxp;
+  if constexpr (P == 1) {
+    z[0] = mul<W>(a[0], b[0]);
+  } else {
+    z[0] = add<W>(mul<W>(a[0], b[0]), neg<W>(mul<W>(a[1], b[1])));
+    z[1] = add<W>(mul<W>(a[0], b[1]), mul<W>(a[1], b[0]));
   }
 }
 
-// The same application by a CTA over kRowLanes virtual lanes (lane q takes
-// rows j+q, j+q+kRowLanes, ...), warp trees and then the four warp sums in
-// order.  All threads of the CTA call it.
+template <int W, int K, int P>
+__device__ __forceinline__ void fx_ld_val(const double *src, fxp::bf<W> (&v)[P]) {
+#pragma unroll
+  for (int p = 0; p < P; ++p) v[p] = fx_ld<W, K>(src + p * K);
+}
+
+template <int W, int K, int P>
+__device__ __forceinline__ void fx_st_val(double *dst, const fxp::bf<W> (&v)[P]) {
+#pragma unroll
+  for (int p = 0; p < P; ++p) fx_st<K, W>(dst + p * K, v[p]);
+}
+
+// rinv[j] = 1 / R_jj (conj(r) / |r|^2 for complex r); not finite for r = 0.
 template <int K, int P>
-__device__ __forceinline__ void house_apply_col_cta_fx(double *M, double *Y, const double *vd, const double *beta,
-                                                       int N, int n, int j, int w) {
+__device__ __forceinline__ void rinv_entry_fx(const double *M, double *rinv, int N, int j) {
+  using namespace fxp;
+  constexpr int W = words_for(K), ST = newton_steps(K);
+  const long long VS = P * K;
+  bf<W> r[P], z[P];
+  fx_ld_val<W, K, P>(M + ((long long)j * N + j) * VS, r);
+  bf<W> S = mul<W>(r[0], r[0]);
+  if constexpr (P == 2) S = add<W>(S, mul<W>(r[1], r[1]));
+  double *dst = rinv + (long long)j * VS;
+  if (is_zero(S)) {
+#pragma unroll
+    for (int l = 0; l < P * K; ++l) dst[l] = __longlong_as_double(0x7ff8000000000000LL);  // NaN
+    return;
+  }
+  const bf<W> rs = recip<W, ST>(S);
+  z[0] = mul<W>(r[0], rs);
+  if constexpr (P == 2) z[1] = neg<W>(mul<W>(r[1], rs));
+  fx_st_val<W, K, P>(dst, z);
+}
+
+// y <- y - R_ic w at Y[(col, i)], w the K-limb value at wsrc (W[c][col] or
+// the same value formed in registers).
+template <int K, int P>
+__device__ __forceinline__ void fx_bs_update(const double *M, double *Y, const double *wsrc, int N, int c, int col,
+                                             int i) {
   using namespace fxp;
   constexpr int W = words_for(K);
-  __shared__ bf<W> s_dot[kRowLanes / 32][P];
-  __shared__ bf<W> s_tau[P];
-  const int nm = n - j - 1;
-  double *T = (w < nm) ? M : Y;
-  const int c = (w < nm) ? j + 1 + w : w - nm;
   const long long VS = P * K;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const bool act = tid < kRowLanes;
-  bf<W> dr = zero<W>(), di = zero<W>();
-  for (int i = j + tid; act && i < N; i += kRowLanes) {
-    bf<W> v[P], t[P];
-    fx_ld_v<W, K, P>(M, vd, N, j, i, v);
+  bf<W> w[P], rc[P], y[P], t[P];
+  fx_ld_val<W, K, P>(wsrc, w);
+  fx_ld_val<W, K, P>(M + ((long long)c * N + i) * VS, rc);
+  double *yp = Y + ((long long)col * N + i) * VS;
+  fx_ld_val<W, K, P>(yp, y);
+  fx_cmul<W, P>(rc, w, t);
 #pragma unroll
-    for (int p = 0; p < P; ++p) t[p] = fx_ld<W, K>(T + ((long long)c * N + i) * VS + p * K);
-    fx_cdot_acc<W, P>(v, t, dr, di);
+  for (int p = 0; p < P; ++p) y[p] = add<W>(y[p], neg<W>(t[p]));
+  fx_st_val<W, K, P>(yp, y);
+}
+
+// dst (P K doubles) = Y[(col, c)] rinv[c], rounded to K limbs: the value of W[c][col]
+template <int K, int P>
+__device__ __forceinline__ void fx_bs_w(const double *Y, const double *rinv, int N, int c, int col, double *dst) {
+  using namespace fxp;
+  constexpr int W = words_for(K);
+  const long long VS = P * K;
+  bf<W> y[P], ri[P], w[P];
+  fx_ld_val<W, K, P>(Y + ((long long)col * N + c) * VS, y);
+  fx_ld_val<W, K, P>(rinv + (long long)c * VS, ri);
+  fx_cmul<W, P>(y, ri, w);
+  fx_st_val<W, K, P>(dst, w);
+}
+
+// backsub_entry in fixed point: element e = (i, col) of step c.
+template <int K, int P>
+__device__ __forceinline__ void backsub_entry_fx(const double *M, double *Y, double *Wm, const double *rinv, int N,
+                                                 int c, long long e) {
+  const int i = (int)(e / N), col = (int)(e % N);
+  if (i == c) {
+    fx_bs_w<K, P>(Y, rinv, N, c, col, Wm + ((long long)c * N + col) * (P * K));
+  } else {
+    double w[P * K];
+    fx_bs_w<K, P>(Y, rinv, N, c, col, w);
+    fx_bs_update<K, P>(M, Y, w, N, c, col, i);
   }
-  if (act) {
-    fx_warp_sum<W>(dr);
-    if constexpr (P == 2) fx_warp_sum<W>(di);
-    if (lane == 0) {
-      s_dot[warp][0] = dr;
-      if constexpr (P == 2) s_dot[warp][1] = di;
-    }
-  }
-  __syncthreads();
-  if (tid < P) {
-    bf<W> d = s_dot[0][tid];
-#pragma unroll
-    for (int q = 1; q < kRowLanes / 32; ++q) d = add<W>(d, s_dot[q][tid]);
-    s_tau[tid] = mul<W>(fx_ld<W, K>(beta + (long long)j * K), d);
-  }
-  __syncthreads();
-  bf<W> tau[P];
-#pragma unroll
-  for (int p = 0; p < P; ++p) tau[p] = s_tau[p];
-  for (int i = j + tid; act && i < N; i += kRowLanes) {
-    bf<W> v[P], t[P];
-    fx_ld_v<W, K, P>(M, vd, N, j, i, v);
-    double *dst = T + ((long long)c * N + i) * VS;
-#pragma unroll
-    for (int p = 0; p < P; ++p) t[p] = fx_ld<W, K>(dst + p * K);
-    fx_axpy<W, P>(tau, v, t);
-#pragma unroll
-    for (int p = 0; p < P; ++p) fx_st<K, W>(dst + p * K, t[p]);
-  }
-  __syncthreads();
 }
 
 }  // namespace mdk

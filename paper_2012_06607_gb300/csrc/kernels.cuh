@@ -716,7 +716,8 @@ __device__ __forceinline__ void house_apply_col_cta(double *M, double *Y, const 
 
 // One step of the QR with lookahead: CTA 0 applies H_j to column j+1 and then
 // builds the Householder vector of column j+1, while the other CTAs apply H_j
-// to columns j+2.. of M and to Y (one warp per column).  The next step needs
+// to columns j+2.. of M and to Y (one CTA per column in fixed point, one warp
+// per column in plain double).  The next step needs
 // both, and column j+1 is touched by CTA 0 only, so the step's critical path is
 // the larger of (column j+1 + Householder vector) and the rest of the update,
 // not their sum.
@@ -724,7 +725,7 @@ template <int K, int P>
 __device__ __forceinline__ void qr_apply_cta(double *M, double *Y, const double *vd, const double *beta, int N, int n,
                                              int j, int w, double (*sm)[K]) {
   if constexpr (K >= 2)
-    house_apply_col_cta_fx<K, P>(M, Y, vd, beta, N, n, j, w);
+    house_apply_col_v128<K, P, true>(M, Y, vd, beta, N, n, j, w);
   else
     house_apply_col_cta<K, P>(M, Y, vd, beta, N, n, j, w, sm);
 }
@@ -732,10 +733,19 @@ __device__ __forceinline__ void qr_apply_cta(double *M, double *Y, const double 
 template <int K, int P>
 __device__ __forceinline__ void qr_apply_warp(double *M, double *Y, const double *vd, const double *beta, int N,
                                               int n, int j, int w, int lane) {
-  if constexpr (K >= 2)
-    house_apply_col_fx<K, P>(M, Y, vd, beta, N, n, j, w, lane);
-  else
+  if constexpr (K >= 2) {
+    (void)lane;
+    house_apply_col_v128<K, P, false>(M, Y, vd, beta, N, n, j, w);
+  } else {
     house_apply_col<K, P>(M, Y, vd, beta, N, n, j, w, lane);
+  }
+}
+
+// CTAs of house_step_kernel after CTA 0: one per trailing target (fixed
+// point, K >= 2) or one warp per target (plain double).
+template <int K>
+__host__ __device__ constexpr bool qr_cta_per_target() {
+  return K >= 2;
 }
 
 template <int K, int P>
@@ -750,15 +760,25 @@ __global__ void __launch_bounds__(kHouseThreads) house_step_kernel(double *M, do
     }
     return;
   }
-  const int warp = ((blockIdx.x - 1) * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  const int w = warp + (ahead ? 1 : 0);
-  if (w >= (n - j - 1) + N) return;
-  qr_apply_warp<K, P>(M, Y, vd, beta, N, n, j, w, lane);
+  if constexpr (qr_cta_per_target<K>()) {
+    const int w = (int)blockIdx.x - 1 + (ahead ? 1 : 0);
+    if (w >= (n - j - 1) + N) return;  // uniform over the CTA
+    qr_apply_cta<K, P>(M, Y, vd, beta, N, n, j, w, sm);
+  } else {
+    const int warp = ((blockIdx.x - 1) * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int w = warp + (ahead ? 1 : 0);
+    if (w >= (n - j - 1) + N) return;
+    qr_apply_warp<K, P>(M, Y, vd, beta, N, n, j, w, lane);
+  }
 }
 
 // rinv[j] = 1 / R_jj
 template <int K, int P>
 __device__ __forceinline__ void rinv_entry(const double *M, double *rinv, int N, int j) {
+  if constexpr (K >= 2) {  // fixed point, as the QR (house_fx.cuh)
+    rinv_entry_fx<K, P>(M, rinv, N, j);
+    return;
+  }
   const long long VS = P * K;
   mdv<K, P> r, one, z;
   ld_aos<K, P>(M + ((long long)j * N + j) * VS, r);
@@ -782,6 +802,10 @@ template <int K, int P>
 __device__ __forceinline__ void backsub_entry(const double *M, double *Y,
                                               double *W, const double *rinv, int N, int c,
                                               long long e) {
+  if constexpr (K >= 2) {  // fixed point, as the QR (house_fx.cuh)
+    backsub_entry_fx<K, P>(M, Y, W, rinv, N, c, e);
+    return;
+  }
   const int i = (int)(e / N), col = (int)(e % N);
   const long long VS = P * K;
   mdv<K, P> y, ri, w;
@@ -973,6 +997,10 @@ __global__ void backsub_row0_kernel(const double *__restrict__ Y, double *__rest
   const int col = blockIdx.x * blockDim.x + threadIdx.x;
   if (col >= N) return;
   const long long VS = P * K;
+  if constexpr (K >= 2) {
+    fx_bs_w<K, P>(Y, rinv, N, c, col, W + ((long long)c * N + col) * VS);
+    return;
+  }
   mdv<K, P> y, ri, w;
   ld_aos<K, P>(Y + ((long long)col * N + c) * VS, y);
   ld_aos<K, P>(rinv + (long long)c * VS, ri);
@@ -987,6 +1015,11 @@ __global__ void backsub_step_kernel(const double *__restrict__ M, double *__rest
   if ((int)blockIdx.x < gA) {  // row c-1, then W[c-1][:]
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= N) return;
+    if constexpr (K >= 2) {
+      fx_bs_update<K, P>(M, Y, W + ((long long)c * N + col) * VS, N, c, col, c - 1);
+      fx_bs_w<K, P>(Y, rinv, N, c - 1, col, W + ((long long)(c - 1) * N + col) * VS);
+      return;
+    }
     mdv<K, P> w, rc, t, yi, ri;
     ld_aos<K, P>(W + ((long long)c * N + col) * VS, w);
     ld_aos<K, P>(M + ((long long)c * N + (c - 1)) * VS, rc);
@@ -1003,6 +1036,10 @@ __global__ void backsub_step_kernel(const double *__restrict__ M, double *__rest
   const long long e = (blockIdx.x - gA) * (long long)blockDim.x + threadIdx.x;
   if (e >= (long long)(c - 1) * N) return;
   const int i = (int)(e % (c - 1)), col = (int)(e / (c - 1));
+  if constexpr (K >= 2) {
+    fx_bs_update<K, P>(M, Y, W + ((long long)c * N + col) * VS, N, c, col, i);
+    return;
+  }
   mdv<K, P> w, rc, t, yi;
   ld_aos<K, P>(W + ((long long)c * N + col) * VS, w);
   ld_aos<K, P>(M + ((long long)c * N + i) * VS, rc);

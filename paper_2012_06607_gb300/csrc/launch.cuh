@@ -191,8 +191,8 @@ cudaError_t Impl<K, P>::factor(const SolveDev &v, cudaStream_t s) {
     // H_j on every target, and the Householder vector of column j+1 (lookahead)
     ProfScope prof(PK_QR_APPLY, s);
     const int rest = (n - j - 1) + N - (j + 1 < n ? 1 : 0);
-    house_step_kernel<K, P><<<1 + (int)blocks_for((long long)rest * 32, kHouseThreads), kHouseThreads, 0, s>>>(
-        v.M, v.Y, v.vd, v.beta, v.status, N, n, j);
+    const int grid = 1 + (qr_cta_per_target<K>() ? rest : (int)blocks_for((long long)rest * 32, kHouseThreads));
+    house_step_kernel<K, P><<<grid, kHouseThreads, 0, s>>>(v.M, v.Y, v.vd, v.beta, v.status, N, n, j);
   }
   {
     ProfScope prof(PK_RINV, s);
