@@ -220,20 +220,27 @@ def reduce_max(dist, v: float) -> float:
 
 
 # ---------------------------------------------------------------- oracle leg
-def oracle_steps_per_s(s, steps: int, warmup: int, want_x: bool = False):
+def oracle_steps_per_s(s, steps: int, warmup: int, want_x: bool = False, threads: int = 0):
+    """The oracle's Newton steps on the host: all cores (OpenMP, threads = 0)
+    or the given number of threads (restored to all cores afterwards)."""
     import oracle
 
-    orc = oracle.Oracle(threads=os.cpu_count() or 1)
-    x = s.x0.copy()
-    for _ in range(warmup):
-        x, _ = orc.newton_step(s, x)
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        x, _ = orc.newton_step(s, x)
-    dt = time.perf_counter() - t0
+    orc = oracle.Oracle(threads=threads or os.cpu_count() or 1)
+    try:
+        x = s.x0.copy()
+        for _ in range(warmup):
+            x, _ = orc.newton_step(s, x)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            x, _ = orc.newton_step(s, x)
+        dt = time.perf_counter() - t0
+        used = orc.threads()
+    finally:
+        if threads:
+            orc.lib.orc_set_threads(os.cpu_count() or 1)
     if want_x:
-        return steps / dt, orc.threads(), dt, x
-    return steps / dt, orc.threads(), dt
+        return steps / dt, used, dt, x
+    return steps / dt, used, dt
 
 
 def err_vs_oracle(got, want) -> float:
@@ -436,8 +443,11 @@ def run_product(args):
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, dt, x_orc = oracle_steps_per_s(s, 1, 0, want_x=True)
+        vs, cs, _ = oracle_steps_per_s(s, 1, 0, threads=1)
         line["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
-                                "sample": "1 full Newton step of the workload from x0 (host cores, OpenMP)"}
+                                "sample": "1 full Newton step of the workload from x0 (host cores, OpenMP)",
+                                "serial": {"value": vs, "unit": "steps/s", "cores": cs,
+                                           "sample": "the same step on one thread"}}
         # the same step on the GPU (outside the timed region), against the oracle's
         x1 = md.to_device(s.x0, dev)
         md.newton_step(sysd, x1, ws, nrm, flags=flags)

@@ -1203,9 +1203,14 @@ std::mutex *aux_mutex(DevAux *a) { return &a->mu; }
 cudaStream_t aux_stream(DevAux *a) { return a->s2; }
 cudaEvent_t aux_event(DevAux *a, int i) { return i == 0 ? a->e0 : a->e1; }
 
-// SMs left to the factorisation while the evaluation runs resident.
+// SMs left to the factorisation while the evaluation runs resident.  With
+// the factorisation in fixed point (about 15 ms of QR and W at quad double
+// n = 64 on six SMs, against 45 ms of evaluation) four suffice: measured
+// 15.81 (6), 16.04 (4) and 16.04 (3) steps/s at n = 64, d = 64, and
+// 21.03 / 20.88 / 20.79 steps/s at octo double n = 128, whose step waits on
+// the factorisation.
 #ifndef MDK_FACTOR_SMS
-#define MDK_FACTOR_SMS 6
+#define MDK_FACTOR_SMS 4
 #endif
 constexpr int kFactorSms = MDK_FACTOR_SMS;
 

@@ -33,6 +33,7 @@ namespace mdk {
 namespace fxp {
 
 constexpr int kZeroExp = -100000;
+constexpr int kNanExp = 100000;  // not a number: from a non-finite input, or 1/0
 
 // words for K limbs: 53K bits and two guard words
 FXP_HD constexpr int words_for(int K) { return (53 * K + 31) / 32 + 2; }
@@ -75,6 +76,24 @@ FXP_HD int clz32(uint32_t v) {  // v != 0
 template <int W>
 FXP_HD bool is_zero(const bf<W> &a) {
   return a.m[0] == 0u;
+}
+
+template <int W>
+FXP_HD bool is_nan(const bf<W> &a) {
+  return a.e == kNanExp;
+}
+
+// NaN: nonzero mantissa (so that is_zero is false) and the NaN exponent; every
+// operation with a NaN operand returns NaN and to_md writes NaN limbs, as the
+// md forms propagate non-finite values.
+template <int W>
+FXP_HD bf<W> nan_value() {
+  bf<W> z;
+#pragma unroll
+  for (int i = 0; i < W; ++i) z.m[i] = i == 0 ? 0x80000000u : 0u;
+  z.e = kNanExp;
+  z.neg = 0;
+  return z;
 }
 
 template <int W>
@@ -161,6 +180,10 @@ template <int W, int K>
 FXP_NI bf<W> from_md(const double (&x)[K]) {
   const uint64_t b0 = dbits(x[0]);
   const int B0 = (int)(b0 >> 52) & 0x7ff;
+  bool finite = true;
+#pragma unroll
+  for (int l = 0; l < K; ++l) finite = finite && (((int)(dbits(x[l]) >> 52) & 0x7ff) != 0x7ff);
+  if (!finite) return nan_value<W>();
   if (((b0 << 1) == 0) || B0 == 0) return zero<W>();  // zero (subnormal leads: treated as zero)
   // |x| < 2^(B0 - 1022) (1 + 2^-52) < 2^T with T = B0 - 1021: digit q of the
   // signed accumulator has weight 2^(T - 32(q+1)), q = 0..W+1
@@ -261,8 +284,8 @@ FXP_HD int first_set(const bf<W> &a, int p) {
 template <int K, int W>
 FXP_NI void to_md(const bf<W> &a, double (&z)[K]) {
 #pragma unroll
-  for (int l = 0; l < K; ++l) z[l] = 0.0;
-  if (is_zero(a)) return;
+  for (int l = 0; l < K; ++l) z[l] = is_nan(a) ? dfrom(0x7ff8000000000000ULL) : 0.0;
+  if (is_zero(a) || is_nan(a)) return;
   int p = 0;  // the top bit is set
 #pragma unroll
   for (int l = 0; l < K; ++l) {
@@ -296,6 +319,7 @@ FXP_HD bf<W> from_double(double x) {
 // products of words i + j <= W), normalized.
 template <int W>
 FXP_NI bf<W> mul(const bf<W> &a, const bf<W> &b) {
+  if (is_nan(a) || is_nan(b)) return nan_value<W>();
   if (is_zero(a) || is_zero(b)) return zero<W>();
   uint64_t col[W + 2];
 #pragma unroll
@@ -339,6 +363,7 @@ FXP_HD bool mag_ge(const bf<W> &a, const bf<W> &b) {
 // a + b (signs included), truncated to W words.
 template <int W>
 FXP_NI bf<W> add(const bf<W> &a, const bf<W> &b) {
+  if (is_nan(a) || is_nan(b)) return nan_value<W>();
   if (is_zero(b)) return a;
   if (is_zero(a)) return b;
   const bool a_big = mag_ge<W>(a, b);
@@ -402,7 +427,7 @@ FXP_HD bf<W> neg(bf<W> a) {
 // a 2^k
 template <int W>
 FXP_HD bf<W> ldexp(bf<W> a, int k) {
-  if (!is_zero(a)) a.e += k;
+  if (!is_zero(a) && !is_nan(a)) a.e += k;
   return a;
 }
 
@@ -423,6 +448,7 @@ FXP_HD constexpr int newton_steps(int K) {
 // leading bits of a scaled into [1/4, 1) by an even power of two.
 template <int W, int STEPS>
 FXP_NI bf<W> rsqrt(const bf<W> &a) {
+  if (is_nan(a) || is_zero(a) || a.neg) return nan_value<W>();  // as 1/sqrt(0) is not finite
   bf<W> as = a;
   const int ee = (a.e % 2 == 0) ? a.e : a.e + 1;  // a = as 2^ee with as in [1/4, 1)
   as.e -= ee;
@@ -446,6 +472,7 @@ FXP_NI bf<W> rsqrt(const bf<W> &a) {
 // 1 / a, a != 0: y <- y + y (1 - a y).
 template <int W, int STEPS>
 FXP_NI bf<W> recip(const bf<W> &a) {
+  if (is_nan(a) || is_zero(a)) return nan_value<W>();  // as 1/0 is not finite
   bf<W> as = a;
   as.e = 0;  // as in [1/2, 1)
   as.neg = 0;

@@ -103,3 +103,23 @@ def test_square_roots_and_reciprocals(fx, K):
         assert _rel(_val(sq[i]) ** 2, A) <= 2 * tol, (K, i, "sqrt")
         assert _rel(_val(rc[i]) * A, Fraction(1)) <= tol, (K, i, "recip")
         _nonoverlapping(sq[i])
+
+
+@pytest.mark.parametrize("K", [2, 4, 8])
+def test_non_finite_values_propagate(fx, K):
+    """A non-finite limb anywhere gives NaN limbs after any operation, and the
+    reciprocal (square root) of zero is not finite, as in md arithmetic."""
+    x = _operands(K, 4, 7, positive=True)
+    y = x.copy()
+    y[0, 0] = np.inf
+    y[1, K - 1] = np.nan
+    y[2, 0] = -np.inf
+    for op in (0, 1, 2):
+        out = _call(fx, K, op, x, y) if op else _call(fx, K, op, y)
+        for i in range(3):
+            assert np.isnan(out[i]).all(), (K, op, i)
+        if op:
+            assert np.isfinite(out[3]).all()
+    z = np.zeros((2, K))
+    for op in (3, 5):
+        assert not np.isfinite(_call(fx, K, op, z)).any(), (K, op)
