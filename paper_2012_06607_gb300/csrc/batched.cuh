@@ -31,6 +31,7 @@ __device__ __forceinline__ void phase_stamp(bool on, unsigned long long *times, 
 // CTA sizes of the batched kernel: kBatchThreads (default) up to kBatchMaxThreads.
 constexpr int kBatchThreads = 128;
 constexpr int kBatchMaxThreads = 384;
+static_assert(kBatchMaxThreads / 32 <= kFxMaxWarps, "fixed-point row sums keep one slot per warp");
 
 template <int K, int P>
 __global__ void batched_step_kernel(const BatchJob *__restrict__ jobs, const int *__restrict__ order, int njobs,

@@ -1412,6 +1412,7 @@ md_status md_newton_series_step(const md_system *sys, double *x, double *dx_norm
   double *f = reinterpret_cast<double *>(base + p->off_f);
   double *A = reinterpret_cast<double *>(base + p->off_A);
   EvalDev e = make_eval(*p, sys, x, f, A, base);
+  e.split = (flags & MD_FLAG_OZAKI) ? 1 : 0;  // series products as split products too
   SolveDev v = make_solve(p->sl, p->N, p->n, p->d, base);
   v.A = A;
   v.b = f;

@@ -280,13 +280,16 @@ FXP_HD int first_set(const bf<W> &a, int p) {
 }
 
 // K-limb md value: each limb is the 53 bits of the mantissa from the first set
-// bit after the previous limb (truncated), so no limb overlaps the next.
+// bit after the previous limb, so no limb overlaps the next; the last limb is
+// rounded to nearest on the next bit (a truncation would bias every result
+// toward zero, and those biases add up along the degrees of the solve).
 template <int K, int W>
 FXP_NI void to_md(const bf<W> &a, double (&z)[K]) {
 #pragma unroll
   for (int l = 0; l < K; ++l) z[l] = is_nan(a) ? dfrom(0x7ff8000000000000ULL) : 0.0;
   if (is_zero(a) || is_nan(a)) return;
   int p = 0;  // the top bit is set
+  int plast = -1, last = -1;
 #pragma unroll
   for (int l = 0; l < K; ++l) {
     if (p < 0 || p >= 32 * W) break;
@@ -305,7 +308,23 @@ FXP_NI void to_md(const bf<W> &a, double (&z)[K]) {
     const int Be = a.e - 1 - p - 52 + 1075;
     if (Be <= 0 || Be >= 2047) break;  // outside the double range: dropped
     z[l] = dfrom(((uint64_t)a.neg << 63) | ((uint64_t)Be << 52) | (mant & ((1ULL << 52) - 1)));
+    plast = p;
+    last = l;
     p = first_set<W>(a, p + 53);
+  }
+  if (last == K - 1) {  // round the last limb on the bit below it
+    const int q = plast + 53;
+    if (q < 32 * W) {
+      uint32_t wq = 0u;
+#pragma unroll
+      for (int i = 0; i < W; ++i)
+        if (i == (q >> 5)) wq = a.m[i];
+      const int Bu = a.e - 1 - plast - 52 + 1023;  // the last limb's unit in the last place
+      if (((wq >> (31 - (q & 31))) & 1u) && Bu > 0) {
+        const double ulp = dfrom((uint64_t)Bu << 52);
+        z[K - 1] = z[K - 1] + (a.neg ? -ulp : ulp);  // exact: (mant + 1) 2^(exp), at most a power of two
+      }
+    }
   }
 }
 

@@ -367,4 +367,54 @@ __device__ __forceinline__ void backsub_entry_fx(const double *M, double *Y, dou
   }
 }
 
+// ------------------------------------------------------ dx_k = W r_k, one row
+// Warps of one CTA at most (the batched kernel's largest CTA: 384 threads).
+constexpr int kFxMaxWarps = 12;
+
+// Row `row` of dx_k = W r_k in fixed point, over the kRowLanes virtual lanes
+// of wmv_row (lane v: plane p = v / Vc, column slot cs = v % Vc, Vc =
+// kRowLanes / P; slot cs sums columns cs, cs + Vc, ... in order): each warp
+// reduces its 32 lanes by an xor tree, then the warp sums of a plane are
+// added in warp order.  Called by every thread of the CTA; the group of
+// kRowLanes threads with index gt (active when act) handles the row, the
+// others only pass the barriers.
+template <int K, int P>
+__device__ __forceinline__ void wmv_row_fx(const double *Wm, const double *r, double *dx, int N, int n, int k,
+                                           int row, int gt, bool act) {
+  using namespace fxp;
+  constexpr int W = words_for(K), Vc = kRowLanes / P, WPP = Vc / 32;  // warps per plane
+  __shared__ bf<W> s_wsum[kFxMaxWarps];
+  const long long VS = P * K;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  bf<W> acc = zero<W>();
+  if (act) {
+    const int p = gt / Vc, cs = gt % Vc;
+    for (int c = cs; c < N; c += Vc) {
+      bf<W> w[P], x[P];
+      fx_ld_val<W, K, P>(Wm + ((long long)row * N + c) * VS, w);
+      fx_ld_val<W, K, P>(r + ((long long)k * N + c) * VS, x);
+      bf<W> t;
+      if constexpr (P == 1) {
+        t = mul<W>(w[0], x[0]);
+      } else if (p == 0) {  // real part: w_re x_re - w_im x_im
+        t = add<W>(mul<W>(w[0], x[0]), neg<W>(mul<W>(w[1], x[1])));
+      } else {  // imaginary part: w_re x_im + w_im x_re
+        t = add<W>(mul<W>(w[0], x[1]), mul<W>(w[1], x[0]));
+      }
+      acc = add<W>(acc, t);
+    }
+    fx_warp_sum<W>(acc);
+    if (lane == 0) s_wsum[warp] = acc;
+  }
+  __syncthreads();
+  if (act && gt < P) {  // lane gt = plane: the plane's warp sums in order
+    const int w0 = warp - (gt >> 5) + gt * WPP;  // first warp of the plane within this group
+    bf<W> z = s_wsum[w0];
+#pragma unroll
+    for (int q = 1; q < WPP; ++q) z = add<W>(z, s_wsum[w0 + q]);
+    fx_st<K, W>(dx + ((long long)k * n + row) * VS + gt * K, z);
+  }
+  __syncthreads();
+}
+
 }  // namespace mdk

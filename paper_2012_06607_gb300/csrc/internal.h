@@ -54,6 +54,7 @@ struct EvalDev {
   const int *stage_off0 = nullptr;  // HOST array, nstages + 1 entries
   int resident_ctas = 0;            // > 0: run the full stages on this many SM-filling CTAs
   int resident_smem = 0;            // dynamic shared memory those CTAs reserve (keeps other CTAs off their SMs)
+  int split = 0;                    // series products in fixed point (the split-product form), K >= 2
   const int *groups = nullptr;
   int ngroups = 0;
   const int *contrib = nullptr;

@@ -24,6 +24,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "conv_fx.cuh"
 #include "house_fx.cuh"
 #include "internal.h"
 #include "md.cuh"
@@ -1144,6 +1145,12 @@ __global__ void __launch_bounds__(kRowLanes) rhs_finish_kernel(const double *__r
 template <int K, int P>
 __device__ __forceinline__ void wmv_row(const double *W, const double *r, double *dx, int N, int n, int k, int row,
                                         double (*sm)[K], int gt, int gn, bool act) {
+  if constexpr (K >= 2) {  // W = A_0^-1 applied in fixed point, as it was formed (house_fx.cuh)
+    (void)sm;
+    (void)gn;  // groups are kRowLanes threads
+    wmv_row_fx<K, P>(W, r, dx, N, n, k, row, gt, act);
+    return;
+  }
   constexpr int Vc = kRowLanes / P;
   const long long VS = P * K;
   const int nleaf = min(N, Vc);

@@ -115,6 +115,20 @@ cudaError_t Impl<K, P>::eval_rest(const EvalDev &e, cudaStream_t s) {
     const int t0 = e.stage_off[st], t1 = e.stage_off[st + 1];
     if (t1 <= t0) continue;
     ProfScope prof(PK_CONV, s);
+    if constexpr (K >= 2) {
+      if (e.split) {  // the split-product form: every term on 32-bit word slices
+        auto kern = conv_stage_fx_kernel<K, P>;
+        int smem = e.resident_ctas > 0 ? e.resident_smem : 0;
+        if (smem > 0 && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+          (void)cudaGetLastError();
+          smem = 0;
+        }
+        const unsigned grid =
+            e.resident_ctas > 0 ? (unsigned)e.resident_ctas : blocks_for(t1 - t0, kConvFxThreads);
+        kern<<<grid, kConvFxThreads, smem, s>>>(e.tasks + 8LL * t0, t1 - t0, e.pool, d);
+        continue;
+      }
+    }
     if (e.resident_ctas > 0) {
       // The CTAs reserve all the shared memory an SM offers (the kernel does
       // not use it), so that kernels on the other stream cannot share their

@@ -123,3 +123,24 @@ def test_non_finite_values_propagate(fx, K):
     z = np.zeros((2, K))
     for op in (3, 5):
         assert not np.isfinite(_call(fx, K, op, z)).any(), (K, op)
+
+
+@pytest.mark.parametrize("K", [2, 4])
+def test_products_round_to_nearest(fx, K):
+    """The conversion back to K limbs rounds the last limb to nearest: the
+    signed error of many products, in units of the last limb's place, averages
+    near zero (a truncation would average about -1/2) and never reaches 1."""
+    x, y = _operands(K, 1500, 11, positive=True), _operands(K, 1500, 12, positive=True)
+    pr = _call(fx, K, 1, x, y)
+    errs = []
+    for i in range(x.shape[0]):
+        want = _val(x[i]) * _val(y[i])
+        last = pr[i, K - 1]
+        if last == 0.0:
+            continue
+        ulp = Fraction(2) ** (int(np.frexp(abs(last))[1]) - 53)
+        errs.append(float((_val(pr[i]) - want) / ulp))
+    errs = np.array(errs)
+    assert len(errs) > 1000
+    assert np.abs(errs).max() <= 0.5 + 1e-3, np.abs(errs).max()
+    assert abs(errs.mean()) < 0.05, errs.mean()

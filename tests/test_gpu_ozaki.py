@@ -1,11 +1,12 @@
-"""Split-product (Ozaki) form of the block Toeplitz update against the oracle.
+"""Split-product (Ozaki) form against the oracle.
 
-The form changes only how r_k = b_k - sum_j A_{k-j} dx_j is computed (exact
-slice products on the BF16 tensor pipe, exact fixed-point accumulation, one
-rounding to K limbs), so it must meet the same per-degree tolerance as the
-plain form, and on the ill-conditioned quad-double system (n = 256, d = 16,
-cond(A_0) = 1e8) its error against the oracle must not exceed the plain
-form's (equal accuracy).
+The form computes r_k = b_k - sum_j A_{k-j} dx_j from exact slice products on
+the BF16 tensor pipe with exact fixed-point accumulation and one rounding to
+K limbs, and (in the Newton step) the series products of the evaluation on
+32-bit word slices with exact products and column sums.  It must meet the same
+per-degree tolerance as the plain form, and on the ill-conditioned
+quad-double system (n = 256, d = 16, cond(A_0) = 1e8) its error against the
+oracle must not exceed the plain form's (equal accuracy).
 """
 import numpy as np
 import pytest
@@ -78,6 +79,46 @@ def test_ozaki_newton_steps(md, orc):
         worst = worst_in_eps(x.cpu().numpy(), xo, s.limbs)
         print(s.name, "ozaki newton worst rel/eps:", worst)
         assert worst <= TOL
+
+
+@pytest.mark.parametrize("K,cplx", [(3, True), (5, False), (8, True), (10, False), (2, False)])
+def test_ozaki_newton_other_precisions(md, orc, K, cplx):
+    """The split-product form (series products on 32-bit word slices, update
+    on 8-bit slices) at other limb counts: four steps of a random system
+    against the oracle's, per degree within 1e3 eps_K."""
+    import torch
+
+    s = mdgen.random_system(60 + K, n=6, K=K, cplx=cplx, d=10, monos=5, maxvars=3, maxdeg=3,
+                            coef_kind="unit" if cplx else "uniform", name=f"oz{K}")
+    sysd = md.DeviceSystem(s)
+    ws = md.workspace(sysd.workspace_bytes(OZAKI))
+    x = md.to_device(s.x0)
+    xo = s.x0.copy()
+    for _ in range(4):
+        md.newton_step(sysd, x, ws, flags=OZAKI)
+        assert md.device_status(ws) == 0
+        xo, _ = orc.newton_step(s, xo)
+    worst = worst_in_eps(x.cpu().numpy(), xo, K)
+    print("ozaki K", K, cplx, "worst rel/eps:", worst)
+    assert worst <= TOL
+
+
+def test_ozaki_octo_double_full_size_step(md, orc):
+    """Octo double real, n = 128, d = 32: one split-product step against the
+    oracle's and against the deca double oracle on the same exact inputs."""
+    s = mdgen.config_system(2, 1)
+    sysd = md.DeviceSystem(s)
+    ws = md.workspace(sysd.workspace_bytes(OZAKI))
+    x = md.to_device(s.x0)
+    md.newton_step(sysd, x, ws, flags=OZAKI)
+    assert md.device_status(ws) == 0
+    xo, _ = orc.newton_step(s, s.x0)
+    worst = worst_in_eps(x.cpu().numpy(), xo, 8)
+    ref = s.with_limbs(10)
+    xr, _ = orc.newton_step(ref, ref.x0)
+    worst2 = worst_in_eps(x.cpu().numpy(), xr, 8)
+    print("cfg2 ozaki step worst rel/eps: oracle", worst, "deca double", worst2)
+    assert worst <= TOL and worst2 <= TOL
 
 
 def test_ozaki_full_size_newton_step(md, orc):
