@@ -533,7 +533,10 @@ def measure_solve3(args, with_err: bool) -> dict:
         import oracle
 
         from math import fsum
-        want = oracle.Oracle(threads=os.cpu_count() or 1).linsolve(K, False, A, b)
+        orc = oracle.Oracle(threads=os.cpu_count() or 1)
+        t0 = time.perf_counter()
+        want = orc.linsolve(K, False, A, b)
+        cpu_solve_s = time.perf_counter() - t0
         for name in ("plain", "ozaki"):
             got = res[name]["dx"]
             e = []
@@ -542,6 +545,8 @@ def measure_solve3(args, with_err: bool) -> dict:
                 scale = max(abs(want[0, 0, i, k]) for i in range(n))
                 e.append(diff / scale)
             err[name] = {"max_rel": max(e), "max_rel_over_eps": max(e) / 2.0 ** (-52 * K)}
+        err["cpu_baseline"] = {"value": 1.0 / cpu_solve_s, "unit": "solves/s", "cores": orc.threads(),
+                               "kind": "oracle", "sample": "one solve (host cores, OpenMP)"}
     upd = {name: sum(v for k, v in res[name]["kernel_ms_per_solve"].items()
                      if k in ("rhs_partial", "rhs_finish", "oz_split", "oz_update")) for name in res}
     return {"metric": "linearized block Toeplitz solves/s (qd real, n=256, d=16, cond(A_0)=1e8)",
@@ -813,9 +818,12 @@ def measure_batched(args, count, rank, world, local, dist, with_loop: bool, err_
         from math import fsum
         orc = oracle.Oracle(threads=os.cpu_count() or 1)
         worst = []
+        cpu_s = 0.0
         for i, got in first.items():
             s = systems[i]
+            t0 = time.perf_counter()
             want, _ = orc.newton_step(s, s.x0)
+            cpu_s += time.perf_counter() - t0
             P, K, n, d = s.planes, s.limbs, s.n, s.degree
             rel = 0.0
             for k in range(d + 1):
@@ -825,6 +833,9 @@ def measure_batched(args, count, rank, world, local, dist, with_loop: bool, err_
                 rel = max(rel, diff / max(scale, 1e-300))
             worst.append({"n": n, "d": d, "limbs": K, "max_rel_over_eps": rel / 2.0 ** (-52 * K)})
         err = {"systems": worst, "max_rel_over_eps": max(w["max_rel_over_eps"] for w in worst),
+               "cpu_baseline": {"value": len(worst) / cpu_s, "unit": "system steps/s", "cores": orc.threads(),
+                                "kind": "oracle", "sample": "the sampled systems' first steps (the largest n of "
+                                                            "each precision; host cores, OpenMP)"},
                "measure": "first step from x0; per degree, max_i |x_gpu - x_oracle| / max_i |x_oracle|, "
                           "in units of eps_K = 2^(-52K)"}
     line = {"metric": f"batched Newton iterations/s ({len(all_systems)} systems, n~U{{8..64}}, d~U{{8..32}}, dd/qd, "
