@@ -141,7 +141,9 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
     qr_house<K, P>(M, vd, beta, status, n, 0);
     for (int j = 0; j < n; ++j) {
       const bool ahead = j + 1 < n;
-      if (ahead) qr_apply_cta<K, P>(M, Y, vd, beta, n, n, j, 0, s_row);
+      // (no register caching of converted rows here: the batched kernel's
+      // register bound would spill them; the values and bits are the same)
+      if (ahead) qr_apply_cta<K, P, false>(M, Y, vd, beta, n, n, j, 0, s_row);
       for (int w = warp + (ahead ? 1 : 0); w < (n - j - 1) + n; w += nwarp)
         qr_apply_warp<K, P>(M, Y, vd, beta, n, n, j, w, lane);
       __syncthreads();

@@ -1213,6 +1213,9 @@ cudaEvent_t aux_event(DevAux *a, int i) { return i == 0 ? a->e0 : a->e1; }
 #define MDK_FACTOR_SMS 4
 #endif
 constexpr int kFactorSms = MDK_FACTOR_SMS;
+// The split-product form keeps the same four: its fixed-point series products
+// remain the step's critical path (measured at n = 64, d = 64: 43.1 steps/s
+// with 4 SMs for the factorisation, 41.2 with 19, 38.8 with 38, 30.6 with 76).
 
 // ------------------------------------------------------------- profiling
 // Optional per-launch timing: when enabled, every launch is bracketed by a

@@ -18,7 +18,9 @@
 namespace mdk {
 
 // Two output coefficients of series products as conv_pair (same task layout
-// and term order), in fixed point.
+// and term order), in fixed point.  The W-word operations are called out of
+// line (inlined, they needed ~156 registers a thread and the kernel ran 25%
+// slower at 384 threads than called at 512, despite the call stack's traffic).
 template <int K, int P>
 __device__ __forceinline__ void conv_pair_fx(double *pool, int d, int outA, int xA, int yA, int kA, int outB, int xB,
                                              int yB) {
@@ -51,12 +53,14 @@ __device__ __forceinline__ void conv_pair_fx(double *pool, int d, int outA, int 
 }
 
 // The resident stage launch of conv_stage_resident_kernel in fixed point
-// (same grid and task numbering; integer work at ~90 registers a thread runs
-// 16 warps an SM).
-constexpr int kConvFxThreads = 512;
+// (same grid and task numbering; ~90 registers a thread: 16 warps an SM).
+template <int K>
+__host__ __device__ constexpr int conv_fx_threads() {
+  return 512;
+}
 
 template <int K, int P>
-__global__ void __launch_bounds__(kConvFxThreads, 1)
+__global__ void __launch_bounds__(conv_fx_threads<K>(), 1)
     conv_stage_fx_kernel(const int *__restrict__ tasks, int ntask, double *pool, int d) {
   for (int t = threadIdx.x * gridDim.x + blockIdx.x; t < ntask; t += gridDim.x * blockDim.x) {
     const int4 t0 = __ldg(reinterpret_cast<const int4 *>(tasks) + 2 * t);

@@ -177,7 +177,7 @@ FXP_HD int normalize_words(uint32_t (&t)[W + 1], uint32_t (&out)[W]) {
 // Exact value of the K-limb md number x (rounded down in magnitude below the
 // last word when its limbs span more than W words).
 template <int W, int K>
-FXP_NI bf<W> from_md(const double (&x)[K]) {
+FXP_HD bf<W> from_md_impl(const double (&x)[K]) {
   const uint64_t b0 = dbits(x[0]);
   const int B0 = (int)(b0 >> 52) & 0x7ff;
   bool finite = true;
@@ -284,7 +284,7 @@ FXP_HD int first_set(const bf<W> &a, int p) {
 // rounded to nearest on the next bit (a truncation would bias every result
 // toward zero, and those biases add up along the degrees of the solve).
 template <int K, int W>
-FXP_NI void to_md(const bf<W> &a, double (&z)[K]) {
+FXP_HD void to_md_impl(const bf<W> &a, double (&z)[K]) {
 #pragma unroll
   for (int l = 0; l < K; ++l) z[l] = is_nan(a) ? dfrom(0x7ff8000000000000ULL) : 0.0;
   if (is_zero(a) || is_nan(a)) return;
@@ -331,13 +331,13 @@ FXP_NI void to_md(const bf<W> &a, double (&z)[K]) {
 template <int W>
 FXP_HD bf<W> from_double(double x) {
   double v[1] = {x};
-  return from_md<W, 1>(v);
+  return from_md_impl<W, 1>(v);
 }
 
 // Truncated product: the top W words of the 2W-word product (partial
 // products of words i + j <= W), normalized.
 template <int W>
-FXP_NI bf<W> mul(const bf<W> &a, const bf<W> &b) {
+FXP_HD bf<W> mul_impl(const bf<W> &a, const bf<W> &b) {
   if (is_nan(a) || is_nan(b)) return nan_value<W>();
   if (is_zero(a) || is_zero(b)) return zero<W>();
   uint64_t col[W + 2];
@@ -381,7 +381,7 @@ FXP_HD bool mag_ge(const bf<W> &a, const bf<W> &b) {
 
 // a + b (signs included), truncated to W words.
 template <int W>
-FXP_NI bf<W> add(const bf<W> &a, const bf<W> &b) {
+FXP_HD bf<W> add_impl(const bf<W> &a, const bf<W> &b) {
   if (is_nan(a) || is_nan(b)) return nan_value<W>();
   if (is_zero(b)) return a;
   if (is_zero(a)) return b;
@@ -435,6 +435,29 @@ FXP_NI bf<W> add(const bf<W> &a, const bf<W> &b) {
   z.e = x.e + 32 - s;
   z.neg = x.neg;
   return z;
+}
+
+// The W-word operations as called (not inlined) on the device; a kernel that
+// needs them inlined (the series products, where passing W-word values through
+// the call stack cost more than the arithmetic) calls the *_impl forms.
+template <int W, int K>
+FXP_NI bf<W> from_md(const double (&x)[K]) {
+  return from_md_impl<W, K>(x);
+}
+
+template <int K, int W>
+FXP_NI void to_md(const bf<W> &a, double (&z)[K]) {
+  to_md_impl<K, W>(a, z);
+}
+
+template <int W>
+FXP_NI bf<W> mul(const bf<W> &a, const bf<W> &b) {
+  return mul_impl<W>(a, b);
+}
+
+template <int W>
+FXP_NI bf<W> add(const bf<W> &a, const bf<W> &b) {
+  return add_impl<W>(a, b);
 }
 
 template <int W>

@@ -184,7 +184,7 @@ __device__ __forceinline__ void house_block_fx(double *M, double *vd, double *be
 // a CTA, one virtual lane each (all threads of the CTA call it); CTA = false:
 // one warp, lane l running virtual lanes l, l+32, l+64, l+96.  Both forms
 // perform the same additions in the same order, so they give the same bits.
-template <int K, int P, bool CTA>
+template <int K, int P, bool CTA, bool CACHE = true>
 __device__ __forceinline__ void house_apply_col_v128(double *M, double *Y, const double *vd, const double *beta,
                                                      int N, int n, int j, int w) {
   using namespace fxp;
@@ -210,12 +210,35 @@ __device__ __forceinline__ void house_apply_col_v128(double *M, double *Y, const
     }
   };
   bf<W> u[P];
+  // CTA form: the lane's first row keeps its converted (v, t) for the update
+  // (where they fit in registers: up to 30 words a row)
+  constexpr bool kCache = CACHE && CTA && P * (W + 2) <= 30;  // same values either way
+  bf<W> cv[P], ct[P];
   if constexpr (CTA) {
     __shared__ bf<W> s_p[kRowLanes][P];
     __shared__ bf<W> s_tau[P];
     if (tid < kRowLanes) {
       bf<W> d[P];
-      partial(tid, d);
+#pragma unroll
+      for (int p = 0; p < P; ++p) d[p] = zero<W>();
+      for (int i = j + tid; i < N; i += kRowLanes) {
+        bf<W> v[P], t[P];
+        fx_ld_v<W, K, P>(M, vd, N, j, i, v);
+#pragma unroll
+        for (int p = 0; p < P; ++p) t[p] = fx_ld<W, K>(T + ((long long)c * N + i) * VS + p * K);
+        if constexpr (P == 1) {
+          fx_cdot_acc<W, P>(v, t, d[0], d[0]);
+        } else {
+          fx_cdot_acc<W, P>(v, t, d[0], d[1]);
+        }
+        if (kCache && i == j + tid) {
+#pragma unroll
+          for (int p = 0; p < P; ++p) {
+            cv[p] = v[p];
+            ct[p] = t[p];
+          }
+        }
+      }
 #pragma unroll
       for (int p = 0; p < P; ++p) s_p[tid][p] = d[p];
     }
@@ -257,10 +280,18 @@ __device__ __forceinline__ void house_apply_col_v128(double *M, double *Y, const
   for (int q = tid; q < kRowLanes; q += qs) {
     for (int i = j + q; i < N; i += kRowLanes) {
       bf<W> v[P], t[P];
-      fx_ld_v<W, K, P>(M, vd, N, j, i, v);
       double *dst = T + ((long long)c * N + i) * VS;
+      if (kCache && i == j + q) {  // converted in the first pass
 #pragma unroll
-      for (int p = 0; p < P; ++p) t[p] = fx_ld<W, K>(dst + p * K);
+        for (int p = 0; p < P; ++p) {
+          v[p] = cv[p];
+          t[p] = ct[p];
+        }
+      } else {
+        fx_ld_v<W, K, P>(M, vd, N, j, i, v);
+#pragma unroll
+        for (int p = 0; p < P; ++p) t[p] = fx_ld<W, K>(dst + p * K);
+      }
       fx_axpy<W, P>(u, v, t);
 #pragma unroll
       for (int p = 0; p < P; ++p) fx_st<K, W>(dst + p * K, t[p]);
@@ -413,6 +444,47 @@ __device__ __forceinline__ void wmv_row_fx(const double *Wm, const double *r, do
 #pragma unroll
     for (int q = 1; q < WPP; ++q) z = add<W>(z, s_wsum[w0 + q]);
     fx_st<K, W>(dx + ((long long)k * n + row) * VS + gt * K, z);
+  }
+  __syncthreads();
+}
+
+// ----------------------------------------- r_k = sgn b_k - (sum of the partials)
+// The finish of the block Toeplitz update in fixed point: the partial sums
+// that rhs_partial left in md (one per chunk of terms) are added in W-word
+// fixed point over the virtual lanes of rhs_finish_row (lane v: plane
+// p = v / Vc, chunk slot cs = v % Vc, slot cs takes chunks cs, cs + Vc, ...
+// in order), each warp's lanes by an xor tree, the warp sums of a plane in
+// warp order, and sgn b_k minus that sum is rounded to K limbs once.  Same
+// calling convention as wmv_row_fx.
+template <int K, int P>
+__device__ __forceinline__ void rhs_finish_row_fx(const double *b, double sgn, const double *part, double *r, int N,
+                                                  int d, int k, int nchunk, int row, int gt, bool act) {
+  using namespace fxp;
+  constexpr int W = words_for(K), Vc = kRowLanes / P, WPP = Vc / 32;
+  __shared__ bf<W> s_fsum[kFxMaxWarps];
+  const long long VS = P * K;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  bf<W> acc = zero<W>();
+  if (act) {
+    const int p = gt / Vc, cs = gt % Vc;
+    for (int c = cs; c < nchunk; c += Vc)
+      acc = add<W>(acc, fx_ld<W, K>(part + ((long long)row * nchunk + c) * VS + p * K));
+    fx_warp_sum<W>(acc);
+    if (lane == 0) s_fsum[warp] = acc;
+  }
+  __syncthreads();
+  if (act && gt < P) {  // lane gt = plane
+    const int w0 = warp - (gt >> 5) + gt * WPP;
+    bf<W> z = s_fsum[w0];
+#pragma unroll
+    for (int q = 1; q < WPP; ++q) z = add<W>(z, s_fsum[w0 + q]);
+    const long long stride = (long long)N * (d + 1);
+    double bv[K];
+#pragma unroll
+    for (int l = 0; l < K; ++l) bv[l] = b[(long long)row * (d + 1) + k + (long long)(gt * K + l) * stride];
+    bf<W> bb = from_md<W, K>(bv);
+    if (sgn < 0.0) bb = neg<W>(bb);
+    fx_st<K, W>(r + ((long long)k * N + row) * VS + gt * K, add<W>(bb, neg<W>(z)));
   }
   __syncthreads();
 }

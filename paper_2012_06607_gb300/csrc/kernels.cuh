@@ -722,11 +722,11 @@ __device__ __forceinline__ void house_apply_col_cta(double *M, double *Y, const 
 // both, and column j+1 is touched by CTA 0 only, so the step's critical path is
 // the larger of (column j+1 + Householder vector) and the rest of the update,
 // not their sum.
-template <int K, int P>
+template <int K, int P, bool CACHE = true>
 __device__ __forceinline__ void qr_apply_cta(double *M, double *Y, const double *vd, const double *beta, int N, int n,
                                              int j, int w, double (*sm)[K]) {
   if constexpr (K >= 2)
-    house_apply_col_v128<K, P, true>(M, Y, vd, beta, N, n, j, w);
+    house_apply_col_v128<K, P, true, CACHE>(M, Y, vd, beta, N, n, j, w);
   else
     house_apply_col_cta<K, P>(M, Y, vd, beta, N, n, j, w, sm);
 }
@@ -1090,6 +1090,12 @@ template <int K, int P>
 __device__ __forceinline__ void rhs_finish_row(const double *b, double sgn, const double *part, double *r, int N,
                                                int d, int k, int nchunk, int row, double (*sm)[K], int gt, int gn,
                                                bool act) {
+  if constexpr (K >= 2) {  // the partials summed in fixed point (house_fx.cuh)
+    (void)sm;
+    (void)gn;  // groups are kRowLanes threads
+    rhs_finish_row_fx<K, P>(b, sgn, part, r, N, d, k, nchunk, row, gt, act);
+    return;
+  }
   constexpr int Vc = kRowLanes / P;
   const long long VS = P * K;
   const int nleaf = min(nchunk, Vc);

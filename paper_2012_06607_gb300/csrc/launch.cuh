@@ -123,9 +123,9 @@ cudaError_t Impl<K, P>::eval_rest(const EvalDev &e, cudaStream_t s) {
           (void)cudaGetLastError();
           smem = 0;
         }
-        const unsigned grid =
-            e.resident_ctas > 0 ? (unsigned)e.resident_ctas : blocks_for(t1 - t0, kConvFxThreads);
-        kern<<<grid, kConvFxThreads, smem, s>>>(e.tasks + 8LL * t0, t1 - t0, e.pool, d);
+        constexpr int T = conv_fx_threads<K>();
+        const unsigned grid = e.resident_ctas > 0 ? (unsigned)e.resident_ctas : blocks_for(t1 - t0, T);
+        kern<<<grid, T, smem, s>>>(e.tasks + 8LL * t0, t1 - t0, e.pool, d);
         continue;
       }
     }
