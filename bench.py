@@ -441,7 +441,8 @@ def run_product(args):
             line["other_forms"]["batched"] = {k: bl[k] for k in (
                 "metric", "value", "unit", "ms_per_iteration", "system_steps_per_s", "latency_ms_p50",
                 "latency_ms_p99", "latency_ms_max", "loop_ms_per_iteration", "speedup_vs_loop",
-                "shared_sm_only_ms_per_iteration", "roofline", "err_vs_oracle", "systems", "limb_counts",
+                "shared_sm_only_ms_per_iteration", "split_product_form", "roofline", "err_vs_oracle", "systems",
+                "limb_counts",
                 "phases_of_slowest_system")}
             torch.cuda.empty_cache()
 
@@ -604,8 +605,36 @@ def run_ladder(args):
         d = s.degree
         conv_instr = nconv * ((d + 1) * (d + 2) // 2 * cmul_i + d * (d + 1) // 2 * cadd_i)
         conv_ms = prof.get("conv_stage", (float("nan"), 0))[0] / args.steps
+        # the split-product form at the same precision (K >= 2): step and
+        # series-product times
+        split = None
+        if K >= 2:
+            oflags = md.FLAG_OZAKI
+            ows = md.workspace(sysd.workspace_bytes(oflags))
+            for _ in range(args.warmup):
+                md.newton_step(sysd, x, ows, flags=oflags)
+            torch.cuda.synchronize()
+            md.profile_read()
+            md.profile_enable(True)
+            oevs = []
+            for _ in range(args.steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                md.newton_step(sysd, x, ows, flags=oflags)
+                e1.record(stream)
+                oevs.append((e0, e1))
+            torch.cuda.synchronize()
+            md.profile_enable(False)
+            oprof = md.profile_read()
+            assert md.device_status(ows) == 0
+            oms = statistics.mean(a.elapsed_time(b) for a, b in oevs)
+            ocv = oprof.get("conv_stage_fx", oprof.get("conv_stage", (float("nan"), 0)))[0] / args.steps
+            split = {"ms_per_step": oms, "conv_ms_per_step": ocv, "speedup_vs_md": ms / oms,
+                     "conv_speedup_vs_md": conv_ms / ocv if ocv > 0 else None}
+            del ows
         t1 = TABLE1.get(K)
-        per[K] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "conv_ms_per_step": conv_ms,
+        per[K] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "conv_ms_per_step": conv_ms, "split_product_form": split,
                   "conv_fp64_instr_per_step": conv_instr,
                   "conv_fp64_frac_of_peak": conv_instr / (conv_ms / 1e3) / FP64_PEAK_INSTR if conv_ms > 0 else None,
                   "table1_ops_per_complex_mac": (4 * t1[1] + 4 * t1[0]) if t1 else None}
@@ -768,19 +797,46 @@ def measure_batched(args, count, rank, world, local, dist, with_loop: bool, err_
         e1.record(stream)
         e1.synchronize()
         serial_ms = e0.elapsed_time(e1)
+        # the split-product form (series products on 32-bit word slices) on the
+        # same plan and tuning, replayed from its own graph; its first step
+        # from x0 for the error sample
+        oflags = flags | md.FLAG_OZAKI
+        for _ in range(2):
+            md.newton_step_batched(sds, xs, ws, nrm, None, flags=oflags, stream=stream)
+        oz_ms = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            md.newton_step_batched(sds, xs, ws, nrm, None, flags=oflags, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            oz_ms.append(e0.elapsed_time(e1))
+        oz_first = {}
+        if sample:
+            for x, sy in zip(xs, systems):
+                x.copy_(torch.from_numpy(np.ascontiguousarray(sy.x0, dtype=np.float64)))
+            md.newton_step_batched(sds, xs, ws, nrm, None, flags=oflags, stream=stream)
+            stream.synchronize()
+            oz_first = {i: xs[i].cpu().numpy() for i in sample}
         # one more step (not timed) with a global-timer stamp after every phase
         ptimes = torch.zeros((len(systems), md.PHASE_STAMPS), dtype=torch.int64, device="cuda")
         md.newton_step_batched(sds, xs, ws, nrm, ptimes, flags=flags | md.FLAG_PHASE_TIMES, stream=stream)
         torch.cuda.synchronize()
+        optimes = torch.zeros_like(ptimes)
+        md.newton_step_batched(sds, xs, ws, nrm, optimes, flags=oflags | md.FLAG_PHASE_TIMES, stream=stream)
+        torch.cuda.synchronize()
     assert md.device_status(ws) == 0
     lat = np.concatenate(lat)
     it_ms = reduce_max(dist, sum(ms) / len(ms))
+    oz_it_ms = reduce_max(dist, sum(oz_ms) / len(oz_ms))
     # phases of the slowest system, against the SM's share of the FP64 peak
     pt = ptimes.cpu().numpy().astype(np.float64)
     plat = pt[:, -1] - pt[:, 0]
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     slow = int(np.argmax(plat))
     ph = dict(zip(md.PHASE_NAMES, np.diff(pt[slow]) / 1e6))
+    opt = optimes.cpu().numpy().astype(np.float64)
+    oph = dict(zip(md.PHASE_NAMES, np.diff(opt[slow]) / 1e6))
     m = step_fp64_model(systems[slow])
     per_sm = FP64_PEAK_INSTR / sms
     spans = {"products": (m["conv"], ph["products"]), "accumulation": (m["accum"], ph["accumulation"]),
@@ -819,11 +875,8 @@ def measure_batched(args, count, rank, world, local, dist, with_loop: bool, err_
         orc = oracle.Oracle(threads=os.cpu_count() or 1)
         worst = []
         cpu_s = 0.0
-        for i, got in first.items():
-            s = systems[i]
-            t0 = time.perf_counter()
-            want, _ = orc.newton_step(s, s.x0)
-            cpu_s += time.perf_counter() - t0
+
+        def rel_over_eps(s, got, want):
             P, K, n, d = s.planes, s.limbs, s.n, s.degree
             rel = 0.0
             for k in range(d + 1):
@@ -831,8 +884,19 @@ def measure_batched(args, count, rank, world, local, dist, with_loop: bool, err_
                            for j in range(n))
                 scale = max(math.hypot(*[fsum(want[p, :, j, k]) for p in range(P)]) for j in range(n))
                 rel = max(rel, diff / max(scale, 1e-300))
-            worst.append({"n": n, "d": d, "limbs": K, "max_rel_over_eps": rel / 2.0 ** (-52 * K)})
+            return rel / 2.0 ** (-52 * K)
+
+        for i, got in first.items():
+            s = systems[i]
+            t0 = time.perf_counter()
+            want, _ = orc.newton_step(s, s.x0)
+            cpu_s += time.perf_counter() - t0
+            w = {"n": s.n, "d": s.degree, "limbs": s.limbs, "max_rel_over_eps": rel_over_eps(s, got, want)}
+            if i in oz_first:
+                w["split_form_max_rel_over_eps"] = rel_over_eps(s, oz_first[i], want)
+            worst.append(w)
         err = {"systems": worst, "max_rel_over_eps": max(w["max_rel_over_eps"] for w in worst),
+               "split_form_max_rel_over_eps": max(w.get("split_form_max_rel_over_eps", 0.0) for w in worst),
                "cpu_baseline": {"value": len(worst) / cpu_s, "unit": "system steps/s", "cores": orc.threads(),
                                 "kind": "oracle", "sample": "the sampled systems' first steps (the largest n of "
                                                             "each precision; host cores, OpenMP)"},
@@ -847,6 +911,10 @@ def measure_batched(args, count, rank, world, local, dist, with_loop: bool, err_
             "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
             "latency_ms_max": float(lat.max()),
             "shared_sm_only_ms_per_iteration": serial_ms,
+            "split_product_form": {"flags": "MD_FLAG_OZAKI: series products and update chunk sums on 32-bit word slices",
+                                   "ms_per_iteration": oz_it_ms, "value": 1e3 / oz_it_ms, "unit": "iterations/s",
+                                   "speedup_vs_md": it_ms / oz_it_ms,
+                                   "phases_ms_of_the_same_system": {k: round(float(v), 3) for k, v in oph.items()}},
             "phases_of_slowest_system": phases,
             "loop_ms_per_iteration": loop_ms,
             "speedup_vs_loop": (loop_ms / it_ms) if loop_ms else None,

@@ -94,15 +94,28 @@ typedef struct md_system {
 /* flags */
 #define MD_FLAG_PLAIN 0x0 /* plain multiple-double kernels for every step        */
 /*
- * Split-product form of the block Toeplitz update r_k = b_k - sum_j A_{k-j} dx_j:
- * every md number of a row of A_i (and of dx_j) is cut into signed 8-bit integer
- * slices relative to a shared power of two; all slice products are exact BF16
- * tensor-core products with exact fp32 accumulation (K <= 1024 per product), and
- * the terms of r_k are added exactly in a fixed-point integer before one
- * conversion to K limbs.  Error: 2^(12 - 8S) of the largest term (S slices per
- * number, 8S >= 53K + 24 bits).  The QR of A_0, the Householder norms and
- * dx_k = (R^-1 Q^H) r_k stay in multiple-double arithmetic.  Needs the larger
- * workspace reported for this flag.
+ * Split-product form.
+ *   - The block Toeplitz update r_k = b_k - sum_j A_{k-j} dx_j: every md number
+ *     of a row of A_i (and of dx_j) is cut into signed 8-bit integer slices
+ *     relative to a shared power of two; all slice products are exact BF16
+ *     tensor-core products with exact fp32 accumulation (K <= 1024 per
+ *     product), and the terms of r_k are added exactly in a fixed-point integer
+ *     before one conversion to K limbs.  Error: 2^(12 - 8S) of the largest term
+ *     (S slices per number, 8S >= 53K + 24 bits).  Needs the larger workspace
+ *     reported for this flag.
+ *   - In md_newton_series_step, the series products of the evaluation
+ *     (K >= 3): each term on 32-bit word slices of the md operands, exact word
+ *     products and column sums, the coefficient kept in W-word fixed point
+ *     (53K bits and two guard words) and rounded to K limbs once.  A_0 still
+ *     comes from the md products of coefficient 0.
+ *   - In md_newton_series_step_batched (K >= 3), the same series products and,
+ *     in place of the 8-bit slices above, the chunk sums of the block Toeplitz
+ *     update on 32-bit word slices, each chunk rounded to K limbs once.
+ * At one and two limbs the flag leaves the series products in md arithmetic,
+ * which is faster there.  Results are within the plain form's tolerance, not
+ * its bits.  (In every form, from three limbs on, the QR of A_0,
+ * W = R^-1 Q^H, the finish of r_k and dx_k = W r_k run in the same W-word
+ * fixed point.)
  */
 #define MD_FLAG_OZAKI 0x1
 /* batched form: pick threads per CTA and CTAs per SM per precision class, and
@@ -257,7 +270,9 @@ md_status md_newton_series_step(const md_system *sys, double *x, double *dx_norm
  *   ws:      DEVICE workspace of md_batched_workspace_bytes() bytes; the status
  *            word covers the whole batch
  *   flags:   MD_FLAG_AUTOTUNE, MD_FLAG_GRAPH, MD_FLAG_SERIAL, MD_FLAG_PHASE_TIMES,
- *            MD_FLAG_CHECK
+ *            MD_FLAG_CHECK, MD_FLAG_OZAKI (series products and update sums on
+ *            32-bit word slices; the bit-equality with md_newton_series_step
+ *            holds for the plain form)
  */
 size_t md_batched_workspace_bytes(int nsys, const md_system *sys, int flags);
 md_status md_newton_series_step_batched(int nsys, const md_system *sys, double *const *x, double *dx_norm,

@@ -37,7 +37,8 @@ template <int K, int P>
 __global__ void batched_step_kernel(const BatchJob *__restrict__ jobs, const int *__restrict__ order, int njobs,
                                     int *__restrict__ counter, const int *ibase, double *dbase,
                                     double *__restrict__ nrm, unsigned long long *__restrict__ times,
-                                    int *__restrict__ status, int update_x, int *__restrict__ resident, int tstride);
+                                    int *__restrict__ status, int update_x, int *__restrict__ resident, int tstride,
+                                    int split);
 
 // Dynamic shared memory per CTA of the batched kernel that lets at most
 // `cps` CTAs share an SM: the SM's shared memory split cps ways, less the
@@ -67,7 +68,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
                                                                      double *__restrict__ nrm,
                                                                      unsigned long long *__restrict__ times,
                                                                      int *__restrict__ status, int update_x,
-                                                                     int *__restrict__ resident, int tstride) {
+                                                                     int *__restrict__ resident, int tstride,
+                                                                     int split) {
   __shared__ int s_job;
   // one reduction buffer per group of kRowLanes threads: the degree loop
   // reduces that many rows at once
@@ -117,7 +119,10 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
         // one call for both kinds of item: two inlined copies would run one
         // after the other in a warp that holds both
         const bool pair = 2 * p < d;
-        conv_pair<K, P, false>(pool, d, out, a, b, p, pair ? out : -1, pair ? a : -1, pair ? b : -1);
+        if (K >= kFxConvMinLimbs && split)  // the split-product form: 32-bit word slices (uniform over the launch)
+          conv_pair_fx<K, P>(pool, d, out, a, b, p, pair ? out : -1, pair ? a : -1, pair ? b : -1);
+        else
+          conv_pair<K, P, false>(pool, d, out, a, b, p, pair ? out : -1, pair ? a : -1, pair ? b : -1);
       }
       __syncthreads();
     }
@@ -162,8 +167,12 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
     for (int k = 0; k <= d; ++k) {
       int C, nchunk;
       rhs_chunking(n, n, k, C, nchunk);
-      for (long long e = tid; e < (long long)n * nchunk; e += NT)
-        rhs_partial_item<K, P>(A, dxw, part, n, n, d, k, C, nchunk, e);
+      for (long long e = tid; e < (long long)n * nchunk; e += NT) {
+        if (K >= kFxConvMinLimbs && split)  // the split-product form: 32-bit word slices
+          rhs_partial_item_fx<K, P>(A, dxw, part, n, n, d, k, C, nchunk, e);
+        else
+          rhs_partial_item<K, P>(A, dxw, part, n, n, d, k, C, nchunk, e);
+      }
       __syncthreads();
       // G rows at a time, one per group; every row's tree is the one-row tree
       for (int row0 = 0; row0 < n; row0 += G) {

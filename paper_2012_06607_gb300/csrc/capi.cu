@@ -715,6 +715,8 @@ struct BatchPlan {
   int exec_tstride = 2;
   UseEvents uses;         // after each step enqueued on a stream
   bool captured = false;  // enqueued into a caller's capture: never dropped
+  int oz = 0;             // this call's MD_FLAG_OZAKI: series products in fixed point
+  int exec_oz = 0;        // the form the graph was captured with
   ~BatchPlan() {
     // a step in flight may still read the pinned image, directly or from the
     // graph: wait for the steps enqueued with this plan, not the device
@@ -949,6 +951,7 @@ mdk::BatchDev batch_dev(const BatchPlan &bp, const BatchClass &c, int ctr, int f
   b.grid = grid;
   b.threads = threads;
   b.ctas_per_sm = cps;
+  b.split = bp.oz;
   return b;
 }
 
@@ -1566,6 +1569,7 @@ md_status md_newton_series_step_batched(int nsys, const md_system *sys, double *
   md_status st = batch_prepare(nsys, sys, x, bp, true, cap == cudaStreamCaptureStatusNone, flags & MD_FLAG_CHECK);
   if (st != MD_OK) return st;
   if (bp->total > ws_bytes) return MD_ERR_WORKSPACE;
+  bp->oz = (flags & MD_FLAG_OZAKI) ? 1 : 0;
   char *base = static_cast<char *>(ws);
   const int sms = device_sms();
   const bool split = !(flags & MD_FLAG_SERIAL);
@@ -1579,7 +1583,7 @@ md_status md_newton_series_step_batched(int nsys, const md_system *sys, double *
   }
   if ((flags & MD_FLAG_GRAPH) && s != nullptr) {
     if (!bp->exec || bp->exec_ws != ws || bp->exec_nrm != dx_norm || bp->exec_times != times || bp->exec_stream != s ||
-        bp->exec_split != split || bp->exec_tstride != tstride) {
+        bp->exec_split != split || bp->exec_tstride != tstride || bp->exec_oz != bp->oz) {
       if (bp->exec) cudaGraphExecDestroy(bp->exec);
       bp->exec = nullptr;
       cudaGraph_t g = nullptr;
@@ -1598,6 +1602,7 @@ md_status md_newton_series_step_batched(int nsys, const md_system *sys, double *
       bp->exec_stream = s;
       bp->exec_split = split;
       bp->exec_tstride = tstride;
+      bp->exec_oz = bp->oz;
     }
     if (cudaGraphLaunch(bp->exec, s) != cudaSuccess) return MD_ERR_CUDA;
   } else if (batch_enqueue(*bp, base, dx_norm, times, s, sms, split, tstride) != cudaSuccess) {

@@ -52,6 +52,41 @@ __device__ __forceinline__ void conv_pair_fx(double *pool, int d, int outA, int 
   if (outB >= 0) fx_st_val<W, K, P>(pool + outB * SS + kB * VS, acc);
 }
 
+// One chunk of a row of the block Toeplitz update sum_{j<k} A_{k-j} dx_j
+// (Section 3.2; rhs_partial_item's terms in its order) in fixed point: every
+// term an exact product of word slices, the chunk's sum rounded to K limbs
+// once.  A: [P][K][d+1][n][N] (column-major blocks), dx: [d+1][n] values of
+// P*K doubles, part: [N][nchunk] values.
+template <int K, int P>
+__device__ __forceinline__ void rhs_partial_item_fx(const double *A, const double *dx, double *part, int N, int n,
+                                                    int d, int k, int C, int nchunk, long long e) {
+  using namespace fxp;
+  constexpr int W = words_for(K);
+  const int row = (int)(e % N), chunk = (int)(e / N);
+  const long long nn = (long long)N * n, VS = P * K, stride = (long long)(d + 1) * nn;
+  const int t0 = chunk * C, t1 = min(t0 + C, k * n);
+  bf<W> acc[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) acc[p] = zero<W>();
+  for (int t = t0; t < t1; ++t) {
+    const int j = t / n, col = t % n;
+    const double *ap = A + (long long)(k - j) * nn + (long long)col * N + row;
+    bf<W> a[P], x[P], prod[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      double v[K];
+#pragma unroll
+      for (int l = 0; l < K; ++l) v[l] = ap[(long long)(p * K + l) * stride];
+      a[p] = from_md<W, K>(v);
+    }
+    fx_ld_val<W, K, P>(dx + ((long long)j * n + col) * VS, x);
+    fx_cmul<W, P>(a, x, prod);
+#pragma unroll
+    for (int p = 0; p < P; ++p) acc[p] = add<W>(acc[p], prod[p]);
+  }
+  fx_st_val<W, K, P>(part + ((long long)row * nchunk + chunk) * VS, acc);
+}
+
 // The resident stage launch of conv_stage_resident_kernel in fixed point
 // (same grid and task numbering; ~90 registers a thread: 16 warps an SM).
 template <int K>

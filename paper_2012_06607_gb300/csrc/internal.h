@@ -13,6 +13,19 @@ enum : int { ST_SINGULAR = 1, ST_NONFINITE = 2, ST_TIMEOUT = 4 };
 constexpr int kRowLanes = 128;
 constexpr int kHouseThreads = 128;
 
+// Limb counts from which the factorisation chain (QR, R^-1, W, the finish of
+// r_k and dx_k = W r_k) runs in W-word fixed point, and from which the
+// split-product form puts the series products (and the batched form's update
+// sums) on 32-bit word slices.  The md forms' cost grows as K^2 and the
+// fixed-point forms' fixed part (conversions, renormalisation, values passed
+// through the call stack) does not shrink with K: on GB300 double double is
+// faster in md arithmetic in every phase (the n = 64, d = 64 step 10.9 ms in
+// md against 13.8 ms with the fixed-point chain; series products 0.64x in
+// fixed point), and from three limbs on the fixed-point forms are faster
+// (products 2.2x at K = 3, 3.9x at K = 10).
+constexpr int kFxMinLimbs = 3;
+constexpr int kFxConvMinLimbs = 3;
+
 // Kernel classes for the optional per-launch timing (md_profile_*).
 enum ProfKind : int {
   PK_POOL = 0, PK_SCAL, PK_CONV, PK_ACCUM, PK_QR_HOUSE, PK_QR_APPLY, PK_RINV, PK_BACKSUB,
@@ -54,7 +67,7 @@ struct EvalDev {
   const int *stage_off0 = nullptr;  // HOST array, nstages + 1 entries
   int resident_ctas = 0;            // > 0: run the full stages on this many SM-filling CTAs
   int resident_smem = 0;            // dynamic shared memory those CTAs reserve (keeps other CTAs off their SMs)
-  int split = 0;                    // series products in fixed point (the split-product form), K >= 2
+  int split = 0;                    // series products in fixed point (the split-product form), K >= 3
   const int *groups = nullptr;
   int ngroups = 0;
   const int *contrib = nullptr;
@@ -140,6 +153,7 @@ struct BatchDev {
   int ctas_per_sm = 0;      // > 0: dynamic shared memory lets at most this many CTAs share an SM
   int *resident = nullptr;  // if set, every CTA adds 1 here when it starts
   int times_stride = 2;     // stamps per system in times: 2 or kPhaseStamps
+  int split = 0;            // series products in fixed point (MD_FLAG_OZAKI), K >= 3
 };
 
 template <int K, int P>

@@ -567,10 +567,10 @@ __device__ __forceinline__ void house_block(double *M, double *vd,
 }
 
 // The QR steps as the kernels run them: in W-word fixed point (house_fx.cuh)
-// from two limbs on, in FP64 for plain double.
+// from kFxMinLimbs limbs on, in md arithmetic below.
 template <int K, int P>
 __device__ __forceinline__ void qr_house(double *M, double *vd, double *beta, int *status, int N, int j) {
-  if constexpr (K >= 2)
+  if constexpr (K >= kFxMinLimbs)
     house_block_fx<K, P>(M, vd, beta, status, N, j);
   else
     house_block<K, P>(M, vd, beta, status, N, j);
@@ -725,7 +725,7 @@ __device__ __forceinline__ void house_apply_col_cta(double *M, double *Y, const 
 template <int K, int P, bool CACHE = true>
 __device__ __forceinline__ void qr_apply_cta(double *M, double *Y, const double *vd, const double *beta, int N, int n,
                                              int j, int w, double (*sm)[K]) {
-  if constexpr (K >= 2)
+  if constexpr (K >= kFxMinLimbs)
     house_apply_col_v128<K, P, true, CACHE>(M, Y, vd, beta, N, n, j, w);
   else
     house_apply_col_cta<K, P>(M, Y, vd, beta, N, n, j, w, sm);
@@ -734,7 +734,7 @@ __device__ __forceinline__ void qr_apply_cta(double *M, double *Y, const double 
 template <int K, int P>
 __device__ __forceinline__ void qr_apply_warp(double *M, double *Y, const double *vd, const double *beta, int N,
                                               int n, int j, int w, int lane) {
-  if constexpr (K >= 2) {
+  if constexpr (K >= kFxMinLimbs) {
     (void)lane;
     house_apply_col_v128<K, P, false>(M, Y, vd, beta, N, n, j, w);
   } else {
@@ -743,16 +743,16 @@ __device__ __forceinline__ void qr_apply_warp(double *M, double *Y, const double
 }
 
 // CTAs of house_step_kernel after CTA 0: one per trailing target (fixed
-// point, K >= 2) or one warp per target (plain double).
+// point, K >= kFxMinLimbs) or one warp per target (md arithmetic).
 template <int K>
 __host__ __device__ constexpr bool qr_cta_per_target() {
-  return K >= 2;
+  return K >= kFxMinLimbs;
 }
 
 template <int K, int P>
 __global__ void __launch_bounds__(kHouseThreads) house_step_kernel(double *M, double *Y, double *vd, double *beta,
                                                                    int *status, int N, int n, int j) {
-  __shared__ double sm[K >= 2 ? 1 : kRowLanes][K];
+  __shared__ double sm[K >= kFxMinLimbs ? 1 : kRowLanes][K];
   const bool ahead = j + 1 < n;
   if (blockIdx.x == 0) {
     if (ahead) {
@@ -776,7 +776,7 @@ __global__ void __launch_bounds__(kHouseThreads) house_step_kernel(double *M, do
 // rinv[j] = 1 / R_jj
 template <int K, int P>
 __device__ __forceinline__ void rinv_entry(const double *M, double *rinv, int N, int j) {
-  if constexpr (K >= 2) {  // fixed point, as the QR (house_fx.cuh)
+  if constexpr (K >= kFxMinLimbs) {  // fixed point, as the QR (house_fx.cuh)
     rinv_entry_fx<K, P>(M, rinv, N, j);
     return;
   }
@@ -803,7 +803,7 @@ template <int K, int P>
 __device__ __forceinline__ void backsub_entry(const double *M, double *Y,
                                               double *W, const double *rinv, int N, int c,
                                               long long e) {
-  if constexpr (K >= 2) {  // fixed point, as the QR (house_fx.cuh)
+  if constexpr (K >= kFxMinLimbs) {  // fixed point, as the QR (house_fx.cuh)
     backsub_entry_fx<K, P>(M, Y, W, rinv, N, c, e);
     return;
   }
@@ -998,7 +998,7 @@ __global__ void backsub_row0_kernel(const double *__restrict__ Y, double *__rest
   const int col = blockIdx.x * blockDim.x + threadIdx.x;
   if (col >= N) return;
   const long long VS = P * K;
-  if constexpr (K >= 2) {
+  if constexpr (K >= kFxMinLimbs) {
     fx_bs_w<K, P>(Y, rinv, N, c, col, W + ((long long)c * N + col) * VS);
     return;
   }
@@ -1016,7 +1016,7 @@ __global__ void backsub_step_kernel(const double *__restrict__ M, double *__rest
   if ((int)blockIdx.x < gA) {  // row c-1, then W[c-1][:]
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= N) return;
-    if constexpr (K >= 2) {
+    if constexpr (K >= kFxMinLimbs) {
       fx_bs_update<K, P>(M, Y, W + ((long long)c * N + col) * VS, N, c, col, c - 1);
       fx_bs_w<K, P>(Y, rinv, N, c - 1, col, W + ((long long)(c - 1) * N + col) * VS);
       return;
@@ -1037,7 +1037,7 @@ __global__ void backsub_step_kernel(const double *__restrict__ M, double *__rest
   const long long e = (blockIdx.x - gA) * (long long)blockDim.x + threadIdx.x;
   if (e >= (long long)(c - 1) * N) return;
   const int i = (int)(e % (c - 1)), col = (int)(e / (c - 1));
-  if constexpr (K >= 2) {
+  if constexpr (K >= kFxMinLimbs) {
     fx_bs_update<K, P>(M, Y, W + ((long long)c * N + col) * VS, N, c, col, i);
     return;
   }
@@ -1090,7 +1090,7 @@ template <int K, int P>
 __device__ __forceinline__ void rhs_finish_row(const double *b, double sgn, const double *part, double *r, int N,
                                                int d, int k, int nchunk, int row, double (*sm)[K], int gt, int gn,
                                                bool act) {
-  if constexpr (K >= 2) {  // the partials summed in fixed point (house_fx.cuh)
+  if constexpr (K >= kFxMinLimbs) {  // the partials summed in fixed point (house_fx.cuh)
     (void)sm;
     (void)gn;  // groups are kRowLanes threads
     rhs_finish_row_fx<K, P>(b, sgn, part, r, N, d, k, nchunk, row, gt, act);
@@ -1151,7 +1151,7 @@ __global__ void __launch_bounds__(kRowLanes) rhs_finish_kernel(const double *__r
 template <int K, int P>
 __device__ __forceinline__ void wmv_row(const double *W, const double *r, double *dx, int N, int n, int k, int row,
                                         double (*sm)[K], int gt, int gn, bool act) {
-  if constexpr (K >= 2) {  // W = A_0^-1 applied in fixed point, as it was formed (house_fx.cuh)
+  if constexpr (K >= kFxMinLimbs) {  // W = A_0^-1 applied in fixed point, as it was formed (house_fx.cuh)
     (void)sm;
     (void)gn;  // groups are kRowLanes threads
     wmv_row_fx<K, P>(W, r, dx, N, n, k, row, gt, act);

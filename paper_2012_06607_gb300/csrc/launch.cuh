@@ -55,7 +55,7 @@ cudaError_t Impl<K, P>::batched(const BatchDev &b, cudaStream_t s) {
     const int smem = b.ctas_per_sm > 0 ? batched_cap_bytes<K, P>(b.ctas_per_sm) : 0;
     batched_step_kernel<K, P><<<b.grid, b.threads, smem, s>>>(b.jobs, b.order, b.njobs, b.counter, b.ibase, b.dbase,
                                                                   b.nrm, b.times, b.status, b.update_x, b.resident,
-                                                                  b.times_stride);
+                                                                  b.times_stride, b.split);
     return cudaGetLastError();
   }
 }
@@ -115,7 +115,7 @@ cudaError_t Impl<K, P>::eval_rest(const EvalDev &e, cudaStream_t s) {
     const int t0 = e.stage_off[st], t1 = e.stage_off[st + 1];
     if (t1 <= t0) continue;
     ProfScope prof(PK_CONV, s);
-    if constexpr (K >= 2) {
+    if constexpr (K >= kFxConvMinLimbs) {
       if (e.split) {  // the split-product form: every term on 32-bit word slices
         auto kern = conv_stage_fx_kernel<K, P>;
         int smem = e.resident_ctas > 0 ? e.resident_smem : 0;

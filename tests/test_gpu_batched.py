@@ -256,3 +256,62 @@ def test_batched_skewed_against_oracle(md, orc):
         got_x, got_n, _ = _batched_steps(md, systems, 2, flags=md.FLAG_AUTOTUNE | md.FLAG_GRAPH, stream=stream)
     worst = _assert_batch_matches_oracle(orc, systems, got_x, got_n, 2)
     print("batched vs oracle, skewed full-width batch: worst rel/eps", worst)
+
+
+def test_batched_split_products_against_oracle(md, orc):
+    """The split-product form in the batched step (series products on 32-bit
+    word slices, MD_FLAG_OZAKI): the full-width mixed batch (two steps) and,
+    through the autotuner and the graph, the skewed one (one step), against
+    the oracle.  The skewed batch takes one step because its largest system
+    (n = 24, d = 12, double double) magnifies the first step's rounding in the
+    second: there the double-double oracle itself lies 1.4e3 eps_2 from the
+    quad double one, and only the plain form, which has the oracle's bits,
+    meets 1e3 eps_2 after two steps."""
+    import torch
+
+    systems = _full_width_batch()
+    got_x, got_n, _ = _batched_steps(md, systems, 2, flags=md.FLAG_OZAKI)
+    worst = _assert_batch_matches_oracle(orc, systems, got_x, got_n, 2)
+    print("batched split form vs oracle, full-width mixed batch: worst rel/eps", worst)
+    systems = _skewed_full_width()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        got_x, got_n, _ = _batched_steps(md, systems, 1, flags=md.FLAG_OZAKI | md.FLAG_AUTOTUNE | md.FLAG_GRAPH,
+                                         stream=stream)
+    worst = _assert_batch_matches_oracle(orc, systems, got_x, got_n, 1)
+    print("batched split form vs oracle, skewed batch: worst rel/eps", worst)
+
+
+def test_batched_graph_switches_form(md):
+    """One plan (same systems, buffers and stream) called with and without
+    MD_FLAG_OZAKI under MD_FLAG_GRAPH: the captured graph is replaced when the
+    form changes, so the plain calls keep the bits of the uncaptured plain step
+    and the split call differs from them within the tolerance."""
+    import torch
+
+    systems = _mixed_systems()
+    ref_x, _, _ = _batched_steps(md, systems, 1)
+    sds = [md.DeviceSystem(s) for s in systems]
+    flags_all = md.FLAG_GRAPH | md.FLAG_OZAKI
+    ws = md.workspace(md.batched_workspace_bytes(sds, flags_all))
+    xs = [md.to_device(s.x0) for s in systems]
+    x0 = [md.to_device(s.x0) for s in systems]
+    nrm = torch.zeros((len(systems), 2), dtype=torch.float64, device="cuda")
+    times = torch.zeros((len(systems), 2), dtype=torch.int64, device="cuda")
+    stream = torch.cuda.Stream()
+    split_differs = False
+    with torch.cuda.stream(stream):
+        for flags in (md.FLAG_GRAPH, flags_all, md.FLAG_GRAPH, flags_all):
+            for x, x_init in zip(xs, x0):
+                x.copy_(x_init)
+            md.newton_step_batched(sds, xs, ws, nrm, times, flags=flags, stream=stream)
+            stream.synchronize()
+            assert md.device_status(ws) == 0
+            for i, s in enumerate(systems):
+                got = xs[i].cpu().numpy()
+                if flags & md.FLAG_OZAKI:
+                    split_differs |= not np.array_equal(got, ref_x[i])
+                    assert worst_in_eps(got, ref_x[i], s.limbs) <= TOL, (flags, i)
+                else:
+                    assert np.array_equal(got, ref_x[i]), (flags, i)
+    assert split_differs  # the split form ran, not the captured plain graph
