@@ -755,7 +755,9 @@ def measure_batched(args, count, rank, world, local, dist, with_loop: bool, err_
     systems = [all_systems[i] for i in mine]
     sds = [md.DeviceSystem(s) for s in systems]
     flags = md.FLAG_AUTOTUNE | md.FLAG_GRAPH
-    ws = md.workspace(md.batched_workspace_bytes(sds, flags))
+    # room for both forms (the split-product form adds fixed-point copies)
+    ws = md.workspace(max(md.batched_workspace_bytes(sds, flags),
+                          md.batched_workspace_bytes(sds, flags | md.FLAG_OZAKI)))
     xs = [md.to_device(s.x0) for s in systems]
     nrm = torch.zeros((len(systems), 2), dtype=torch.float64, device="cuda")
     times = torch.zeros((len(systems), 2), dtype=torch.int64, device="cuda")
@@ -797,11 +799,11 @@ def measure_batched(args, count, rank, world, local, dist, with_loop: bool, err_
         e1.record(stream)
         e1.synchronize()
         serial_ms = e0.elapsed_time(e1)
-        # the split-product form (series products on 32-bit word slices) on the
-        # same plan and tuning, replayed from its own graph; its first step
-        # from x0 for the error sample
+        # the split-product form (series products on 32-bit word slices), its
+        # own plan, tuning and graph on the same buffers; its first step from
+        # x0 for the error sample
         oflags = flags | md.FLAG_OZAKI
-        for _ in range(2):
+        for _ in range(max(args.warmup, 2)):
             md.newton_step_batched(sds, xs, ws, nrm, None, flags=oflags, stream=stream)
         oz_ms = []
         for _ in range(args.steps):

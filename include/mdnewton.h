@@ -267,12 +267,15 @@ md_status md_newton_series_step(const md_system *sys, double *x, double *dx_norm
  *   times:   DEVICE unsigned long long[nsys][2] or NULL: global-timer
  *            nanoseconds at the start and end of each system's step
  *            ([nsys][MD_PHASE_STAMPS] with MD_FLAG_PHASE_TIMES)
- *   ws:      DEVICE workspace of md_batched_workspace_bytes() bytes; the status
- *            word covers the whole batch
+ *   ws:      DEVICE workspace of md_batched_workspace_bytes(nsys, sys, flags)
+ *            bytes (MD_FLAG_OZAKI adds fixed-point copies of the series pool,
+ *            A and dx for systems of three or more limbs); the status word
+ *            covers the whole batch
  *   flags:   MD_FLAG_AUTOTUNE, MD_FLAG_GRAPH, MD_FLAG_SERIAL, MD_FLAG_PHASE_TIMES,
  *            MD_FLAG_CHECK, MD_FLAG_OZAKI (series products and update sums on
  *            32-bit word slices; the bit-equality with md_newton_series_step
- *            holds for the plain form)
+ *            holds for the plain form).  The two forms keep separate plans,
+ *            tunings and graphs.
  */
 size_t md_batched_workspace_bytes(int nsys, const md_system *sys, int flags);
 md_status md_newton_series_step_batched(int nsys, const md_system *sys, double *const *x, double *dx_norm,

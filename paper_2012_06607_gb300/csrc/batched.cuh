@@ -100,8 +100,20 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
     double *scal = dbase + J.scal;
     double *f = dbase + J.f;
     double *A = dbase + J.A;
+    // the split-product form (uniform over the launch): products and update
+    // sums on 32-bit word slices, operands from packed fixed-point copies
+    const bool fx = K >= kFxConvMinLimbs && split;
+    uint32_t *fxpool = reinterpret_cast<uint32_t *>(dbase + J.fxpool);
+    uint32_t *fxA = reinterpret_cast<uint32_t *>(dbase + J.fxA);
+    uint32_t *fxdx = reinterpret_cast<uint32_t *>(dbase + J.fxdx);
+    constexpr int PW = packed_words(fxp::words_for(K));
     // ---- evaluate and differentiate
-    for (long long e = tid; e < (long long)n * (d + 1); e += NT) pool_load_entry<K, P>(J.x, pool, n, d, e);
+    for (long long e = tid; e < (long long)n * (d + 1); e += NT) {
+      if (fx)
+        pool_load_entry_fx<K, P>(J.x, pool, fxpool, n, d, e);
+      else
+        pool_load_entry<K, P>(J.x, pool, n, d, e);
+    }
     for (int i = tid; i < J.nscal; i += NT) prep_scal_entry<K, P>(ibase + J.scal_src, J.coef, J.nmono, scal, i);
     const long long Awords = (long long)P * K * (d + 1) * n * n;
     for (long long e = tid; e < Awords; e += NT) A[e] = 0.0;
@@ -119,8 +131,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
         // one call for both kinds of item: two inlined copies would run one
         // after the other in a warp that holds both
         const bool pair = 2 * p < d;
-        if (K >= kFxConvMinLimbs && split)  // the split-product form: 32-bit word slices (uniform over the launch)
-          conv_pair_fx<K, P>(pool, d, out, a, b, p, pair ? out : -1, pair ? a : -1, pair ? b : -1);
+        if (fx)
+          conv_pair_fx<K, P, true>(pool, d, out, a, b, p, pair ? out : -1, pair ? a : -1, pair ? b : -1, fxpool);
         else
           conv_pair<K, P, false>(pool, d, out, a, b, p, pair ? out : -1, pair ? a : -1, pair ? b : -1);
       }
@@ -132,6 +144,11 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
     for (long long e = tid; e < (long long)J.ngroups * (d + 1); e += NT)
       accum_entry<K, P>(groups, contrib, pool, scal, J.cst, f, A, n, n, d, (int)(e / (d + 1)), (int)(e % (d + 1)));
     __syncthreads();
+    if (fx) {  // A's values converted once for the update sums of every degree
+      const long long cnt = (long long)(d + 1) * n * n;
+      for (long long e = tid; e < cnt; e += NT) fx_pack_value<K, P>(A + e, cnt, fxA + e * P * PW);
+      __syncthreads();
+    }
     phase_stamp(phases, times, (long long)tstride * job + 3);
     // ---- solve A(t) dx(t) = -f(t)
     double *M = dbase + J.M, *Y = dbase + J.Y, *W = dbase + J.W;
@@ -168,8 +185,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
       int C, nchunk;
       rhs_chunking(n, n, k, C, nchunk);
       for (long long e = tid; e < (long long)n * nchunk; e += NT) {
-        if (K >= kFxConvMinLimbs && split)  // the split-product form: 32-bit word slices
-          rhs_partial_item_fx<K, P>(A, dxw, part, n, n, d, k, C, nchunk, e);
+        if (fx)
+          rhs_partial_item_fx<K, P>(fxA, fxdx, part, n, n, k, C, nchunk, e);
         else
           rhs_partial_item<K, P>(A, dxw, part, n, n, d, k, C, nchunk, e);
       }
@@ -183,6 +200,11 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
       for (int row0 = 0; row0 < n; row0 += G) {
         const bool act = grp < G && row0 + grp < n;
         wmv_row<K, P>(W, r, dxw, n, n, k, act ? row0 + grp : 0, s_rows[act ? grp : 0], gt, kRowLanes, act);
+      }
+      if (fx && k < d) {  // dx_k for the update sums of the later degrees (wmv_row ends with a barrier)
+        for (int e = tid; e < n; e += NT)
+          fx_pack_value<K, P>(dxw + ((long long)k * n + e) * (P * K), 1, fxdx + ((long long)k * n + e) * P * PW);
+        __syncthreads();
       }
     }
     phase_stamp(phases, times, (long long)tstride * job + 8);

@@ -147,7 +147,7 @@ struct Plan {
   std::vector<int> op_stage_off;  // nstages + 1 product offsets
   // workspace offsets (bytes)
   size_t off_pool = 0, off_scal = 0, off_tasks = 0, off_scalsrc = 0, off_groups = 0, off_contrib = 0, off_tasks0 = 0;
-  size_t off_f = 0, off_A = 0, off_prod = 0, off_solve = 0, total = 0;
+  size_t off_f = 0, off_A = 0, off_prod = 0, off_fxpool = 0, fxpool_bytes = 0, off_solve = 0, total = 0;
   SolveLayout sl{};
   uint64_t checksum = 0;
   // the planned structure itself, compared with the caller's on every cache
@@ -412,6 +412,11 @@ md_status build_plan(const md_system *s, Plan &p, int flags = 0) {
   p.off_f = o; o = align256(o + (size_t)N * (d + 1) * VS);
   p.off_A = o; o = align256(o + (size_t)(d + 1) * N * n * VS);
   p.off_prod = o; o = align256(o + (p.contrib.size() / 4) * (size_t)(d + 1) * VS);
+  // the split-product form's fixed-point copy of the pool (K >= kFxConvMinLimbs)
+  p.fxpool_bytes = ((flags & MD_FLAG_OZAKI) && p.K >= mdk::kFxConvMinLimbs)
+                       ? sizeof(unsigned) * (size_t)p.nslots * (d + 1) * p.P * mdk::fx_packed_words_for(p.K)
+                       : 0;
+  p.off_fxpool = o; o = align256(o + p.fxpool_bytes);
   p.off_solve = o;
   p.sl = solve_layout(p.K, p.P, N, n, d, o, flags);
   p.total = o + p.sl.bytes;
@@ -483,6 +488,7 @@ md_status check_plan(const Plan &p) {
       {p.off_f, (size_t)N * (d + 1) * VS},
       {p.off_A, (size_t)(d + 1) * N * n * VS},
       {p.off_prod, (size_t)ncon * (d + 1) * VS},
+      {p.off_fxpool, p.fxpool_bytes},
       {p.off_solve, p.sl.bytes}};
   size_t prev_end = 256;  // the status header
   for (const auto &r : ends) {
@@ -715,8 +721,7 @@ struct BatchPlan {
   int exec_tstride = 2;
   UseEvents uses;         // after each step enqueued on a stream
   bool captured = false;  // enqueued into a caller's capture: never dropped
-  int oz = 0;             // this call's MD_FLAG_OZAKI: series products in fixed point
-  int exec_oz = 0;        // the form the graph was captured with
+  int oz = 0;             // laid out for MD_FLAG_OZAKI (a plan of its own per form)
   ~BatchPlan() {
     // a step in flight may still read the pinned image, directly or from the
     // graph: wait for the steps enqueued with this plan, not the device
@@ -753,7 +758,7 @@ double job_cost(const Plan &p) {
 }
 
 md_status batch_prepare(int nsys, const md_system *sys, double *const *x, std::shared_ptr<BatchPlan> &out,
-                        bool need_image, bool may_sync, bool check = false) {
+                        bool need_image, bool may_sync, bool check = false, int oz = 0) {
   if (nsys < 1 || !sys) return MD_ERR_ARG;
   std::vector<Plan *> plans(nsys);
   std::vector<std::shared_ptr<PlanEntry>> holds(nsys);
@@ -784,6 +789,7 @@ md_status batch_prepare(int nsys, const md_system *sys, double *const *x, std::s
     const void *ptrs[3] = {sys[i].coef, sys[i].cst, x ? (const void *)x[i] : nullptr};
     key = fnv(key, ptrs, sizeof(ptrs));
   }
+  key = fnv(key, &oz, sizeof(oz));  // each form has its own layout (and tuning and graph)
   {
     std::lock_guard<std::mutex> lk(g_mu);
     std::shared_ptr<BatchPlan> hit = g_batch.find(key);
@@ -795,6 +801,7 @@ md_status batch_prepare(int nsys, const md_system *sys, double *const *x, std::s
   }
   std::shared_ptr<BatchPlan> bp = std::make_shared<BatchPlan>();
   bp->nsys = nsys;
+  bp->oz = oz;
   bp->jobs.resize(nsys);
   // classes by (K, P), jobs ordered by decreasing cost
   std::map<int, int> cls_of;
@@ -870,6 +877,13 @@ md_status batch_prepare(int nsys, const md_system *sys, double *const *x, std::s
     J.r = nd; nd += (size_t)D1 * n * VS;
     J.dxw = nd; nd += (size_t)D1 * n * VS;
     J.part = nd; nd += (size_t)n * p.sl.maxchunk * VS;
+    if (oz && p.K >= mdk::kFxConvMinLimbs) {  // packed fixed-point copies, in doubles (PW is a multiple of 4)
+      const size_t FV = (size_t)p.P * mdk::fx_packed_words_for(p.K) / 2;
+      nd = a32(nd);
+      J.fxpool = nd; nd += (size_t)p.nslots * D1 * FV;
+      J.fxA = nd; nd += (size_t)D1 * n * n * FV;
+      J.fxdx = nd; nd += (size_t)D1 * n * FV;
+    }
     J.coef = sys[i].coef;
     J.cst = sys[i].cst;
     J.x = x ? x[i] : nullptr;
@@ -1146,6 +1160,7 @@ EvalDev make_eval(const Plan &p, const md_system *s, const double *x, double *f,
   e.prod = reinterpret_cast<double *>(base + p.off_prod);
   e.tasks0 = reinterpret_cast<const int *>(base + p.off_tasks0);
   e.stage_off0 = p.stage_off0.data();
+  e.fxpool = p.fxpool_bytes ? reinterpret_cast<unsigned *>(base + p.off_fxpool) : nullptr;
   return e;
 }
 
@@ -1418,7 +1433,9 @@ md_status md_newton_series_step(const md_system *sys, double *x, double *dx_norm
   double *f = reinterpret_cast<double *>(base + p->off_f);
   double *A = reinterpret_cast<double *>(base + p->off_A);
   EvalDev e = make_eval(*p, sys, x, f, A, base);
-  e.split = (flags & MD_FLAG_OZAKI) ? 1 : 0;  // series products as split products too
+  // series products as split products too (from kFxConvMinLimbs limbs on,
+  // where the plan holds the fixed-point pool)
+  e.split = ((flags & MD_FLAG_OZAKI) && e.fxpool) ? 1 : 0;
   SolveDev v = make_solve(p->sl, p->N, p->n, p->d, base);
   v.A = A;
   v.b = f;
@@ -1546,9 +1563,8 @@ md_status md_batched_job_costs(int nsys, const md_system *sys, double *cost) {
 }
 
 size_t md_batched_workspace_bytes(int nsys, const md_system *sys, int flags) {
-  (void)flags;
   std::shared_ptr<BatchPlan> bp;
-  if (batch_prepare(nsys, sys, nullptr, bp, false, false) != MD_OK) return 0;
+  if (batch_prepare(nsys, sys, nullptr, bp, false, false, false, (flags & MD_FLAG_OZAKI) ? 1 : 0) != MD_OK) return 0;
   return bp->total;
 }
 
@@ -1566,10 +1582,10 @@ md_status md_newton_series_step_batched(int nsys, const md_system *sys, double *
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return MD_ERR_CUDA;
   std::shared_ptr<BatchPlan> bp;
-  md_status st = batch_prepare(nsys, sys, x, bp, true, cap == cudaStreamCaptureStatusNone, flags & MD_FLAG_CHECK);
+  md_status st = batch_prepare(nsys, sys, x, bp, true, cap == cudaStreamCaptureStatusNone, flags & MD_FLAG_CHECK,
+                               (flags & MD_FLAG_OZAKI) ? 1 : 0);
   if (st != MD_OK) return st;
   if (bp->total > ws_bytes) return MD_ERR_WORKSPACE;
-  bp->oz = (flags & MD_FLAG_OZAKI) ? 1 : 0;
   char *base = static_cast<char *>(ws);
   const int sms = device_sms();
   const bool split = !(flags & MD_FLAG_SERIAL);
@@ -1583,7 +1599,7 @@ md_status md_newton_series_step_batched(int nsys, const md_system *sys, double *
   }
   if ((flags & MD_FLAG_GRAPH) && s != nullptr) {
     if (!bp->exec || bp->exec_ws != ws || bp->exec_nrm != dx_norm || bp->exec_times != times || bp->exec_stream != s ||
-        bp->exec_split != split || bp->exec_tstride != tstride || bp->exec_oz != bp->oz) {
+        bp->exec_split != split || bp->exec_tstride != tstride) {
       if (bp->exec) cudaGraphExecDestroy(bp->exec);
       bp->exec = nullptr;
       cudaGraph_t g = nullptr;
@@ -1602,7 +1618,6 @@ md_status md_newton_series_step_batched(int nsys, const md_system *sys, double *
       bp->exec_stream = s;
       bp->exec_split = split;
       bp->exec_tstride = tstride;
-      bp->exec_oz = bp->oz;
     }
     if (cudaGraphLaunch(bp->exec, s) != cudaSuccess) return MD_ERR_CUDA;
   } else if (batch_enqueue(*bp, base, dx_norm, times, s, sms, split, tstride) != cudaSuccess) {

@@ -17,17 +17,116 @@
 
 namespace mdk {
 
-// Two output coefficients of series products as conv_pair (same task layout
-// and term order), in fixed point.  The W-word operations are called out of
-// line (inlined, they needed ~156 registers a thread and the kernel ran 25%
-// slower at 384 threads than called at 512, despite the call stack's traffic).
+// The fixed-point copy of the series pool: every value of the md pool
+// [series][d+1][P][K] as a W-word number, stored in packed_words(W) 32-bit
+// words (the mantissa words, then the exponent shifted left by one with the
+// sign in bit 0, zeros to a multiple of four words), so that a value moves in
+// 16-byte loads.  The products convert each operand once, where it is made,
+// instead of at every term that reads it (a K-limb conversion costs about as
+// much as two W-word products).
+__host__ __device__ constexpr int packed_words(int W) { return (W + 4) & ~3; }
+static_assert(packed_words(fxp::words_for(3)) == fx_packed_words_for(3) &&
+                  packed_words(fxp::words_for(10)) == fx_packed_words_for(10),
+              "the host's workspace layout uses the same packed size");
+
+template <int W>
+__device__ __forceinline__ void fx_st_packed(uint32_t *dst, const fxp::bf<W> &a) {
+  constexpr int PW = packed_words(W);
+  uint32_t w[PW];
+#pragma unroll
+  for (int i = 0; i < PW; ++i) w[i] = i < W ? a.m[i] : 0u;
+  w[W] = ((uint32_t)a.e << 1) | (uint32_t)(a.neg & 1);
+#pragma unroll
+  for (int q = 0; q < PW / 4; ++q)
+    reinterpret_cast<uint4 *>(dst)[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+}
+
+template <int W>
+__device__ __forceinline__ fxp::bf<W> fx_ld_packed(const uint32_t *src) {
+  constexpr int PW = packed_words(W);
+  uint32_t w[PW];
+#pragma unroll
+  for (int q = 0; q < PW / 4; ++q) {
+    const uint4 v = reinterpret_cast<const uint4 *>(src)[q];
+    w[4 * q] = v.x;
+    w[4 * q + 1] = v.y;
+    w[4 * q + 2] = v.z;
+    w[4 * q + 3] = v.w;
+  }
+  fxp::bf<W> a;
+#pragma unroll
+  for (int i = 0; i < W; ++i) a.m[i] = w[i];
+  a.e = (int)w[W] >> 1;
+  a.neg = (int)(w[W] & 1u);
+  return a;
+}
+
+// A value of P planes rounded to K limbs, stored in the md pool and, as the
+// exact value of those limbs, in the fixed-point pool.
+template <int W, int K, int P>
+__device__ __forceinline__ void fx_st_both(double *dst, uint32_t *pdst, const fxp::bf<W> (&v)[P]) {
+  constexpr int PW = packed_words(W);
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    double z[K];
+    fxp::to_md<K, W>(v[p], z);
+#pragma unroll
+    for (int l = 0; l < K; ++l) dst[p * K + l] = z[l];
+    fx_st_packed<W>(pdst + p * PW, fxp::from_md<W, K>(z));
+  }
+}
+
+// One md value of P planes (limb l of plane p at src[(p K + l) stride]) into
+// the packed fixed-point form at dst (P packed values).
 template <int K, int P>
+__device__ __forceinline__ void fx_pack_value(const double *src, long long stride, uint32_t *dst) {
+  constexpr int W = fxp::words_for(K), PW = packed_words(W);
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    double v[K];
+#pragma unroll
+    for (int l = 0; l < K; ++l) v[l] = src[(long long)(p * K + l) * stride];
+    fx_st_packed<W>(dst + p * PW, fxp::from_md<W, K>(v));
+  }
+}
+
+// The inputs' series into both pools (pool_load_entry, and each value
+// converted once for the fixed-point products).
+template <int K, int P>
+__device__ __forceinline__ void pool_load_entry_fx(const double *x, double *pool, uint32_t *fxpool, int n, int d,
+                                                   long long e) {
+  constexpr int PW = packed_words(fxp::words_for(K));
+  const long long stride = (long long)n * (d + 1);
+  fx_pack_value<K, P>(x + e, stride, fxpool + e * P * PW);
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+#pragma unroll
+    for (int l = 0; l < K; ++l) pool[e * (P * K) + p * K + l] = x[e + (long long)(p * K + l) * stride];
+}
+
+template <int K, int P>
+__global__ void pool_load_x_fx_kernel(const double *__restrict__ x, double *__restrict__ pool,
+                                      uint32_t *__restrict__ fxpool, int n, int d) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)n * (d + 1)) return;
+  pool_load_entry_fx<K, P>(x, pool, fxpool, n, d, e);
+}
+
+// Two output coefficients of series products as conv_pair (same task layout
+// and term order), in fixed point.  PACKED: the operands come from the
+// fixed-point pool and the outputs go to both pools; otherwise every operand
+// is converted from the md pool at each term.  The W-word operations are
+// called out of line (inlined, they needed ~156 registers a thread and the
+// kernel ran 25% slower at 384 threads than called at 512, despite the call
+// stack's traffic).
+template <int K, int P, bool PACKED = false>
 __device__ __forceinline__ void conv_pair_fx(double *pool, int d, int outA, int xA, int yA, int kA, int outB, int xB,
-                                             int yB) {
+                                             int yB, uint32_t *fxpool = nullptr) {
   using namespace fxp;
-  constexpr int W = words_for(K);
+  constexpr int W = words_for(K), PW = packed_words(W);
   const int kB = d - kA;
   const long long VS = P * K, SS = (long long)(d + 1) * VS;
+  const long long FS = (long long)(d + 1) * P * PW, FV = (long long)P * PW;  // fixed-point pool strides
   const int total = (outB >= 0) ? (d + 2) : (kA + 1);
   bf<W> acc[P];
 #pragma unroll
@@ -35,11 +134,18 @@ __device__ __forceinline__ void conv_pair_fx(double *pool, int d, int outA, int 
   for (int it = 0; it < total; ++it) {
     const bool first = it <= kA;
     const int i = first ? it : it - kA - 1;
-    const double *xp = pool + (first ? xA : xB) * SS + i * VS;
-    const double *yp = pool + (first ? yA : yB) * SS + ((first ? kA : kB) - i) * VS;
+    const int sx = first ? xA : xB, sy = first ? yA : yB, iy = (first ? kA : kB) - i;
     bf<W> a[P], b[P], t[P];
-    fx_ld_val<W, K, P>(xp, a);
-    fx_ld_val<W, K, P>(yp, b);
+    if constexpr (PACKED) {
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        a[p] = fx_ld_packed<W>(fxpool + sx * FS + i * FV + p * PW);
+        b[p] = fx_ld_packed<W>(fxpool + sy * FS + iy * FV + p * PW);
+      }
+    } else {
+      fx_ld_val<W, K, P>(pool + sx * SS + i * VS, a);
+      fx_ld_val<W, K, P>(pool + sy * SS + iy * VS, b);
+    }
     fx_cmul<W, P>(a, b, t);
     if (it == kA + 1) {
 #pragma unroll
@@ -47,39 +153,48 @@ __device__ __forceinline__ void conv_pair_fx(double *pool, int d, int outA, int 
     }
 #pragma unroll
     for (int p = 0; p < P; ++p) acc[p] = add<W>(acc[p], t[p]);
-    if (it == kA) fx_st_val<W, K, P>(pool + outA * SS + kA * VS, acc);
+    if (it == kA) {
+      if constexpr (PACKED)
+        fx_st_both<W, K, P>(pool + outA * SS + kA * VS, fxpool + outA * FS + kA * FV, acc);
+      else
+        fx_st_val<W, K, P>(pool + outA * SS + kA * VS, acc);
+    }
   }
-  if (outB >= 0) fx_st_val<W, K, P>(pool + outB * SS + kB * VS, acc);
+  if (outB >= 0) {
+    if constexpr (PACKED)
+      fx_st_both<W, K, P>(pool + outB * SS + kB * VS, fxpool + outB * FS + kB * FV, acc);
+    else
+      fx_st_val<W, K, P>(pool + outB * SS + kB * VS, acc);
+  }
 }
 
 // One chunk of a row of the block Toeplitz update sum_{j<k} A_{k-j} dx_j
-// (Section 3.2; rhs_partial_item's terms in its order) in fixed point: every
+// (Section 3.2; rhs_partial_item's terms in its order) in fixed point: the
+// operands from packed fixed-point copies of A (fxA: the values of A in A's
+// order [d+1][n][N], P packed values each) and of dx (fxdx: [d+1][n]), every
 // term an exact product of word slices, the chunk's sum rounded to K limbs
-// once.  A: [P][K][d+1][n][N] (column-major blocks), dx: [d+1][n] values of
-// P*K doubles, part: [N][nchunk] values.
+// once into part ([N][nchunk] values).
 template <int K, int P>
-__device__ __forceinline__ void rhs_partial_item_fx(const double *A, const double *dx, double *part, int N, int n,
-                                                    int d, int k, int C, int nchunk, long long e) {
+__device__ __forceinline__ void rhs_partial_item_fx(const uint32_t *fxA, const uint32_t *fxdx, double *part, int N,
+                                                    int n, int k, int C, int nchunk, long long e) {
   using namespace fxp;
-  constexpr int W = words_for(K);
+  constexpr int W = words_for(K), PW = packed_words(W);
   const int row = (int)(e % N), chunk = (int)(e / N);
-  const long long nn = (long long)N * n, VS = P * K, stride = (long long)(d + 1) * nn;
+  const long long nn = (long long)N * n, VS = P * K;
   const int t0 = chunk * C, t1 = min(t0 + C, k * n);
   bf<W> acc[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) acc[p] = zero<W>();
   for (int t = t0; t < t1; ++t) {
     const int j = t / n, col = t % n;
-    const double *ap = A + (long long)(k - j) * nn + (long long)col * N + row;
+    const uint32_t *ap = fxA + ((long long)(k - j) * nn + (long long)col * N + row) * P * PW;
+    const uint32_t *xp = fxdx + ((long long)j * n + col) * P * PW;
     bf<W> a[P], x[P], prod[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-      double v[K];
-#pragma unroll
-      for (int l = 0; l < K; ++l) v[l] = ap[(long long)(p * K + l) * stride];
-      a[p] = from_md<W, K>(v);
+      a[p] = fx_ld_packed<W>(ap + p * PW);
+      x[p] = fx_ld_packed<W>(xp + p * PW);
     }
-    fx_ld_val<W, K, P>(dx + ((long long)j * n + col) * VS, x);
     fx_cmul<W, P>(a, x, prod);
 #pragma unroll
     for (int p = 0; p < P; ++p) acc[p] = add<W>(acc[p], prod[p]);
@@ -96,11 +211,11 @@ __host__ __device__ constexpr int conv_fx_threads() {
 
 template <int K, int P>
 __global__ void __launch_bounds__(conv_fx_threads<K>(), 1)
-    conv_stage_fx_kernel(const int *__restrict__ tasks, int ntask, double *pool, int d) {
+    conv_stage_fx_kernel(const int *__restrict__ tasks, int ntask, double *pool, uint32_t *fxpool, int d) {
   for (int t = threadIdx.x * gridDim.x + blockIdx.x; t < ntask; t += gridDim.x * blockDim.x) {
     const int4 t0 = __ldg(reinterpret_cast<const int4 *>(tasks) + 2 * t);
     const int4 t1 = __ldg(reinterpret_cast<const int4 *>(tasks) + 2 * t + 1);
-    conv_pair_fx<K, P>(pool, d, t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z);
+    conv_pair_fx<K, P, true>(pool, d, t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, fxpool);
   }
 }
 

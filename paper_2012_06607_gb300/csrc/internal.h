@@ -26,6 +26,10 @@ constexpr int kHouseThreads = 128;
 constexpr int kFxMinLimbs = 3;
 constexpr int kFxConvMinLimbs = 3;
 
+// 32-bit words of one value of the split-product form's fixed-point pool:
+// packed_words(words_for(K)) of conv_fx.cuh, for the host's workspace layout.
+__host__ __device__ constexpr int fx_packed_words_for(int K) { return ((53 * K + 31) / 32 + 2 + 4) & ~3; }
+
 // Kernel classes for the optional per-launch timing (md_profile_*).
 enum ProfKind : int {
   PK_POOL = 0, PK_SCAL, PK_CONV, PK_ACCUM, PK_QR_HOUSE, PK_QR_APPLY, PK_RINV, PK_BACKSUB,
@@ -68,6 +72,7 @@ struct EvalDev {
   int resident_ctas = 0;            // > 0: run the full stages on this many SM-filling CTAs
   int resident_smem = 0;            // dynamic shared memory those CTAs reserve (keeps other CTAs off their SMs)
   int split = 0;                    // series products in fixed point (the split-product form), K >= 3
+  unsigned *fxpool = nullptr;       // with split: the pool's values in packed fixed point (conv_fx.cuh)
   const int *groups = nullptr;
   int ngroups = 0;
   const int *contrib = nullptr;
@@ -132,6 +137,9 @@ struct BatchJob {
   long long groups;     // ibase offset: 4 ints per group (16-byte aligned)
   long long contrib;    // ibase offset: 4 ints per contribution (16-byte aligned)
   long long pool, scal, f, A, M, Y, W, vd, beta, rinv, r, dxw, part;  // dbase offsets (doubles)
+  // the split-product form's packed fixed-point copies of the pool, A and dx
+  // (dbase offsets in doubles, 16-byte aligned; laid out only for that form)
+  long long fxpool, fxA, fxdx;
   const double *coef;
   const double *cst;
   double *x;

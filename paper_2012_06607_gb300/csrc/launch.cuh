@@ -82,7 +82,15 @@ cudaError_t Impl<K, P>::eval0(const EvalDev &e, cudaStream_t s) {
   const long long nx = (long long)n * (d + 1);
   {
     ProfScope prof(PK_POOL, s);
-    pool_load_x_kernel<K, P><<<blocks_for(nx, 128), 128, 0, s>>>(e.x, e.pool, n, d);
+    if constexpr (K >= kFxConvMinLimbs) {
+      if (e.split) {  // both pools: the fixed-point products read the converted copy
+        pool_load_x_fx_kernel<K, P><<<blocks_for(nx, 128), 128, 0, s>>>(e.x, e.pool, e.fxpool, n, d);
+      } else {
+        pool_load_x_kernel<K, P><<<blocks_for(nx, 128), 128, 0, s>>>(e.x, e.pool, n, d);
+      }
+    } else {
+      pool_load_x_kernel<K, P><<<blocks_for(nx, 128), 128, 0, s>>>(e.x, e.pool, n, d);
+    }
   }
   if (e.nscal > 0) {
     ProfScope prof(PK_SCAL, s);
@@ -125,7 +133,7 @@ cudaError_t Impl<K, P>::eval_rest(const EvalDev &e, cudaStream_t s) {
         }
         constexpr int T = conv_fx_threads<K>();
         const unsigned grid = e.resident_ctas > 0 ? (unsigned)e.resident_ctas : blocks_for(t1 - t0, T);
-        kern<<<grid, T, smem, s>>>(e.tasks + 8LL * t0, t1 - t0, e.pool, d);
+        kern<<<grid, T, smem, s>>>(e.tasks + 8LL * t0, t1 - t0, e.pool, e.fxpool, d);
         continue;
       }
     }

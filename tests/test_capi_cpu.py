@@ -299,3 +299,31 @@ def test_plan_check_fuzz_host_only():
     c.n = 0  # invalid
     assert md.lib().md_plan_check(ctypes.byref(c), 0) == 1  # MD_ERR_ARG
     assert md.lib().md_status_string(9) == b"bounds check failed"
+
+
+def test_split_form_workspace_host_only():
+    """MD_FLAG_OZAKI lays out fixed-point copies (the series pool; for the
+    batched form also A and dx) only from three limbs on: the split-form
+    workspace grows at K = 4 by at least the pool copy, and the batched
+    double-double workspace is the same in both forms."""
+    import paper_2012_06607_gb300 as md
+
+    keep = []
+    s2 = mdgen.small_system_fast(np.random.default_rng(3), 6, 5, 2, monos=6)
+    s4 = s2.with_limbs(4)
+    lib = md.lib()
+    for s, grows in ((s2, False), (s4, True)):
+        arr = (md.md_system * 1)()
+        arr[0] = md._host_md_system(s, keep)
+        plain = lib.md_batched_workspace_bytes(1, arr, 0)
+        split = lib.md_batched_workspace_bytes(1, arr, md.FLAG_OZAKI)
+        assert plain > 0 and split > 0
+        if grows:
+            n, d = s.n, s.degree
+            words = ((53 * 4 + 31) // 32 + 2 + 4) & ~3  # packed 32-bit words per plane value
+            copy_A = 4 * 2 * words * (d + 1) * n * n
+            assert split >= plain + copy_A
+        else:
+            assert split == plain
+    c4 = md._host_md_system(s4, keep)
+    assert lib.md_workspace_bytes(ctypes.byref(c4), md.FLAG_OZAKI) > lib.md_workspace_bytes(ctypes.byref(c4), 0)

@@ -283,10 +283,10 @@ def test_batched_split_products_against_oracle(md, orc):
 
 
 def test_batched_graph_switches_form(md):
-    """One plan (same systems, buffers and stream) called with and without
-    MD_FLAG_OZAKI under MD_FLAG_GRAPH: the captured graph is replaced when the
-    form changes, so the plain calls keep the bits of the uncaptured plain step
-    and the split call differs from them within the tolerance."""
+    """The same systems, buffers and stream called with and without
+    MD_FLAG_OZAKI under MD_FLAG_GRAPH, alternating: each form replays its own
+    plan and graph, so the plain calls keep the bits of the uncaptured plain
+    step and the split calls differ from them within the tolerance."""
     import torch
 
     systems = _mixed_systems()
