@@ -283,6 +283,18 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------- main leg
+def tune_factor_sms(md, sysd, x, ws, nrm, flags, dev):
+    """MD_FLAG_AUTOTUNE of the single step: the calls that time the candidate
+    SM counts of the factorisation (untimed here, before the warm-up); from
+    the call after them the plan runs the fastest count."""
+    import torch
+
+    if flags & md.FLAG_AUTOTUNE:
+        for _ in range(15):
+            md.newton_step(sysd, x, ws, nrm, flags=flags)
+            torch.cuda.synchronize(dev)
+
+
 def run_product(args):
     import numpy as np
     import torch
@@ -299,6 +311,8 @@ def run_product(args):
     P, K, n, d = s.planes, s.limbs, s.n, s.degree
     sysd = md.DeviceSystem(s, device=dev)
     flags = (md.FLAG_OZAKI if args.update == "split" else 0) | (md.FLAG_LU if args.factor == "lu" else 0)
+    if not args.no_autotune:
+        flags |= md.FLAG_AUTOTUNE
     wsb = sysd.workspace_bytes(flags)
     ws = md.workspace(wsb, device=dev)
     x = md.to_device(s.x0, dev)
@@ -306,6 +320,7 @@ def run_product(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    tune_factor_sms(md, sysd, x, ws, nrm, flags, dev)
     for _ in range(args.warmup):
         md.newton_step(sysd, x, ws, nrm, flags=flags)
     torch.cuda.synchronize(dev)
@@ -372,7 +387,9 @@ def run_product(args):
                        "update": ("split products: series products on 32-bit word slices (integer pipe), "
                                   "update on 8-bit slices (BF16 tensor pipe)") if args.update == "split"
                        else "md arithmetic",
-                       "factor": "LU with partial pivoting" if args.factor == "lu" else "Householder QR"},
+                       "factor": "LU with partial pivoting" if args.factor == "lu" else "Householder QR",
+                       "factor_sms": "autotuned over 15 untimed calls before the warm-up (MD_FLAG_AUTOTUNE)"
+                       if not args.no_autotune else "4 (default)"},
             "roofline": roofline, "gpu_launches": launches, "clocks": clk, "device_status": status,
             "kernel_ms": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
             "wall_s_timed_region": wall, "dx_norm_last": float(nrm[0].item()),
@@ -407,9 +424,10 @@ def run_product(args):
     # the other update form on the same GPU, same workload and timing (context,
     # not the headline): the split-product update against md arithmetic
     if args.update == "md" and not args.no_other_form:
-        oflags = md.FLAG_OZAKI | (flags & md.FLAG_LU)
+        oflags = md.FLAG_OZAKI | (flags & (md.FLAG_LU | md.FLAG_AUTOTUNE))
         ows = md.workspace(sysd.workspace_bytes(oflags), device=dev)
         xo = md.to_device(s.x0, dev)
+        tune_factor_sms(md, sysd, xo, ows, nrm, oflags, dev)
         for _ in range(args.warmup):
             md.newton_step(sysd, xo, ows, nrm, flags=oflags)
         torch.cuda.synchronize(dev)
@@ -463,7 +481,7 @@ def run_product(args):
                                  "measure": "one step from x0; per degree, max_i |x_gpu - x_oracle| / max_i |x_oracle|"}
         sp = line.get("other_forms", {}).get("split_product_form")
         if sp is not None:  # the split-product form's step from x0 against the same oracle step
-            sflags = md.FLAG_OZAKI | (flags & md.FLAG_LU)
+            sflags = md.FLAG_OZAKI | (flags & (md.FLAG_LU | md.FLAG_AUTOTUNE))
             sws = md.workspace(sysd.workspace_bytes(sflags), device=dev)
             x2 = md.to_device(s.x0, dev)
             md.newton_step(sysd, x2, sws, nrm, flags=sflags)
@@ -941,6 +959,8 @@ def main():
     ap.add_argument("--impl", default="product", choices=["product", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other-form", action="store_true", help="skip timing the split-product update beside md")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="single step: keep the default SM count of the factorisation (no MD_FLAG_AUTOTUNE)")
     ap.add_argument("--form", default="plain", choices=["plain", "solve3", "batched", "ladder", "elementwise"],
                     help="plain: the Newton-step benchmark; solve3: plain vs split-product solve; "
                          "batched: 2048-system batched step vs a per-system loop; ladder: the headline step at every precision; elementwise: md add/mul HBM vs FP64 bound")

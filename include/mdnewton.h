@@ -120,7 +120,13 @@ typedef struct md_system {
 #define MD_FLAG_OZAKI 0x1
 /* batched form: pick threads per CTA and CTAs per SM per precision class, and
    the threads of the whole-SM CTAs, by timing trial steps (first call only;
-   trial steps do not update x) */
+   trial steps do not update x).
+   single step (md_newton_series_step, without MD_FLAG_SERIAL): pick how many
+   SMs the factorisation of A_0 keeps while the evaluation runs, per plan and
+   form: the first 14 calls outside a stream capture each time one of seven
+   counts (4 to 48; events on the caller's stream, read later without
+   waiting), and once all are read the fastest is kept.  Results do not
+   depend on it; calls before then use the default (4). */
 #define MD_FLAG_AUTOTUNE 0x2
 /* batched form: capture the step (plan upload + persistent launches) in a CUDA
    graph on the first call and replay it on later calls with the same arguments
@@ -244,7 +250,8 @@ md_status md_lstsq_series(int limbs, int is_complex, int neq, int n, int degree,
  *            of Section 6), [1] = max over all coefficients; both from the
  *            leading limbs.
  *   ws:      DEVICE workspace of md_workspace_bytes(sys, flags) bytes.
- *   flags:   MD_FLAG_OZAKI, MD_FLAG_LU, MD_FLAG_SERIAL, MD_FLAG_CHECK
+ *   flags:   MD_FLAG_OZAKI, MD_FLAG_LU, MD_FLAG_SERIAL, MD_FLAG_CHECK,
+ *            MD_FLAG_AUTOTUNE
  */
 md_status md_newton_series_step(const md_system *sys, double *x, double *dx_norm, void *ws, size_t ws_bytes,
                                 int flags, void *stream);

@@ -536,11 +536,41 @@ struct UseEvents {
   }
 };
 
+// MD_FLAG_AUTOTUNE of the single step: how many SMs the factorisation keeps
+// while the evaluation's resident CTAs run.  The results do not depend on it
+// (the same kernels and task numbering on any grid); the time does, by the
+// balance of evaluation and factorisation.  The first 2 kN calls of a plan
+// each run one candidate between two timing events on the caller's stream;
+// a later call reads them (without waiting) and keeps the fastest.
+struct FactorTune {
+  static constexpr int kN = 7;
+  static constexpr int kCand[kN] = {4, 8, 12, 16, 24, 32, 48};
+  std::mutex mu;
+  int best = 0;  // the chosen count, once tuned
+  int next = 0;  // measurements started
+  int dev = -1;  // the device the events belong to
+  float ms[kN];
+  bool done[2 * kN] = {};
+  cudaEvent_t a[2 * kN] = {}, b[2 * kN] = {};
+  FactorTune() {
+    for (float &v : ms) v = 1e30f;
+  }
+  void release() {
+    for (int i = 0; i < 2 * kN; ++i) {
+      if (a[i]) cudaEventDestroy(a[i]);
+      if (b[i]) cudaEventDestroy(b[i]);
+      a[i] = b[i] = nullptr;
+    }
+  }
+  ~FactorTune() { release(); }
+};
+
 struct PlanEntry {
   Plan plan;
   int *pinned = nullptr;  // tables laid out exactly as in the workspace, from off_tasks
   size_t image_bytes = 0;
   UseEvents uses;
+  FactorTune tune;
   // used while a stream was being captured: a caller's graph may copy from
   // the pinned image whenever it is replayed, so the entry is never dropped
   bool captured = false;
@@ -1231,9 +1261,60 @@ cudaEvent_t aux_event(DevAux *a, int i) { return i == 0 ? a->e0 : a->e1; }
 #define MDK_FACTOR_SMS 4
 #endif
 constexpr int kFactorSms = MDK_FACTOR_SMS;
-// The split-product form keeps the same four: its fixed-point series products
-// remain the step's critical path (measured at n = 64, d = 64: 43.1 steps/s
-// with 4 SMs for the factorisation, 41.2 with 19, 38.8 with 38, 30.6 with 76).
+// Other balances want more (measured: the split-product form at n = 64,
+// d = 64, whose fixed-point products now take less time than the
+// factorisation on four SMs, 19.2 ms with 4 and 15.1 with 16; the octo double
+// n = 128 plain step 41.8 ms with 4 and 35.1 with 48): MD_FLAG_AUTOTUNE picks
+// the count per plan (FactorTune).
+
+// The count for this call of the step, and the timing events to record
+// around it (null: untimed).  Under MD_FLAG_AUTOTUNE, outside a capture.
+md_status factor_sms_for(FactorTune &t, int flags, cudaStream_t s, int &fsms, cudaEvent_t &ta, cudaEvent_t &tb) {
+  fsms = kFactorSms;
+  ta = tb = nullptr;
+  if (!(flags & MD_FLAG_AUTOTUNE) || !not_capturing(s)) return MD_OK;
+  std::lock_guard<std::mutex> lk(t.mu);
+  if (t.best) {
+    fsms = t.best;
+    return MD_OK;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MD_ERR_CUDA;
+  if (t.dev >= 0 && t.dev != dev) return MD_OK;  // tuning on another device: the default here
+  t.dev = dev;
+  constexpr int kM = 2 * FactorTune::kN;
+  if (t.next < kM) {
+    const int i = t.next;
+    if ((!t.a[i] && cudaEventCreate(&t.a[i]) != cudaSuccess) || (!t.b[i] && cudaEventCreate(&t.b[i]) != cudaSuccess))
+      return MD_ERR_CUDA;
+    t.next++;
+    fsms = FactorTune::kCand[i % FactorTune::kN];
+    ta = t.a[i];
+    tb = t.b[i];
+    return MD_OK;
+  }
+  bool all = true;
+  for (int i = 0; i < kM; ++i) {
+    if (t.done[i]) continue;
+    const cudaError_t q = cudaEventQuery(t.b[i]);
+    if (q == cudaErrorNotReady) {
+      all = false;
+      continue;
+    }
+    float ms = 0.f;
+    if (q != cudaSuccess || cudaEventElapsedTime(&ms, t.a[i], t.b[i]) != cudaSuccess) return MD_ERR_CUDA;
+    t.ms[i % FactorTune::kN] = std::min(t.ms[i % FactorTune::kN], ms);
+    t.done[i] = true;
+  }
+  if (!all) return MD_OK;
+  int bi = 0;
+  for (int c = 1; c < FactorTune::kN; ++c)
+    if (t.ms[c] < t.ms[bi]) bi = c;
+  t.best = FactorTune::kCand[bi];
+  t.release();
+  fsms = t.best;
+  return MD_OK;
+}
 
 // ------------------------------------------------------------- profiling
 // Optional per-launch timing: when enabled, every launch is bracketed by a
@@ -1449,11 +1530,15 @@ md_status md_newton_series_step(const md_system *sys, double *x, double *dx_norm
     return cuda_status(dispatch(p->K, p->P, 3, &v, s));
   }
   // evaluation prologue and coefficient 0 (gives A_0) -> factorisation on the
-  // second stream, concurrently with the remaining products on SMs - kFactorSms
+  // second stream, concurrently with the remaining products on SMs - fsms
   // resident CTAs -> degree loop once both are done
-  e.resident_ctas = std::max(1, device_sms() - kFactorSms);
+  int fsms = kFactorSms;
+  cudaEvent_t ta = nullptr, tb = nullptr;
+  if ((st = factor_sms_for(hold->tune, flags, s, fsms, ta, tb)) != MD_OK) return st;
+  e.resident_ctas = std::max(1, device_sms() - fsms);
   e.resident_smem = device_smem_optin();
   std::lock_guard<std::mutex> lk(ax->mu);
+  if (ta && cudaEventRecord(ta, s) != cudaSuccess) return MD_ERR_CUDA;
   if (dispatch(p->K, p->P, 5, &e, s) != cudaSuccess) return MD_ERR_CUDA;
   if (cudaEventRecord(ax->e0, s) != cudaSuccess || cudaStreamWaitEvent(ax->s2, ax->e0, 0) != cudaSuccess)
     return MD_ERR_CUDA;
@@ -1461,7 +1546,8 @@ md_status md_newton_series_step(const md_system *sys, double *x, double *dx_norm
   if (cudaEventRecord(ax->e1, ax->s2) != cudaSuccess) return MD_ERR_CUDA;
   if (dispatch(p->K, p->P, 6, &e, s) != cudaSuccess) return MD_ERR_CUDA;
   if (cudaStreamWaitEvent(s, ax->e1, 0) != cudaSuccess) return MD_ERR_CUDA;
-  return cuda_status(dispatch(p->K, p->P, 8, &v, s));
+  if (dispatch(p->K, p->P, 8, &v, s) != cudaSuccess) return MD_ERR_CUDA;
+  return cuda_status(tb ? cudaEventRecord(tb, s) : cudaSuccess);
 }
 
 md_status md_rcond_a0(const md_system *sys, void *ws, size_t ws_bytes, int flags, double *rcond, void *stream) {

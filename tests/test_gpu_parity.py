@@ -238,6 +238,29 @@ def test_newton_against_more_limbs(md, orc, cfg, steps, Kref):
     assert worst <= TOL
 
 
+@pytest.mark.parametrize("form", ["plain", "split"])
+def test_autotuned_step_equals_default(md, form):
+    """MD_FLAG_AUTOTUNE changes how many SMs the factorisation keeps while the
+    evaluation runs (one count per call over the first 14 calls of a plan,
+    the fastest kept from the 15th on), never the result: 18 autotuned steps
+    from x0 give the bits of 18 default steps, plain and split-product form."""
+    import torch
+
+    s = mdgen.config_system(1, 1)
+    sysd = md.DeviceSystem(s)
+    base = md.FLAG_OZAKI if form == "split" else 0
+    outs = []
+    for flags in (base, base | md.FLAG_AUTOTUNE):
+        ws = md.workspace(sysd.workspace_bytes(flags))
+        x = md.to_device(s.x0)
+        for _ in range(18):
+            md.newton_step(sysd, x, ws, flags=flags)
+            torch.cuda.synchronize()
+        assert md.device_status(ws) == 0
+        outs.append(x.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+
+
 def test_deterministic(md):
     import torch
 
