@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
         // after the other in a warp that holds both
         const bool pair = 2 * p < d;
         if (fx)
-          conv_pair_fx<K, P, true>(pool, d, out, a, b, p, pair ? out : -1, pair ? a : -1, pair ? b : -1, fxpool);
+          conv_pair_fx<K, P>(pool, fxpool, d, out, a, b, p, pair ? out : -1, pair ? a : -1, pair ? b : -1);
         else
           conv_pair<K, P, false>(pool, d, out, a, b, p, pair ? out : -1, pair ? a : -1, pair ? b : -1);
       }

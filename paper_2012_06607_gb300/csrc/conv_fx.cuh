@@ -112,16 +112,32 @@ __global__ void pool_load_x_fx_kernel(const double *__restrict__ x, double *__re
   pool_load_entry_fx<K, P>(x, pool, fxpool, n, d, e);
 }
 
+// acc += a b (complex for P = 2) with the W-word products and sums inlined:
+// the values stay in registers (the out-of-line forms pass every operand and
+// result through the call stack, and that local-memory traffic, not the
+// integer arithmetic, bounded the products).  The same operations in the same
+// order as fx_cmul followed by add.
+template <int W, int P>
+__device__ __forceinline__ void fx_cmac_inl(fxp::bf<W> (&acc)[P], const fxp::bf<W> (&a)[P],
+                                            const fxp::bf<W> (&b)[P]) {
+  using namespace fxp;
+  if constexpr (P == 1) {
+    acc[0] = add_impl<W>(acc[0], mul_impl<W>(a[0], b[0]));
+  } else {
+    const bf<W> re = add_impl<W>(mul_impl<W>(a[0], b[0]), neg<W>(mul_impl<W>(a[1], b[1])));
+    const bf<W> im = add_impl<W>(mul_impl<W>(a[0], b[1]), mul_impl<W>(a[1], b[0]));
+    acc[0] = add_impl<W>(acc[0], re);
+    acc[1] = add_impl<W>(acc[1], im);
+  }
+}
+
 // Two output coefficients of series products as conv_pair (same task layout
-// and term order), in fixed point.  PACKED: the operands come from the
-// fixed-point pool and the outputs go to both pools; otherwise every operand
-// is converted from the md pool at each term.  The W-word operations are
-// called out of line (inlined, they needed ~156 registers a thread and the
-// kernel ran 25% slower at 384 threads than called at 512, despite the call
-// stack's traffic).
-template <int K, int P, bool PACKED = false>
-__device__ __forceinline__ void conv_pair_fx(double *pool, int d, int outA, int xA, int yA, int kA, int outB, int xB,
-                                             int yB, uint32_t *fxpool = nullptr) {
+// and term order), in fixed point: the operands from the fixed-point pool,
+// every term inlined (fx_cmac_inl), the outputs rounded to K limbs into the
+// md pool and, as the exact values of those limbs, into the fixed-point pool.
+template <int K, int P>
+__device__ __forceinline__ void conv_pair_fx(double *pool, uint32_t *fxpool, int d, int outA, int xA, int yA, int kA,
+                                             int outB, int xB, int yB) {
   using namespace fxp;
   constexpr int W = words_for(K), PW = packed_words(W);
   const int kB = d - kA;
@@ -135,37 +151,20 @@ __device__ __forceinline__ void conv_pair_fx(double *pool, int d, int outA, int 
     const bool first = it <= kA;
     const int i = first ? it : it - kA - 1;
     const int sx = first ? xA : xB, sy = first ? yA : yB, iy = (first ? kA : kB) - i;
-    bf<W> a[P], b[P], t[P];
-    if constexpr (PACKED) {
+    bf<W> a[P], b[P];
 #pragma unroll
-      for (int p = 0; p < P; ++p) {
-        a[p] = fx_ld_packed<W>(fxpool + sx * FS + i * FV + p * PW);
-        b[p] = fx_ld_packed<W>(fxpool + sy * FS + iy * FV + p * PW);
-      }
-    } else {
-      fx_ld_val<W, K, P>(pool + sx * SS + i * VS, a);
-      fx_ld_val<W, K, P>(pool + sy * SS + iy * VS, b);
+    for (int p = 0; p < P; ++p) {
+      a[p] = fx_ld_packed<W>(fxpool + sx * FS + i * FV + p * PW);
+      b[p] = fx_ld_packed<W>(fxpool + sy * FS + iy * FV + p * PW);
     }
-    fx_cmul<W, P>(a, b, t);
     if (it == kA + 1) {
 #pragma unroll
       for (int p = 0; p < P; ++p) acc[p] = zero<W>();
     }
-#pragma unroll
-    for (int p = 0; p < P; ++p) acc[p] = add<W>(acc[p], t[p]);
-    if (it == kA) {
-      if constexpr (PACKED)
-        fx_st_both<W, K, P>(pool + outA * SS + kA * VS, fxpool + outA * FS + kA * FV, acc);
-      else
-        fx_st_val<W, K, P>(pool + outA * SS + kA * VS, acc);
-    }
+    fx_cmac_inl<W, P>(acc, a, b);
+    if (it == kA) fx_st_both<W, K, P>(pool + outA * SS + kA * VS, fxpool + outA * FS + kA * FV, acc);
   }
-  if (outB >= 0) {
-    if constexpr (PACKED)
-      fx_st_both<W, K, P>(pool + outB * SS + kB * VS, fxpool + outB * FS + kB * FV, acc);
-    else
-      fx_st_val<W, K, P>(pool + outB * SS + kB * VS, acc);
-  }
+  if (outB >= 0) fx_st_both<W, K, P>(pool + outB * SS + kB * VS, fxpool + outB * FS + kB * FV, acc);
 }
 
 // One chunk of a row of the block Toeplitz update sum_{j<k} A_{k-j} dx_j
@@ -189,24 +188,24 @@ __device__ __forceinline__ void rhs_partial_item_fx(const uint32_t *fxA, const u
     const int j = t / n, col = t % n;
     const uint32_t *ap = fxA + ((long long)(k - j) * nn + (long long)col * N + row) * P * PW;
     const uint32_t *xp = fxdx + ((long long)j * n + col) * P * PW;
-    bf<W> a[P], x[P], prod[P];
+    bf<W> a[P], x[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) {
       a[p] = fx_ld_packed<W>(ap + p * PW);
       x[p] = fx_ld_packed<W>(xp + p * PW);
     }
-    fx_cmul<W, P>(a, x, prod);
-#pragma unroll
-    for (int p = 0; p < P; ++p) acc[p] = add<W>(acc[p], prod[p]);
+    fx_cmac_inl<W, P>(acc, a, x);
   }
   fx_st_val<W, K, P>(part + ((long long)row * nchunk + chunk) * VS, acc);
 }
 
 // The resident stage launch of conv_stage_resident_kernel in fixed point
-// (same grid and task numbering; ~90 registers a thread: 16 warps an SM).
+// (same grid and task numbering).  Threads per CTA by limb count so that the
+// inlined terms fit in registers without spilling: 512 threads (128
+// registers) up to three limbs, 384 (168) at four, 256 (255) from five on.
 template <int K>
 __host__ __device__ constexpr int conv_fx_threads() {
-  return 512;
+  return K <= 3 ? 512 : (K == 4 ? 384 : 256);
 }
 
 template <int K, int P>
@@ -215,7 +214,7 @@ __global__ void __launch_bounds__(conv_fx_threads<K>(), 1)
   for (int t = threadIdx.x * gridDim.x + blockIdx.x; t < ntask; t += gridDim.x * blockDim.x) {
     const int4 t0 = __ldg(reinterpret_cast<const int4 *>(tasks) + 2 * t);
     const int4 t1 = __ldg(reinterpret_cast<const int4 *>(tasks) + 2 * t + 1);
-    conv_pair_fx<K, P, true>(pool, d, t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, fxpool);
+    conv_pair_fx<K, P>(pool, fxpool, d, t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z);
   }
 }
 

@@ -125,12 +125,14 @@ cudaError_t Impl<K, P>::eval_rest(const EvalDev &e, cudaStream_t s) {
     ProfScope prof(PK_CONV, s);
     if constexpr (K >= kFxConvMinLimbs) {
       if (e.split) {  // the split-product form: every term on 32-bit word slices
+        // No shared memory reserved: the CTAs' registers (threads x registers
+        // of conv_fx_threads) fill the SM's register file, which keeps the
+        // factorisation's CTAs off their SMs as well, and the L1 left to the
+        // kernel holds the operands it re-reads.
         auto kern = conv_stage_fx_kernel<K, P>;
-        int smem = e.resident_ctas > 0 ? e.resident_smem : 0;
-        if (smem > 0 && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+        const int smem = 0;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0) != cudaSuccess)
           (void)cudaGetLastError();
-          smem = 0;
-        }
         constexpr int T = conv_fx_threads<K>();
         const unsigned grid = e.resident_ctas > 0 ? (unsigned)e.resident_ctas : blocks_for(t1 - t0, T);
         kern<<<grid, T, smem, s>>>(e.tasks + 8LL * t0, t1 - t0, e.pool, e.fxpool, d);
