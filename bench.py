@@ -582,6 +582,73 @@ def measure_solve3(args, with_err: bool) -> dict:
             "data": "synthetic", "dtype": "f64 (quad double); bf16 slices for the split products"}
 
 
+# The paper's octo double schedule (Table 2): truncation degrees 8, 16, 24,
+# 32 with at most 5, 6, 12 and 16 iterations, tolerance 1e-32 on the update.
+RUN_DEGREES = (8, 16, 24, 32)
+RUN_MAX_ITER = (5, 6, 12, 16)
+
+
+def run_driver(args):
+    """Newton with degree continuation through md_newton_series_run on the
+    octo double n = 128 system (config 2, the shape of the paper's Table 2
+    runs) under the paper's octo double schedule, plain and split-product
+    form: seconds per run, iterations per level, the final update norms.
+    The paper's Table 2 times (88 Xeon threads, cyclic 128-roots surface) are
+    quoted beside it as context; the oracle's first level is the CPU sample."""
+    import numpy as np
+    import torch
+
+    import mdgen
+    import paper_2012_06607_gb300 as md
+
+    s = mdgen.config_system(2, args.seed)
+    sysd = md.DeviceSystem(s)
+    sched = md.schedule(RUN_DEGREES, RUN_MAX_ITER, tol=1e-32)
+    forms = {}
+    for name, flags in (("plain", 0), ("split_product", md.FLAG_OZAKI)):
+        ws = md.workspace(md.newton_run_workspace_bytes(sysd, sched, flags))
+        for _ in range(max(args.warmup, 1)):  # plans and first launches of every level
+            x = md.to_device(s.x0)
+            md.newton_run(sysd, x, ws, sched, flags=flags)
+        torch.cuda.synchronize()
+        secs = []
+        rep = None
+        for _ in range(args.steps):
+            x = md.to_device(s.x0)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            rep = md.newton_run(sysd, x, ws, sched, flags=flags)
+            b.record()
+            b.synchronize()
+            secs.append(a.elapsed_time(b) / 1e3)
+        assert md.device_status(ws) == 0
+        forms[name] = {"seconds_per_run": statistics.median(secs), "levels_done": rep["levels_done"],
+                       "iterations": rep["iterations"], "converged": rep["converged"],
+                       "dx_norm_last": rep["dx_norm"][-1] if rep["dx_norm"] else None}
+        del ws
+    line = {"metric": "Newton runs with degree continuation (od real, n=128, d 8->16->24->32)", "form": "run",
+            "value": forms["plain"]["seconds_per_run"], "unit": "s", "higher_is_better": False,
+            "plain": forms["plain"], "split_product": forms["split_product"],
+            "speedup_split": forms["plain"]["seconds_per_run"] / forms["split_product"]["seconds_per_run"],
+            "schedule": {"degrees": list(RUN_DEGREES), "max_iter": list(RUN_MAX_ITER), "tol": 1e-32},
+            "paper_table2_octo_double_s": {"8": 128, "16": 472, "24": 1934, "32": 4400,
+                                           "note": "88 threads of two Xeon E5-2699, cyclic 128-roots surface "
+                                                   "(another system): context, not the same workload"},
+            "steps": args.steps, "warmup": args.warmup, "data": "synthetic", "dtype": "f64 (octo double)"}
+    if not args.no_cpu_baseline:
+        import oracle
+
+        orc = oracle.Oracle(threads=os.cpu_count() or 1)
+        t0 = time.perf_counter()
+        _, crep = orc.newton_run(s, RUN_DEGREES[:1], RUN_MAX_ITER[:1], 1e-32, 1.0)
+        cpu_s = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": cpu_s, "unit": "s", "cores": orc.threads(), "kind": "oracle",
+                                "sample": f"the first level only (d = 8, {crep['iterations']} iterations)"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ladder(args):
     """The cost of higher precision (Section 2, Table 1): the Newton step of
     the same system (the headline workload, its exact coefficients re-expanded
@@ -961,9 +1028,9 @@ def main():
     ap.add_argument("--no-other-form", action="store_true", help="skip timing the split-product update beside md")
     ap.add_argument("--no-autotune", action="store_true",
                     help="single step: keep the default SM count of the factorisation (no MD_FLAG_AUTOTUNE)")
-    ap.add_argument("--form", default="plain", choices=["plain", "solve3", "batched", "ladder", "elementwise"],
+    ap.add_argument("--form", default="plain", choices=["plain", "solve3", "batched", "ladder", "elementwise", "run"],
                     help="plain: the Newton-step benchmark; solve3: plain vs split-product solve; "
-                         "batched: 2048-system batched step vs a per-system loop; ladder: the headline step at every precision; elementwise: md add/mul HBM vs FP64 bound")
+                         "batched: 2048-system batched step vs a per-system loop; ladder: the headline step at every precision; elementwise: md add/mul HBM vs FP64 bound; run: Newton with the paper's octo double degree continuation, plain and split form")
     ap.add_argument("--update", default="md", choices=["md", "split"],
                     help="block Toeplitz update of the plain form: md arithmetic or split-product")
     ap.add_argument("--batch", type=int, default=2048)
@@ -984,6 +1051,8 @@ def main():
         return run_batched(args)
     if args.form == "ladder":
         return run_ladder(args)
+    if args.form == "run":
+        return run_driver(args)
     if args.form == "elementwise":
         return run_elementwise(args)
     return run_product(args)
