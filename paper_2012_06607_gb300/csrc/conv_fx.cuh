@@ -9,9 +9,11 @@
 // products, on the integer multiplier: on GB300 the integer pipe retires ~30
 // times the FP64 pipe's lanes per cycle, and a quad double complex
 // multiply-add costs 712 FP64 instructions in md arithmetic.  The result is
-// at least as accurate as the md form (one truncation to K limbs instead of
-// a rounding in every operation) but not its bits: the split-product form is
-// checked against the oracle by tolerance, the plain form keeps the bits.
+// at least as accurate as the md form (one rounding to K limbs, to nearest,
+// instead of a rounding in every operation) but not its bits: the
+// split-product form is checked against the oracle by tolerance, the plain
+// form keeps the bits.  Used from kFxConvMinLimbs limbs on: at double double
+// the md form is faster.
 #pragma once
 #include "house_fx.cuh"
 
