@@ -114,7 +114,13 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
       else
         pool_load_entry<K, P>(J.x, pool, n, d, e);
     }
-    for (int i = tid; i < J.nscal; i += NT) prep_scal_entry<K, P>(ibase + J.scal_src, J.coef, J.nmono, scal, i);
+    uint32_t *fxscal = reinterpret_cast<uint32_t *>(dbase + J.fxscal);
+    for (int i = tid; i < J.nscal; i += NT) {
+      if (fx)
+        prep_scal_entry_fx<K, P>(ibase + J.scal_src, J.coef, J.nmono, scal, fxscal, i);
+      else
+        prep_scal_entry<K, P>(ibase + J.scal_src, J.coef, J.nmono, scal, i);
+    }
     const long long Awords = (long long)P * K * (d + 1) * n * n;
     for (long long e = tid; e < Awords; e += NT) A[e] = 0.0;
     __syncthreads();
@@ -141,8 +147,13 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
     phase_stamp(phases, times, (long long)tstride * job + 2);
     const int4 *groups = reinterpret_cast<const int4 *>(ibase + J.groups);
     const int4 *contrib = reinterpret_cast<const int4 *>(ibase + J.contrib);
-    for (long long e = tid; e < (long long)J.ngroups * (d + 1); e += NT)
-      accum_entry<K, P>(groups, contrib, pool, scal, J.cst, f, A, n, n, d, (int)(e / (d + 1)), (int)(e % (d + 1)));
+    for (long long e = tid; e < (long long)J.ngroups * (d + 1); e += NT) {
+      if (fx)
+        accum_entry_fx<K, P>(groups, contrib, fxpool, fxscal, J.cst, f, A, n, n, d, (int)(e / (d + 1)),
+                             (int)(e % (d + 1)));
+      else
+        accum_entry<K, P>(groups, contrib, pool, scal, J.cst, f, A, n, n, d, (int)(e / (d + 1)), (int)(e % (d + 1)));
+    }
     __syncthreads();
     if (fx) {  // A's values converted once for the update sums of every degree
       const long long cnt = (long long)(d + 1) * n * n;

@@ -147,7 +147,10 @@ struct Plan {
   std::vector<int> op_stage_off;  // nstages + 1 product offsets
   // workspace offsets (bytes)
   size_t off_pool = 0, off_scal = 0, off_tasks = 0, off_scalsrc = 0, off_groups = 0, off_contrib = 0, off_tasks0 = 0;
-  size_t off_f = 0, off_A = 0, off_prod = 0, off_fxpool = 0, fxpool_bytes = 0, off_solve = 0, total = 0;
+  size_t off_f = 0, off_A = 0, off_prod = 0, off_solve = 0, total = 0;
+  // the split-product form's packed fixed-point copies (pool, coefficients,
+  // contribution values), one region; fxpool_bytes = 0 when not laid out
+  size_t off_fxpool = 0, off_fxscal = 0, off_fxprod = 0, fxpool_bytes = 0;
   SolveLayout sl{};
   uint64_t checksum = 0;
   // the planned structure itself, compared with the caller's on every cache
@@ -412,11 +415,19 @@ md_status build_plan(const md_system *s, Plan &p, int flags = 0) {
   p.off_f = o; o = align256(o + (size_t)N * (d + 1) * VS);
   p.off_A = o; o = align256(o + (size_t)(d + 1) * N * n * VS);
   p.off_prod = o; o = align256(o + (p.contrib.size() / 4) * (size_t)(d + 1) * VS);
-  // the split-product form's fixed-point copy of the pool (K >= kFxConvMinLimbs)
-  p.fxpool_bytes = ((flags & MD_FLAG_OZAKI) && p.K >= mdk::kFxConvMinLimbs)
-                       ? sizeof(unsigned) * (size_t)p.nslots * (d + 1) * p.P * mdk::fx_packed_words_for(p.K)
-                       : 0;
-  p.off_fxpool = o; o = align256(o + p.fxpool_bytes);
+  // the split-product form's fixed-point copies (K >= kFxConvMinLimbs)
+  p.off_fxpool = o;
+  if ((flags & MD_FLAG_OZAKI) && p.K >= mdk::kFxConvMinLimbs) {
+    const size_t FV = sizeof(unsigned) * p.P * mdk::fx_packed_words_for(p.K);  // bytes per value
+    size_t q = o;
+    q = align256(q + (size_t)p.nslots * (d + 1) * FV);
+    p.off_fxscal = q;
+    q = align256(q + (size_t)std::max(nscal, 1) * FV);
+    p.off_fxprod = q;
+    q = align256(q + (size_t)std::max<size_t>(p.contrib.size() / 4, 1) * (d + 1) * FV);
+    p.fxpool_bytes = q - o;
+    o = q;
+  }
   p.off_solve = o;
   p.sl = solve_layout(p.K, p.P, N, n, d, o, flags);
   p.total = o + p.sl.bytes;
@@ -913,6 +924,7 @@ md_status batch_prepare(int nsys, const md_system *sys, double *const *x, std::s
       J.fxpool = nd; nd += (size_t)p.nslots * D1 * FV;
       J.fxA = nd; nd += (size_t)D1 * n * n * FV;
       J.fxdx = nd; nd += (size_t)D1 * n * FV;
+      J.fxscal = nd; nd += (size_t)std::max(J.nscal, 1) * FV;
     }
     J.coef = sys[i].coef;
     J.cst = sys[i].cst;
@@ -1190,7 +1202,11 @@ EvalDev make_eval(const Plan &p, const md_system *s, const double *x, double *f,
   e.prod = reinterpret_cast<double *>(base + p.off_prod);
   e.tasks0 = reinterpret_cast<const int *>(base + p.off_tasks0);
   e.stage_off0 = p.stage_off0.data();
-  e.fxpool = p.fxpool_bytes ? reinterpret_cast<unsigned *>(base + p.off_fxpool) : nullptr;
+  if (p.fxpool_bytes) {
+    e.fxpool = reinterpret_cast<unsigned *>(base + p.off_fxpool);
+    e.fxscal = reinterpret_cast<unsigned *>(base + p.off_fxscal);
+    e.fxprod = reinterpret_cast<unsigned *>(base + p.off_fxprod);
+  }
   return e;
 }
 

@@ -169,6 +169,148 @@ __device__ __forceinline__ void conv_pair_fx(double *pool, uint32_t *fxpool, int
   if (outB >= 0) fx_st_both<W, K, P>(pool + outB * SS + kB * VS, fxpool + outB * FS + kB * FV, acc);
 }
 
+// z = a b (complex for P = 2) with the W-word products and sums inlined (the
+// operations of fx_cmul).
+template <int W, int P>
+__device__ __forceinline__ void fx_cmul_inl(const fxp::bf<W> (&a)[P], const fxp::bf<W> (&b)[P],
+                                            fxp::bf<W> (&z)[P]) {
+  using namespace fxp;
+  if constexpr (P == 1) {
+    z[0] = mul_impl<W>(a[0], b[0]);
+  } else {
+    z[0] = add_impl<W>(mul_impl<W>(a[0], b[0]), neg<W>(mul_impl<W>(a[1], b[1])));
+    z[1] = add_impl<W>(mul_impl<W>(a[0], b[1]), mul_impl<W>(a[1], b[0]));
+  }
+}
+
+// ------------------------------------------------- accumulation of f and A_k
+// The split-product form's accumulation (Section 4, the linearization): the
+// steps of accum_contrib_value / accum_entry on the packed fixed-point copies
+// of the coefficients (fxscal: nscal values of P packed planes) and of the
+// series pool, each contribution value an exact word-slice product, each
+// entry's sum (constant term, then the contributions in list order) kept in
+// W-word fixed point and rounded to K limbs once.
+
+// Coefficient k of one contribution: c s_{k-a} for a product slot s, c at
+// k = a for the unit series, zero for k < a.
+template <int K, int P>
+__device__ __forceinline__ void accum_contrib_value_fx(const int4 C, const uint32_t *fxpool, const uint32_t *fxscal,
+                                                       int d, int k, fxp::bf<fxp::words_for(K)> (&v)[P]) {
+  using namespace fxp;
+  constexpr int W = words_for(K), PW = packed_words(W);
+#pragma unroll
+  for (int p = 0; p < P; ++p) v[p] = zero<W>();
+  if (k < C.z) return;
+  bf<W> c[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) c[p] = fx_ld_packed<W>(fxscal + ((long long)C.y * P + p) * PW);
+  if (C.x < 0) {
+    if (k == C.z) {
+#pragma unroll
+      for (int p = 0; p < P; ++p) v[p] = c[p];
+    }
+    return;
+  }
+  bf<W> sv[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+    sv[p] = fx_ld_packed<W>(fxpool + (((long long)C.x * (d + 1) + (k - C.z)) * P + p) * PW);
+  fx_cmul_inl<W, P>(c, sv, v);
+}
+
+// The sum of one entry (group g, coefficient k) from its constant term and
+// the contribution values get(q), q < G.w, rounded to K limbs into f or A.
+template <int K, int P, class Get>
+__device__ __forceinline__ void accum_finish_fx(const int4 G, const double *cst, double *f, double *A, int N, int n,
+                                                int d, int k, Get get) {
+  using namespace fxp;
+  constexpr int W = words_for(K);
+  bf<W> acc[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) acc[p] = zero<W>();
+  if (G.y < 0 && k == 0) {
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      double c[K];
+#pragma unroll
+      for (int l = 0; l < K; ++l) c[l] = cst[G.x + (long long)(p * K + l) * N];
+      acc[p] = from_md<W, K>(c);
+    }
+  }
+  for (int q = 0; q < G.w; ++q) {
+    bf<W> v[P];
+    get(q, v);
+#pragma unroll
+    for (int p = 0; p < P; ++p) acc[p] = add_impl<W>(acc[p], v[p]);
+  }
+  // f: [P][K][N][d+1]; A: [P][K][d+1][n][N]
+  double *dst;
+  long long stride;
+  if (G.y < 0) {
+    dst = f + (long long)G.x * (d + 1) + k;
+    stride = (long long)N * (d + 1);
+  } else {
+    const long long nn = (long long)N * n;
+    dst = A + (long long)k * nn + (long long)G.y * N + G.x;
+    stride = (long long)(d + 1) * nn;
+  }
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    double z[K];
+    to_md<K, W>(acc[p], z);
+#pragma unroll
+    for (int l = 0; l < K; ++l) dst[(long long)(p * K + l) * stride] = z[l];
+  }
+}
+
+// One entry in one pass (the batched kernel's form of accum_entry).
+template <int K, int P>
+__device__ __forceinline__ void accum_entry_fx(const int4 *groups, const int4 *contrib, const uint32_t *fxpool,
+                                               const uint32_t *fxscal, const double *cst, double *f, double *A, int N,
+                                               int n, int d, int g, int k) {
+  const int4 G = groups[g];
+  accum_finish_fx<K, P>(G, cst, f, A, N, n, d, k, [&](int q, fxp::bf<fxp::words_for(K)>(&v)[P]) {
+    accum_contrib_value_fx<K, P>(contrib[G.z + q], fxpool, fxscal, d, k, v);
+  });
+}
+
+// Two passes, as accum_prod_kernel / accum_sum_kernel: every contribution
+// value (packed) to fxprod [contribution][k], then each entry's sum.
+template <int K, int P>
+__global__ void __launch_bounds__(128) accum_prod_fx_kernel(const int4 *__restrict__ contrib, int ncontrib,
+                                                            const uint32_t *__restrict__ fxpool,
+                                                            const uint32_t *__restrict__ fxscal,
+                                                            uint32_t *__restrict__ fxprod, int d) {
+  constexpr int W = fxp::words_for(K), PW = packed_words(W);
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)ncontrib * (d + 1)) return;
+  const int q = (int)(e / (d + 1)), k = (int)(e % (d + 1));
+  fxp::bf<W> v[P];
+  accum_contrib_value_fx<K, P>(contrib[q], fxpool, fxscal, d, k, v);
+#pragma unroll
+  for (int p = 0; p < P; ++p) fx_st_packed<W>(fxprod + (e * P + p) * PW, v[p]);
+}
+
+// Entries (group, k); the A groups at k = 0 are skipped when skip_A0 is set
+// (coefficient 0 of A comes from the md pre-pass).
+template <int K, int P>
+__global__ void __launch_bounds__(128) accum_sum_fx_kernel(const int4 *__restrict__ groups, int ngroups,
+                                                           const uint32_t *__restrict__ fxprod,
+                                                           const double *__restrict__ cst, double *__restrict__ f,
+                                                           double *__restrict__ A, int N, int n, int d, int skip_A0) {
+  constexpr int W = fxp::words_for(K), PW = packed_words(W);
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)ngroups * (d + 1)) return;
+  const int g = (int)(e / (d + 1)), k = (int)(e % (d + 1));
+  const int4 G = groups[g];
+  if (skip_A0 && k == 0 && G.y >= 0) return;
+  accum_finish_fx<K, P>(G, cst, f, A, N, n, d, k, [&](int q, fxp::bf<W>(&v)[P]) {
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+      v[p] = fx_ld_packed<W>(fxprod + (((long long)(G.z + q) * (d + 1) + k) * P + p) * PW);
+  });
+}
+
 // One chunk of a row of the block Toeplitz update sum_{j<k} A_{k-j} dx_j
 // (Section 3.2; rhs_partial_item's terms in its order) in fixed point: the
 // operands from packed fixed-point copies of A (fxA: the values of A in A's

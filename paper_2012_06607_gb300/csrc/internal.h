@@ -73,6 +73,8 @@ struct EvalDev {
   int resident_smem = 0;            // dynamic shared memory those CTAs reserve (keeps other CTAs off their SMs)
   int split = 0;                    // series products in fixed point (the split-product form), K >= 3
   unsigned *fxpool = nullptr;       // with split: the pool's values in packed fixed point (conv_fx.cuh)
+  unsigned *fxscal = nullptr;       // with split: the scaled coefficients, packed
+  unsigned *fxprod = nullptr;       // with split: the contribution values [ncontrib][d+1], packed
   const int *groups = nullptr;
   int ngroups = 0;
   const int *contrib = nullptr;
@@ -139,7 +141,7 @@ struct BatchJob {
   long long pool, scal, f, A, M, Y, W, vd, beta, rinv, r, dxw, part;  // dbase offsets (doubles)
   // the split-product form's packed fixed-point copies of the pool, A and dx
   // (dbase offsets in doubles, 16-byte aligned; laid out only for that form)
-  long long fxpool, fxA, fxdx;
+  long long fxpool, fxA, fxdx, fxscal;
   const double *coef;
   const double *cst;
   double *x;

@@ -247,6 +247,23 @@ __global__ void prep_scal_kernel(const int *__restrict__ src, int nscal, const d
   prep_scal_entry<K, P>(src, coef, nmono, scal, i);
 }
 
+// The scaled coefficients of prep_scal_entry, also in packed fixed point.
+template <int K, int P>
+__device__ __forceinline__ void prep_scal_entry_fx(const int *src, const double *coef, int nmono, double *scal,
+                                                   uint32_t *fxscal, int i) {
+  constexpr int PW = packed_words(fxp::words_for(K));
+  prep_scal_entry<K, P>(src, coef, nmono, scal, i);
+  fx_pack_value<K, P>(scal + (long long)i * (P * K), 1, fxscal + (long long)i * P * PW);
+}
+
+template <int K, int P>
+__global__ void prep_scal_fx_kernel(const int *__restrict__ src, int nscal, const double *__restrict__ coef, int nmono,
+                                    double *__restrict__ scal, uint32_t *__restrict__ fxscal) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nscal) return;
+  prep_scal_entry_fx<K, P>(src, coef, nmono, scal, fxscal, i);
+}
+
 // Two output coefficients of series products: the first job computes
 // coefficient kA of product (outA = xA * yA), the second coefficient kB of
 // (outB = xB * yB); kA + kB = d, so the loop has d+2 iterations (outB < 0: only

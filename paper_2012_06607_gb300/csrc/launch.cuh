@@ -94,7 +94,13 @@ cudaError_t Impl<K, P>::eval0(const EvalDev &e, cudaStream_t s) {
   }
   if (e.nscal > 0) {
     ProfScope prof(PK_SCAL, s);
-    prep_scal_kernel<K, P><<<blocks_for(e.nscal, 64), 64, 0, s>>>(e.scal_src, e.nscal, e.coef, e.nmono, e.scal);
+    bool fx = false;
+    if constexpr (K >= kFxConvMinLimbs) fx = e.split != 0;
+    if (fx)  // also packed, for the fixed-point accumulation
+      prep_scal_fx_kernel<K, P><<<blocks_for(e.nscal, 64), 64, 0, s>>>(e.scal_src, e.nscal, e.coef, e.nmono, e.scal,
+                                                                       e.fxscal);
+    else
+      prep_scal_kernel<K, P><<<blocks_for(e.nscal, 64), 64, 0, s>>>(e.scal_src, e.nscal, e.coef, e.nmono, e.scal);
   }
   const size_t Abytes = sizeof(double) * P * K * (size_t)(d + 1) * e.N * n;
   if ((err = cudaMemsetAsync(e.A, 0, Abytes, s)) != cudaSuccess) return err;
@@ -154,6 +160,24 @@ cudaError_t Impl<K, P>::eval_rest(const EvalDev &e, cudaStream_t s) {
                                                                                            t1 - t0, e.pool, d);
     } else {
       conv_stage_kernel<K, P><<<blocks_for(t1 - t0, 64), 64, 0, s>>>(e.tasks + 8LL * t0, t1 - t0, e.pool, d);
+    }
+  }
+  if constexpr (K >= kFxConvMinLimbs) {
+    if (e.split) {  // the split-product form: contribution values and sums in fixed point
+      if (e.ncontrib > 0) {
+        ProfScope prof(PK_ACCUM, s);
+        const long long work = (long long)e.ncontrib * (d + 1);
+        accum_prod_fx_kernel<K, P><<<blocks_for(work, 128), 128, 0, s>>>(reinterpret_cast<const int4 *>(e.contrib),
+                                                                         e.ncontrib, e.fxpool, e.fxscal, e.fxprod, d);
+      }
+      if (e.ngroups > 0) {
+        ProfScope prof(PK_ACCUM, s);
+        const long long work = (long long)e.ngroups * (d + 1);
+        accum_sum_fx_kernel<K, P><<<blocks_for(work, 128), 128, 0, s>>>(reinterpret_cast<const int4 *>(e.groups),
+                                                                        e.ngroups, e.fxprod, e.cst, e.f, e.A, e.N, n,
+                                                                        d, 1);
+      }
+      return cudaGetLastError();
     }
   }
   if (e.ncontrib > 0) {
