@@ -290,9 +290,11 @@ def tune_factor_sms(md, sysd, x, ws, nrm, flags, dev):
     import torch
 
     if flags & md.FLAG_AUTOTUNE:
-        for _ in range(15):
+        for _ in range(16):
             md.newton_step(sysd, x, ws, nrm, flags=flags)
             torch.cuda.synchronize(dev)
+        if md.plan_factor_sms(sysd, flags) <= 0:
+            raise RuntimeError("the factorisation's SM count was not tuned")
 
 
 def run_product(args):
@@ -388,7 +390,7 @@ def run_product(args):
                                   "update on 8-bit slices (BF16 tensor pipe)") if args.update == "split"
                        else "md arithmetic",
                        "factor": "LU with partial pivoting" if args.factor == "lu" else "Householder QR",
-                       "factor_sms": "autotuned over 15 untimed calls before the warm-up (MD_FLAG_AUTOTUNE)"
+                       "factor_sms": "autotuned over 16 untimed calls before the warm-up (MD_FLAG_AUTOTUNE)"
                        if not args.no_autotune else "4 (default)"},
             "roofline": roofline, "gpu_launches": launches, "clocks": clk, "device_status": status,
             "kernel_ms": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},

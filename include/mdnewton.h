@@ -123,10 +123,11 @@ typedef struct md_system {
    trial steps do not update x).
    single step (md_newton_series_step, without MD_FLAG_SERIAL): pick how many
    SMs the factorisation of A_0 keeps while the evaluation runs, per plan and
-   form: the first 14 calls outside a stream capture each time one of seven
-   counts (4 to 48; events on the caller's stream, read later without
-   waiting), and once all are read the fastest is kept.  Results do not
-   depend on it; calls before then use the default (4). */
+   form: after one untimed call, the next 14 calls outside a stream capture
+   each time one of seven counts (4 to 48; events on the caller's stream,
+   read later without waiting), and once all are read the fastest is kept
+   (md_plan_factor_sms reports it).  Results do not depend on it; calls
+   before then use the default (4). */
 #define MD_FLAG_AUTOTUNE 0x2
 /* batched form: capture the step (plan upload + persistent launches) in a CUDA
    graph on the first call and replay it on later calls with the same arguments
@@ -448,6 +449,17 @@ md_status md_newton_series_run(const md_system *sys, double *x, const md_newton_
  * it; only the cache's hit rate does.  Host only.
  */
 void md_plan_cache_hash_mask(unsigned long long mask);
+
+/*
+ * The number of SMs the factorisation of A_0 keeps while the evaluation runs
+ * (MD_FLAG_AUTOTUNE) in the cached plan of this system's structure and form
+ * (MD_FLAG_OZAKI in flags selects the split-product form; no counterpart in
+ * the paper).  Returns the tuned count once the tuning has ended, 0 while it
+ * has not (the step then uses the default of 4), -1 when no plan of this
+ * structure and form is cached (md_newton_series_step has not run on it) or
+ * the structure is invalid.  Host only; results never depend on it.
+ */
+int md_plan_factor_sms(const md_system *sys, int flags);
 
 /*
  * Optional timing of the library's own kernels (tracing support; not part of

@@ -104,6 +104,8 @@ def lib():
         L.md_wait_selftest.argtypes = [vp, sz, i, vp]
         L.md_plan_cache_hash_mask.argtypes = [ctypes.c_ulonglong]
         L.md_plan_cache_hash_mask.restype = None
+        L.md_plan_factor_sms.argtypes = [ctypes.POINTER(md_system), i]
+        L.md_plan_factor_sms.restype = i
         for name in ("md_elementwise", "md_series_conv", "md_eval_diff", "md_linsolve_series",
                      "md_newton_series_step", "md_get_device_status", "md_newton_series_run", "md_rcond_a0",
                      "md_linsolve_rcond", "md_lstsq_series", "md_lstsq_rcond", "md_wait_selftest"):
@@ -119,7 +121,8 @@ def exported_symbols():
             "md_newton_series_step_batched", "md_linsolve_series_static", "md_profile_enable",
             "md_profile_read", "md_profile_kind_name", "md_newton_run_workspace_bytes", "md_newton_series_run",
             "md_rcond_a0", "md_linsolve_rcond", "md_lstsq_workspace_bytes", "md_lstsq_series", "md_lstsq_rcond",
-            "md_batched_job_costs", "md_plan_check", "md_wait_selftest", "md_plan_cache_hash_mask"]
+            "md_batched_job_costs", "md_plan_check", "md_wait_selftest", "md_plan_cache_hash_mask",
+            "md_plan_factor_sms"]
 
 
 # --------------------------------------------------------------- helpers
@@ -406,6 +409,12 @@ def newton_step_batched(systems, xs, ws, dx_norm=None, times=None, flags: int = 
 
 def device_status(ws, stream=None) -> int:
     return int(lib().md_get_device_status(_ptr(ws), _stream(stream)))
+
+
+def plan_factor_sms(sysd: DeviceSystem, flags: int = 0) -> int:
+    """md_plan_factor_sms: the tuned SM count of the factorisation in the
+    cached plan of this system and form (0 while untuned, -1 if no plan)."""
+    return int(lib().md_plan_factor_sms(sysd.c(), int(flags)))
 
 
 def wait_selftest(ws, target: int, stream=None) -> None:

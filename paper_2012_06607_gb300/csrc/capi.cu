@@ -550,15 +550,19 @@ struct UseEvents {
 // MD_FLAG_AUTOTUNE of the single step: how many SMs the factorisation keeps
 // while the evaluation's resident CTAs run.  The results do not depend on it
 // (the same kernels and task numbering on any grid); the time does, by the
-// balance of evaluation and factorisation.  The first 2 kN calls of a plan
-// each run one candidate between two timing events on the caller's stream;
-// a later call reads them (without waiting) and keeps the fastest.
+// balance of evaluation and factorisation.  The first call of a plan is not
+// timed (it uploads the plan and loads the kernels, and its two streams
+// interleave unlike later calls: measured, it could come out shorter than any
+// later call at the same count).  The next 2 kN calls each run one candidate
+// between two timing events on the caller's stream; a later call reads them
+// (without waiting) and keeps the fastest.
 struct FactorTune {
   static constexpr int kN = 7;
   static constexpr int kCand[kN] = {4, 8, 12, 16, 24, 32, 48};
   std::mutex mu;
-  int best = 0;  // the chosen count, once tuned
-  int next = 0;  // measurements started
+  int best = 0;       // the chosen count, once tuned
+  bool warm = false;  // the first (untimed) call has run
+  int next = 0;       // measurements started
   int dev = -1;  // the device the events belong to
   float ms[kN];
   bool done[2 * kN] = {};
@@ -1298,6 +1302,10 @@ md_status factor_sms_for(FactorTune &t, int flags, cudaStream_t s, int &fsms, cu
   if (cudaGetDevice(&dev) != cudaSuccess) return MD_ERR_CUDA;
   if (t.dev >= 0 && t.dev != dev) return MD_OK;  // tuning on another device: the default here
   t.dev = dev;
+  if (!t.warm) {  // the plan's first call: untimed
+    t.warm = true;
+    return MD_OK;
+  }
   constexpr int kM = 2 * FactorTune::kN;
   if (t.next < kM) {
     const int i = t.next;
@@ -1734,6 +1742,19 @@ md_status md_newton_series_step_batched(int nsys, const md_system *sys, double *
 }
 
 void md_plan_cache_hash_mask(unsigned long long mask) { g_hash_mask.store(mask ? mask : ~0ULL); }
+
+int md_plan_factor_sms(const md_system *sys, int flags) {
+  if (check_system_header(sys) != MD_OK) return -1;
+  const uint64_t cs = structure_checksum(sys) ^ (0x9e3779b97f4a7c15ULL * (uint64_t)(flags & MD_FLAG_OZAKI));
+  std::shared_ptr<PlanEntry> hold;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    hold = g_plans.find(cs);
+  }
+  if (!hold || !same_structure(hold->plan, sys) || hold->plan.oz != ((flags & MD_FLAG_OZAKI) ? 1 : 0)) return -1;
+  std::lock_guard<std::mutex> lk(hold->tune.mu);
+  return hold->tune.best;
+}
 
 void md_profile_enable(int on) {
   std::lock_guard<std::mutex> lk(g_prof_mu);

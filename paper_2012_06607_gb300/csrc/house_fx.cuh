@@ -32,11 +32,94 @@ __device__ __forceinline__ fxp::bf<W> fx_shfl_xor(const fxp::bf<W> &a, int off) 
   return o;
 }
 
-// Sum over the 32 lanes of a warp (xor tree); every lane gets it.
+// The sum over the 32 lanes of a warp of NV values per lane; every lane gets
+// it.  Every value is shifted once to the largest exponent among them, into
+// a frame of W + 2 words (a word of headroom for the sign and the carries,
+// the W mantissa words, a guard word; bits below the frame are dropped); the
+// frames are added as two's-complement integers, within the lane and then
+// over the lanes by an xor tree (integer addition is exact, so every lane
+// gets the same total whatever the order), and the total is normalized
+// once.  A NaN anywhere gives NaN.  (A tree of W-word additions would
+// align, truncate and renormalise at each of its levels: about 20 times the
+// instructions on the chains that wait for this sum.)
+template <int W, int NV>
+__device__ __forceinline__ fxp::bf<W> fx_warp_sum_n(const fxp::bf<W> (&v)[NV]) {
+  using namespace fxp;
+  constexpr int F = W + 2;
+  constexpr unsigned kAll = 0xffffffffu;
+  bool nan = false;
+  int emax = kZeroExp;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    nan = nan || is_nan(v[q]);
+    if (!is_zero(v[q])) emax = max(emax, v[q].e);
+  }
+  if (__any_sync(kAll, nan)) return nan_value<W>();
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) emax = max(emax, __shfl_xor_sync(kAll, emax, off));
+  if (emax == kZeroExp) return zero<W>();
+  uint32_t S[F];
+#pragma unroll
+  for (int i = 0; i < F; ++i) S[i] = 0u;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    if (is_zero(v[q])) continue;
+    uint32_t X[F];
+    X[0] = 0u;
+#pragma unroll
+    for (int i = 0; i < W; ++i) X[i + 1] = v[q].m[i];
+    X[F - 1] = 0u;
+    shr_bits<F>(X, emax - v[q].e);
+    uint64_t c = v[q].neg ? 1u : 0u;  // two's complement: invert and add one
+#pragma unroll
+    for (int i = F - 1; i >= 0; --i) {
+      const uint64_t t = (uint64_t)S[i] + (v[q].neg ? (uint32_t)~X[i] : X[i]) + c;
+      S[i] = (uint32_t)t;
+      c = t >> 32;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    uint32_t T[F];
+#pragma unroll
+    for (int i = 0; i < F; ++i) T[i] = __shfl_xor_sync(kAll, S[i], off);
+    uint64_t c = 0;
+#pragma unroll
+    for (int i = F - 1; i >= 0; --i) {
+      const uint64_t t = (uint64_t)S[i] + T[i] + c;
+      S[i] = (uint32_t)t;
+      c = t >> 32;
+    }
+  }
+  bf<W> z;
+  z.neg = (int)(S[0] >> 31);
+  if (z.neg) {  // magnitude
+    uint64_t c = 1;
+#pragma unroll
+    for (int i = F - 1; i >= 0; --i) {
+      const uint64_t t = (uint64_t)(uint32_t)~S[i] + c;
+      S[i] = (uint32_t)t;
+      c = t >> 32;
+    }
+  }
+  int lead = 32 * F;  // position of the first set bit from the top of word 0
+#pragma unroll
+  for (int i = F - 1; i >= 0; --i)
+    if (S[i]) lead = 32 * i + clz32(S[i]);
+  if (lead >= 32 * F) return zero<W>();
+  shl_bits<F>(S, lead);
+#pragma unroll
+  for (int i = 0; i < W; ++i) z.m[i] = S[i];
+  // the total is S 2^(emax - 32(W+1)); after the shift its top W words are m
+  z.e = emax + 32 - lead;
+  return z;
+}
+
+// Sum over the 32 lanes of a warp; every lane gets it.
 template <int W>
 __device__ __forceinline__ void fx_warp_sum(fxp::bf<W> &a) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) a = fxp::add<W>(a, fx_shfl_xor<W>(a, off));
+  const fxp::bf<W> v[1] = {a};
+  a = fx_warp_sum_n<W, 1>(v);
 }
 
 template <int W, int K>
@@ -179,11 +262,12 @@ __device__ __forceinline__ void house_block_fx(double *M, double *vd, double *be
 // H_j applied to target column w (targets as in house_apply_col: w < n-j-1
 // is column j+1+w of M, otherwise column w-(n-j-1) of Y) over 128 virtual
 // lanes: lane q takes rows j+q, j+q+128, ... in order and holds their partial
-// dot product p_q; the column's dot product is the xor tree over 32 values
-// u_l = (p_l + p_{l+64}) + (p_{l+32} + p_{l+96}).  CTA = true: 128 threads of
-// a CTA, one virtual lane each (all threads of the CTA call it); CTA = false:
-// one warp, lane l running virtual lanes l, l+32, l+64, l+96.  Both forms
-// perform the same additions in the same order, so they give the same bits.
+// dot product p_q; the column's dot product is the exact aligned sum of the
+// 128 values (fx_warp_sum_n, lane l holding p_l, p_{l+32}, p_{l+64},
+// p_{l+96}).  CTA = true: 128 threads of a CTA, one virtual lane each (all
+// threads of the CTA call it); CTA = false: one warp, lane l running virtual
+// lanes l, l+32, l+64, l+96.  Both forms sum the same values exactly, so they
+// give the same bits.
 template <int K, int P, bool CTA, bool CACHE = true>
 __device__ __forceinline__ void house_apply_col_v128(double *M, double *Y, const double *vd, const double *beta,
                                                      int N, int n, int j, int w) {
@@ -245,10 +329,10 @@ __device__ __forceinline__ void house_apply_col_v128(double *M, double *Y, const
     __syncthreads();
     if (tid < 32) {
 #pragma unroll
-      for (int p = 0; p < P; ++p)
-        u[p] = add<W>(add<W>(s_p[tid][p], s_p[tid + 64][p]), add<W>(s_p[tid + 32][p], s_p[tid + 96][p]));
-#pragma unroll
-      for (int p = 0; p < P; ++p) fx_warp_sum<W>(u[p]);
+      for (int p = 0; p < P; ++p) {
+        const bf<W> v4[4] = {s_p[tid][p], s_p[tid + 32][p], s_p[tid + 64][p], s_p[tid + 96][p]};
+        u[p] = fx_warp_sum_n<W, 4>(v4);
+      }
       if (tid == 0) {
         const bf<W> bt = fx_ld<W, K>(beta + (long long)j * K);
 #pragma unroll
@@ -259,17 +343,15 @@ __device__ __forceinline__ void house_apply_col_v128(double *M, double *Y, const
 #pragma unroll
     for (int p = 0; p < P; ++p) u[p] = s_tau[p];
   } else {
-    bf<W> a[P], b[P], s02[P];
-    partial(tid, a);
-    partial(tid + 64, b);
-#pragma unroll
-    for (int p = 0; p < P; ++p) s02[p] = add<W>(a[p], b[p]);
-    partial(tid + 32, a);
-    partial(tid + 96, b);
+    bf<W> q0[P], q1[P], q2[P], q3[P];
+    partial(tid, q0);
+    partial(tid + 32, q1);
+    partial(tid + 64, q2);
+    partial(tid + 96, q3);
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-      u[p] = add<W>(s02[p], add<W>(a[p], b[p]));
-      fx_warp_sum<W>(u[p]);
+      const bf<W> v4[4] = {q0[p], q1[p], q2[p], q3[p]};
+      u[p] = fx_warp_sum_n<W, 4>(v4);
     }
     const bf<W> bt = fx_ld<W, K>(beta + (long long)j * K);
 #pragma unroll

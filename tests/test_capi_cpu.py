@@ -327,3 +327,19 @@ def test_split_form_workspace_host_only():
             assert split == plain
     c4 = md._host_md_system(s4, keep)
     assert lib.md_workspace_bytes(ctypes.byref(c4), md.FLAG_OZAKI) > lib.md_workspace_bytes(ctypes.byref(c4), 0)
+
+
+def test_plan_factor_sms_without_plan_host_only():
+    """md_plan_factor_sms reports -1 for a structure and form no step has
+    planned, and for an invalid structure (host-only lookups)."""
+    import paper_2012_06607_gb300 as md
+
+    keep = []
+    s = mdgen.small_system_fast(np.random.default_rng(11), 7, 5, 4, monos=7)
+    c = md._host_md_system(s, keep)
+    lib = md.lib()
+    assert lib.md_plan_factor_sms(ctypes.byref(c), 0) == -1
+    assert lib.md_plan_factor_sms(ctypes.byref(c), md.FLAG_OZAKI) == -1
+    bad = md._host_md_system(s, keep)
+    bad.limbs = 6  # not a supported precision
+    assert lib.md_plan_factor_sms(ctypes.byref(bad), 0) == -1

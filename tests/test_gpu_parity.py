@@ -241,9 +241,10 @@ def test_newton_against_more_limbs(md, orc, cfg, steps, Kref):
 @pytest.mark.parametrize("form", ["plain", "split"])
 def test_autotuned_step_equals_default(md, form):
     """MD_FLAG_AUTOTUNE changes how many SMs the factorisation keeps while the
-    evaluation runs (one count per call over the first 14 calls of a plan,
-    the fastest kept from the 15th on), never the result: 18 autotuned steps
-    from x0 give the bits of 18 default steps, plain and split-product form."""
+    evaluation runs (one untimed call, then one count per call over the next
+    14 calls of a plan, the fastest kept from the 16th on), never the
+    result: 18 autotuned steps from x0 give the bits of 18 default steps,
+    plain and split-product form, and the tuning has ended by then."""
     import torch
 
     s = mdgen.config_system(1, 1)
@@ -258,6 +259,10 @@ def test_autotuned_step_equals_default(md, form):
             torch.cuda.synchronize()
         assert md.device_status(ws) == 0
         outs.append(x.cpu().numpy())
+        if flags & md.FLAG_AUTOTUNE:
+            assert md.plan_factor_sms(sysd, flags) in (4, 8, 12, 16, 24, 32, 48)
+        else:
+            assert md.plan_factor_sms(sysd, flags) == 0  # untuned plan: the default count
     assert np.array_equal(outs[0], outs[1])
 
 
