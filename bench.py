@@ -372,11 +372,17 @@ def run_product(args):
     conv_ms, conv_launches = prof.get("conv_stage", (float("nan"), 0))
     # the timed region ran args.steps steps: conv_ms and conv_launches cover all of them
     achieved = args.steps * conv_instr / (conv_ms / 1e3) if conv_ms > 0 else None
+    if args.update == "split" and K >= 3:
+        # the split form's products run on the integer pipe: the FP64 count of
+        # the md algorithms does not measure them (ncu figures of that kernel:
+        # profiles/conv_stage_fx_qd_n64_d64.md)
+        achieved = None
     roofline = {"bound": "alu", "kernel": "conv_stage", "achieved": achieved / 1e12 if achieved else None,
                 "peak": FP64_PEAK_INSTR / 1e12, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_INSTR if achieved else None,
                 "traffic": CONV_TRAFFIC_BYTES_PER_LAUNCH if args.update == "md" and args.config == CFG else None,
                 "traffic_unit": "bytes per launch (ncu DRAM read + write)",
-                "counted": "FP64 instructions of the md algorithms (an fma counts once)",
+                "counted": "FP64 instructions of the md algorithms (an fma counts once)" if achieved else
+                           "not counted: the split form's series products run on 32-bit word slices (integer pipe)",
                 "launches_in_timed_region": conv_launches, "avg_launch_ms": conv_ms / max(conv_launches, 1),
                 "dominant_by_time": dom_name,
                 "paper_ops_per_s": args.steps * conv_paper / (conv_ms / 1e3) if conv_ms > 0 else None,
