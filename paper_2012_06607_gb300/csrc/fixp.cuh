@@ -486,10 +486,48 @@ FXP_HD constexpr int newton_steps(int K) {
   return K <= 1 ? 0 : (53 * K + 16 <= 100 ? 1 : (53 * K + 16 <= 200 ? 2 : (53 * K + 16 <= 400 ? 3 : 4)));
 }
 
-// 1 / sqrt(a), a > 0: y <- y + y (1 - a y^2) / 2.  The seed comes from the
-// leading bits of a scaled into [1/4, 1) by an even power of two.
+// a with W2 words (the top min(W, W2) words; zeros below, or the low words
+// dropped: truncation toward zero).
+template <int W2, int W>
+FXP_HD bf<W2> resize(const bf<W> &a) {
+  bf<W2> z;
+#pragma unroll
+  for (int i = 0; i < W2; ++i) z.m[i] = i < W ? a.m[i] : 0u;
+  z.e = a.e;
+  z.neg = a.neg;
+  return z;
+}
+
+// Words for Newton step s of STEPS: the step doubles the accuracy to
+// 50 2^(s+1) bits (from a ~50-bit seed), so it is carried out on that many
+// bits, 16 more and a guard word; the last step on all W words.
+FXP_HD constexpr int stage_words(int W, int s, int STEPS) {
+  return s + 1 >= STEPS ? W : ((((50 << (s + 1)) + 16 + 31) / 32 + 1) < W ? ((50 << (s + 1)) + 16 + 31) / 32 + 1 : W);
+}
+
+// One step y <- y + y (1 - a y^2) / 2 on WS words.
+template <int W, int WS>
+FXP_HD void rsqrt_step(const bf<W> &a, bf<W> &y) {
+  const bf<WS> as = resize<WS>(a), ys = resize<WS>(y), one = from_double<WS>(1.0);
+  const bf<WS> t = mul<WS>(mul<WS>(as, ys), ys);
+  const bf<WS> r = add<WS>(one, neg<WS>(t));
+  y = resize<W>(add<WS>(ys, ldexp<WS>(mul<WS>(ys, r), -1)));
+}
+
+// One step y <- y + y (1 - a y) on WS words.
+template <int W, int WS>
+FXP_HD void recip_step(const bf<W> &a, bf<W> &y) {
+  const bf<WS> as = resize<WS>(a), ys = resize<WS>(y), one = from_double<WS>(1.0);
+  const bf<WS> r = add<WS>(one, neg<WS>(mul<WS>(as, ys)));
+  y = resize<W>(add<WS>(ys, mul<WS>(ys, r)));
+}
+
+// 1 / sqrt(a), a > 0: y <- y + y (1 - a y^2) / 2, each step on the words its
+// accuracy needs (stage_words).  The seed comes from the leading bits of a
+// scaled into [1/4, 1) by an even power of two.
 template <int W, int STEPS>
 FXP_NI bf<W> rsqrt(const bf<W> &a) {
+  static_assert(STEPS <= 4, "at most four Newton steps");
   if (is_nan(a) || is_zero(a) || a.neg) return nan_value<W>();  // as 1/sqrt(0) is not finite
   bf<W> as = a;
   const int ee = (a.e % 2 == 0) ? a.e : a.e + 1;  // a = as 2^ee with as in [1/4, 1)
@@ -501,31 +539,28 @@ FXP_NI bf<W> rsqrt(const bf<W> &a) {
   const double y0 = 1.0 / __builtin_sqrt(s);
 #endif
   bf<W> y = from_double<W>(y0);
-  bf<W> one = from_double<W>(1.0);
-#pragma unroll 1
-  for (int it = 0; it < STEPS; ++it) {
-    const bf<W> t = mul<W>(mul<W>(as, y), y);
-    const bf<W> r = add<W>(one, neg<W>(t));
-    y = add<W>(y, ldexp<W>(mul<W>(y, r), -1));
-  }
+  if constexpr (STEPS > 0) rsqrt_step<W, stage_words(W, 0, STEPS)>(as, y);
+  if constexpr (STEPS > 1) rsqrt_step<W, stage_words(W, 1, STEPS)>(as, y);
+  if constexpr (STEPS > 2) rsqrt_step<W, stage_words(W, 2, STEPS)>(as, y);
+  if constexpr (STEPS > 3) rsqrt_step<W, stage_words(W, 3, STEPS)>(as, y);
   return ldexp<W>(y, -ee / 2);
 }
 
-// 1 / a, a != 0: y <- y + y (1 - a y).
+// 1 / a, a != 0: y <- y + y (1 - a y), each step on the words its accuracy
+// needs.
 template <int W, int STEPS>
 FXP_NI bf<W> recip(const bf<W> &a) {
+  static_assert(STEPS <= 4, "at most four Newton steps");
   if (is_nan(a) || is_zero(a)) return nan_value<W>();  // as 1/0 is not finite
   bf<W> as = a;
   as.e = 0;  // as in [1/2, 1)
   as.neg = 0;
   const double s = lead_double<W>(as);
   bf<W> y = from_double<W>(1.0 / s);
-  bf<W> one = from_double<W>(1.0);
-#pragma unroll 1
-  for (int it = 0; it < STEPS; ++it) {
-    const bf<W> r = add<W>(one, neg<W>(mul<W>(as, y)));
-    y = add<W>(y, mul<W>(y, r));
-  }
+  if constexpr (STEPS > 0) recip_step<W, stage_words(W, 0, STEPS)>(as, y);
+  if constexpr (STEPS > 1) recip_step<W, stage_words(W, 1, STEPS)>(as, y);
+  if constexpr (STEPS > 2) recip_step<W, stage_words(W, 2, STEPS)>(as, y);
+  if constexpr (STEPS > 3) recip_step<W, stage_words(W, 3, STEPS)>(as, y);
   y.e -= a.e;
   y.neg = a.neg;
   return y;
