@@ -106,11 +106,14 @@ typedef struct md_system {
  *   - In md_newton_series_step, the series products of the evaluation
  *     (K >= 3): each term on 32-bit word slices of the md operands, exact word
  *     products and column sums, the coefficient kept in W-word fixed point
- *     (53K bits and two guard words) and rounded to K limbs once.  A_0 still
- *     comes from the md products of coefficient 0.
- *   - In md_newton_series_step_batched (K >= 3), the same series products and,
- *     in place of the 8-bit slices above, the chunk sums of the block Toeplitz
- *     update on 32-bit word slices, each chunk rounded to K limbs once.
+ *     (53K bits and two guard words) and rounded to K limbs once; and the
+ *     accumulation of f and A_k the same way (each contribution an exact
+ *     word-slice product, each entry's sum rounded once).  A_0 still comes
+ *     from the md products and sums of coefficient 0.
+ *   - In md_newton_series_step_batched (K >= 3), the same series products and
+ *     accumulation and, in place of the 8-bit slices above, the chunk sums of
+ *     the block Toeplitz update on 32-bit word slices, each chunk rounded to
+ *     K limbs once.
  * At one and two limbs the flag leaves the series products in md arithmetic,
  * which is faster there.  Results are within the plain form's tolerance, not
  * its bits.  (In every form, from three limbs on, the QR of A_0,
