@@ -188,7 +188,19 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batched_step_kernel(const Ba
     __syncthreads();
     phase_stamp(phases, times, (long long)tstride * job + 6);
     for (int c = n - 1; c >= 0; --c) {
-      for (long long e = tid; e < (long long)(c + 1) * n; e += NT) backsub_entry<K, P>(M, Y, W, rinv, n, c, e);
+      if constexpr (K >= kFxMinLimbs) {
+        // row c of W once, then the rows above it read it: the values that
+        // backsub_entry forms in every element (the same bits)
+        for (int col = tid; col < n; col += NT)
+          fx_bs_w<K, P>(Y, rinv, n, c, col, W + ((long long)c * n + col) * (P * K));
+        __syncthreads();
+        for (long long e = tid; e < (long long)c * n; e += NT) {
+          const int i = (int)(e / n), col = (int)(e % n);
+          fx_bs_update<K, P>(M, Y, W + ((long long)c * n + col) * (P * K), n, c, col, i);
+        }
+      } else {
+        for (long long e = tid; e < (long long)(c + 1) * n; e += NT) backsub_entry<K, P>(M, Y, W, rinv, n, c, e);
+      }
       __syncthreads();
     }
     phase_stamp(phases, times, (long long)tstride * job + 7);
