@@ -31,3 +31,19 @@ def test_fp64_model_scales_with_degree_and_limbs():
     m4 = bench.step_fp64_model(s.with_limbs(4))
     assert m4["conv"] > 3 * m2["conv"] and m4["total"] > 3 * m2["total"]
     assert m2["total"] == pytest.approx(sum(v for k, v in m2.items() if k != "total"))
+
+
+def test_run_form_uses_the_papers_octo_double_schedule():
+    """--form run follows Table 2's octo double row (Section 6): the truncation
+    degrees, the iteration counts as per-level limits, and the quoted seconds
+    (tests/golden/table2_octo_double.txt)."""
+    import bench
+
+    rows = []
+    with open(os.path.join(ROOT, "tests", "golden", "table2_octo_double.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                rows.append(tuple(int(v) for v in line.split()))
+    assert tuple(r[0] for r in rows) == bench.RUN_DEGREES
+    assert tuple(r[1] for r in rows) == bench.RUN_MAX_ITER
+    assert {r[0]: r[2] for r in rows} == bench.PAPER_TABLE2_OD_SECONDS
