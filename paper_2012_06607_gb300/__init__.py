@@ -241,7 +241,10 @@ def linsolve(limbs: int, is_complex: bool, A, b, ws, dx=None, flags: int = 0, st
 
 
 def newton_step(sysd: DeviceSystem, x, ws, dx_norm=None, flags: int = 0, stream=None):
-    """In-place step on x ([P][K][n][d+1] CUDA tensor); dx_norm: CUDA double[2] or None."""
+    """In-place step on x ([P][K][n][d+1] CUDA tensor); dx_norm: CUDA double[2] or None.
+    flags: FLAG_OZAKI (the split-product form; size ws with the same flag),
+    FLAG_LU, FLAG_SERIAL, FLAG_CHECK, FLAG_AUTOTUNE (the factorisation's SM
+    count tuned over the plan's first calls; see plan_factor_sms)."""
     _check(lib().md_newton_series_step(sysd.c(), _ptr(x), _ptr(dx_norm), _ptr(ws), ws.numel(), flags,
                                        _stream(stream)), "md_newton_series_step")
     return x
