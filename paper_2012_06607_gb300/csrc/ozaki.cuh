@@ -33,12 +33,25 @@ __host__ __device__ constexpr int oz_digits(int K) { return (53 * K + 24 + 128 +
 
 __host__ __device__ inline int oz_kpad(int n) { return (n + 15) / 16 * 16; }
 
+// The exponent that marks a row, a vector or a right-hand side holding a
+// non-finite limb: it puts the output's accumulator top above
+// kOzNonFiniteTop, every finite term then falls below the accumulator (and
+// is dropped), and oz_finish_kernel writes NaN limbs, as md arithmetic
+// propagates non-finite values.
+constexpr int kOzNonFinite = 1 << 20;
+constexpr int kOzNonFiniteTop = kOzNonFinite / 2;
+
+__device__ __forceinline__ bool oz_finite(double x) {
+  return (((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ffULL) != 0x7ffULL;
+}
+
 // exponent e with |v| < 2^(e-1) for the md number whose leading limb is x0
-// (-2000 for zero).
+// (-2000 for zero, kOzNonFinite for a non-finite limb).
 __device__ __forceinline__ int oz_exp_bound(double x0) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x0) & 0x7fffffffffffffffULL;
   if (b == 0ULL) return -2000;
   int ex = (int)(b >> 52);
+  if (ex == 0x7ff) return kOzNonFinite;
   if (ex == 0) {  // subnormal: frexp exponent
     ex = -1022 - (__clzll((long long)b) - 12) + 1;
     return ex + 1;
@@ -215,7 +228,13 @@ __global__ void oz_split_rows_kernel(const double *__restrict__ A, __nv_bfloat16
   int e = -2000;
   for (int c = lane; c < n; c += 32)
 #pragma unroll
-    for (int p = 0; p < P; ++p) e = max(e, oz_exp_bound(A[(long long)(p * K) * stride + (long long)i * nn + (long long)c * n + row]));
+    for (int p = 0; p < P; ++p) {
+      e = max(e, oz_exp_bound(A[(long long)(p * K) * stride + (long long)i * nn + (long long)c * n + row]));
+#pragma unroll
+      for (int l = 1; l < K; ++l)
+        if (!oz_finite(A[(long long)(p * K + l) * stride + (long long)i * nn + (long long)c * n + row]))
+          e = kOzNonFinite;
+    }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, off));
   if (lane == 0) eA[i * n + row] = e;
@@ -247,7 +266,12 @@ __global__ void oz_split_vec_kernel(const double *__restrict__ dxw, __nv_bfloat1
   int e = -2000;
   for (int c = tid; c < n; c += blockDim.x)
 #pragma unroll
-    for (int p = 0; p < P; ++p) e = max(e, oz_exp_bound(dxw[((long long)j * n + c) * VS + p * K]));
+    for (int p = 0; p < P; ++p) {
+      e = max(e, oz_exp_bound(dxw[((long long)j * n + c) * VS + p * K]));
+#pragma unroll
+      for (int l = 1; l < K; ++l)
+        if (!oz_finite(dxw[((long long)j * n + c) * VS + p * K + l])) e = kOzNonFinite;
+    }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, off));
   if ((tid & 31) == 0) s_e[tid >> 5] = e;
@@ -320,6 +344,9 @@ __device__ __forceinline__ int oz_top(const int *eA, const int *ex, const double
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) etop = max(etop, __shfl_xor_sync(0xffffffffu, etop, off));
   etop = max(etop, oz_exp_bound(b[((long long)(q * K) * n + row) * (d + 1) + k]));
+#pragma unroll
+  for (int l = 1; l < K; ++l)
+    if (!oz_finite(b[((long long)(q * K + l) * n + row) * (d + 1) + k])) etop = kOzNonFinite;
   return etop + 64;
 }
 
@@ -512,7 +539,12 @@ __global__ void oz_finish_kernel(const int *__restrict__ eA, const int *__restri
   for (int l = 0; l < K; ++l)
     oz_add_double<W>(a, top, b[((long long)(q * K + l) * n + row) * (d + 1) + k], sgn < 0.0 ? -1 : 1);
   double z[K];
-  oz_to_md<W, K>(a, top, z);
+  if (top >= kOzNonFiniteTop) {  // a non-finite limb among the inputs of this output
+#pragma unroll
+    for (int l = 0; l < K; ++l) z[l] = __longlong_as_double(0x7ff8000000000000LL);
+  } else {
+    oz_to_md<W, K>(a, top, z);
+  }
   const long long VS = P * K;
 #pragma unroll
   for (int l = 0; l < K; ++l) r[((long long)k * n + row) * VS + q * K + l] = z[l];
