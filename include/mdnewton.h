@@ -114,8 +114,9 @@ typedef struct md_system {
  *     accumulation and, in place of the 8-bit slices above, the chunk sums of
  *     the block Toeplitz update on 32-bit word slices, each chunk rounded to
  *     K limbs once.
- * At one and two limbs the flag leaves the series products in md arithmetic,
- * which is faster there.  Results are within the plain form's tolerance, not
+ * Non-finite values propagate as in md arithmetic (an output with a
+ * non-finite input limb is NaN).  At one and two limbs the flag leaves the
+ * series products in md arithmetic, which is faster there.  Results are within the plain form's tolerance, not
  * its bits.  (In every form, from three limbs on, the QR of A_0,
  * W = R^-1 Q^H, the finish of r_k and dx_k = W r_k run in the same W-word
  * fixed point.)
